@@ -1,0 +1,19 @@
+"""CPU FP64 oracle for the NeuRLP-PDE least-squares solve.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports this package;
+only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may call it.  It shares no code with the CUDA path: it assembles
+the sparse constraint matrix A and vector d row by row as Section 3 of the
+paper defines them (Eqs. 3-8), solves the least-squares problem exactly through
+the saddle-point system of Eq. 10 with a sparse LU factorisation, and computes
+parameter gradients from the saddle-point system of Eq. 11 and the gradient
+formulas that follow it.
+
+Modules
+  assemble   rows of A and d (Eqs. 3-8), boundary set, row counts
+  solve      least-squares solve via Eq. 10 (and via Eq. 9 as a cross-check)
+  grad       adjoint solve (Eq. 11) and dL/dc, dL/db, dL/domega
+  cg64       FP64 conjugate gradient on the normal equations (Eq. 9) over the
+             assembled CSR matrix, in plain C with OpenMP, for grids too large
+             for the direct factorisation
+"""
