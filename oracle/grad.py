@@ -55,3 +55,9 @@ def gradients(geom, A, d, kind, owner, z, lam, dz, dlam):
 def dense_dA(A, z, lam, dz, dlam):
     """dl/dA as a dense matrix (tiny grids only): d_lambda z^T + lambda d_z^T."""
     return np.outer(dlam, z) + np.outer(lam, dz)
+
+
+def adjoint_elim(elim, g_z):
+    """Eq. 11 through NormalElim: A^T A d_z = g_z, d_lambda = -A d_z."""
+    dz = elim.solve(np.asarray(g_z, dtype=np.float64))
+    return dz, -(elim.A @ dz)

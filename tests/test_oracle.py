@@ -338,3 +338,32 @@ def test_gradient_identities():
     dz, dlam = og.adjoint(kkt, g)
     assert np.linalg.norm(dlam + A @ dz) <= 1e-9 * np.linalg.norm(dlam)
     assert np.linalg.norm(A.T @ (A @ dz) - g) <= 1e-9 * np.linalg.norm(g)
+
+
+@pytest.mark.parametrize("n,per,st", [((6, 6), (False, False), 3), ((6, 8), (False, True), 5),
+                                      ((4, 5, 6), (False, True, False), 3),
+                                      ((5, 6, 6), (False, True, True), 5)])
+def test_elimination_route_matches_dense_lstsq(n, per, st):
+    """The block-elimination solve of Eq. 9 against numpy's dense least
+    squares, for the forward problem and for an adjoint right-hand side."""
+    w = wl.random_problem(13, n, per, st, final_time_rows=True)
+    V = asm.n_vars(len(n))
+    A, d, kind, owner = asm.assemble(w.geom, w.full_coeff()[:, 0], w.rhs[0], w.omega[0])
+    z, lam, el = osv.solve_lsq_elim(A, d, V)
+    Ad = A.toarray()
+    zref = np.linalg.lstsq(Ad, d, rcond=None)[0]
+    assert np.linalg.norm(z - zref) <= 1e-10 * np.linalg.norm(zref)
+    g = np.random.default_rng(1).normal(size=A.shape[1])
+    dz, dlam = og.adjoint_elim(el, g)
+    dzref = np.linalg.solve(Ad.T @ Ad, g)
+    assert np.linalg.norm(dz - dzref) <= 1e-9 * np.linalg.norm(dzref)
+    assert np.linalg.norm(dlam + Ad @ dzref) <= 1e-9 * np.linalg.norm(Ad @ dzref)
+
+
+def test_elimination_route_matches_kkt_route_3d():
+    w = wl.reaction_diffusion_2d(batch=1, n=(8, 8, 8))
+    A, d, kind, owner = asm.assemble(w.geom, w.full_coeff()[:, 0], w.rhs[0], w.omega[0])
+    z1, lam1, _ = osv.solve_lsq(A, d)
+    z2, lam2, _ = osv.solve_lsq_elim(A, d, 7)
+    assert np.linalg.norm(z1 - z2) <= 1e-9 * np.linalg.norm(z1)
+    assert osv.normal_residual(A, d, z2) < 1e-12
