@@ -1,0 +1,155 @@
+/*
+ * mpn.h — C ABI of the batched NeuRLP-PDE least-squares solver (sm_103a).
+ *
+ * The solver computes, for a batch of independent PDE instances on a regular
+ * (t, x[, y]) grid, the least-squares solution z* = argmin ||A z - d||_2 of the
+ * constraint system of Section 3 of "Mechanistic PDE Networks" (Eqs. 3-8):
+ *   equation rows        sum_v c_{v,i} z_{v,i} = b_i              (Eq. 3)
+ *   Dirichlet rows       u_i = omega_i,  i in the boundary set    (Eq. 4)
+ *   derivative rows      s^k z_{m,i} = finite difference of u     (Eq. 5)
+ *   Taylor smoothness    u_i +- s u'_i + s^2/2 u''_i = u_{next/prev}(Eqs. 6-7)
+ * through its normal equations A^T A z = A^T d (Eq. 9), and the adjoint
+ * solve A^T A d_z = g_z of the backward saddle-point system (Eq. 11) with the
+ * parameter gradients that follow it.
+ *
+ * Unknowns per grid point (V = 1 + 2D for D grid dimensions, time first):
+ *   v = 0: u,  v = 1 + 2d: first derivative along d,  v = 2 + 2d: second.
+ * Layouts (all row-major, last grid dimension fastest, N = n_t n_x [n_y]):
+ *   z, g_z, dz       [B][V][N]  float
+ *   fields, dfields  [F][B][N]  float   coefficient fields
+ *   scalars,dscalars [V][B]     float   per-instance coefficients (read for
+ *                                       v with field_of[v] < 0)
+ *   rhs, drhs        [B][N]     float   b of the equation rows
+ *   omega, domega    [B][N]     float   Dirichlet values; read (and written)
+ *                                       only on boundary points
+ *   u0               [B][N]     float   optional warm start for u
+ * The coefficient of unknown v at point i of instance b is
+ *   fields[field_of[v]][b][i] if field_of[v] >= 0, else scalars[v][b].
+ *
+ * Boundary set: the t = 0 face, both faces of every non-periodic spatial
+ * dimension, and the t = t_f face when final_time_rows is set.
+ * Derivative rows sit at every point; non-periodic edges use second-order
+ * one-sided three-point forms (the paper says one-sided differences are used
+ * at the grid edges without giving their order).
+ *
+ * Ownership: every array argument is caller-owned DEVICE memory unless marked
+ * host.  The problem object owns its workspace (allocated by mpn_create).
+ * Calls are asynchronous on `stream` (a cudaStream_t) except that each
+ * refinement sweep reads a few per-instance scalars back to the host, so a
+ * solve call returns after its work is complete.
+ *
+ * Errors: every call returns an mpn_status.  Nothing aborts or hangs: PCG
+ * and refinement counts are capped; a non-finite value or a growing residual
+ * is reported, and stats are filled in either way.
+ */
+#ifndef MPN_H
+#define MPN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MPN_OK = 0,
+  MPN_ERR_INVALID_ARG = 1,   /* bad descriptor, null pointer, bad size */
+  MPN_ERR_UNSUPPORTED = 2,   /* valid for the method, not for this solver */
+  MPN_ERR_NOT_CONVERGED = 3, /* max_refine reached above tolerance */
+  MPN_ERR_NONFINITE = 4,     /* NaN/Inf in inputs or iterates */
+  MPN_ERR_DIVERGED = 5,      /* refinement correction grew */
+  MPN_ERR_CUDA = 6,          /* a CUDA call failed (see mpn_last_cuda_error) */
+  MPN_ERR_NO_MEMORY = 7
+} mpn_status;
+
+typedef struct mpn_desc {
+  int ndim;               /* D = 2 (t, x) or 3 (t, x, y) */
+  int n[3];               /* grid points per dimension, time first; n[2] = 1 if D = 2 */
+  double step[3];         /* uniform steps s_t, s_x, s_y */
+  int periodic[3];        /* periodic[0] must be 0 */
+  int stencil;            /* derivative rows: 3 (supported) or 5 (MPN_ERR_UNSUPPORTED) */
+  int final_time_rows;    /* 1: Dirichlet rows also on t = t_f */
+  int batch;              /* B independent instances */
+  int nfields;            /* F coefficient fields */
+  int field_of[7];        /* per unknown: field index, or -1 for a per-instance scalar */
+  double tol;             /* stop when the predicted relative error of u is <= tol */
+  int max_refine;         /* cap on FP64 refinement sweeps */
+  int inner_iters;        /* FP32 PCG iterations per refinement sweep */
+  int cheb_degree;        /* Chebyshev-Jacobi smoothing steps, pre and post */
+  int coarse_min;         /* spatial dims are halved while the half is >= this */
+  int max_coarse;         /* largest coarsest-level system (unknowns per instance) */
+} mpn_desc;
+
+typedef struct mpn_stats {
+  int sweeps;             /* FP64 refinement sweeps done */
+  int pcg_iters;          /* FP32 PCG iterations done (all sweeps) */
+  double rel_residual;    /* max over instances: ||r|| / ||r_0|| of the reduced normal equations, FP64 */
+  double rel_update;      /* max over instances: last ||delta u|| / ||u|| */
+  double pred_error;      /* max over instances: predicted relative error of u */
+} mpn_stats;
+
+typedef struct mpn_problem mpn_problem;
+
+/* Fills *desc with defaults (tol 1e-7, max_refine 12, inner_iters 6,
+ * cheb_degree 4, coarse_min 4, max_coarse 2048, stencil 3). */
+int mpn_default_desc(mpn_desc* desc);
+
+/* Validates the descriptor, builds the grid hierarchy (spatial halving, time
+ * kept) and allocates the workspace on the current device.  *out receives the
+ * problem.  Errors: INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA. */
+int mpn_create(const mpn_desc* desc, mpn_problem** out);
+
+/* Bytes of device workspace owned by the problem. */
+size_t mpn_workspace_bytes(const mpn_problem* p);
+
+/* Number of multigrid levels and their grid shapes (host array [levels][3]). */
+int mpn_levels(const mpn_problem* p, int* nlevels, int* shapes /* host, 3 * 16 ints */);
+
+/* Forward pass (Eqs. 9-10): writes z* [B][V][N] and, if z64 is non-null, the
+ * FP64 solution [B][V][N] (double).  u0 is an optional warm start.  stats is
+ * a host pointer (nullable). */
+int mpn_forward(mpn_problem* p, const float* fields, const float* scalars,
+                const float* rhs, const float* omega, const float* u0,
+                float* z, double* z64, mpn_stats* stats, void* stream);
+
+/* Backward pass (Eq. 11 and the gradients after it): given g_z = dl/dz*
+ * [B][V][N], solves A^T A d_z = g_z and writes dl/dfields [F][B][N],
+ * dl/dscalars [V][B] (entries of field-backed v are written as 0),
+ * dl/drhs [B][N] and dl/domega [B][N] (zero off the boundary set).  z is the
+ * forward solution; if null it is recomputed.  dz (nullable) receives d_z.
+ * flags bit 0 (MPN_REUSE_SETUP): the coefficients are the ones of the last
+ * mpn_forward on this problem, so its multigrid setup is reused. */
+#define MPN_REUSE_SETUP 1
+int mpn_adjoint(mpn_problem* p, const float* fields, const float* scalars,
+                const float* rhs, const float* omega, const float* z,
+                const float* g_z, float* dfields, float* dscalars, float* drhs,
+                float* domega, float* dz, int flags, mpn_stats* stats, void* stream);
+
+/* dl/dz of l = mean over (b, i) of (u - target)^2, written into g_z [B][V][N]
+ * (zero on the derivative unknowns): the loss used by the benchmarks. */
+int mpn_mse_grad(mpn_problem* p, const float* z, const float* target, float* g_z,
+                 void* stream);
+
+/* Diagnostic: q = S u for the reduced normal operator S on the finest grid
+ * (the Schur complement of A^T A onto the u unknowns, FP32), with the
+ * multigrid setup of the given coefficients.  u, q: [B][N]. */
+int mpn_apply_reduced(mpn_problem* p, const float* fields, const float* scalars,
+                      const float* u, float* q, void* stream);
+
+/* Live timing of the finest-level Chebyshev smoothing step (the solver's
+ * dominant kernel work): CUDA events around each of its launches on the
+ * solve stream.  Reads the totals accumulated since the last reset (time in
+ * ms, launches, algorithmic bytes = 4 (7 + F) N B per launch: e, d, r, Dinv,
+ * rho and the F fields read once, e and d written); then, if enable >= 0,
+ * switches timing on (1) or off (0) and resets the totals. */
+int mpn_profile(mpn_problem* p, int enable, double* ms_total, long long* launches, double* bytes);
+
+void mpn_destroy(mpn_problem* p);
+const char* mpn_strerror(int status);
+const char* mpn_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPN_H */

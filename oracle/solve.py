@@ -102,7 +102,13 @@ class NormalElim:
         self.Muw = Muw
         self.Mwu = Muw.T.tocsr()
         S = (Muu - Muw @ self.Mww_inv @ self.Mwu).tocsc()
+        self.S = S
         self.lu = spla.splu(S, permc_spec="COLAMD")
+
+    def reduced_rhs(self, rhs):
+        """u-part of the eliminated right-hand side: rhs_u - M_uw M_ww^{-1} rhs_w."""
+        N = self.N
+        return rhs[:N] - self.Muw @ (self.Mww_inv @ rhs[N:])
 
     def solve_normal(self, rhs):
         """One elimination solve of A^T A z = rhs."""

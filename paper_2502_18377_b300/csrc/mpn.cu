@@ -1,0 +1,636 @@
+// C ABI and host orchestration of the batched NeuRLP-PDE solver (sm_103a).
+//
+// Solve structure (forward and adjoint alike):
+//   setup      coefficients copied into the problem, point weights rho,
+//              hierarchy built by halving the spatial dimensions (time kept),
+//              coefficient fields and rho carried down by full weighting,
+//              Chebyshev-Jacobi scaling by a power-method lambda_max per level
+//              and instance, coarsest system factorised and inverted.
+//   refinement FP64 residual r = g - S u of the reduced normal equations
+//              (Schur complement of A^T A, Eq. 9, onto u), normalised to FP32,
+//              a fixed number of multigrid-preconditioned CG iterations in
+//              FP32, u += correction in FP64; one device-to-host read of a few
+//              scalars per sweep decides whether to stop.
+//   recovery   every derivative unknown from u, point by point (FP64).
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+
+#include "../../include/mpn.h"
+#include "mpn_kernels.cuh"
+
+#define MAXL 16
+
+static thread_local char g_cuda_err[256] = "";
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      snprintf(g_cuda_err, sizeof(g_cuda_err), "%s at %s:%d", cudaGetErrorString(e_), \
+               __FILE__, __LINE__);                                                    \
+      return MPN_ERR_CUDA;                                                             \
+    }                                                                                  \
+  } while (0)
+#define CKL() CK(cudaGetLastError())
+#define TRY(x) do { int s_ = (x); if (s_ != MPN_OK) return s_; } while (0)
+
+struct Level {
+  Grid g;
+  int cz[3];           // dims halved from this level to the next
+  float* fields = nullptr;  // [F][B][N]
+  float *rho = nullptr, *dinv = nullptr;
+  float *r = nullptr, *e = nullptr, *d = nullptr, *y = nullptr, *t = nullptr;
+};
+
+struct mpn_problem {
+  mpn_desc desc;
+  int D, V, F, B;
+  int L;
+  Level lv[MAXL];
+  int M, bw;           // coarsest system size and band width
+  float *Kband = nullptr, *Kinv = nullptr;
+  int* ferr = nullptr;
+  float *scalars = nullptr, *rhs = nullptr, *omega = nullptr;
+  int* field_of_dev = nullptr;
+  float *x = nullptr, *pv = nullptr, *q = nullptr, *z = nullptr;
+  double *u64 = nullptr, *r64 = nullptr, *y64 = nullptr, *g64 = nullptr;
+  double *zd = nullptr, *dzd = nullptr, *kap = nullptr;
+  double *part = nullptr;  // partial-sum slots [NSLOT][B][PMAX]
+  double *dscal = nullptr; // device scalars: scale[B], rz_old[B], out[8][B]
+  float* lam = nullptr;    // lambda_max per level and instance [L][B]
+  double* hbuf = nullptr;  // pinned host buffer
+  size_t bytes = 0;
+  bool setup_ok = false;
+  float cheb_c1[32], cheb_c2[32], cheb_inv_th;
+  std::vector<void*> allocs;
+  // live timing of the finest-level smoothing step (events on the solve stream)
+  int prof_on = 0, prof_used = 0;
+  std::vector<cudaEvent_t> prof_ev;
+  double prof_ms = 0, prof_bytes = 0;
+  long long prof_n = 0;
+};
+
+enum { S_RZ = 0, S_PQ, S_RN, S_DU, S_UN, S_PW, S_GN, S_GR0, NSLOT = S_GR0 + 8 };
+
+static inline double* slot(mpn_problem* p, int k) { return p->part + (size_t)k * p->B * MPN_PMAX; }
+
+static int nblk(int N) { int b = (N + MPN_TPB - 1) / MPN_TPB; return b < 1 ? 1 : (b > MPN_PMAX ? MPN_PMAX : b); }
+
+static int dalloc(mpn_problem* p, void** ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    snprintf(g_cuda_err, sizeof(g_cuda_err), "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MPN_ERR_NO_MEMORY : MPN_ERR_CUDA;
+  }
+  p->allocs.push_back(*ptr);
+  p->bytes += bytes;
+  return MPN_OK;
+}
+template <class T>
+static int dalloc_t(mpn_problem* p, T** ptr, size_t n) { return dalloc(p, (void**)ptr, n * sizeof(T)); }
+
+static Grid make_grid(int D, const int n[3], const double s[3], const int per[3], int final_rows, float theta) {
+  Grid g;
+  memset(&g, 0, sizeof(g));
+  g.D = D;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = d < D ? n[d] : 1;
+    g.per[d] = d < D ? per[d] : 0;
+    double sd = d < D ? s[d] : 1.0;
+    g.ds1[d] = 1.0 / sd; g.ds2[d] = 1.0 / (sd * sd);
+    g.is1[d] = (float)g.ds1[d]; g.is2[d] = (float)g.ds2[d];
+  }
+  g.stride[2] = 1; g.stride[1] = g.n[2]; g.stride[0] = g.n[1] * g.n[2];
+  g.N = g.n[0] * g.n[1] * g.n[2];
+  g.final_rows = final_rows;
+  g.theta = theta;
+  return g;
+}
+
+static Coef make_coef(const mpn_problem* p, const float* fields) {
+  Coef c;
+  c.V = p->V; c.F = p->F; c.B = p->B;
+  for (int v = 0; v < 7; ++v) c.field_of[v] = v < p->V ? p->desc.field_of[v] : -1;
+  c.fields = fields;
+  c.scalars = p->scalars;
+  return c;
+}
+
+extern "C" int mpn_default_desc(mpn_desc* d) {
+  if (!d) return MPN_ERR_INVALID_ARG;
+  memset(d, 0, sizeof(*d));
+  d->ndim = 2;
+  d->n[0] = d->n[1] = 32; d->n[2] = 1;
+  d->step[0] = d->step[1] = d->step[2] = 1.0;
+  d->stencil = 3;
+  d->batch = 1;
+  for (int v = 0; v < 7; ++v) d->field_of[v] = -1;
+  d->tol = 1e-7;
+  d->max_refine = 12;
+  d->inner_iters = 6;
+  d->cheb_degree = 4;
+  d->coarse_min = 4;
+  d->max_coarse = 2048;
+  return MPN_OK;
+}
+
+extern "C" const char* mpn_strerror(int s) {
+  switch (s) {
+    case MPN_OK: return "ok";
+    case MPN_ERR_INVALID_ARG: return "invalid argument";
+    case MPN_ERR_UNSUPPORTED: return "unsupported configuration";
+    case MPN_ERR_NOT_CONVERGED: return "refinement did not reach the tolerance";
+    case MPN_ERR_NONFINITE: return "non-finite value in inputs or iterates";
+    case MPN_ERR_DIVERGED: return "refinement correction grew";
+    case MPN_ERR_CUDA: return "CUDA error";
+    case MPN_ERR_NO_MEMORY: return "out of device memory";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* mpn_last_cuda_error(void) { return g_cuda_err; }
+
+extern "C" void mpn_destroy(mpn_problem* p) {
+  if (!p) return;
+  for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
+  for (void* a : p->allocs) cudaFree(a);
+  if (p->hbuf) cudaFreeHost(p->hbuf);
+  delete p;
+}
+
+extern "C" size_t mpn_workspace_bytes(const mpn_problem* p) { return p ? p->bytes : 0; }
+
+extern "C" int mpn_levels(const mpn_problem* p, int* nl, int* shapes) {
+  if (!p || !nl) return MPN_ERR_INVALID_ARG;
+  *nl = p->L;
+  if (shapes)
+    for (int k = 0; k < p->L; ++k)
+      for (int d = 0; d < 3; ++d) shapes[3 * k + d] = p->lv[k].g.n[d];
+  return MPN_OK;
+}
+
+extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
+  if (!desc || !out) return MPN_ERR_INVALID_ARG;
+  *out = nullptr;
+  const mpn_desc& d = *desc;
+  if (d.ndim != 2 && d.ndim != 3) return MPN_ERR_INVALID_ARG;
+  if (d.batch < 1 || d.nfields < 0 || d.nfields > 7) return MPN_ERR_INVALID_ARG;
+  if (d.periodic[0]) return MPN_ERR_INVALID_ARG;
+  if (d.stencil == 5) return MPN_ERR_UNSUPPORTED;
+  if (d.stencil != 3) return MPN_ERR_INVALID_ARG;
+  if (d.inner_iters < 1 || d.max_refine < 1 || d.cheb_degree < 1 || d.cheb_degree > 30) return MPN_ERR_INVALID_ARG;
+  if (d.coarse_min < 3 || !(d.tol > 0)) return MPN_ERR_INVALID_ARG;
+  int V = 1 + 2 * d.ndim;
+  for (int k = 0; k < d.ndim; ++k) {
+    if (d.n[k] < 3 || !(d.step[k] > 0)) return MPN_ERR_INVALID_ARG;
+  }
+  if (d.ndim == 2 && d.n[2] != 1 && d.n[2] != 0) return MPN_ERR_INVALID_ARG;
+  for (int v = 0; v < V; ++v)
+    if (d.field_of[v] < -1 || d.field_of[v] >= d.nfields) return MPN_ERR_INVALID_ARG;
+  long long Nfine = 1;
+  for (int k = 0; k < d.ndim; ++k) Nfine *= d.n[k];
+  if (Nfine * V * d.batch > (1LL << 31)) return MPN_ERR_UNSUPPORTED;
+
+  mpn_problem* p = new mpn_problem();
+  p->desc = d;
+  p->D = d.ndim; p->V = V; p->F = d.nfields; p->B = d.batch;
+  if (p->D == 2) p->desc.n[2] = 1;
+
+  // hierarchy: halve spatial dims (t kept) while the half is >= coarse_min
+  int n[3] = {p->desc.n[0], p->desc.n[1], p->desc.n[2]};
+  double s[3] = {d.step[0], d.step[1], p->D == 3 ? d.step[2] : 1.0};
+  int per[3] = {0, d.periodic[1], p->D == 3 ? d.periodic[2] : 0};
+  float theta = 1.f;
+  p->L = 0;
+  while (true) {
+    Level& l = p->lv[p->L];
+    l.g = make_grid(p->D, n, s, per, d.final_time_rows, theta);
+    int nd = 0;
+    for (int k = 0; k < 3; ++k) {
+      l.cz[k] = (k >= 1 && k < p->D && n[k] % 2 == 0 && n[k] / 2 >= d.coarse_min) ? 1 : 0;
+      nd += l.cz[k];
+    }
+    p->L++;
+    if (nd == 0 || p->L == MAXL) { for (int k = 0; k < 3; ++k) l.cz[k] = 0; break; }
+    for (int k = 0; k < 3; ++k) if (l.cz[k]) { n[k] /= 2; s[k] *= 2; }
+    theta *= (float)(1 << nd);
+  }
+  Level& lc = p->lv[p->L - 1];
+  p->M = lc.g.N;
+  int plane = lc.g.n[1] * lc.g.n[2];
+  p->bw = std::min(p->M - 1, 3 * plane - 1);
+  if (p->M > d.max_coarse || (size_t)p->M * (p->bw + 1) * sizeof(float) > 200 * 1024) {
+    delete p;
+    return MPN_ERR_UNSUPPORTED;
+  }
+
+  int B = p->B, F = p->F;
+  int rc = MPN_OK;
+#define AL(ptr, n) do { rc = dalloc_t(p, &(ptr), (size_t)(n)); if (rc) { mpn_destroy(p); return rc; } } while (0)
+  for (int k = 0; k < p->L; ++k) {
+    Level& l = p->lv[k];
+    size_t N = (size_t)l.g.N * B;
+    AL(l.fields, (size_t)std::max(F, 1) * N);
+    AL(l.rho, N); AL(l.dinv, N);
+    AL(l.r, N); AL(l.e, N); AL(l.d, N); AL(l.y, N); AL(l.t, N);
+  }
+  size_t N0 = (size_t)p->lv[0].g.N * B;
+  AL(p->Kband, (size_t)B * p->M * (p->bw + 1));
+  AL(p->Kinv, (size_t)B * p->M * p->M);
+  AL(p->ferr, B);
+  AL(p->scalars, (size_t)V * B);
+  AL(p->rhs, N0); AL(p->omega, N0);
+  AL(p->field_of_dev, 8);
+  AL(p->x, N0); AL(p->pv, N0); AL(p->q, N0); AL(p->z, N0);
+  AL(p->u64, N0); AL(p->r64, N0); AL(p->y64, N0); AL(p->g64, N0);
+  AL(p->zd, N0 * V); AL(p->dzd, N0 * V); AL(p->kap, N0 * V);
+  AL(p->part, (size_t)NSLOT * B * MPN_PMAX);
+  AL(p->dscal, (size_t)16 * B);
+  AL(p->lam, (size_t)MAXL * B);
+#undef AL
+  int fo[8];
+  for (int v = 0; v < 8; ++v) fo[v] = v < V ? d.field_of[v] : -1;
+  if (cudaMemcpy(p->field_of_dev, fo, sizeof(fo), cudaMemcpyHostToDevice) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
+  if (cudaMallocHost((void**)&p->hbuf, sizeof(double) * 16 * B) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
+
+  // Chebyshev coefficients on [lo, 1] for Dinv scaled by 1 / lambda_max
+  const double lo = 0.1, th = (1.0 + lo) / 2, de = (1.0 - lo) / 2, sg = th / de;
+  p->cheb_inv_th = (float)(1.0 / th);
+  double r0 = 1.0 / sg;
+  for (int k = 1; k < d.cheb_degree && k < 32; ++k) {
+    double r1 = 1.0 / (2 * sg - r0);
+    p->cheb_c1[k] = (float)(r1 * r0);
+    p->cheb_c2[k] = (float)(2 * r1 / de);
+    r0 = r1;
+  }
+  *out = p;
+  return MPN_OK;
+}
+
+// ------------------------------------------------------------------ pieces
+#define PROF_PAIRS 1024
+static void prof_mark(mpn_problem* p, cudaStream_t st) {
+  if (!p->prof_on || p->prof_used >= 2 * PROF_PAIRS) return;
+  cudaEventRecord(p->prof_ev[p->prof_used++], st);
+}
+// Accumulates the recorded (start, end) pairs; the stream has been synchronised.
+static void prof_flush(mpn_problem* p) {
+  if (!p->prof_on) return;
+  const Level& l = p->lv[0];
+  // algorithmic bytes of one smoothing step on the finest grid: read e, d, r,
+  // dinv, rho and the F coefficient fields once, write e and d (FP32)
+  double bytes = 4.0 * (7 + p->F) * (double)l.g.N * p->B;
+  for (int k = 0; k + 1 < p->prof_used; k += 2) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p->prof_ev[k], p->prof_ev[k + 1]) == cudaSuccess) {
+      p->prof_ms += ms; p->prof_n += 1; p->prof_bytes += bytes;
+    }
+  }
+  p->prof_used = 0;
+}
+// q = S x at level k (FP32), optional <x, q> partials into `part`.
+static int apply_S(mpn_problem* p, int k, const float* x, float* q, double* part, cudaStream_t st) {
+  Level& l = p->lv[k];
+  Coef cf = make_coef(p, l.fields);
+  dim3 gr(nblk(l.g.N), p->B);
+  k_Lpass<float><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, x, nullptr, nullptr, l.y);
+  k_LTpass<float><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.y, nullptr, nullptr, nullptr, x, -1.f, q,
+                                          part ? x : nullptr, part);
+  CKL();
+  return MPN_OK;
+}
+
+static int setup(mpn_problem* p, const float* fields, const float* scalars, cudaStream_t st) {
+  int B = p->B, F = p->F, V = p->V;
+  p->setup_ok = false;
+  Level& l0 = p->lv[0];
+  if (F > 0) CK(cudaMemcpyAsync(l0.fields, fields, sizeof(float) * (size_t)F * B * l0.g.N, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(p->scalars, scalars, sizeof(float) * (size_t)V * B, cudaMemcpyDeviceToDevice, st));
+  {
+    Coef cf = make_coef(p, l0.fields);
+    k_rho_fine<<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho);
+    CKL();
+  }
+  for (int k = 1; k < p->L; ++k) {
+    Level& lf = p->lv[k - 1];
+    Level& lc = p->lv[k];
+    int nd = lf.cz[0] + lf.cz[1] + lf.cz[2];
+    dim3 gf(nblk(lc.g.N), F * B);
+    if (F > 0)
+      k_restrict_field<<<gf, MPN_TPB, 0, st>>>(lf.g, lc.g, lf.cz[0], lf.cz[1], lf.cz[2], lf.fields, lc.fields, 1.f);
+    k_restrict_field<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(lf.g, lc.g, lf.cz[0], lf.cz[1], lf.cz[2], lf.rho,
+                                                               lc.rho, (float)(1 << nd));
+    CKL();
+  }
+  for (int k = 0; k < p->L; ++k) {
+    Level& l = p->lv[k];
+    Coef cf = make_coef(p, l.fields);
+    dim3 gr(nblk(l.g.N), B);
+    k_diag_inv<<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.dinv);
+    CKL();
+    if (k == p->L - 1) break;
+    // power method for lambda_max(Dinv S)
+    k_fill_hash<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.t);
+    double* pw = slot(p, S_PW);
+    for (int it = 0; it < 12; ++it) {
+      TRY(apply_S(p, k, l.t, l.d, nullptr, st));
+      k_power_w<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.dinv, l.d, l.e, pw);
+      if (it < 11) k_power_norm<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.e, l.t, pw, gr.x);
+    }
+    k_scale_dinv<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.dinv, pw, gr.x, 1.1f, p->lam + k * B);
+    CKL();
+  }
+  // coarsest: banded assembly, Cholesky, explicit inverse
+  Level& lc = p->lv[p->L - 1];
+  Coef cfc = make_coef(p, lc.fields);
+  CK(cudaMemsetAsync(p->ferr, 0, sizeof(int) * B, st));
+  k_coarse_assemble<<<dim3(nblk(p->M), B), MPN_TPB, 0, st>>>(lc.g, cfc, lc.rho, p->bw, p->Kband);
+  size_t smem = sizeof(float) * (size_t)p->M * (p->bw + 1);
+  CK(cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_coarse_factor<<<B, 512, smem, st>>>(p->M, p->bw, p->Kband, p->ferr);
+  k_coarse_inverse<<<dim3((p->M + 127) / 128, B), 128, 0, st>>>(p->M, p->bw, p->Kband, p->Kinv);
+  CKL();
+  p->setup_ok = true;
+  return MPN_OK;
+}
+
+// One V-cycle at level k: e_k ~ S_k^{-1} r_k.  On return e_k + d_k (d_k
+// pending, unless k is the coarsest level, where d is not used) is the result.
+static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
+  Level& l = p->lv[k];
+  int B = p->B;
+  dim3 gr(nblk(l.g.N), B);
+  if (k == p->L - 1) {
+    k_coarse_solve<<<dim3((p->M * 32 + MPN_TPB - 1) / MPN_TPB, B), MPN_TPB, 0, st>>>(p->M, p->Kinv, l.r, l.e);
+    CKL();
+    return MPN_OK;
+  }
+  Coef cf = make_coef(p, l.fields);
+  int m = p->desc.cheb_degree;
+  // pre-smoothing from e = 0
+  k_cheb_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, l.e, l.d);
+  for (int s = 1; s < m; ++s) {
+    if (k == 0) prof_mark(p, st);
+    k_Lpass<float><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.e, l.d, nullptr, l.y);
+    k_cheb_B<<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.y, l.e, l.d, l.r, l.dinv, 1, p->cheb_c1[s], p->cheb_c2[s]);
+    if (k == 0) prof_mark(p, st);
+  }
+  // residual of e + d, restricted
+  k_Lpass<float><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.e, l.d, nullptr, l.y);
+  k_res_B<<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.y, l.e, l.d, l.r, l.t);
+  Level& lc = p->lv[k + 1];
+  k_restrict_vec<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], l.t, lc.r);
+  CKL();
+  TRY(vcycle(p, k + 1, st));
+  k_prolong_add<<<gr, MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], lc.e,
+                                        (k + 1 == p->L - 1) ? nullptr : lc.d, l.e);
+  // post-smoothing
+  k_Lpass<float><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.e, nullptr, nullptr, l.y);
+  k_cheb_B<<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.y, l.e, l.d, l.r, l.dinv, 0, 0.f, p->cheb_inv_th);
+  for (int s = 1; s < m; ++s) {
+    if (k == 0) prof_mark(p, st);
+    k_Lpass<float><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.e, l.d, nullptr, l.y);
+    k_cheb_B<<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.y, l.e, l.d, l.r, l.dinv, 1, p->cheb_c1[s], p->cheb_c2[s]);
+    if (k == 0) prof_mark(p, st);
+  }
+  CKL();
+  return MPN_OK;
+}
+
+// z = V(r) at the finest level with partial <r, z> in slot S_RZ.
+static int precond(mpn_problem* p, cudaStream_t st) {
+  Level& l = p->lv[0];
+  TRY(vcycle(p, 0, st));
+  dim3 gr(nblk(l.g.N), p->B);
+  k_final_z<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.e, p->L > 1 ? l.d : nullptr, l.r, p->z, slot(p, S_RZ));
+  CKL();
+  return MPN_OK;
+}
+
+// Inner FP32 PCG on S x = r (r = lv[0].r), fixed iteration count, x = p->x.
+static int pcg(mpn_problem* p, int iters, cudaStream_t st) {
+  Level& l = p->lv[0];
+  dim3 gr(nblk(l.g.N), p->B);
+  int P = gr.x;
+  double* rz_old = p->dscal + p->B;
+  TRY(precond(p, st));
+  k_pcg_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, p->z, p->x, p->pv);
+  for (int it = 0; it < iters; ++it) {
+    TRY(apply_S(p, 0, p->pv, p->q, slot(p, S_PQ), st));
+    k_pcg_xr<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), slot(p, S_PQ), P, P, p->pv, p->q, p->x, l.r, rz_old);
+    CKL();
+    if (it == iters - 1) break;
+    TRY(precond(p, st));
+    k_pcg_p<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), P, rz_old, p->z, p->pv);
+    CKL();
+  }
+  return MPN_OK;
+}
+
+// FP64 residual r64 = rhs_vec - S u64 where rhs_vec is either the forward
+// right-hand side L^T rho b + theta 1_B omega (g_adj null) or g_adj.
+static int residual64(mpn_problem* p, const double* u, const double* g_adj, double* out, cudaStream_t st) {
+  Level& l = p->lv[0];
+  Coef cf = make_coef(p, l.fields);
+  dim3 gr(nblk(l.g.N), p->B);
+  k_Lpass<double><<<gr, MPN_TPB, 0, st>>>(l.g, cf, nullptr, u, nullptr, g_adj ? nullptr : p->rhs, p->y64);
+  k_LTpass<double><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, nullptr, g_adj, g_adj ? nullptr : p->omega, u, 1.0,
+                                           out, nullptr, nullptr);
+  CKL();
+  return MPN_OK;
+}
+
+// Solve S u = rhs (forward: g_adj null; adjoint: the FP64 rhs g_adj) by FP64
+// refinement around FP32 MG-PCG.  u64 holds the initial guess on entry.
+static int refine_solve(mpn_problem* p, const double* g_adj, mpn_stats* stats, cudaStream_t st) {
+  Level& l = p->lv[0];
+  int B = p->B, N = l.g.N;
+  dim3 gr(nblk(N), B);
+  int P = gr.x;
+  double* scale = p->dscal;
+  double* outv = p->dscal + 2 * B;  // [slots][B]
+  std::vector<double> prev_upd(B, 1.0);
+  mpn_stats sres;
+  memset(&sres, 0, sizeof(sres));
+  int status = MPN_ERR_NOT_CONVERGED;
+  // ||rhs|| for the relative residual
+  {
+    double* tmp = p->r64;
+    TRY(residual64(p, nullptr, g_adj, tmp, st));
+    k_norm2_d<<<gr, MPN_TPB, 0, st>>>(N, tmp, slot(p, S_GN));
+    CKL();
+  }
+  std::vector<double> gnorm(B, 0.0);
+  for (int sweep = 0; sweep < p->desc.max_refine; ++sweep) {
+    TRY(residual64(p, p->u64, g_adj, p->r64, st));
+    k_norm2_d<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN));
+    k_to32<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN), P, l.r, scale);
+    CKL();
+    TRY(pcg(p, p->desc.inner_iters, st));
+    k_update64<<<gr, MPN_TPB, 0, st>>>(N, p->x, scale, p->u64, slot(p, S_DU), slot(p, S_UN));
+    // slots S_RN, S_DU, S_UN, (S_PW unused), S_GN -> outv
+    k_collect<<<B, 64, 0, st>>>(B, 5, slot(p, S_RN), P, outv);
+    CKL();
+    CK(cudaMemcpyAsync(p->hbuf, outv, sizeof(double) * 5 * B, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    prof_flush(p);
+    const double* h = p->hbuf;
+    double maxpred = 0, maxupd = 0, maxres = 0;
+    bool bad = false, grew = false;
+    for (int b = 0; b < B; ++b) {
+      double rn = sqrt(h[0 * B + b]), du = sqrt(h[1 * B + b]), un = sqrt(h[2 * B + b]);
+      if (sweep == 0) gnorm[b] = sqrt(h[4 * B + b]);
+      if (!std::isfinite(rn) || !std::isfinite(du) || !std::isfinite(un)) bad = true;
+      double upd = un > 0 ? du / un : (du > 0 ? 1.0 : 0.0);
+      double pred = sweep == 0 ? upd : upd * std::min(1.0, upd / std::max(prev_upd[b], 1e-300));
+      if (sweep >= 2 && upd > 10.0 * prev_upd[b] && upd > 1e-3) grew = true;
+      prev_upd[b] = upd;
+      maxpred = std::max(maxpred, pred);
+      maxupd = std::max(maxupd, upd);
+      maxres = std::max(maxres, gnorm[b] > 0 ? rn / gnorm[b] : 0.0);
+    }
+    sres.sweeps = sweep + 1;
+    sres.pcg_iters = (sweep + 1) * p->desc.inner_iters;
+    sres.rel_update = maxupd;
+    sres.pred_error = maxpred;
+    sres.rel_residual = maxres;
+    if (bad) { status = MPN_ERR_NONFINITE; break; }
+    if (grew) { status = MPN_ERR_DIVERGED; break; }
+    if ((sweep >= 1 && maxpred <= p->desc.tol) || maxupd <= p->desc.tol * 0.1) { status = MPN_OK; break; }
+  }
+  // final residual
+  if (status == MPN_OK || status == MPN_ERR_NOT_CONVERGED) {
+    TRY(residual64(p, p->u64, g_adj, p->r64, st));
+    k_norm2_d<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN));
+    k_collect<<<B, 64, 0, st>>>(B, 1, slot(p, S_RN), P, outv);
+    CKL();
+    CK(cudaMemcpyAsync(p->hbuf, outv, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double maxres = 0;
+    for (int b = 0; b < B; ++b)
+      maxres = std::max(maxres, gnorm[b] > 0 ? sqrt(p->hbuf[b]) / gnorm[b] : 0.0);
+    sres.rel_residual = maxres;
+  }
+  if (stats) *stats = sres;
+  return status;
+}
+
+static int check_ptrs(const void* a, const void* b) { return (a && b) ? MPN_OK : MPN_ERR_INVALID_ARG; }
+
+static int forward_impl(mpn_problem* p, const float* fields, const float* scalars, const float* rhs,
+                        const float* omega, const float* u0, float* z, double* z64, mpn_stats* stats,
+                        cudaStream_t st) {
+  Level& l = p->lv[0];
+  int B = p->B;
+  size_t N0 = (size_t)l.g.N * B;
+  TRY(setup(p, fields, scalars, st));
+  CK(cudaMemcpyAsync(p->rhs, rhs, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(p->omega, omega, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
+  dim3 gr(nblk(l.g.N), B);
+  k_set_u<<<gr, MPN_TPB, 0, st>>>(l.g.N, u0, p->u64);
+  CKL();
+  int status = refine_solve(p, nullptr, stats, st);
+  if (status != MPN_OK && status != MPN_ERR_NOT_CONVERGED) return status;
+  Coef cf = make_coef(p, l.fields);
+  k_recover<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->u64, p->rhs, nullptr, z, z64);
+  CKL();
+  CK(cudaStreamSynchronize(st));
+  return status;
+}
+
+extern "C" int mpn_forward(mpn_problem* p, const float* fields, const float* scalars, const float* rhs,
+                           const float* omega, const float* u0, float* z, double* z64, mpn_stats* stats,
+                           void* stream) {
+  if (!p) return MPN_ERR_INVALID_ARG;
+  TRY(check_ptrs(scalars, rhs));
+  if (!omega || (!z && !z64)) return MPN_ERR_INVALID_ARG;
+  if (p->F > 0 && !fields) return MPN_ERR_INVALID_ARG;
+  return forward_impl(p, fields, scalars, rhs, omega, u0, z, z64, stats, (cudaStream_t)stream);
+}
+
+extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* scalars, const float* rhs,
+                           const float* omega, const float* z, const float* g_z, float* dfields, float* dscalars,
+                           float* drhs, float* domega, float* dz, int flags, mpn_stats* stats, void* stream) {
+  if (!p) return MPN_ERR_INVALID_ARG;
+  TRY(check_ptrs(scalars, rhs));
+  TRY(check_ptrs(omega, g_z));
+  TRY(check_ptrs(dscalars, drhs));
+  if (!domega) return MPN_ERR_INVALID_ARG;
+  if (p->F > 0 && (!fields || !dfields)) return MPN_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Level& l = p->lv[0];
+  int B = p->B, V = p->V;
+  size_t N0 = (size_t)l.g.N * B;
+  dim3 gr(nblk(l.g.N), B);
+  const float* zf = z;
+  if (!z) {
+    // recompute the forward solution (FP64, kept internally)
+    int s = forward_impl(p, fields, scalars, rhs, omega, nullptr, nullptr, p->zd, nullptr, st);
+    if (s != MPN_OK && s != MPN_ERR_NOT_CONVERGED) return s;
+    zf = nullptr;
+  } else if (!(flags & MPN_REUSE_SETUP) || !p->setup_ok) {
+    TRY(setup(p, fields, scalars, st));
+    CK(cudaMemcpyAsync(p->rhs, rhs, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(p->omega, omega, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
+  } else {
+    CK(cudaMemcpyAsync(p->rhs, rhs, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(p->omega, omega, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
+  }
+  Coef cf = make_coef(p, l.fields);
+  // reduced right-hand side g_u - M_{u zeta} M_{zeta zeta}^{-1} g_zeta (FP64)
+  k_adj_kappa<<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
+  k_adj_rhs<<<gr, MPN_TPB, 0, st>>>(l.g, g_z, p->kap, p->g64);
+  k_set_u<<<gr, MPN_TPB, 0, st>>>(l.g.N, nullptr, p->u64);
+  CKL();
+  int status = refine_solve(p, p->g64, stats, st);
+  if (status != MPN_OK && status != MPN_ERR_NOT_CONVERGED) return status;
+  k_recover<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->u64, nullptr, g_z, dz, p->dzd);
+  double* gp = slot(p, S_GR0);
+  k_gradients<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rhs, zf, zf ? nullptr : p->zd, p->dzd, dfields, drhs, domega, gp);
+  k_scalar_grads<<<B, 64, 0, st>>>(V, B, p->field_of_dev, gp, gr.x, dscalars);
+  CKL();
+  CK(cudaStreamSynchronize(st));
+  return status;
+}
+
+extern "C" int mpn_mse_grad(mpn_problem* p, const float* z, const float* target, float* g_z, void* stream) {
+  if (!p || !z || !target || !g_z) return MPN_ERR_INVALID_ARG;
+  Level& l = p->lv[0];
+  k_mse_grad<<<dim3(nblk(l.g.N), p->B), MPN_TPB, 0, (cudaStream_t)stream>>>(l.g.N, p->V, p->B, z, target, g_z);
+  CKL();
+  return MPN_OK;
+}
+
+extern "C" int mpn_apply_reduced(mpn_problem* p, const float* fields, const float* scalars, const float* u, float* q,
+                                 void* stream) {
+  if (!p || !scalars || !u || !q) return MPN_ERR_INVALID_ARG;
+  if (p->F > 0 && !fields) return MPN_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  TRY(setup(p, fields, scalars, st));
+  TRY(apply_S(p, 0, u, q, nullptr, st));
+  CK(cudaStreamSynchronize(st));
+  return MPN_OK;
+}
+
+extern "C" int mpn_profile(mpn_problem* p, int enable, double* ms_total, long long* launches, double* bytes) {
+  if (!p) return MPN_ERR_INVALID_ARG;
+  if (ms_total) *ms_total = p->prof_ms;
+  if (launches) *launches = p->prof_n;
+  if (bytes) *bytes = p->prof_bytes;
+  if (enable >= 0) {
+    if (enable && p->prof_ev.empty()) {
+      p->prof_ev.resize(2 * PROF_PAIRS);
+      for (auto& e : p->prof_ev) CK(cudaEventCreate(&e));
+    }
+    p->prof_on = enable;
+    p->prof_used = 0;
+    p->prof_ms = 0; p->prof_n = 0; p->prof_bytes = 0;
+  }
+  return MPN_OK;
+}

@@ -1,0 +1,224 @@
+// Device-side building blocks of the NeuRLP-PDE solver: grid geometry,
+// coefficient access, the difference weights of the derivative rows (Eq. 5,
+// three-point central, second-order one-sided at non-periodic edges) and the
+// per-point algebra of the eliminated derivative unknowns.
+//
+// Reduced normal equations.  The derivative unknowns of point i appear only
+// in the rows owned by i (its equation row, Eq. 3, and its derivative and
+// Taylor rows, Eqs. 5-7), so they are eliminated exactly from A^T A z = A^T d
+// (Eq. 9), point by point.  In the scaled unknowns w = (s u', s^2 u'') of one
+// dimension, the Taylor rows equal D1 + D2/2 and -D1 + D2/2 as functionals,
+// so the rows of dimension d contribute delta^T W delta with
+// delta = w - a(u) (a = the difference forms of Eq. 5) and
+//   W = [[3, 0], [0, 3/2]]         interior / periodic (D1, D2, TF, TB)
+//   W = [[2, 1/2], [1/2, 5/4]]     first point of a non-periodic dim (no TB)
+//   W = [[2, -1/2], [-1/2, 5/4]]   last point (no TF).
+// With beta = (c_{1+2d}/s_d, c_{2+2d}/s_d^2) and e = L_i u - b_i (L the
+// finite-difference operator with the same difference forms), minimising over
+// delta gives the point weight rho_i = 1 / (1 + sum_d beta_d^T W_d^{-1} beta_d)
+// and the u-only system
+//   S u = L^T rho (b - ...) ,  S = L^T diag(rho) L + diag(1_B)
+// (Schur complement of A^T A onto u), solved here by multigrid PCG.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MPN_TPB 256
+#define MPN_PMAX 128   // partial sums per instance (max CTAs per instance)
+
+struct Grid {
+  int D;          // 2 or 3
+  int n[3];       // n[2] = 1 when D = 2
+  int per[3];     // periodic flags (per[0] = 0)
+  int stride[3];  // point-index strides
+  int N;          // points per instance
+  int final_rows; // Dirichlet rows on t = t_f
+  float theta;    // weight of the Dirichlet rows at this level
+  float is1[3], is2[3];    // 1/s, 1/s^2
+  double ds1[3], ds2[3];   // 1/s, 1/s^2 in FP64
+};
+
+struct Coef {
+  int V, F, B;
+  int field_of[7];
+  const float* fields;   // [F][B][N] at this level
+  const float* scalars;  // [V][B]
+};
+
+__device__ __forceinline__ float coefv(const Coef& c, int v, int b, int p, int N) {
+  int f = c.field_of[v];
+  return f >= 0 ? __ldg(c.fields + ((size_t)f * c.B + b) * N + p) : __ldg(c.scalars + v * c.B + b);
+}
+
+__device__ __forceinline__ void decode(const Grid& g, int p, int pos[3]) {
+  pos[2] = p % g.n[2];
+  int q = p / g.n[2];
+  pos[1] = q % g.n[1];
+  pos[0] = q / g.n[1];
+}
+
+// Point index of the neighbour at offset o along d (wrapping when periodic).
+// The caller guarantees the target exists for non-periodic dims.
+__device__ __forceinline__ int nbr(const Grid& g, int p, const int pos[3], int d, int o) {
+  int c = pos[d] + o;
+  if (g.per[d]) { c %= g.n[d]; if (c < 0) c += g.n[d]; }
+  return p + (c - pos[d]) * g.stride[d];
+}
+
+// Weight of u_{pos+o} in the difference form of order `order` at coordinate
+// `pos` (Eq. 5): s^order * u^(order) = sum_o w(o) u_{pos+o}.
+__device__ __forceinline__ float dweight(int order, int pos, int n, int per, int o) {
+  if (per || (pos > 0 && pos < n - 1)) {
+    if (order == 1) return o == -1 ? -0.5f : (o == 1 ? 0.5f : 0.f);
+    return o == 0 ? -2.f : ((o == 1 || o == -1) ? 1.f : 0.f);
+  }
+  if (pos == 0) {
+    if (order == 1) return o == 0 ? -1.5f : (o == 1 ? 2.f : (o == 2 ? -0.5f : 0.f));
+    return o == 0 ? 1.f : (o == 1 ? -2.f : (o == 2 ? 1.f : 0.f));
+  }
+  if (order == 1) return o == 0 ? 1.5f : (o == -1 ? -2.f : (o == -2 ? 0.5f : 0.f));
+  return o == 0 ? 1.f : (o == -1 ? -2.f : (o == -2 ? 1.f : 0.f));
+}
+
+// 0 interior/periodic, 1 first point, 2 last point of a non-periodic dim.
+__device__ __forceinline__ int edge_class(const Grid& g, int d, int pos) {
+  if (g.per[d]) return 0;
+  return pos == 0 ? 1 : (pos == g.n[d] - 1 ? 2 : 0);
+}
+
+__device__ __forceinline__ bool is_boundary(const Grid& g, const int pos[3]) {
+  if (pos[0] == 0) return true;
+  if (g.final_rows && pos[0] == g.n[0] - 1) return true;
+  for (int d = 1; d < g.D; ++d)
+    if (!g.per[d] && (pos[d] == 0 || pos[d] == g.n[d] - 1)) return true;
+  return false;
+}
+
+// W_d for the edge class (symmetric 2x2: w11, w12, w22).
+__device__ __forceinline__ void wmat(int cls, double& w11, double& w12, double& w22) {
+  if (cls == 0) { w11 = 3.0; w12 = 0.0; w22 = 1.5; }
+  else { w11 = 2.0; w12 = cls == 1 ? 0.5 : -0.5; w22 = 1.25; }
+}
+
+// W_d^{-1} x.
+__device__ __forceinline__ void winv(int cls, double x1, double x2, double& y1, double& y2) {
+  if (cls == 0) { y1 = x1 / 3.0; y2 = x2 / 1.5; return; }
+  double sg = cls == 1 ? 1.0 : -1.0;
+  y1 = (1.25 * x1 - 0.5 * sg * x2) / 2.25;
+  y2 = (-0.5 * sg * x1 + 2.0 * x2) / 2.25;
+}
+
+template <class T> __device__ __forceinline__ T is1_of(const Grid& g, int d);
+template <> __device__ __forceinline__ float is1_of<float>(const Grid& g, int d) { return g.is1[d]; }
+template <> __device__ __forceinline__ double is1_of<double>(const Grid& g, int d) { return g.ds1[d]; }
+template <class T> __device__ __forceinline__ T is2_of(const Grid& g, int d);
+template <> __device__ __forceinline__ float is2_of<float>(const Grid& g, int d) { return g.is2[d]; }
+template <> __device__ __forceinline__ double is2_of<double>(const Grid& g, int d) { return g.ds2[d]; }
+
+// Point weight rho_i = 1 / (1 + sum_d beta_d^T W_d^{-1} beta_d).
+template <class T>
+__device__ __forceinline__ T rho_point(const Grid& g, const Coef& cf, int b, int p, const int pos[3]) {
+  T gam = 0;
+  for (int d = 0; d < g.D; ++d) {
+    T b1 = (T)coefv(cf, 1 + 2 * d, b, p, g.N) * is1_of<T>(g, d);
+    T b2 = (T)coefv(cf, 2 + 2 * d, b, p, g.N) * is2_of<T>(g, d);
+    int cls = edge_class(g, d, pos[d]);
+    if (cls == 0) gam += b1 * b1 / (T)3 + (T)2 * b2 * b2 / (T)3;
+    else {
+      T sg = cls == 1 ? (T)1 : (T)-1;
+      gam += ((T)1.25 * b1 * b1 - sg * b1 * b2 + (T)2 * b2 * b2) / (T)2.25;
+    }
+  }
+  return (T)1 / ((T)1 + gam);
+}
+
+// (L x)_i: the equation row evaluated with every derivative replaced by its
+// difference form.  x2 (nullable) is added to x on the fly.
+template <class T>
+__device__ __forceinline__ T Lrow(const Grid& g, const Coef& cf, int b, int p, const int pos[3],
+                                  const T* __restrict__ x, const T* __restrict__ x2) {
+  T xc = x[p]; if (x2) xc += x2[p];
+  T acc = (T)coefv(cf, 0, b, p, g.N) * xc;
+  for (int d = 0; d < g.D; ++d) {
+    T c1 = (T)coefv(cf, 1 + 2 * d, b, p, g.N);
+    T c2 = (T)coefv(cf, 2 + 2 * d, b, p, g.N);
+    if (c1 == (T)0 && c2 == (T)0) continue;
+    T a1 = 0, a2 = 0;
+#pragma unroll
+    for (int o = -2; o <= 2; ++o) {
+      float w1 = dweight(1, pos[d], g.n[d], g.per[d], o);
+      float w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
+      if (w1 == 0.f && w2 == 0.f) continue;
+      T xv;
+      if (o == 0) xv = xc;
+      else { int q = nbr(g, p, pos, d, o); xv = x[q]; if (x2) xv += x2[q]; }
+      a1 += (T)w1 * xv; a2 += (T)w2 * xv;
+    }
+    acc += c1 * a1 * is1_of<T>(g, d) + c2 * a2 * is2_of<T>(g, d);
+  }
+  return acc;
+}
+
+// (L^T y)_j: gather over the rows i whose difference forms touch point j.
+template <class T>
+__device__ __forceinline__ T LTgather(const Grid& g, const Coef& cf, int b, int p, const int pos[3],
+                                      const T* __restrict__ y) {
+  T acc = (T)coefv(cf, 0, b, p, g.N) * y[p];
+  for (int d = 0; d < g.D; ++d) {
+#pragma unroll
+    for (int o = -2; o <= 2; ++o) {
+      int ip = pos[d] - o;
+      if (g.per[d]) { ip %= g.n[d]; if (ip < 0) ip += g.n[d]; }
+      else if (ip < 0 || ip >= g.n[d]) continue;
+      float w1 = dweight(1, ip, g.n[d], g.per[d], o);
+      float w2 = dweight(2, ip, g.n[d], g.per[d], o);
+      if (w1 == 0.f && w2 == 0.f) continue;
+      int q = p + (ip - pos[d]) * g.stride[d];
+      T c1 = (T)coefv(cf, 1 + 2 * d, b, q, g.N);
+      T c2 = (T)coefv(cf, 2 + 2 * d, b, q, g.N);
+      acc += y[q] * (c1 * (T)w1 * is1_of<T>(g, d) + c2 * (T)w2 * is2_of<T>(g, d));
+    }
+  }
+  return acc;
+}
+
+// ---------------------------------------------------------------- reductions
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; result valid in thread 0.  Fixed order: deterministic.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[32];
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0;
+  if (wid == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    r = lane < nw ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// Sum of the P partials of instance b (consumer-side second stage); every
+// thread of the block receives the same value.
+__device__ __forceinline__ double sum_partials(const double* __restrict__ part, int b, int P) {
+  __shared__ double res;
+  if (threadIdx.x < 32) {
+    double v = 0;
+    for (int k = threadIdx.x; k < P; k += 32) v += part[b * MPN_PMAX + k];
+    v = warp_sum(v);
+    if (threadIdx.x == 0) res = v;
+  }
+  __syncthreads();
+  double out = res;
+  __syncthreads();
+  return out;
+}

@@ -1,0 +1,701 @@
+// Kernels of the NeuRLP-PDE solver.  Every kernel is batch-strided: the
+// instance is blockIdx.y and the points of that instance are covered by a
+// grid-stride loop over blockIdx.x (gridDim.x <= MPN_PMAX, so kernels that
+// reduce write one partial per block: part[b * MPN_PMAX + blockIdx.x]).
+#pragma once
+#include "mpn_device.cuh"
+
+#define GRID_LOOP(p, N) for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (N); p += gridDim.x * blockDim.x)
+
+// ------------------------------------------------------------------- setup
+// rho at the finest level from the coefficients.
+__global__ void k_rho_fine(Grid g, Coef cf, float* __restrict__ rho) {
+  int b = blockIdx.y;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode(g, p, pos);
+    rho[(size_t)b * g.N + p] = (float)rho_point<double>(g, cf, b, p, pos);
+  }
+}
+
+// Full-weighting restriction of a point field (1/4, 1/2, 1/4 per coarsened
+// dimension; clamped at non-periodic edges), times `scale`.  fine/coarse are
+// [nb][Nf] / [nb][Nc] with the batch-like index in blockIdx.y.
+__global__ void k_restrict_field(Grid gf, Grid gc, int c0, int c1, int c2, const float* __restrict__ fine,
+                                 float* __restrict__ coarse, float scale) {
+  int b = blockIdx.y;
+  int cz[3] = {c0, c1, c2};
+  const float* f = fine + (size_t)b * gf.N;
+  GRID_LOOP(p, gc.N) {
+    int pos[3]; decode(gc, p, pos);
+    int lo[3], cnt[3], idx[3][3]; float w[3][3];
+    for (int d = 0; d < 3; ++d) {
+      if (!cz[d]) { cnt[d] = 1; idx[d][0] = pos[d]; w[d][0] = 1.f; continue; }
+      cnt[d] = 3;
+      int c = 2 * pos[d];
+      int m = c - 1, pl = c + 1, n = gf.n[d];
+      if (gf.per[d]) { m = (m + n) % n; pl = pl % n; }
+      else { m = m < 0 ? 0 : m; pl = pl >= n ? n - 1 : pl; }
+      idx[d][0] = m; idx[d][1] = c; idx[d][2] = pl;
+      w[d][0] = 0.25f; w[d][1] = 0.5f; w[d][2] = 0.25f;
+      (void)lo;
+    }
+    float acc = 0.f;
+    for (int a = 0; a < cnt[0]; ++a)
+      for (int bb = 0; bb < cnt[1]; ++bb)
+        for (int c = 0; c < cnt[2]; ++c) {
+          int q = (idx[0][a] * gf.n[1] + idx[1][bb]) * gf.n[2] + idx[2][c];
+          acc += w[0][a] * w[1][bb] * w[2][c] * f[q];
+        }
+    coarse[(size_t)b * gc.N + p] = scale * acc;
+  }
+}
+
+// 1 / diag(S) with S = L^T diag(rho) L + theta diag(1_B).
+__global__ void k_diag_inv(Grid g, Coef cf, const float* __restrict__ rho, float* __restrict__ dinv) {
+  int b = blockIdx.y;
+  const float* rh = rho + (size_t)b * g.N;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode(g, p, pos);
+    // own row: L_jj
+    double Ljj = coefv(cf, 0, b, p, g.N);
+    for (int d = 0; d < g.D; ++d)
+      Ljj += (double)coefv(cf, 1 + 2 * d, b, p, g.N) * dweight(1, pos[d], g.n[d], g.per[d], 0) * g.ds1[d] +
+             (double)coefv(cf, 2 + 2 * d, b, p, g.N) * dweight(2, pos[d], g.n[d], g.per[d], 0) * g.ds2[d];
+    double acc = (double)rh[p] * Ljj * Ljj;
+    for (int d = 0; d < g.D; ++d)
+      for (int o = -2; o <= 2; ++o) {
+        if (o == 0) continue;
+        int ip = pos[d] - o;
+        if (g.per[d]) { ip %= g.n[d]; if (ip < 0) ip += g.n[d]; }
+        else if (ip < 0 || ip >= g.n[d]) continue;
+        float w1 = dweight(1, ip, g.n[d], g.per[d], o), w2 = dweight(2, ip, g.n[d], g.per[d], o);
+        if (w1 == 0.f && w2 == 0.f) continue;
+        int q = p + (ip - pos[d]) * g.stride[d];
+        double Lij = (double)coefv(cf, 1 + 2 * d, b, q, g.N) * w1 * g.ds1[d] +
+                     (double)coefv(cf, 2 + 2 * d, b, q, g.N) * w2 * g.ds2[d];
+        acc += (double)rh[q] * Lij * Lij;
+      }
+    if (is_boundary(g, pos)) acc += g.theta;
+    dinv[(size_t)b * g.N + p] = acc > 0 ? (float)(1.0 / acc) : 0.f;
+  }
+}
+
+// ------------------------------------------------------ operator: two passes
+// y = rho (src - L (x + x2)); rho null => computed from the coefficients;
+// x null => L x = 0.
+template <class T>
+__global__ void k_Lpass(Grid g, Coef cf, const float* __restrict__ rho, const T* __restrict__ x,
+                        const T* __restrict__ x2, const float* __restrict__ src, T* __restrict__ y) {
+  int b = blockIdx.y;
+  size_t off = (size_t)b * g.N;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode(g, p, pos);
+    T Lx = x ? Lrow<T>(g, cf, b, p, pos, x + off, x2 ? x2 + off : nullptr) : (T)0;
+    T r = rho ? (T)rho[off + p] : rho_point<T>(g, cf, b, p, pos);
+    T s = src ? (T)src[off + p] : (T)0;
+    y[off + p] = r * (s - Lx);
+  }
+}
+
+// out = sgn * (base + L^T y + theta 1_B (omega - x)); base/omega/x nullable.
+// If dotv is non-null, writes per-block partials of <out, dotv>.
+template <class T>
+__global__ void k_LTpass(Grid g, Coef cf, const T* __restrict__ y, const float* __restrict__ base,
+                         const T* __restrict__ baseT, const float* __restrict__ omega, const T* __restrict__ x,
+                         T sgn, T* __restrict__ out, const T* __restrict__ dotv, double* __restrict__ part) {
+  int b = blockIdx.y;
+  size_t off = (size_t)b * g.N;
+  double acc = 0;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode(g, p, pos);
+    T v = LTgather<T>(g, cf, b, p, pos, y + off);
+    if (base) v += (T)base[off + p];
+    if (baseT) v += baseT[off + p];
+    if (is_boundary(g, pos)) {
+      T bc = omega ? (T)omega[off + p] : (T)0;
+      if (x) bc -= x[off + p];
+      v += (T)g.theta * bc;
+    }
+    v *= sgn;
+    out[off + p] = v;
+    if (dotv) acc += (double)v * (double)dotv[off + p];
+  }
+  if (dotv) {
+    double s = block_sum(acc);
+    if (threadIdx.x == 0) part[b * MPN_PMAX + blockIdx.x] = s;
+  }
+}
+
+// --------------------------------------------------- Chebyshev-Jacobi smoother
+// The smoother iterates e <- e + d with
+//   d_0 = Dinv r_0 / th,  d_k = c1_k d_{k-1} + c2_k Dinv r_k,
+// r_k = r - S e_k, Dinv already scaled by 1 / lambda_max(Dinv S).
+__global__ void k_cheb_init(int N, const float* __restrict__ r, const float* __restrict__ dinv, float inv_th,
+                            float* __restrict__ e, float* __restrict__ d) {
+  size_t off = (size_t)blockIdx.y * N;
+  GRID_LOOP(p, N) {
+    e[off + p] = 0.f;
+    d[off + p] = inv_th * dinv[off + p] * r[off + p];
+  }
+}
+
+// mode 0: first post-smoothing step: res = r - S e (y from x = e); d = Dinv res / th.
+// mode 1: e += d; res = r - S e (y from x = e + d); d = c1 d + c2 Dinv res.
+__global__ void k_cheb_B(Grid g, Coef cf, const float* __restrict__ y, float* __restrict__ e,
+                         float* __restrict__ d, const float* __restrict__ r, const float* __restrict__ dinv,
+                         int mode, float c1, float c2) {
+  int b = blockIdx.y;
+  size_t off = (size_t)b * g.N;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode(g, p, pos);
+    float ev = e[off + p];
+    float dv = d[off + p];
+    if (mode == 1) ev += dv;
+    float res = r[off + p] + LTgather<float>(g, cf, b, p, pos, y + off);
+    if (is_boundary(g, pos)) res -= g.theta * ev;
+    if (mode == 1) { e[off + p] = ev; d[off + p] = c1 * dv + c2 * dinv[off + p] * res; }
+    else d[off + p] = c2 * dinv[off + p] * res;
+  }
+}
+
+// e += d; t = r - S e   (y from x = e + d).
+__global__ void k_res_B(Grid g, Coef cf, const float* __restrict__ y, float* __restrict__ e,
+                        const float* __restrict__ d, const float* __restrict__ r, float* __restrict__ t) {
+  int b = blockIdx.y;
+  size_t off = (size_t)b * g.N;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode(g, p, pos);
+    float ev = e[off + p] + d[off + p];
+    float res = r[off + p] + LTgather<float>(g, cf, b, p, pos, y + off);
+    if (is_boundary(g, pos)) res -= g.theta * ev;
+    e[off + p] = ev;
+    t[off + p] = res;
+  }
+}
+
+// ------------------------------------------------------ grid transfers (P^T, P)
+// Interpolation P along a coarsened dimension (nf = 2 nc fine points):
+// fine 2j <- coarse j; fine 2j+1 <- (j + j+1) / 2, wrapping when periodic;
+// the last fine point of a non-periodic dimension copies the last coarse one.
+// Restriction is P^T.
+__global__ void k_restrict_vec(Grid gf, Grid gc, int c0, int c1, int c2, const float* __restrict__ fine,
+                               float* __restrict__ coarse) {
+  int b = blockIdx.y;
+  int cz[3] = {c0, c1, c2};
+  const float* f = fine + (size_t)b * gf.N;
+  GRID_LOOP(p, gc.N) {
+    int pos[3]; decode(gc, p, pos);
+    int cnt[3], idx[3][3]; float w[3][3];
+    for (int d = 0; d < 3; ++d) {
+      if (!cz[d]) { cnt[d] = 1; idx[d][0] = pos[d]; w[d][0] = 1.f; continue; }
+      int J = pos[d], nc = gc.n[d], nf = gf.n[d];
+      int k = 0;
+      idx[d][k] = 2 * J; w[d][k++] = 1.f;
+      idx[d][k] = 2 * J + 1; w[d][k++] = (J + 1 < nc) ? 0.5f : (gf.per[d] ? 0.5f : 1.f);
+      if (J >= 1) { idx[d][k] = 2 * J - 1; w[d][k++] = 0.5f; }
+      else if (gf.per[d]) { idx[d][k] = nf - 1; w[d][k++] = 0.5f; }
+      cnt[d] = k;
+    }
+    float acc = 0.f;
+    for (int a = 0; a < cnt[0]; ++a)
+      for (int bb = 0; bb < cnt[1]; ++bb)
+        for (int c = 0; c < cnt[2]; ++c) {
+          int q = (idx[0][a] * gf.n[1] + idx[1][bb]) * gf.n[2] + idx[2][c];
+          acc += w[0][a] * w[1][bb] * w[2][c] * f[q];
+        }
+    coarse[(size_t)b * gc.N + p] = acc;
+  }
+}
+
+// ef += P (ec + dc)   (dc nullable: pending Chebyshev step of the coarse level)
+__global__ void k_prolong_add(Grid gf, Grid gc, int c0, int c1, int c2, const float* __restrict__ ec,
+                              const float* __restrict__ dc, float* __restrict__ ef) {
+  int b = blockIdx.y;
+  int cz[3] = {c0, c1, c2};
+  const float* E = ec + (size_t)b * gc.N;
+  const float* Dd = dc ? dc + (size_t)b * gc.N : nullptr;
+  GRID_LOOP(p, gf.N) {
+    int pos[3]; decode(gf, p, pos);
+    int cnt[3], idx[3][2]; float w[3][2];
+    for (int d = 0; d < 3; ++d) {
+      if (!cz[d]) { cnt[d] = 1; idx[d][0] = pos[d]; w[d][0] = 1.f; continue; }
+      int i = pos[d], nc = gc.n[d];
+      if ((i & 1) == 0) { cnt[d] = 1; idx[d][0] = i >> 1; w[d][0] = 1.f; }
+      else {
+        int j = i >> 1;
+        if (j + 1 < nc) { cnt[d] = 2; idx[d][0] = j; idx[d][1] = j + 1; w[d][0] = w[d][1] = 0.5f; }
+        else if (gf.per[d]) { cnt[d] = 2; idx[d][0] = j; idx[d][1] = 0; w[d][0] = w[d][1] = 0.5f; }
+        else { cnt[d] = 1; idx[d][0] = j; w[d][0] = 1.f; }
+      }
+    }
+    float acc = 0.f;
+    for (int a = 0; a < cnt[0]; ++a)
+      for (int bb = 0; bb < cnt[1]; ++bb)
+        for (int c = 0; c < cnt[2]; ++c) {
+          int q = (idx[0][a] * gc.n[1] + idx[1][bb]) * gc.n[2] + idx[2][c];
+          float v = E[q];
+          if (Dd) v += Dd[q];
+          acc += w[0][a] * w[1][bb] * w[2][c] * v;
+        }
+    ef[(size_t)b * gf.N + p] += acc;
+  }
+}
+
+// ------------------------------------------------------ coarsest-level solve
+// Banded lower storage: Kb[b][j][j - k] = S[j][k] for 0 <= j - k <= bw.
+__global__ void k_coarse_assemble(Grid g, Coef cf, const float* __restrict__ rho, int bw, float* __restrict__ Kb) {
+  int b = blockIdx.y;
+  const float* rh = rho + (size_t)b * g.N;
+  float* K = Kb + (size_t)b * g.N * (bw + 1);
+  GRID_LOOP(j, g.N) {
+    int pj[3]; decode(g, j, pj);
+    float* row = K + (size_t)j * (bw + 1);
+    for (int k = 0; k <= bw; ++k) row[k] = 0.f;
+    if (is_boundary(g, pj)) row[0] += g.theta;
+    // rows i of L that touch j: i = j (center) and i = j - o e_d
+    for (int d0 = -1; d0 < g.D; ++d0) {
+      for (int o = -2; o <= 2; ++o) {
+        int i, pi[3] = {pj[0], pj[1], pj[2]};
+        double Lij;
+        if (d0 < 0) {
+          if (o != 0) continue;
+          i = j;
+          Lij = coefv(cf, 0, b, i, g.N);
+          for (int d = 0; d < g.D; ++d)
+            Lij += (double)coefv(cf, 1 + 2 * d, b, i, g.N) * dweight(1, pi[d], g.n[d], g.per[d], 0) * g.ds1[d] +
+                   (double)coefv(cf, 2 + 2 * d, b, i, g.N) * dweight(2, pi[d], g.n[d], g.per[d], 0) * g.ds2[d];
+        } else {
+          if (o == 0) continue;
+          int ip = pj[d0] - o;
+          if (g.per[d0]) { ip %= g.n[d0]; if (ip < 0) ip += g.n[d0]; }
+          else if (ip < 0 || ip >= g.n[d0]) continue;
+          float w1 = dweight(1, ip, g.n[d0], g.per[d0], o), w2 = dweight(2, ip, g.n[d0], g.per[d0], o);
+          if (w1 == 0.f && w2 == 0.f) continue;
+          i = j + (ip - pj[d0]) * g.stride[d0];
+          pi[d0] = ip;
+          Lij = (double)coefv(cf, 1 + 2 * d0, b, i, g.N) * w1 * g.ds1[d0] +
+                (double)coefv(cf, 2 + 2 * d0, b, i, g.N) * w2 * g.ds2[d0];
+        }
+        double f = Lij * (double)rh[i];
+        // row i of L: center and off-center entries
+        double Lii = coefv(cf, 0, b, i, g.N);
+        for (int d = 0; d < g.D; ++d)
+          Lii += (double)coefv(cf, 1 + 2 * d, b, i, g.N) * dweight(1, pi[d], g.n[d], g.per[d], 0) * g.ds1[d] +
+                 (double)coefv(cf, 2 + 2 * d, b, i, g.N) * dweight(2, pi[d], g.n[d], g.per[d], 0) * g.ds2[d];
+        if (i <= j && j - i <= bw) row[j - i] += (float)(f * Lii);
+        for (int d = 0; d < g.D; ++d)
+          for (int o2 = -2; o2 <= 2; ++o2) {
+            if (o2 == 0) continue;
+            float w1 = dweight(1, pi[d], g.n[d], g.per[d], o2), w2 = dweight(2, pi[d], g.n[d], g.per[d], o2);
+            if (w1 == 0.f && w2 == 0.f) continue;
+            int k = nbr(g, i, pi, d, o2);
+            double Lik = (double)coefv(cf, 1 + 2 * d, b, i, g.N) * w1 * g.ds1[d] +
+                         (double)coefv(cf, 2 + 2 * d, b, i, g.N) * w2 * g.ds2[d];
+            if (k <= j && j - k <= bw) row[j - k] += (float)(f * Lik);
+          }
+      }
+    }
+  }
+}
+
+// Banded Cholesky, one block per instance, band held in shared memory.
+// A non-positive pivot is replaced by 1 and flagged in err[b].
+__global__ void k_coarse_factor(int M, int bw, float* __restrict__ Kb, int* __restrict__ err) {
+  extern __shared__ float sb[];
+  int b = blockIdx.x;
+  float* K = Kb + (size_t)b * M * (bw + 1);
+  int W = bw + 1;
+  for (int t = threadIdx.x; t < M * W; t += blockDim.x) sb[t] = K[t];
+  __syncthreads();
+  for (int k = 0; k < M; ++k) {
+    if (threadIdx.x == 0) {
+      float a = sb[k * W];
+      if (!(a > 0.f)) { a = 1.f; err[b] = 1; }
+      sb[k * W] = sqrtf(a);
+    }
+    __syncthreads();
+    float piv = sb[k * W];
+    for (int t = threadIdx.x; t < bw; t += blockDim.x) {
+      int i = k + 1 + t;
+      if (i < M) sb[i * W + (i - k)] /= piv;
+    }
+    __syncthreads();
+    int npair = bw * (bw + 1) / 2;
+    for (int t = threadIdx.x; t < npair; t += blockDim.x) {
+      // enumerate (ii, jj) with 0 <= jj <= ii < bw: i = k+1+ii, j = k+1+jj
+      int ii = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+      while (ii * (ii + 1) / 2 > t) --ii;
+      int jj = t - ii * (ii + 1) / 2;
+      int i = k + 1 + ii, j = k + 1 + jj;
+      if (i < M) sb[i * W + (i - j)] -= sb[i * W + (i - k)] * sb[j * W + (j - k)];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < M * W; t += blockDim.x) K[t] = sb[t];
+}
+
+// Explicit inverse from the banded factor: thread c solves L L^T x = e_c and
+// writes column c of Kinv (symmetric).
+__global__ void k_coarse_inverse(int M, int bw, const float* __restrict__ Lb, float* __restrict__ Kinv) {
+  int b = blockIdx.y;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= M) return;
+  const float* L = Lb + (size_t)b * M * (bw + 1);
+  float* X = Kinv + (size_t)b * M * M;
+  int W = bw + 1;
+  for (int i = 0; i < c; ++i) X[(size_t)i * M + c] = 0.f;
+  for (int i = c; i < M; ++i) {
+    float s = (i == c) ? 1.f : 0.f;
+    int j0 = max(c, i - bw);
+    for (int j = j0; j < i; ++j) s -= L[i * W + (i - j)] * X[(size_t)j * M + c];
+    X[(size_t)i * M + c] = s / L[i * W];
+  }
+  for (int i = M - 1; i >= 0; --i) {
+    float s = X[(size_t)i * M + c];
+    int j1 = min(M - 1, i + bw);
+    for (int j = i + 1; j <= j1; ++j) s -= L[j * W + (j - i)] * X[(size_t)j * M + c];
+    X[(size_t)i * M + c] = s / L[i * W];
+  }
+}
+
+// e = Kinv r at the coarsest level: one warp per row.
+__global__ void k_coarse_solve(int M, const float* __restrict__ Kinv, const float* __restrict__ r,
+                               float* __restrict__ e) {
+  int b = blockIdx.y;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= M) return;
+  const float* row = Kinv + ((size_t)b * M + warp) * M;
+  const float* rr = r + (size_t)b * M;
+  float s = 0.f;
+  for (int j = lane; j < M; j += 32) s += row[j] * rr[j];
+  s = warp_sum(s);
+  if (lane == 0) e[(size_t)b * M + warp] = s;
+}
+
+// ------------------------------------------------------------ power method
+__global__ void k_fill_hash(int N, float* __restrict__ x) {
+  size_t off = (size_t)blockIdx.y * N;
+  GRID_LOOP(p, N) {
+    uint32_t h = (uint32_t)(p * 2654435761u) ^ (uint32_t)(blockIdx.y * 40503u + 12345u);
+    h ^= h >> 15; h *= 2246822519u; h ^= h >> 13;
+    x[off + p] = (float)(h & 0xffff) / 65536.f + 0.25f;
+  }
+}
+
+// w = dinv * q, partial ||w||^2
+__global__ void k_power_w(int N, const float* __restrict__ dinv, const float* __restrict__ q,
+                          float* __restrict__ w, double* __restrict__ part) {
+  int b = blockIdx.y;
+  size_t off = (size_t)b * N;
+  double acc = 0;
+  GRID_LOOP(p, N) {
+    float v = dinv[off + p] * q[off + p];
+    w[off + p] = v;
+    acc += (double)v * v;
+  }
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) part[b * MPN_PMAX + blockIdx.x] = s;
+}
+
+// x = w / ||w||
+__global__ void k_power_norm(int N, const float* __restrict__ w, float* __restrict__ x,
+                             const double* __restrict__ part, int P) {
+  int b = blockIdx.y;
+  double nn = sqrt(sum_partials(part, b, P));
+  float inv = nn > 0 ? (float)(1.0 / nn) : 0.f;
+  size_t off = (size_t)b * N;
+  GRID_LOOP(p, N) x[off + p] = w[off + p] * inv;
+}
+
+// dinv *= 1 / (safety * lambda),  lambda = ||w|| of the last power step.
+__global__ void k_scale_dinv(int N, float* __restrict__ dinv, const double* __restrict__ part, int P,
+                             float safety, float* __restrict__ lam_out) {
+  int b = blockIdx.y;
+  double lam = sqrt(sum_partials(part, b, P));
+  float s = lam > 0 ? (float)(1.0 / (safety * lam)) : 1.f;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && lam_out) lam_out[b] = (float)lam;
+  size_t off = (size_t)b * N;
+  GRID_LOOP(p, N) dinv[off + p] *= s;
+}
+
+// --------------------------------------------------------------------- PCG
+// z = e + d (d nullable); partial <r, z>.
+__global__ void k_final_z(int N, const float* __restrict__ e, const float* __restrict__ d,
+                          const float* __restrict__ r, float* __restrict__ z, double* __restrict__ part) {
+  int b = blockIdx.y;
+  size_t off = (size_t)b * N;
+  double acc = 0;
+  GRID_LOOP(p, N) {
+    float v = e[off + p];
+    if (d) v += d[off + p];
+    z[off + p] = v;
+    acc += (double)v * r[off + p];
+  }
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) part[b * MPN_PMAX + blockIdx.x] = s;
+}
+
+// x = 0; p = z   (start of PCG; <r, z> partials already produced)
+__global__ void k_pcg_init(int N, const float* __restrict__ z, float* __restrict__ x, float* __restrict__ pv) {
+  size_t off = (size_t)blockIdx.y * N;
+  GRID_LOOP(p, N) { x[off + p] = 0.f; pv[off + p] = z[off + p]; }
+}
+
+// alpha = <r,z> / <p,q>; x += alpha p; r -= alpha q; saves <r,z> in rz_old.
+__global__ void k_pcg_xr(int N, const double* __restrict__ part_rz, const double* __restrict__ part_pq, int P,
+                         int Prz, const float* __restrict__ pv, const float* __restrict__ q, float* __restrict__ x,
+                         float* __restrict__ r, double* __restrict__ rz_old) {
+  int b = blockIdx.y;
+  double rz = sum_partials(part_rz, b, Prz);
+  double pq = sum_partials(part_pq, b, P);
+  float alpha = (pq > 0 && rz > 0) ? (float)(rz / pq) : 0.f;
+  if (blockIdx.x == 0 && threadIdx.x == 0) rz_old[b] = rz;
+  size_t off = (size_t)b * N;
+  GRID_LOOP(p, N) {
+    x[off + p] += alpha * pv[off + p];
+    r[off + p] -= alpha * q[off + p];
+  }
+}
+
+// beta = <r,z>_new / <r,z>_old; p = z + beta p
+__global__ void k_pcg_p(int N, const double* __restrict__ part_rz, int P, const double* __restrict__ rz_old,
+                        const float* __restrict__ z, float* __restrict__ pv) {
+  int b = blockIdx.y;
+  double rz = sum_partials(part_rz, b, P);
+  double ro = rz_old[b];
+  float beta = (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f;
+  size_t off = (size_t)b * N;
+  GRID_LOOP(p, N) pv[off + p] = z[off + p] + beta * pv[off + p];
+}
+
+// ------------------------------------------------------- FP64 refinement glue
+// partial ||v||^2 (double input)
+__global__ void k_norm2_d(int N, const double* __restrict__ v, double* __restrict__ part) {
+  int b = blockIdx.y;
+  size_t off = (size_t)b * N;
+  double acc = 0;
+  GRID_LOOP(p, N) { double t = v[off + p]; acc += t * t; }
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) part[b * MPN_PMAX + blockIdx.x] = s;
+}
+
+// r32 = r64 / ||r64|| ; the norm is saved in scale[b]
+__global__ void k_to32(int N, const double* __restrict__ r64, const double* __restrict__ part, int P,
+                       float* __restrict__ r32, double* __restrict__ scale) {
+  int b = blockIdx.y;
+  double nn = sqrt(sum_partials(part, b, P));
+  if (blockIdx.x == 0 && threadIdx.x == 0) scale[b] = nn;
+  double inv = nn > 0 ? 1.0 / nn : 0.0;
+  size_t off = (size_t)b * N;
+  GRID_LOOP(p, N) r32[off + p] = (float)(r64[off + p] * inv);
+}
+
+// u += scale * x; partials ||scale x||^2 and ||u||^2
+__global__ void k_update64(int N, const float* __restrict__ x, const double* __restrict__ scale,
+                           double* __restrict__ u, double* __restrict__ part_du, double* __restrict__ part_u) {
+  int b = blockIdx.y;
+  double s = scale[b];
+  size_t off = (size_t)b * N;
+  double a1 = 0, a2 = 0;
+  GRID_LOOP(p, N) {
+    double du = s * (double)x[off + p];
+    double un = u[off + p] + du;
+    u[off + p] = un;
+    a1 += du * du; a2 += un * un;
+  }
+  double s1 = block_sum(a1);
+  double s2 = block_sum(a2);
+  if (threadIdx.x == 0) { part_du[b * MPN_PMAX + blockIdx.x] = s1; part_u[b * MPN_PMAX + blockIdx.x] = s2; }
+}
+
+// out[k][b] = sum of partial slot k of instance b (k < nslots)
+__global__ void k_collect(int B, int nslots, const double* __restrict__ part, int P, double* __restrict__ out) {
+  int b = blockIdx.x;
+  for (int k = 0; k < nslots; ++k) {
+    double v = sum_partials(part + (size_t)k * B * MPN_PMAX, b, P);
+    if (threadIdx.x == 0) out[k * B + b] = v;
+  }
+}
+
+__global__ void k_set_u(int N, const float* __restrict__ u0, double* __restrict__ u) {
+  size_t off = (size_t)blockIdx.y * N;
+  GRID_LOOP(p, N) u[off + p] = u0 ? (double)u0[off + p] : 0.0;
+}
+
+// ----------------------------------------------- derivative unknowns and grads
+// Given u (FP64), writes every unknown of z.  The derivative unknowns of point
+// i minimise the rows owned by i:  w = (W + beta beta^T)^{-1} h with
+// h_d = W_d a_d(u) + beta_d (bE - c_0 u) + S^{-1} g_zeta (scaled units
+// w = (s u', s^2 u'')).  Forward: bE = b, g = 0.  Adjoint: bE = 0, g = the
+// derivative part of g_z.
+__global__ void k_recover(Grid g, Coef cf, const double* __restrict__ u, const float* __restrict__ bE,
+                          const float* __restrict__ gz, float* __restrict__ zf, double* __restrict__ zd) {
+  int b = blockIdx.y;
+  size_t off = (size_t)b * g.N;
+  int V = 1 + 2 * g.D;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode(g, p, pos);
+    double uc = u[off + p];
+    double c0 = coefv(cf, 0, b, p, g.N);
+    double rhsE = (bE ? (double)bE[off + p] : 0.0) - c0 * uc;
+    double h[3][2], wi[3][2], be[3][2];
+    double bwh = 0, gam = 0;
+    for (int d = 0; d < g.D; ++d) {
+      double a1 = 0, a2 = 0;
+      for (int o = -2; o <= 2; ++o) {
+        float w1 = dweight(1, pos[d], g.n[d], g.per[d], o), w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
+        if (w1 == 0.f && w2 == 0.f) continue;
+        double xv = o == 0 ? uc : u[off + nbr(g, p, pos, d, o)];
+        a1 += w1 * xv; a2 += w2 * xv;
+      }
+      int cls = edge_class(g, d, pos[d]);
+      double w11, w12, w22; wmat(cls, w11, w12, w22);
+      double b1 = coefv(cf, 1 + 2 * d, b, p, g.N) * g.ds1[d];
+      double b2 = coefv(cf, 2 + 2 * d, b, p, g.N) * g.ds2[d];
+      be[d][0] = b1; be[d][1] = b2;
+      double h1 = w11 * a1 + w12 * a2 + b1 * rhsE;
+      double h2 = w12 * a1 + w22 * a2 + b2 * rhsE;
+      if (gz) {
+        h1 += (double)gz[((size_t)b * V + 1 + 2 * d) * g.N + p] * g.ds1[d];
+        h2 += (double)gz[((size_t)b * V + 2 + 2 * d) * g.N + p] * g.ds2[d];
+      }
+      h[d][0] = h1; h[d][1] = h2;
+      winv(cls, h1, h2, wi[d][0], wi[d][1]);        // W^{-1} h
+      double q1, q2; winv(cls, b1, b2, q1, q2);     // W^{-1} beta
+      bwh += b1 * wi[d][0] + b2 * wi[d][1];
+      gam += b1 * q1 + b2 * q2;
+    }
+    double fac = bwh / (1.0 + gam);
+    size_t zb = (size_t)b * V * g.N;
+    if (zf) zf[zb + p] = (float)uc;
+    if (zd) zd[zb + p] = uc;
+    for (int d = 0; d < g.D; ++d) {
+      int cls = edge_class(g, d, pos[d]);
+      double q1, q2; winv(cls, be[d][0], be[d][1], q1, q2);
+      double w1 = wi[d][0] - q1 * fac;
+      double w2 = wi[d][1] - q2 * fac;
+      double z1 = w1 * g.ds1[d], z2 = w2 * g.ds2[d];
+      if (zf) { zf[zb + (size_t)(1 + 2 * d) * g.N + p] = (float)z1; zf[zb + (size_t)(2 + 2 * d) * g.N + p] = (float)z2; }
+      if (zd) { zd[zb + (size_t)(1 + 2 * d) * g.N + p] = z1; zd[zb + (size_t)(2 + 2 * d) * g.N + p] = z2; }
+    }
+  }
+}
+
+// Adjoint right-hand side, part 1: per point psi = (W + beta beta^T)^{-1} S^{-1} g_zeta
+// and the coefficients of M_{u zeta} M_{zeta zeta}^{-1} g_zeta as a scatter through
+// the difference forms: kap[0] = c_0 beta.psi (center), kap[1+2d], kap[2+2d] = -(W_d psi_d).
+__global__ void k_adj_kappa(Grid g, Coef cf, const float* __restrict__ gz, double* __restrict__ kap) {
+  int b = blockIdx.y;
+  int V = 1 + 2 * g.D;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode(g, p, pos);
+    double hw[3][2], be[3][2], bwh = 0, gam = 0;
+    for (int d = 0; d < g.D; ++d) {
+      int cls = edge_class(g, d, pos[d]);
+      double b1 = coefv(cf, 1 + 2 * d, b, p, g.N) * g.ds1[d];
+      double b2 = coefv(cf, 2 + 2 * d, b, p, g.N) * g.ds2[d];
+      be[d][0] = b1; be[d][1] = b2;
+      double h1 = (double)gz[((size_t)b * V + 1 + 2 * d) * g.N + p] * g.ds1[d];
+      double h2 = (double)gz[((size_t)b * V + 2 + 2 * d) * g.N + p] * g.ds2[d];
+      winv(cls, h1, h2, hw[d][0], hw[d][1]);
+      double q1, q2; winv(cls, b1, b2, q1, q2);
+      bwh += b1 * hw[d][0] + b2 * hw[d][1];
+      gam += b1 * q1 + b2 * q2;
+    }
+    double fac = bwh / (1.0 + gam);
+    double bpsi = 0;
+    for (int d = 0; d < g.D; ++d) {
+      int cls = edge_class(g, d, pos[d]);
+      double q1, q2; winv(cls, be[d][0], be[d][1], q1, q2);
+      double ps1 = hw[d][0] - q1 * fac, ps2 = hw[d][1] - q2 * fac;
+      bpsi += be[d][0] * ps1 + be[d][1] * ps2;
+      double w11, w12, w22; wmat(cls, w11, w12, w22);
+      kap[((size_t)(1 + 2 * d) * gridDim.y + b) * g.N + p] = -(w11 * ps1 + w12 * ps2);
+      kap[((size_t)(2 + 2 * d) * gridDim.y + b) * g.N + p] = -(w12 * ps1 + w22 * ps2);
+    }
+    kap[(size_t)b * g.N + p] = coefv(cf, 0, b, p, g.N) * bpsi;
+  }
+}
+
+// Adjoint right-hand side, part 2: rhs_u = g_u - scatter(kap)  (FP64).
+__global__ void k_adj_rhs(Grid g, const float* __restrict__ gz, const double* __restrict__ kap,
+                          double* __restrict__ out) {
+  int b = blockIdx.y;
+  int V = 1 + 2 * g.D, B = gridDim.y;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode(g, p, pos);
+    double acc = kap[(size_t)b * g.N + p];
+    for (int d = 0; d < g.D; ++d)
+      for (int o = -2; o <= 2; ++o) {
+        int ip = pos[d] - o;
+        if (g.per[d]) { ip %= g.n[d]; if (ip < 0) ip += g.n[d]; }
+        else if (ip < 0 || ip >= g.n[d]) continue;
+        float w1 = dweight(1, ip, g.n[d], g.per[d], o), w2 = dweight(2, ip, g.n[d], g.per[d], o);
+        if (w1 == 0.f && w2 == 0.f) continue;
+        int q = p + (ip - pos[d]) * g.stride[d];
+        acc += w1 * kap[((size_t)(1 + 2 * d) * B + b) * g.N + q] + w2 * kap[((size_t)(2 + 2 * d) * B + b) * g.N + q];
+      }
+    out[(size_t)b * g.N + p] = (double)gz[(size_t)b * V * g.N + p] - acc;
+  }
+}
+
+// Gradients (formulas after Eq. 11) from z* and d_z:
+//   lambda_E = b - sum_v c_v z_v,  dlambda_E = -sum_v c_v dz_v,
+//   dl/dc_v = dlambda_E z_v + lambda_E dz_v,  dl/db = -dlambda_E,
+//   dl/domega = dz_u on boundary points.
+// Field gradients sum over the unknowns sharing a field; scalar gradients are
+// reduced per instance (partials in part[v]).
+__global__ void k_gradients(Grid g, Coef cf, const float* __restrict__ rhs, const float* __restrict__ zf,
+                            const double* __restrict__ zd, const double* __restrict__ dz, float* __restrict__ dfields,
+                            float* __restrict__ drhs, float* __restrict__ domega, double* __restrict__ part) {
+  int b = blockIdx.y;
+  int V = 1 + 2 * g.D;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  size_t zb = (size_t)b * V * g.N;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode(g, p, pos);
+    double zv[7], dv[7], cv[7];
+    double lam = rhs[(size_t)b * g.N + p], dlam = 0;
+    for (int v = 0; v < V; ++v) {
+      zv[v] = zf ? (double)zf[zb + (size_t)v * g.N + p] : zd[zb + (size_t)v * g.N + p];
+      dv[v] = dz[zb + (size_t)v * g.N + p];
+      cv[v] = coefv(cf, v, b, p, g.N);
+      lam -= cv[v] * zv[v];
+      dlam -= cv[v] * dv[v];
+    }
+    for (int f = 0; f < cf.F; ++f) {
+      double s = 0;
+      for (int v = 0; v < V; ++v) if (cf.field_of[v] == f) s += dlam * zv[v] + lam * dv[v];
+      dfields[((size_t)f * cf.B + b) * g.N + p] = (float)s;
+    }
+    for (int v = 0; v < V; ++v) if (cf.field_of[v] < 0) acc[v] += dlam * zv[v] + lam * dv[v];
+    drhs[(size_t)b * g.N + p] = (float)(-dlam);
+    domega[(size_t)b * g.N + p] = is_boundary(g, pos) ? (float)dv[0] : 0.f;
+  }
+  for (int v = 0; v < V; ++v) {
+    double s = block_sum(acc[v]);
+    if (threadIdx.x == 0) part[((size_t)v * cf.B + b) * MPN_PMAX + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_scalar_grads(int V, int B, const int* __restrict__ field_of_dev, const double* __restrict__ part,
+                               int P, float* __restrict__ dscalars) {
+  int b = blockIdx.x;
+  for (int v = 0; v < V; ++v) {
+    double s = sum_partials(part + (size_t)v * B * MPN_PMAX, b, P);
+    if (threadIdx.x == 0) dscalars[v * B + b] = field_of_dev[v] < 0 ? (float)s : 0.f;
+  }
+}
+
+// g_z = d/dz of mean_{b,i} (u - target)^2
+__global__ void k_mse_grad(int N, int V, int B, const float* __restrict__ z, const float* __restrict__ tgt,
+                           float* __restrict__ gz) {
+  int b = blockIdx.y;
+  float sc = 2.f / ((float)N * (float)B);
+  size_t zb = (size_t)b * V * N;
+  GRID_LOOP(p, N) {
+    gz[zb + p] = sc * (z[zb + p] - tgt[(size_t)b * N + p]);
+    for (int v = 1; v < V; ++v) gz[zb + (size_t)v * N + p] = 0.f;
+  }
+}

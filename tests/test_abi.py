@@ -1,0 +1,45 @@
+"""The C-ABI library builds, loads and exports every symbol include/mpn.h
+declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "mpn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpn_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_declared_symbols():
+    from paper_2502_18377_b300.csrc import build
+    lib_path = build.build()
+    lib = ctypes.CDLL(lib_path)
+    names = _declared()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_declares_every_export():
+    from paper_2502_18377_b300 import binding
+    assert sorted(binding.EXPORTS) == _declared()
+    binding.load()
+
+
+def test_error_strings_without_gpu():
+    from paper_2502_18377_b300 import binding
+    lib = binding.load()
+    assert lib.mpn_strerror(0) == b"ok"
+    assert b"unsupported" in lib.mpn_strerror(2)
+    d = binding.MpnDesc()
+    assert lib.mpn_default_desc(ctypes.byref(d)) == 0
+    assert d.stencil == 3 and d.inner_iters >= 1
+    h = ctypes.c_void_p()
+    d.stencil = 5
+    assert lib.mpn_create(ctypes.byref(d), ctypes.byref(h)) == 2      # five-point rows: unsupported
+    d.stencil = 3
+    d.periodic[0] = 1
+    assert lib.mpn_create(ctypes.byref(d), ctypes.byref(h)) == 1      # periodic time: invalid

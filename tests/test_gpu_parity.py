@@ -1,0 +1,180 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Both sides receive the same float32-rounded seeded inputs.  Tolerances:
+  * forward z and adjoint d_z: relative L2 error <= 1e-6 per instance, on the
+    whole z and on the u block (the solver's accuracy target);
+  * gradients: relative L2 <= 1e-5 (they are formed from the FP32 z);
+  * reduced operator apply (FP32): relative L2 <= 2e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import assemble as asm
+from oracle import grad as og
+from oracle import solve as osv
+from paper_2502_18377_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FWD_TOL = 1e-6
+GRAD_TOL = 1e-5
+
+
+def _round(w):
+    """float32-rounded copy of a workload (what the GPU path receives)."""
+    r = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    return wl.Workload(w.name, w.geom, list(w.field_of), r(w.scalars), r(w.fields), r(w.rhs),
+                       r(w.omega), None if w.target is None else r(w.target))
+
+
+def _dev(a):
+    return torch.tensor(np.asarray(a, dtype=np.float32), device="cuda").contiguous()
+
+
+def _solver(w, **kw):
+    from paper_2502_18377_b300.binding import Solver
+    return Solver(w.geom, w.batch, w.field_of, w.fields.shape[0], **kw)
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def _oracle_instance(w, b):
+    c = w.full_coeff()[:, b]
+    A, d, kind, owner = asm.assemble(w.geom, c, w.rhs[b], w.omega[b])
+    z, lam, el = osv.solve_lsq_elim(A, d, asm.n_vars(w.ndim))
+    return A, d, kind, owner, z, lam, el
+
+
+CASES = [
+    ("c1_full", lambda: wl.advection_diffusion_1d()),
+    ("c2_small", lambda: wl.reaction_diffusion_2d(batch=3, n=(8, 16, 16))),
+    ("c2_ragged", lambda: wl.reaction_diffusion_2d(batch=2, n=(10, 12, 20))),
+    ("c3_small", lambda: wl.linearized_burgers_1d(batch=2, n=(32, 64))),
+    ("c5_small", lambda: wl.transport_2d(batch=2, n=(8, 16, 16))),
+    ("rand_dirichlet_2d", lambda: wl.random_problem(21, (12, 32), (False, False), batch=2)),
+    ("rand_odd_2d_final", lambda: wl.random_problem(22, (9, 13), (False, False), batch=2,
+                                                    final_time_rows=True)),
+    ("rand_mixed_3d", lambda: wl.random_problem(23, (7, 16, 12), (False, True, False), batch=2)),
+    ("rand_scalars_3d", lambda: wl.random_problem(24, (6, 8, 8), (False, True, True), batch=3,
+                                                  field_all=False)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_forward_matches_oracle(name, make):
+    w = _round(make())
+    s = _solver(w)
+    z = s.forward(_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega)).cpu().numpy()
+    V, N = asm.n_vars(w.ndim), w.npoints
+    for b in range(w.batch):
+        zr = _oracle_instance(w, b)[4]
+        assert _rel(z[b].ravel(), zr) <= FWD_TOL, (name, b, _rel(z[b].ravel(), zr), s.last_stats)
+        assert _rel(z[b, 0], zr[:N]) <= FWD_TOL
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_adjoint_and_gradients_match_oracle(name, make):
+    w = _round(make())
+    s = _solver(w)
+    F = w.fields.shape[0]
+    args = (_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega))
+    z = s.forward(*args)
+    rng = np.random.default_rng(5)
+    V, N = asm.n_vars(w.ndim), w.npoints
+    g = rng.normal(size=(w.batch, V, N)).astype(np.float32)
+    dfields, dscal, drhs, dom, dz = s.adjoint(*args, z, _dev(g), reuse_setup=True, want_dz=True)
+    dfields, dscal, drhs, dom, dz = (t.cpu().numpy() for t in (dfields, dscal, drhs, dom, dz))
+    zc = z.cpu().numpy()
+    for b in range(w.batch):
+        A, d, kind, owner, zr, lam, el = _oracle_instance(w, b)
+        dzr, dlamr = og.adjoint_elim(el, g[b].astype(np.float64).ravel())
+        assert _rel(dz[b].ravel(), dzr) <= FWD_TOL, (name, b, _rel(dz[b].ravel(), dzr))
+        dc, db, dw = og.gradients(w.geom, A, d, kind, owner, zr, lam, dzr, dlamr)
+        for f in range(F):
+            ref = sum(dc[v] for v in range(V) if w.field_of[v] == f)
+            assert _rel(dfields[f, b], ref) <= GRAD_TOL, (name, "field", f, _rel(dfields[f, b], ref))
+        for v in range(V):
+            if w.field_of[v] < 0:
+                assert abs(dscal[v, b] - dc[v].sum()) <= GRAD_TOL * max(1.0, np.abs(dc[v]).sum())
+        assert _rel(drhs[b], db) <= GRAD_TOL
+        assert _rel(dom[b], dw) <= GRAD_TOL
+
+
+def test_reduced_operator_matches_oracle_schur():
+    """S u (FP32 kernels) against the oracle's Schur complement of A^T A."""
+    for w in (wl.random_problem(31, (9, 20), (False, True), batch=2),
+              wl.random_problem(32, (6, 10, 12), (False, False, True), batch=2, final_time_rows=True),
+              _round(wl.reaction_diffusion_2d(batch=2, n=(8, 16, 16)))):
+        w = _round(w)
+        s = _solver(w)
+        rng = np.random.default_rng(0)
+        u = rng.normal(size=(w.batch, w.npoints)).astype(np.float32)
+        q = s.apply_reduced(_dev(w.fields), _dev(w.scalars), _dev(u)).cpu().numpy()
+        for b in range(w.batch):
+            A, d, kind, owner, zr, lam, el = _oracle_instance(w, b)
+            ref = el.S @ u[b].astype(np.float64)
+            assert _rel(q[b], ref) <= 2e-5, _rel(q[b], ref)
+
+
+def test_forward_is_deterministic():
+    w = _round(wl.reaction_diffusion_2d(batch=2, n=(8, 16, 16)))
+    s = _solver(w)
+    args = (_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega))
+    z1 = s.forward(*args).cpu().numpy()
+    z2 = s.forward(*args).cpu().numpy()
+    assert np.array_equal(z1, z2)
+
+
+def test_gradients_match_finite_differences_burgers():
+    """Linearized Burgers, L = mean((u - target)^2): dL/dc, dL/df and dL/du0
+    from the adjoint kernels against central differences of the FP64 oracle
+    at 20 random coordinates (relative 1e-3)."""
+    w = _round(wl.linearized_burgers_1d(batch=1, n=(16, 32)))
+    N = w.npoints
+    s = _solver(w)
+    args = [_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega)]
+    z = s.forward(*args)
+    tgt = _dev(w.target)
+    gz = s.mse_grad(z, tgt)
+    dfields, dscal, drhs, dom = s.adjoint(*args, z, gz, reuse_setup=True)
+    dfields, drhs, dom = dfields.cpu().numpy()[0, 0], drhs.cpu().numpy()[0], dom.cpu().numpy()[0]
+
+    def loss(fields, rhs, omega):
+        ww = wl.Workload(w.name, w.geom, w.field_of, w.scalars, fields, rhs, omega)
+        A, d, *_ = asm.assemble(w.geom, ww.full_coeff()[:, 0], rhs[0], omega[0])
+        zz, _, _ = osv.solve_lsq_elim(A, d, 5)
+        return float(((zz[:N] - w.target[0]) ** 2).mean())
+
+    rng = np.random.default_rng(3)
+    h = 1e-4
+    checked = 0
+    for k in range(20):
+        kind = k % 3
+        if kind == 0:
+            p = rng.integers(0, N)
+            fp, fm = w.fields.copy(), w.fields.copy()
+            fp[0, 0, p] += h; fm[0, 0, p] -= h
+            fd = (loss(fp, w.rhs, w.omega) - loss(fm, w.rhs, w.omega)) / (2 * h)
+            an = dfields[p]
+        elif kind == 1:
+            p = rng.integers(0, N)
+            rp, rm = w.rhs.copy(), w.rhs.copy()
+            rp[0, p] += h; rm[0, p] -= h
+            fd = (loss(w.fields, rp, w.omega) - loss(w.fields, rm, w.omega)) / (2 * h)
+            an = drhs[p]
+        else:
+            p = rng.integers(0, w.geom["n"][1])   # a point of the t = 0 face
+            op, om = w.omega.copy(), w.omega.copy()
+            op[0, p] += h; om[0, p] -= h
+            fd = (loss(w.fields, w.rhs, op) - loss(w.fields, w.rhs, om)) / (2 * h)
+            an = dom[p]
+        scale = max(abs(fd), 1e-3 * max(np.abs(dfields).max(), np.abs(drhs).max(), np.abs(dom).max()))
+        assert abs(an - fd) <= 1e-3 * scale, (k, kind, an, fd)
+        checked += 1
+    assert checked == 20
