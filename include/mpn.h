@@ -83,7 +83,8 @@ typedef struct mpn_desc {
 typedef struct mpn_stats {
   int sweeps;             /* FP64 refinement sweeps done */
   int pcg_iters;          /* FP32 PCG iterations done (all sweeps) */
-  double rel_residual;    /* max over instances: ||r|| / ||r_0|| of the reduced normal equations, FP64 */
+  double rel_residual;    /* max over instances: ||r|| / ||rhs|| of the reduced normal equations (FP64),
+                             taken at the start of the last sweep, before its correction */
   double rel_update;      /* max over instances: last ||delta u|| / ||u|| */
   double pred_error;      /* max over instances: predicted relative error of u */
 } mpn_stats;
@@ -115,10 +116,13 @@ int mpn_forward(mpn_problem* p, const float* fields, const float* scalars,
 /* Backward pass (Eq. 11 and the gradients after it): given g_z = dl/dz*
  * [B][V][N], solves A^T A d_z = g_z and writes dl/dfields [F][B][N],
  * dl/dscalars [V][B] (entries of field-backed v are written as 0),
- * dl/drhs [B][N] and dl/domega [B][N] (zero off the boundary set).  z is the
- * forward solution; if null it is recomputed.  dz (nullable) receives d_z.
- * flags bit 0 (MPN_REUSE_SETUP): the coefficients are the ones of the last
- * mpn_forward on this problem, so its multigrid setup is reused. */
+ * dl/drhs [B][N] and dl/domega [B][N] (zero off the boundary set).
+ * dz (nullable) receives d_z.  The duals lambda* and d_lambda are formed in
+ * FP64 from the FP64 forward solution the problem keeps.
+ * flags bit 0 (MPN_REUSE_SETUP): the data are those of the last mpn_forward
+ * on this problem, so its multigrid setup and FP64 solution are reused;
+ * without it (or if no forward was done) the forward solve is recomputed
+ * first.  z (the caller's FP32 forward output) may be null; it is not read. */
 #define MPN_REUSE_SETUP 1
 int mpn_adjoint(mpn_problem* p, const float* fields, const float* scalars,
                 const float* rhs, const float* omega, const float* z,

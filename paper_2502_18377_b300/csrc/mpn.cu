@@ -22,6 +22,7 @@
 
 #include "../../include/mpn.h"
 #include "mpn_kernels.cuh"
+#include "mpn_tile.cuh"
 
 #define MAXL 16
 
@@ -45,6 +46,10 @@ struct Level {
   float* fields = nullptr;  // [F][B][N]
   float *rho = nullptr, *dinv = nullptr;
   float *r = nullptr, *e = nullptr, *d = nullptr, *y = nullptr, *t = nullptr;
+  float *eb[2] = {nullptr, nullptr}, *db[2] = {nullptr, nullptr};  // ping-pong iterates
+  int ce = 0, cd = 0;  // current buffers
+  int T[3], ntile[3], tiles;  // shared-memory tile shape of k_tile
+  size_t smem, smem64;
 };
 
 struct mpn_problem {
@@ -59,13 +64,16 @@ struct mpn_problem {
   int* field_of_dev = nullptr;
   float *x = nullptr, *pv = nullptr, *q = nullptr, *z = nullptr;
   double *u64 = nullptr, *r64 = nullptr, *y64 = nullptr, *g64 = nullptr;
-  double *zd = nullptr, *dzd = nullptr, *kap = nullptr;
+  double* rho64 = nullptr;  // finest-level point weights in FP64 (refinement residual)
+  double *kap = nullptr;
+  double *uf64 = nullptr;  // FP64 u of the last forward (the adjoint's lambda*)
   double *part = nullptr;  // partial-sum slots [NSLOT][B][PMAX]
   double *dscal = nullptr; // device scalars: scale[B], rz_old[B], out[8][B]
   float* lam = nullptr;    // lambda_max per level and instance [L][B]
   double* hbuf = nullptr;  // pinned host buffer
   size_t bytes = 0;
   bool setup_ok = false;
+  bool zd_valid = false;   // uf64 holds the FP64 u of the last forward
   float cheb_c1[32], cheb_c2[32], cheb_inv_th;
   std::vector<void*> allocs;
   // live timing of the finest-level smoothing step (events on the solve stream)
@@ -79,7 +87,7 @@ enum { S_RZ = 0, S_PQ, S_RN, S_DU, S_UN, S_PW, S_GN, S_GR0, NSLOT = S_GR0 + 8 };
 
 static inline double* slot(mpn_problem* p, int k) { return p->part + (size_t)k * p->B * MPN_PMAX; }
 
-static int nblk(int N) { int b = (N + MPN_TPB - 1) / MPN_TPB; return b < 1 ? 1 : (b > MPN_PMAX ? MPN_PMAX : b); }
+static int nblk(int N) { int b = (N + MPN_TPB - 1) / MPN_TPB; return b < 1 ? 1 : (b > 64 ? 64 : b); }
 
 static int dalloc(mpn_problem* p, void** ptr, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -218,7 +226,14 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
     }
     p->L++;
     if (nd == 0 || p->L == MAXL) { for (int k = 0; k < 3; ++k) l.cz[k] = 0; break; }
-    for (int k = 0; k < 3; ++k) if (l.cz[k]) { n[k] /= 2; s[k] *= 2; }
+    // periodic dims: nested halving (step doubled); non-periodic dims: the
+    // coarse points span the same interval (both Dirichlet faces kept)
+    for (int k = 0; k < 3; ++k)
+      if (l.cz[k]) {
+        int nc = n[k] / 2;
+        s[k] = per[k] ? 2.0 * s[k] : s[k] * (double)(n[k] - 1) / (double)(nc - 1);
+        n[k] = nc;
+      }
     theta *= (float)(1 << nd);
   }
   Level& lc = p->lv[p->L - 1];
@@ -239,6 +254,26 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
     AL(l.fields, (size_t)std::max(F, 1) * N);
     AL(l.rho, N); AL(l.dinv, N);
     AL(l.r, N); AL(l.e, N); AL(l.d, N); AL(l.y, N); AL(l.t, N);
+    AL(l.eb[1], N); AL(l.db[1], N);
+    l.eb[0] = l.e; l.db[0] = l.d;
+    // tile of about 1024 points, fastest dimension first
+    int n0 = l.g.n[0], n1 = l.g.n[1], n2 = l.g.n[2];
+    if (p->D == 3) {
+      l.T[2] = std::min(n2, 32);
+      l.T[1] = std::min(n1, std::max(1, 256 / l.T[2]));
+      l.T[0] = std::min(n0, std::max(1, 1024 / (l.T[1] * l.T[2])));
+    } else {
+      l.T[2] = 1;
+      l.T[1] = std::min(n1, 256);
+      l.T[0] = std::min(n0, std::max(1, 1024 / l.T[1]));
+    }
+    for (int k2 = 0; k2 < 3; ++k2) l.ntile[k2] = (l.g.n[k2] + l.T[k2] - 1) / l.T[k2];
+    l.tiles = l.ntile[0] * l.ntile[1] * l.ntile[2];
+    int h2 = p->D == 3 ? 4 : 0;
+    size_t nbox = (size_t)(l.T[0] + 4) * (l.T[1] + 4) * (l.T[2] + h2);
+    l.smem = nbox * (3 * sizeof(float) + sizeof(float) * F);
+    l.smem64 = nbox * (3 * sizeof(double) + sizeof(float) * F);
+    if (l.tiles > MPN_PMAX || l.smem64 > 200 * 1024) { mpn_destroy(p); return MPN_ERR_UNSUPPORTED; }
   }
   size_t N0 = (size_t)p->lv[0].g.N * B;
   AL(p->Kband, (size_t)B * p->M * (p->bw + 1));
@@ -248,8 +283,8 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   AL(p->rhs, N0); AL(p->omega, N0);
   AL(p->field_of_dev, 8);
   AL(p->x, N0); AL(p->pv, N0); AL(p->q, N0); AL(p->z, N0);
-  AL(p->u64, N0); AL(p->r64, N0); AL(p->y64, N0); AL(p->g64, N0);
-  AL(p->zd, N0 * V); AL(p->dzd, N0 * V); AL(p->kap, N0 * V);
+  AL(p->u64, N0); AL(p->r64, N0); AL(p->y64, N0); AL(p->g64, N0); AL(p->rho64, N0);
+  AL(p->uf64, N0); AL(p->kap, N0 * V);
   AL(p->part, (size_t)NSLOT * B * MPN_PMAX);
   AL(p->dscal, (size_t)16 * B);
   AL(p->lam, (size_t)MAXL * B);
@@ -258,6 +293,20 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   for (int v = 0; v < 8; ++v) fo[v] = v < V ? d.field_of[v] : -1;
   if (cudaMemcpy(p->field_of_dev, fo, sizeof(fo), cudaMemcpyHostToDevice) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
   if (cudaMallocHost((void**)&p->hbuf, sizeof(double) * 16 * B) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
+  {
+    size_t mx = 0, mx64 = 0;
+    for (int k = 0; k < p->L; ++k) { mx = std::max(mx, p->lv[k].smem); mx64 = std::max(mx64, p->lv[k].smem64); }
+    int attr = (int)std::max(mx, (size_t)48 * 1024), attr64 = (int)std::max(mx64, (size_t)48 * 1024);
+    cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)std::max(sizeof(float) * (p->bw + 1) * 128, (size_t)48 * 1024));
+    if (p->D == 3) {
+      cudaFuncSetAttribute(k_tile<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, attr);
+      cudaFuncSetAttribute(k_tile<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, attr64);
+    } else {
+      cudaFuncSetAttribute(k_tile<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, attr);
+      cudaFuncSetAttribute(k_tile<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, attr64);
+    }
+  }
 
   // Chebyshev coefficients on [lo, 1] for Dinv scaled by 1 / lambda_max
   const double lo = 0.1, th = (1.0 + lo) / 2, de = (1.0 - lo) / 2, sg = th / de;
@@ -294,14 +343,31 @@ static void prof_flush(mpn_problem* p) {
   }
   p->prof_used = 0;
 }
-// q = S x at level k (FP32), optional <x, q> partials into `part`.
-static int apply_S(mpn_problem* p, int k, const float* x, float* q, double* part, cudaStream_t st) {
+template <class T>
+static void launch_tile(mpn_problem* p, int k, TileArgs<T> a, int mode, cudaStream_t st) {
   Level& l = p->lv[k];
   Coef cf = make_coef(p, l.fields);
-  dim3 gr(nblk(l.g.N), p->B);
-  k_Lpass<float><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, x, nullptr, nullptr, l.y);
-  k_LTpass<float><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.y, nullptr, nullptr, nullptr, x, -1.f, q,
-                                          part ? x : nullptr, part);
+  if (!a.dinv) a.dinv = l.dinv;
+  for (int d = 0; d < 3; ++d) { a.tile[d] = l.T[d]; a.ntile[d] = l.ntile[d]; }
+  dim3 gr(l.tiles, p->B);
+  size_t sm = sizeof(T) == 8 ? l.smem64 : l.smem;
+  if (p->D == 3) k_tile<3, T><<<gr, MPN_TPB, sm, st>>>(l.g, cf, a, mode);
+  else k_tile<2, T><<<gr, MPN_TPB, sm, st>>>(l.g, cf, a, mode);
+}
+
+static TileArgs<float> targs(mpn_problem* p, int k) {
+  TileArgs<float> a;
+  memset(&a, 0, sizeof(a));
+  a.rho = p->lv[k].rho;
+  a.dinv = p->lv[k].dinv;
+  return a;
+}
+
+// q = S x at level k (FP32), optional <x, q> partials into `part` (one per tile).
+static int apply_S(mpn_problem* p, int k, const float* x, float* q, double* part, cudaStream_t st) {
+  TileArgs<float> a = targs(p, k);
+  a.ein = x; a.out = q; a.part = part;
+  launch_tile(p, k, a, TM_APPLY, st);
   CKL();
   return MPN_OK;
 }
@@ -309,12 +375,13 @@ static int apply_S(mpn_problem* p, int k, const float* x, float* q, double* part
 static int setup(mpn_problem* p, const float* fields, const float* scalars, cudaStream_t st) {
   int B = p->B, F = p->F, V = p->V;
   p->setup_ok = false;
+  p->zd_valid = false;
   Level& l0 = p->lv[0];
   if (F > 0) CK(cudaMemcpyAsync(l0.fields, fields, sizeof(float) * (size_t)F * B * l0.g.N, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(p->scalars, scalars, sizeof(float) * (size_t)V * B, cudaMemcpyDeviceToDevice, st));
   {
     Coef cf = make_coef(p, l0.fields);
-    k_rho_fine<<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho);
+    k_rho_fine<<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, p->rho64);
     CKL();
   }
   for (int k = 1; k < p->L; ++k) {
@@ -354,50 +421,62 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
   size_t smem = sizeof(float) * (size_t)p->M * (p->bw + 1);
   CK(cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_coarse_factor<<<B, 512, smem, st>>>(p->M, p->bw, p->Kband, p->ferr);
-  k_coarse_inverse<<<dim3((p->M + 127) / 128, B), 128, 0, st>>>(p->M, p->bw, p->Kband, p->Kinv);
+  k_coarse_inverse<<<dim3((p->M + 127) / 128, B), 128, sizeof(float) * (p->bw + 1) * 128, st>>>(p->M, p->bw, p->Kband,
+                                                                                                p->Kinv);
   CKL();
   p->setup_ok = true;
   return MPN_OK;
 }
 
-// One V-cycle at level k: e_k ~ S_k^{-1} r_k.  On return e_k + d_k (d_k
-// pending, unless k is the coarsest level, where d is not used) is the result.
+// One V-cycle at level k: e ~ S_k^{-1} r_k.  On return the result is
+// eb[ce] + db[cd] (the last Chebyshev direction pending), except at the
+// coarsest level, where it is eb[ce] alone.
 static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   Level& l = p->lv[k];
   int B = p->B;
   dim3 gr(nblk(l.g.N), B);
   if (k == p->L - 1) {
-    k_coarse_solve<<<dim3((p->M * 32 + MPN_TPB - 1) / MPN_TPB, B), MPN_TPB, 0, st>>>(p->M, p->Kinv, l.r, l.e);
+    l.ce = 0;
+    k_coarse_solve<<<dim3((p->M * 32 + MPN_TPB - 1) / MPN_TPB, B), MPN_TPB, 0, st>>>(p->M, p->Kinv, l.r, l.eb[0]);
     CKL();
     return MPN_OK;
   }
-  Coef cf = make_coef(p, l.fields);
   int m = p->desc.cheb_degree;
+  bool prof = (k == 0);
+  TileArgs<float> a = targs(p, k);
+  a.r = l.r;
   // pre-smoothing from e = 0
-  k_cheb_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, l.e, l.d);
+  l.ce = 0; l.cd = 0;
+  k_cheb_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, l.eb[0], l.db[0]);
   for (int s = 1; s < m; ++s) {
-    if (k == 0) prof_mark(p, st);
-    k_Lpass<float><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.e, l.d, nullptr, l.y);
-    k_cheb_B<<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.y, l.e, l.d, l.r, l.dinv, 1, p->cheb_c1[s], p->cheb_c2[s]);
-    if (k == 0) prof_mark(p, st);
+    a.ein = l.eb[l.ce]; a.din = l.db[l.cd]; a.eout = l.eb[1 - l.ce]; a.dout = l.db[1 - l.cd];
+    a.c1 = p->cheb_c1[s]; a.c2 = p->cheb_c2[s];
+    if (prof) prof_mark(p, st);
+    launch_tile(p, k, a, TM_CHEB, st);
+    if (prof) prof_mark(p, st);
+    l.ce = 1 - l.ce; l.cd = 1 - l.cd;
   }
-  // residual of e + d, restricted
-  k_Lpass<float><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.e, l.d, nullptr, l.y);
-  k_res_B<<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.y, l.e, l.d, l.r, l.t);
+  // residual of e + d (e absorbs d), restricted to the coarse level
+  a.ein = l.eb[l.ce]; a.din = l.db[l.cd]; a.eout = l.eb[1 - l.ce]; a.out = l.t;
+  launch_tile(p, k, a, TM_RES, st);
+  l.ce = 1 - l.ce;
   Level& lc = p->lv[k + 1];
   k_restrict_vec<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], l.t, lc.r);
   CKL();
   TRY(vcycle(p, k + 1, st));
-  k_prolong_add<<<gr, MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], lc.e,
-                                        (k + 1 == p->L - 1) ? nullptr : lc.d, l.e);
+  k_prolong_add<<<gr, MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], lc.eb[lc.ce],
+                                        (k + 1 == p->L - 1) ? nullptr : lc.db[lc.cd], l.eb[l.ce]);
   // post-smoothing
-  k_Lpass<float><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.e, nullptr, nullptr, l.y);
-  k_cheb_B<<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.y, l.e, l.d, l.r, l.dinv, 0, 0.f, p->cheb_inv_th);
+  a.ein = l.eb[l.ce]; a.din = nullptr; a.dout = l.db[1 - l.cd]; a.c2 = p->cheb_inv_th;
+  launch_tile(p, k, a, TM_POST0, st);
+  l.cd = 1 - l.cd;
   for (int s = 1; s < m; ++s) {
-    if (k == 0) prof_mark(p, st);
-    k_Lpass<float><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.e, l.d, nullptr, l.y);
-    k_cheb_B<<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.y, l.e, l.d, l.r, l.dinv, 1, p->cheb_c1[s], p->cheb_c2[s]);
-    if (k == 0) prof_mark(p, st);
+    a.ein = l.eb[l.ce]; a.din = l.db[l.cd]; a.eout = l.eb[1 - l.ce]; a.dout = l.db[1 - l.cd];
+    a.c1 = p->cheb_c1[s]; a.c2 = p->cheb_c2[s];
+    if (prof) prof_mark(p, st);
+    launch_tile(p, k, a, TM_CHEB, st);
+    if (prof) prof_mark(p, st);
+    l.ce = 1 - l.ce; l.cd = 1 - l.cd;
   }
   CKL();
   return MPN_OK;
@@ -408,7 +487,7 @@ static int precond(mpn_problem* p, cudaStream_t st) {
   Level& l = p->lv[0];
   TRY(vcycle(p, 0, st));
   dim3 gr(nblk(l.g.N), p->B);
-  k_final_z<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.e, p->L > 1 ? l.d : nullptr, l.r, p->z, slot(p, S_RZ));
+  k_final_z<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.eb[l.ce], p->L > 1 ? l.db[l.cd] : nullptr, l.r, p->z, slot(p, S_RZ));
   CKL();
   return MPN_OK;
 }
@@ -423,7 +502,7 @@ static int pcg(mpn_problem* p, int iters, cudaStream_t st) {
   k_pcg_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, p->z, p->x, p->pv);
   for (int it = 0; it < iters; ++it) {
     TRY(apply_S(p, 0, p->pv, p->q, slot(p, S_PQ), st));
-    k_pcg_xr<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), slot(p, S_PQ), P, P, p->pv, p->q, p->x, l.r, rz_old);
+    k_pcg_xr<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), slot(p, S_PQ), l.tiles, P, p->pv, p->q, p->x, l.r, rz_old);
     CKL();
     if (it == iters - 1) break;
     TRY(precond(p, st));
@@ -433,26 +512,34 @@ static int pcg(mpn_problem* p, int iters, cudaStream_t st) {
   return MPN_OK;
 }
 
-// FP64 residual r64 = rhs_vec - S u64 where rhs_vec is either the forward
-// right-hand side L^T rho b + theta 1_B omega (g_adj null) or g_adj.
-static int residual64(mpn_problem* p, const double* u, const double* g_adj, double* out, cudaStream_t st) {
+// FP64 residual out = rhs_vec - S u (u nullable => 0) where rhs_vec is either
+// the forward right-hand side L^T rho b + theta 1_B omega (g_adj null) or
+// g_adj; partials of ||out||^2 into `part` (one per tile).
+static int residual64(mpn_problem* p, const double* u, const double* g_adj, double* out, double* part,
+                      cudaStream_t st) {
   Level& l = p->lv[0];
   Coef cf = make_coef(p, l.fields);
-  dim3 gr(nblk(l.g.N), p->B);
-  k_Lpass<double><<<gr, MPN_TPB, 0, st>>>(l.g, cf, nullptr, u, nullptr, g_adj ? nullptr : p->rhs, p->y64);
-  k_LTpass<double><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, nullptr, g_adj, g_adj ? nullptr : p->omega, u, 1.0,
-                                           out, nullptr, nullptr);
+  dim3 gr(l.tiles, p->B);   // partial count per instance = tiles (as every refinement reduction)
+  const float* src = g_adj ? nullptr : p->rhs;
+  const float* om = g_adj ? nullptr : p->omega;
+  if (p->D == 3) {
+    k_res64_y<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    k_res64_q<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
+  } else {
+    k_res64_y<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    k_res64_q<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
+  }
   CKL();
   return MPN_OK;
 }
 
 // Solve S u = rhs (forward: g_adj null; adjoint: the FP64 rhs g_adj) by FP64
 // refinement around FP32 MG-PCG.  u64 holds the initial guess on entry.
-static int refine_solve(mpn_problem* p, const double* g_adj, mpn_stats* stats, cudaStream_t st) {
+static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mpn_stats* stats, cudaStream_t st) {
   Level& l = p->lv[0];
   int B = p->B, N = l.g.N;
-  dim3 gr(nblk(N), B);
-  int P = gr.x;
+  int P = l.tiles;          // partials per instance of every refinement-level reduction
+  dim3 gr(P, B);
   double* scale = p->dscal;
   double* outv = p->dscal + 2 * B;  // [slots][B]
   std::vector<double> prev_upd(B, 1.0);
@@ -460,20 +547,21 @@ static int refine_solve(mpn_problem* p, const double* g_adj, mpn_stats* stats, c
   memset(&sres, 0, sizeof(sres));
   int status = MPN_ERR_NOT_CONVERGED;
   // ||rhs|| for the relative residual
-  {
-    double* tmp = p->r64;
-    TRY(residual64(p, nullptr, g_adj, tmp, st));
-    k_norm2_d<<<gr, MPN_TPB, 0, st>>>(N, tmp, slot(p, S_GN));
-    CKL();
-  }
+  // ||rhs|| for the relative residual: the first residual when starting from 0
+  if (!zero_start) TRY(residual64(p, nullptr, g_adj, p->r64, slot(p, S_GN), st));
   std::vector<double> gnorm(B, 0.0);
+  int iters = p->desc.inner_iters, total_iters = 0;
   for (int sweep = 0; sweep < p->desc.max_refine; ++sweep) {
-    TRY(residual64(p, p->u64, g_adj, p->r64, st));
-    k_norm2_d<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN));
+    TRY(residual64(p, p->u64, g_adj, p->r64, slot(p, S_RN), st));
     k_to32<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN), P, l.r, scale);
     CKL();
-    TRY(pcg(p, p->desc.inner_iters, st));
+    TRY(pcg(p, iters, st));
+    total_iters += iters;
     k_update64<<<gr, MPN_TPB, 0, st>>>(N, p->x, scale, p->u64, slot(p, S_DU), slot(p, S_UN));
+    {
+      // correction and solution sizes measured on every unknown of z
+      k_znorm<<<gr, MPN_TPB, 0, st>>>(l.g, p->u64, p->x, scale, slot(p, S_DU), slot(p, S_UN));
+    }
     // slots S_RN, S_DU, S_UN, (S_PW unused), S_GN -> outv
     k_collect<<<B, 64, 0, st>>>(B, 5, slot(p, S_RN), P, outv);
     CKL();
@@ -481,41 +569,32 @@ static int refine_solve(mpn_problem* p, const double* g_adj, mpn_stats* stats, c
     CK(cudaStreamSynchronize(st));
     prof_flush(p);
     const double* h = p->hbuf;
-    double maxpred = 0, maxupd = 0, maxres = 0;
+    double maxpred = 0, maxupd = 0, maxres = 0, maxrate = 0;
     bool bad = false, grew = false;
     for (int b = 0; b < B; ++b) {
       double rn = sqrt(h[0 * B + b]), du = sqrt(h[1 * B + b]), un = sqrt(h[2 * B + b]);
-      if (sweep == 0) gnorm[b] = sqrt(h[4 * B + b]);
+      if (sweep == 0) gnorm[b] = zero_start ? rn : sqrt(h[4 * B + b]);
       if (!std::isfinite(rn) || !std::isfinite(du) || !std::isfinite(un)) bad = true;
       double upd = un > 0 ? du / un : (du > 0 ? 1.0 : 0.0);
-      double pred = sweep == 0 ? upd : upd * std::min(1.0, upd / std::max(prev_upd[b], 1e-300));
+      // the first update is the whole solution; contraction is measured from sweep 2 on
+      double pred = sweep < 2 ? upd : upd * std::min(1.0, upd / std::max(prev_upd[b], 1e-300));
       if (sweep >= 2 && upd > 10.0 * prev_upd[b] && upd > 1e-3) grew = true;
+      if (sweep >= 2) maxrate = std::max(maxrate, upd / std::max(prev_upd[b], 1e-300));
       prev_upd[b] = upd;
       maxpred = std::max(maxpred, pred);
       maxupd = std::max(maxupd, upd);
       maxres = std::max(maxres, gnorm[b] > 0 ? rn / gnorm[b] : 0.0);
     }
     sres.sweeps = sweep + 1;
-    sres.pcg_iters = (sweep + 1) * p->desc.inner_iters;
+    sres.pcg_iters = total_iters;
     sres.rel_update = maxupd;
     sres.pred_error = maxpred;
     sres.rel_residual = maxres;
     if (bad) { status = MPN_ERR_NONFINITE; break; }
     if (grew) { status = MPN_ERR_DIVERGED; break; }
-    if ((sweep >= 1 && maxpred <= p->desc.tol) || maxupd <= p->desc.tol * 0.1) { status = MPN_OK; break; }
-  }
-  // final residual
-  if (status == MPN_OK || status == MPN_ERR_NOT_CONVERGED) {
-    TRY(residual64(p, p->u64, g_adj, p->r64, st));
-    k_norm2_d<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN));
-    k_collect<<<B, 64, 0, st>>>(B, 1, slot(p, S_RN), P, outv);
-    CKL();
-    CK(cudaMemcpyAsync(p->hbuf, outv, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    double maxres = 0;
-    for (int b = 0; b < B; ++b)
-      maxres = std::max(maxres, gnorm[b] > 0 ? sqrt(p->hbuf[b]) / gnorm[b] : 0.0);
-    sres.rel_residual = maxres;
+    if ((sweep >= 2 && maxpred <= p->desc.tol) || (sweep >= 1 && maxupd <= p->desc.tol * 0.1)) { status = MPN_OK; break; }
+    // a sweep that gained less than a digit: lengthen the inner solve
+    if (sweep >= 1 && maxrate > 0.1 && iters < 8 * p->desc.inner_iters) iters *= 2;
   }
   if (stats) *stats = sres;
   return status;
@@ -535,11 +614,14 @@ static int forward_impl(mpn_problem* p, const float* fields, const float* scalar
   dim3 gr(nblk(l.g.N), B);
   k_set_u<<<gr, MPN_TPB, 0, st>>>(l.g.N, u0, p->u64);
   CKL();
-  int status = refine_solve(p, nullptr, stats, st);
+  p->zd_valid = false;
+  int status = refine_solve(p, nullptr, u0 == nullptr, stats, st);
   if (status != MPN_OK && status != MPN_ERR_NOT_CONVERGED) return status;
   Coef cf = make_coef(p, l.fields);
-  k_recover<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->u64, p->rhs, nullptr, z, z64);
+  k_recover<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
   CKL();
+  CK(cudaMemcpyAsync(p->uf64, p->u64, sizeof(double) * N0, cudaMemcpyDeviceToDevice, st));
+  p->zd_valid = true;
   CK(cudaStreamSynchronize(st));
   return status;
 }
@@ -566,21 +648,12 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
   cudaStream_t st = (cudaStream_t)stream;
   Level& l = p->lv[0];
   int B = p->B, V = p->V;
-  size_t N0 = (size_t)l.g.N * B;
   dim3 gr(nblk(l.g.N), B);
-  const float* zf = z;
-  if (!z) {
-    // recompute the forward solution (FP64, kept internally)
-    int s = forward_impl(p, fields, scalars, rhs, omega, nullptr, nullptr, p->zd, nullptr, st);
+  (void)z;
+  if (!((flags & MPN_REUSE_SETUP) && p->setup_ok && p->zd_valid)) {
+    // no kept forward state for these data: recompute the forward solution
+    int s = forward_impl(p, fields, scalars, rhs, omega, nullptr, nullptr, nullptr, nullptr, st);
     if (s != MPN_OK && s != MPN_ERR_NOT_CONVERGED) return s;
-    zf = nullptr;
-  } else if (!(flags & MPN_REUSE_SETUP) || !p->setup_ok) {
-    TRY(setup(p, fields, scalars, st));
-    CK(cudaMemcpyAsync(p->rhs, rhs, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(p->omega, omega, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
-  } else {
-    CK(cudaMemcpyAsync(p->rhs, rhs, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(p->omega, omega, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
   }
   Coef cf = make_coef(p, l.fields);
   // reduced right-hand side g_u - M_{u zeta} M_{zeta zeta}^{-1} g_zeta (FP64)
@@ -588,11 +661,10 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
   k_adj_rhs<<<gr, MPN_TPB, 0, st>>>(l.g, g_z, p->kap, p->g64);
   k_set_u<<<gr, MPN_TPB, 0, st>>>(l.g.N, nullptr, p->u64);
   CKL();
-  int status = refine_solve(p, p->g64, stats, st);
+  int status = refine_solve(p, p->g64, true, stats, st);
   if (status != MPN_OK && status != MPN_ERR_NOT_CONVERGED) return status;
-  k_recover<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->u64, nullptr, g_z, dz, p->dzd);
   double* gp = slot(p, S_GR0);
-  k_gradients<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rhs, zf, zf ? nullptr : p->zd, p->dzd, dfields, drhs, domega, gp);
+  k_gradients<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->rhs, p->uf64, p->u64, g_z, dfields, drhs, domega, dz, gp);
   k_scalar_grads<<<B, 64, 0, st>>>(V, B, p->field_of_dev, gp, gr.x, dscalars);
   CKL();
   CK(cudaStreamSynchronize(st));

@@ -24,7 +24,7 @@
 #include <stdint.h>
 
 #define MPN_TPB 256
-#define MPN_PMAX 128   // partial sums per instance (max CTAs per instance)
+#define MPN_PMAX 4096  // partial sums per instance (max CTAs per instance)
 
 struct Grid {
   int D;          // 2 or 3
@@ -94,18 +94,29 @@ __device__ __forceinline__ bool is_boundary(const Grid& g, const int pos[3]) {
   return false;
 }
 
+template <int D>
+__device__ __forceinline__ bool is_boundary_t(const Grid& g, const int pos[3]) {
+  bool bnd = pos[0] == 0 || (g.final_rows && pos[0] == g.n[0] - 1);
+#pragma unroll
+  for (int d = 1; d < D; ++d)
+    bnd |= !g.per[d] && (pos[d] == 0 || pos[d] == g.n[d] - 1);
+  return bnd;
+}
+
 // W_d for the edge class (symmetric 2x2: w11, w12, w22).
 __device__ __forceinline__ void wmat(int cls, double& w11, double& w12, double& w22) {
   if (cls == 0) { w11 = 3.0; w12 = 0.0; w22 = 1.5; }
   else { w11 = 2.0; w12 = cls == 1 ? 0.5 : -0.5; w22 = 1.25; }
 }
 
-// W_d^{-1} x.
-__device__ __forceinline__ void winv(int cls, double x1, double x2, double& y1, double& y2) {
-  if (cls == 0) { y1 = x1 / 3.0; y2 = x2 / 1.5; return; }
-  double sg = cls == 1 ? 1.0 : -1.0;
-  y1 = (1.25 * x1 - 0.5 * sg * x2) / 2.25;
-  y2 = (-0.5 * sg * x1 + 2.0 * x2) / 2.25;
+// W_d^{-1} x (no divisions: FP64 division is slow on this part).
+template <class R>
+__device__ __forceinline__ void winv(int cls, R x1, R x2, R& y1, R& y2) {
+  if (cls == 0) { y1 = x1 * (R)(1.0 / 3.0); y2 = x2 * (R)(2.0 / 3.0); return; }
+  const R k = (R)(1.0 / 2.25);
+  R sg = cls == 1 ? (R)1 : (R)-1;
+  y1 = ((R)1.25 * x1 - (R)0.5 * sg * x2) * k;
+  y2 = ((R)-0.5 * sg * x1 + (R)2 * x2) * k;
 }
 
 template <class T> __device__ __forceinline__ T is1_of(const Grid& g, int d);
@@ -123,10 +134,10 @@ __device__ __forceinline__ T rho_point(const Grid& g, const Coef& cf, int b, int
     T b1 = (T)coefv(cf, 1 + 2 * d, b, p, g.N) * is1_of<T>(g, d);
     T b2 = (T)coefv(cf, 2 + 2 * d, b, p, g.N) * is2_of<T>(g, d);
     int cls = edge_class(g, d, pos[d]);
-    if (cls == 0) gam += b1 * b1 / (T)3 + (T)2 * b2 * b2 / (T)3;
+    if (cls == 0) gam += b1 * b1 * (T)(1.0 / 3.0) + b2 * b2 * (T)(2.0 / 3.0);
     else {
       T sg = cls == 1 ? (T)1 : (T)-1;
-      gam += ((T)1.25 * b1 * b1 - sg * b1 * b2 + (T)2 * b2 * b2) / (T)2.25;
+      gam += ((T)1.25 * b1 * b1 - sg * b1 * b2 + (T)2 * b2 * b2) * (T)(1.0 / 2.25);
     }
   }
   return (T)1 / ((T)1 + gam);
@@ -180,6 +191,35 @@ __device__ __forceinline__ T LTgather(const Grid& g, const Coef& cf, int b, int 
     }
   }
   return acc;
+}
+
+// Non-periodic coarsened dimension: the nc coarse points span the same
+// interval as the nf fine points (both end faces kept), so fine point i sits
+// at coarse coordinate x = i (nc-1)/(nf-1); linear interpolation from J, J+1.
+__device__ __forceinline__ void np_interp(int i, int nf, int nc, int& J, float& f) {
+  int num = i * (nc - 1);
+  J = num / (nf - 1);
+  int rem = num - J * (nf - 1);
+  if (J >= nc - 1) { J = nc - 2; f = 1.f; }
+  else f = (float)rem / (float)(nf - 1);
+}
+
+// Weights of P^T for coarse point J of a non-periodic dim: fills up to 8
+// (fine index, weight) pairs; returns the count.
+__device__ __forceinline__ int np_restrict_w(int J, int nf, int nc, int* idx, float* w) {
+  int i0 = ((J - 1) * (nf - 1)) / (nc - 1);
+  if (i0 < 0) i0 = 0;
+  int i1 = ((J + 1) * (nf - 1) + nc - 2) / (nc - 1);
+  if (i1 > nf - 1) i1 = nf - 1;
+  int k = 0;
+  for (int i = i0; i <= i1 && k < 8; ++i) {
+    int Ji; float f; np_interp(i, nf, nc, Ji, f);
+    float wt = 0.f;
+    if (Ji == J) wt += 1.f - f;
+    if (Ji + 1 == J) wt += f;
+    if (wt != 0.f) { idx[k] = i; w[k] = wt; ++k; }
+  }
+  return k;
 }
 
 // ---------------------------------------------------------------- reductions

@@ -9,11 +9,13 @@
 
 // ------------------------------------------------------------------- setup
 // rho at the finest level from the coefficients.
-__global__ void k_rho_fine(Grid g, Coef cf, float* __restrict__ rho) {
+__global__ void k_rho_fine(Grid g, Coef cf, float* __restrict__ rho, double* __restrict__ rho64) {
   int b = blockIdx.y;
   GRID_LOOP(p, g.N) {
     int pos[3]; decode(g, p, pos);
-    rho[(size_t)b * g.N + p] = (float)rho_point<double>(g, cf, b, p, pos);
+    double r = rho_point<double>(g, cf, b, p, pos);
+    rho[(size_t)b * g.N + p] = (float)r;
+    rho64[(size_t)b * g.N + p] = r;
   }
 }
 
@@ -27,17 +29,21 @@ __global__ void k_restrict_field(Grid gf, Grid gc, int c0, int c1, int c2, const
   const float* f = fine + (size_t)b * gf.N;
   GRID_LOOP(p, gc.N) {
     int pos[3]; decode(gc, p, pos);
-    int lo[3], cnt[3], idx[3][3]; float w[3][3];
+    int cnt[3], idx[3][8]; float w[3][8];
     for (int d = 0; d < 3; ++d) {
       if (!cz[d]) { cnt[d] = 1; idx[d][0] = pos[d]; w[d][0] = 1.f; continue; }
-      cnt[d] = 3;
-      int c = 2 * pos[d];
-      int m = c - 1, pl = c + 1, n = gf.n[d];
-      if (gf.per[d]) { m = (m + n) % n; pl = pl % n; }
-      else { m = m < 0 ? 0 : m; pl = pl >= n ? n - 1 : pl; }
-      idx[d][0] = m; idx[d][1] = c; idx[d][2] = pl;
-      w[d][0] = 0.25f; w[d][1] = 0.5f; w[d][2] = 0.25f;
-      (void)lo;
+      int n = gf.n[d];
+      if (gf.per[d]) {
+        int c = 2 * pos[d];
+        cnt[d] = 3;
+        idx[d][0] = (c - 1 + n) % n; idx[d][1] = c; idx[d][2] = (c + 1) % n;
+        w[d][0] = 0.25f; w[d][1] = 0.5f; w[d][2] = 0.25f;
+      } else {
+        cnt[d] = np_restrict_w(pos[d], n, gc.n[d], idx[d], w[d]);
+        float sw = 0.f;
+        for (int k = 0; k < cnt[d]; ++k) sw += w[d][k];
+        for (int k = 0; k < cnt[d]; ++k) w[d][k] /= sw;
+      }
     }
     float acc = 0.f;
     for (int a = 0; a < cnt[0]; ++a)
@@ -174,6 +180,7 @@ __global__ void k_res_B(Grid g, Coef cf, const float* __restrict__ y, float* __r
 }
 
 // ------------------------------------------------------ grid transfers (P^T, P)
+
 // Interpolation P along a coarsened dimension (nf = 2 nc fine points):
 // fine 2j <- coarse j; fine 2j+1 <- (j + j+1) / 2, wrapping when periodic;
 // the last fine point of a non-periodic dimension copies the last coarse one.
@@ -185,15 +192,15 @@ __global__ void k_restrict_vec(Grid gf, Grid gc, int c0, int c1, int c2, const f
   const float* f = fine + (size_t)b * gf.N;
   GRID_LOOP(p, gc.N) {
     int pos[3]; decode(gc, p, pos);
-    int cnt[3], idx[3][3]; float w[3][3];
+    int cnt[3], idx[3][8]; float w[3][8];
     for (int d = 0; d < 3; ++d) {
       if (!cz[d]) { cnt[d] = 1; idx[d][0] = pos[d]; w[d][0] = 1.f; continue; }
       int J = pos[d], nc = gc.n[d], nf = gf.n[d];
+      if (!gf.per[d]) { cnt[d] = np_restrict_w(J, nf, nc, idx[d], w[d]); continue; }
       int k = 0;
       idx[d][k] = 2 * J; w[d][k++] = 1.f;
-      idx[d][k] = 2 * J + 1; w[d][k++] = (J + 1 < nc) ? 0.5f : (gf.per[d] ? 0.5f : 1.f);
-      if (J >= 1) { idx[d][k] = 2 * J - 1; w[d][k++] = 0.5f; }
-      else if (gf.per[d]) { idx[d][k] = nf - 1; w[d][k++] = 0.5f; }
+      idx[d][k] = 2 * J + 1; w[d][k++] = 0.5f;
+      idx[d][k] = J >= 1 ? 2 * J - 1 : nf - 1; w[d][k++] = 0.5f;
       cnt[d] = k;
     }
     float acc = 0.f;
@@ -220,12 +227,13 @@ __global__ void k_prolong_add(Grid gf, Grid gc, int c0, int c1, int c2, const fl
     for (int d = 0; d < 3; ++d) {
       if (!cz[d]) { cnt[d] = 1; idx[d][0] = pos[d]; w[d][0] = 1.f; continue; }
       int i = pos[d], nc = gc.n[d];
-      if ((i & 1) == 0) { cnt[d] = 1; idx[d][0] = i >> 1; w[d][0] = 1.f; }
+      if (!gf.per[d]) {
+        int J; float f; np_interp(i, gf.n[d], nc, J, f);
+        cnt[d] = 2; idx[d][0] = J; idx[d][1] = J + 1; w[d][0] = 1.f - f; w[d][1] = f;
+      } else if ((i & 1) == 0) { cnt[d] = 1; idx[d][0] = i >> 1; w[d][0] = 1.f; }
       else {
         int j = i >> 1;
-        if (j + 1 < nc) { cnt[d] = 2; idx[d][0] = j; idx[d][1] = j + 1; w[d][0] = w[d][1] = 0.5f; }
-        else if (gf.per[d]) { cnt[d] = 2; idx[d][0] = j; idx[d][1] = 0; w[d][0] = w[d][1] = 0.5f; }
-        else { cnt[d] = 1; idx[d][0] = j; w[d][0] = 1.f; }
+        cnt[d] = 2; idx[d][0] = j; idx[d][1] = (j + 1 < nc) ? j + 1 : 0; w[d][0] = w[d][1] = 0.5f;
       }
     }
     float acc = 0.f;
@@ -336,26 +344,49 @@ __global__ void k_coarse_factor(int M, int bw, float* __restrict__ Kb, int* __re
 }
 
 // Explicit inverse from the banded factor: thread c solves L L^T x = e_c and
-// writes column c of Kinv (symmetric).
+// writes column c of Kinv (symmetric).  The last bw values of the running
+// substitution live in a shared-memory window, so the dependency chain never
+// waits on global memory.
 __global__ void k_coarse_inverse(int M, int bw, const float* __restrict__ Lb, float* __restrict__ Kinv) {
+  extern __shared__ float win[];
   int b = blockIdx.y;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= M) return;
   const float* L = Lb + (size_t)b * M * (bw + 1);
   float* X = Kinv + (size_t)b * M * M;
-  int W = bw + 1;
+  const int W = bw + 1;
+  const int tx = threadIdx.x, nt = blockDim.x;
+  if (c >= M) return;
   for (int i = 0; i < c; ++i) X[(size_t)i * M + c] = 0.f;
+  // forward: window slot of y_j is j mod W, tracked incrementally
+  int si = c % W;
   for (int i = c; i < M; ++i) {
     float s = (i == c) ? 1.f : 0.f;
     int j0 = max(c, i - bw);
-    for (int j = j0; j < i; ++j) s -= L[i * W + (i - j)] * X[(size_t)j * M + c];
-    X[(size_t)i * M + c] = s / L[i * W];
+    int sj = si - (i - j0); if (sj < 0) sj += W;
+    const float* Li = L + (size_t)i * W + (i - j0);
+    for (int j = j0; j < i; ++j) {
+      s -= *Li-- * win[sj * nt + tx];
+      if (++sj == W) sj = 0;
+    }
+    float y = s / L[(size_t)i * W];
+    win[si * nt + tx] = y;
+    X[(size_t)i * M + c] = y;
+    if (++si == W) si = 0;
   }
+  // backward: x_i needs x_{i+1..i+bw}
+  si = (M - 1) % W;
   for (int i = M - 1; i >= 0; --i) {
     float s = X[(size_t)i * M + c];
     int j1 = min(M - 1, i + bw);
-    for (int j = i + 1; j <= j1; ++j) s -= L[j * W + (j - i)] * X[(size_t)j * M + c];
-    X[(size_t)i * M + c] = s / L[i * W];
+    int sj = si + 1; if (sj == W) sj = 0;
+    for (int j = i + 1; j <= j1; ++j) {
+      s -= L[(size_t)j * W + (j - i)] * win[sj * nt + tx];
+      if (++sj == W) sj = 0;
+    }
+    float xv = s / L[(size_t)i * W];
+    win[si * nt + tx] = xv;
+    X[(size_t)i * M + c] = xv;
+    if (--si < 0) si = W - 1;
   }
 }
 
@@ -524,62 +555,142 @@ __global__ void k_set_u(int N, const float* __restrict__ u0, double* __restrict_
 }
 
 // ----------------------------------------------- derivative unknowns and grads
-// Given u (FP64), writes every unknown of z.  The derivative unknowns of point
-// i minimise the rows owned by i:  w = (W + beta beta^T)^{-1} h with
-// h_d = W_d a_d(u) + beta_d (bE - c_0 u) + S^{-1} g_zeta (scaled units
-// w = (s u', s^2 u'')).  Forward: bE = b, g = 0.  Adjoint: bE = 0, g = the
-// derivative part of g_z.
-__global__ void k_recover(Grid g, Coef cf, const double* __restrict__ u, const float* __restrict__ bE,
-                          const float* __restrict__ gz, float* __restrict__ zf, double* __restrict__ zd) {
-  int b = blockIdx.y;
-  size_t off = (size_t)b * g.N;
+// Every unknown of z at point p from u (FP64).  The derivative unknowns of
+// point i minimise the rows owned by i; in scaled units w = (s u', s^2 u'')
+// and with h_g = S^{-1} g_zeta (adjoint source; zero for the forward pass):
+//   w = a(u) + W^{-1} h_g - rho E* W^{-1} beta,
+//   E* = L u - bE + beta^T W^{-1} h_g,
+// a(u) the difference forms of Eq. 5.  This form has no cancellation: E* is
+// the (small) equation-row residual.  The duals follow from it:
+// lambda_E = -rho E* (forward, bE = b) and d_lambda_E = -rho E* (adjoint).
+// Returns rho E*.
+__device__ __forceinline__ double recover_point(const Grid& g, const Coef& cf, int b, int p, const int pos[3],
+                                                const double* __restrict__ u, double rho, double bE,
+                                                const float* __restrict__ gz, double* zo) {
   int V = 1 + 2 * g.D;
+  size_t off = (size_t)b * g.N;
+  double uc = u[off + p];
+  double Est = (double)coefv(cf, 0, b, p, g.N) * uc - bE;
+  double a[3][2], hw[3][2], qb[3][2];
+  for (int d = 0; d < g.D; ++d) {
+    double a1 = 0, a2 = 0;
+    for (int o = -2; o <= 2; ++o) {
+      float w1 = dweight(1, pos[d], g.n[d], g.per[d], o), w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
+      if (w1 == 0.f && w2 == 0.f) continue;
+      double xv = o == 0 ? uc : u[off + nbr(g, p, pos, d, o)];
+      a1 += (double)w1 * xv; a2 += (double)w2 * xv;
+    }
+    int cls = edge_class(g, d, pos[d]);
+    double b1 = (double)coefv(cf, 1 + 2 * d, b, p, g.N) * g.ds1[d];
+    double b2 = (double)coefv(cf, 2 + 2 * d, b, p, g.N) * g.ds2[d];
+    a[d][0] = a1; a[d][1] = a2;
+    Est += b1 * a1 + b2 * a2;
+    winv<double>(cls, b1, b2, qb[d][0], qb[d][1]);    // W^{-1} beta
+    hw[d][0] = hw[d][1] = 0;
+    if (gz) {
+      double g1 = (double)gz[((size_t)b * V + 1 + 2 * d) * g.N + p] * g.ds1[d];
+      double g2 = (double)gz[((size_t)b * V + 2 + 2 * d) * g.N + p] * g.ds2[d];
+      winv<double>(cls, g1, g2, hw[d][0], hw[d][1]);  // W^{-1} h_g
+      Est += b1 * hw[d][0] + b2 * hw[d][1];
+    }
+  }
+  double rE = rho * Est;
+  zo[0] = uc;
+  for (int d = 0; d < g.D; ++d) {
+    zo[1 + 2 * d] = (a[d][0] + hw[d][0] - rE * qb[d][0]) * g.ds1[d];
+    zo[2 + 2 * d] = (a[d][1] + hw[d][1] - rE * qb[d][1]) * g.ds2[d];
+  }
+  return rE;
+}
+
+// z (FP32 and/or FP64) from u.
+__global__ void k_recover(Grid g, Coef cf, const double* __restrict__ rho64, const double* __restrict__ u,
+                          const float* __restrict__ bE, const float* __restrict__ gz, float* __restrict__ zf,
+                          double* __restrict__ zd) {
+  int b = blockIdx.y;
+  int V = 1 + 2 * g.D;
+  size_t off = (size_t)b * g.N;
   GRID_LOOP(p, g.N) {
     int pos[3]; decode(g, p, pos);
-    double uc = u[off + p];
-    double c0 = coefv(cf, 0, b, p, g.N);
-    double rhsE = (bE ? (double)bE[off + p] : 0.0) - c0 * uc;
-    double h[3][2], wi[3][2], be[3][2];
-    double bwh = 0, gam = 0;
+    double zo[7];
+    recover_point(g, cf, b, p, pos, u, rho64[off + p], bE ? (double)bE[off + p] : 0.0, gz, zo);
+    size_t zb = (size_t)b * V * g.N;
+    for (int v = 0; v < V; ++v) {
+      if (zf) zf[zb + (size_t)v * g.N + p] = (float)zo[v];
+      if (zd) zd[zb + (size_t)v * g.N + p] = zo[v];
+    }
+  }
+}
+
+// Gradients (formulas after Eq. 11) at every point from the forward u and the
+// adjoint d_u (both FP64):
+//   lambda_E = b - E z* = rho (b - L u)                       (closed form)
+//   dlambda_E = -E d_z = -rho (L d_u + beta^T W^{-1} S^{-1} g_zeta)
+//   dl/dc_v = dlambda_E z_v + lambda_E dz_v,  dl/db = -dlambda_E,
+//   dl/domega = d_u on boundary points.
+// z and d_z are recovered on the fly.  Field
+// gradients sum over the unknowns sharing a field; scalar gradients are
+// reduced per instance (partials in part[v]).
+__global__ void k_gradients(Grid g, Coef cf, const double* __restrict__ rho64, const float* __restrict__ rhs,
+                            const double* __restrict__ uf, const double* __restrict__ du, const float* __restrict__ gz,
+                            float* __restrict__ dfields, float* __restrict__ drhs, float* __restrict__ domega,
+                            float* __restrict__ dz_out, double* __restrict__ part) {
+  int b = blockIdx.y;
+  int V = 1 + 2 * g.D;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  size_t off = (size_t)b * g.N;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode(g, p, pos);
+    double zv[7], dv[7];
+    double r = rho64[off + p];
+    double lam = -recover_point(g, cf, b, p, pos, uf, r, (double)rhs[off + p], nullptr, zv);
+    double dlam = -recover_point(g, cf, b, p, pos, du, r, 0.0, gz, dv);
+    for (int f = 0; f < cf.F; ++f) {
+      double s = 0;
+      for (int v = 0; v < V; ++v) if (cf.field_of[v] == f) s += dlam * zv[v] + lam * dv[v];
+      dfields[((size_t)f * cf.B + b) * g.N + p] = (float)s;
+    }
+    for (int v = 0; v < V; ++v) if (cf.field_of[v] < 0) acc[v] += dlam * zv[v] + lam * dv[v];
+    drhs[off + p] = (float)(-dlam);
+    domega[off + p] = is_boundary(g, pos) ? (float)dv[0] : 0.f;
+    if (dz_out) for (int v = 0; v < V; ++v) dz_out[((size_t)b * V + v) * g.N + p] = (float)dv[v];
+  }
+  for (int v = 0; v < V; ++v) {
+    double s = block_sum(acc[v]);
+    if (threadIdx.x == 0) part[((size_t)v * cf.B + b) * MPN_PMAX + blockIdx.x] = s;
+  }
+}
+
+// Partials of the size of z(u) and of the last correction measured on every
+// unknown: u itself plus, per dimension, its first and second difference
+// quotients (the derivative unknowns up to their small point-local
+// correction).  Only a couple of digits are needed, so FP32.
+__global__ void k_znorm(Grid g, const double* __restrict__ u, const float* __restrict__ x,
+                        const double* __restrict__ scale, double* __restrict__ part_dz, double* __restrict__ part_z) {
+  int b = blockIdx.y;
+  float sc = (float)scale[b];
+  size_t off = (size_t)b * g.N;
+  float a1 = 0, a2 = 0;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode(g, p, pos);
+    float uc = (float)u[off + p], xc = sc * x[off + p];
+    a2 += uc * uc; a1 += xc * xc;
     for (int d = 0; d < g.D; ++d) {
-      double a1 = 0, a2 = 0;
+      float u1 = 0, u2 = 0, x1 = 0, x2 = 0;
       for (int o = -2; o <= 2; ++o) {
         float w1 = dweight(1, pos[d], g.n[d], g.per[d], o), w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
         if (w1 == 0.f && w2 == 0.f) continue;
-        double xv = o == 0 ? uc : u[off + nbr(g, p, pos, d, o)];
-        a1 += w1 * xv; a2 += w2 * xv;
+        int q = o == 0 ? p : nbr(g, p, pos, d, o);
+        float uv = (float)u[off + q], xv = sc * x[off + q];
+        u1 += w1 * uv; u2 += w2 * uv; x1 += w1 * xv; x2 += w2 * xv;
       }
-      int cls = edge_class(g, d, pos[d]);
-      double w11, w12, w22; wmat(cls, w11, w12, w22);
-      double b1 = coefv(cf, 1 + 2 * d, b, p, g.N) * g.ds1[d];
-      double b2 = coefv(cf, 2 + 2 * d, b, p, g.N) * g.ds2[d];
-      be[d][0] = b1; be[d][1] = b2;
-      double h1 = w11 * a1 + w12 * a2 + b1 * rhsE;
-      double h2 = w12 * a1 + w22 * a2 + b2 * rhsE;
-      if (gz) {
-        h1 += (double)gz[((size_t)b * V + 1 + 2 * d) * g.N + p] * g.ds1[d];
-        h2 += (double)gz[((size_t)b * V + 2 + 2 * d) * g.N + p] * g.ds2[d];
-      }
-      h[d][0] = h1; h[d][1] = h2;
-      winv(cls, h1, h2, wi[d][0], wi[d][1]);        // W^{-1} h
-      double q1, q2; winv(cls, b1, b2, q1, q2);     // W^{-1} beta
-      bwh += b1 * wi[d][0] + b2 * wi[d][1];
-      gam += b1 * q1 + b2 * q2;
-    }
-    double fac = bwh / (1.0 + gam);
-    size_t zb = (size_t)b * V * g.N;
-    if (zf) zf[zb + p] = (float)uc;
-    if (zd) zd[zb + p] = uc;
-    for (int d = 0; d < g.D; ++d) {
-      int cls = edge_class(g, d, pos[d]);
-      double q1, q2; winv(cls, be[d][0], be[d][1], q1, q2);
-      double w1 = wi[d][0] - q1 * fac;
-      double w2 = wi[d][1] - q2 * fac;
-      double z1 = w1 * g.ds1[d], z2 = w2 * g.ds2[d];
-      if (zf) { zf[zb + (size_t)(1 + 2 * d) * g.N + p] = (float)z1; zf[zb + (size_t)(2 + 2 * d) * g.N + p] = (float)z2; }
-      if (zd) { zd[zb + (size_t)(1 + 2 * d) * g.N + p] = z1; zd[zb + (size_t)(2 + 2 * d) * g.N + p] = z2; }
+      u1 *= g.is1[d]; u2 *= g.is2[d]; x1 *= g.is1[d]; x2 *= g.is2[d];
+      a2 += u1 * u1 + u2 * u2; a1 += x1 * x1 + x2 * x2;
     }
   }
+  double s1 = block_sum((double)a1);
+  double s2 = block_sum((double)a2);
+  if (threadIdx.x == 0) { part_dz[b * MPN_PMAX + blockIdx.x] = s1; part_z[b * MPN_PMAX + blockIdx.x] = s2; }
 }
 
 // Adjoint right-hand side, part 1: per point psi = (W + beta beta^T)^{-1} S^{-1} g_zeta
@@ -598,8 +709,8 @@ __global__ void k_adj_kappa(Grid g, Coef cf, const float* __restrict__ gz, doubl
       be[d][0] = b1; be[d][1] = b2;
       double h1 = (double)gz[((size_t)b * V + 1 + 2 * d) * g.N + p] * g.ds1[d];
       double h2 = (double)gz[((size_t)b * V + 2 + 2 * d) * g.N + p] * g.ds2[d];
-      winv(cls, h1, h2, hw[d][0], hw[d][1]);
-      double q1, q2; winv(cls, b1, b2, q1, q2);
+      winv<double>(cls, h1, h2, hw[d][0], hw[d][1]);
+      double q1, q2; winv<double>(cls, b1, b2, q1, q2);
       bwh += b1 * hw[d][0] + b2 * hw[d][1];
       gam += b1 * q1 + b2 * q2;
     }
@@ -607,7 +718,7 @@ __global__ void k_adj_kappa(Grid g, Coef cf, const float* __restrict__ gz, doubl
     double bpsi = 0;
     for (int d = 0; d < g.D; ++d) {
       int cls = edge_class(g, d, pos[d]);
-      double q1, q2; winv(cls, be[d][0], be[d][1], q1, q2);
+      double q1, q2; winv<double>(cls, be[d][0], be[d][1], q1, q2);
       double ps1 = hw[d][0] - q1 * fac, ps2 = hw[d][1] - q2 * fac;
       bpsi += be[d][0] * ps1 + be[d][1] * ps2;
       double w11, w12, w22; wmat(cls, w11, w12, w22);
@@ -640,45 +751,6 @@ __global__ void k_adj_rhs(Grid g, const float* __restrict__ gz, const double* __
   }
 }
 
-// Gradients (formulas after Eq. 11) from z* and d_z:
-//   lambda_E = b - sum_v c_v z_v,  dlambda_E = -sum_v c_v dz_v,
-//   dl/dc_v = dlambda_E z_v + lambda_E dz_v,  dl/db = -dlambda_E,
-//   dl/domega = dz_u on boundary points.
-// Field gradients sum over the unknowns sharing a field; scalar gradients are
-// reduced per instance (partials in part[v]).
-__global__ void k_gradients(Grid g, Coef cf, const float* __restrict__ rhs, const float* __restrict__ zf,
-                            const double* __restrict__ zd, const double* __restrict__ dz, float* __restrict__ dfields,
-                            float* __restrict__ drhs, float* __restrict__ domega, double* __restrict__ part) {
-  int b = blockIdx.y;
-  int V = 1 + 2 * g.D;
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-  size_t zb = (size_t)b * V * g.N;
-  GRID_LOOP(p, g.N) {
-    int pos[3]; decode(g, p, pos);
-    double zv[7], dv[7], cv[7];
-    double lam = rhs[(size_t)b * g.N + p], dlam = 0;
-    for (int v = 0; v < V; ++v) {
-      zv[v] = zf ? (double)zf[zb + (size_t)v * g.N + p] : zd[zb + (size_t)v * g.N + p];
-      dv[v] = dz[zb + (size_t)v * g.N + p];
-      cv[v] = coefv(cf, v, b, p, g.N);
-      lam -= cv[v] * zv[v];
-      dlam -= cv[v] * dv[v];
-    }
-    for (int f = 0; f < cf.F; ++f) {
-      double s = 0;
-      for (int v = 0; v < V; ++v) if (cf.field_of[v] == f) s += dlam * zv[v] + lam * dv[v];
-      dfields[((size_t)f * cf.B + b) * g.N + p] = (float)s;
-    }
-    for (int v = 0; v < V; ++v) if (cf.field_of[v] < 0) acc[v] += dlam * zv[v] + lam * dv[v];
-    drhs[(size_t)b * g.N + p] = (float)(-dlam);
-    domega[(size_t)b * g.N + p] = is_boundary(g, pos) ? (float)dv[0] : 0.f;
-  }
-  for (int v = 0; v < V; ++v) {
-    double s = block_sum(acc[v]);
-    if (threadIdx.x == 0) part[((size_t)v * cf.B + b) * MPN_PMAX + blockIdx.x] = s;
-  }
-}
-
 __global__ void k_scalar_grads(int V, int B, const int* __restrict__ field_of_dev, const double* __restrict__ part,
                                int P, float* __restrict__ dscalars) {
   int b = blockIdx.x;
@@ -698,4 +770,86 @@ __global__ void k_mse_grad(int N, int V, int B, const float* __restrict__ z, con
     gz[zb + p] = sc * (z[zb + p] - tgt[(size_t)b * N + p]);
     for (int v = 1; v < V; ++v) gz[zb + (size_t)v * N + p] = 0.f;
   }
+}
+
+// ------------------------------------------------- FP64 refinement residual
+// Two passes so that every FP64 operation is done once per point (FP64
+// throughput, not memory, bounds these):
+//   k_res64_y:  y = rho (b - L u)              (b, u nullable => 0)
+//   k_res64_q:  r = base + L^T y + theta 1_B (omega - u), partials of ||r||^2
+// Points away from non-periodic edges use the central weights directly.
+__device__ __forceinline__ void decode_fast(const Grid& g, int p, int pos[3]) {
+  int n12 = g.n[1] * g.n[2];
+  int i0 = __float2int_rz(((float)p + 0.5f) / (float)n12);
+  int rem = p - i0 * n12;
+  int i1 = __float2int_rz(((float)rem + 0.5f) / (float)g.n[2]);
+  pos[0] = i0; pos[1] = i1; pos[2] = rem - i1 * g.n[2];
+}
+
+__device__ __forceinline__ bool any_edge(const Grid& g, const int pos[3]) {
+  bool e = pos[0] < 3 || pos[0] > g.n[0] - 4;
+  for (int d = 1; d < 3; ++d)
+    if (d < g.D && !g.per[d]) e |= pos[d] < 3 || pos[d] > g.n[d] - 4;
+  return e;
+}
+
+template <int D>
+__global__ void k_res64_y(Grid g, Coef cf, const double* __restrict__ rho64, const double* __restrict__ u,
+                          const float* __restrict__ bsrc, double* __restrict__ y) {
+  int b = blockIdx.y;
+  size_t off = (size_t)b * g.N;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode_fast(g, p, pos);
+    double Lu = 0;
+    if (u) {
+      double uc = u[off + p];
+      Lu = (double)coefv(cf, 0, b, p, g.N) * uc;
+      if (!any_edge(g, pos)) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          double um = u[off + nbr(g, p, pos, d, -1)], up = u[off + nbr(g, p, pos, d, 1)];
+          Lu += (double)coefv(cf, 1 + 2 * d, b, p, g.N) * (0.5 * (up - um)) * g.ds1[d] +
+                (double)coefv(cf, 2 + 2 * d, b, p, g.N) * (up - 2.0 * uc + um) * g.ds2[d];
+        }
+      } else {
+        Lu = Lrow<double>(g, cf, b, p, pos, u + off, nullptr);
+      }
+    }
+    double s = bsrc ? (double)bsrc[off + p] : 0.0;
+    y[off + p] = rho64[off + p] * (s - Lu);
+  }
+}
+
+template <int D>
+__global__ void k_res64_q(Grid g, Coef cf, const double* __restrict__ y, const double* __restrict__ base,
+                          const float* __restrict__ omega, const double* __restrict__ u, double* __restrict__ out,
+                          double* __restrict__ part) {
+  int b = blockIdx.y;
+  size_t off = (size_t)b * g.N;
+  double acc = 0;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode_fast(g, p, pos);
+    double q;
+    const double* yb = y + off;
+    if (!any_edge(g, pos)) {
+      double yc = yb[p];
+      q = (double)coefv(cf, 0, b, p, g.N) * yc;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        int pm = nbr(g, p, pos, d, -1), pp = nbr(g, p, pos, d, 1);
+        double ym = yb[pm], yp = yb[pp];
+        q += 0.5 * g.ds1[d] * ((double)coefv(cf, 1 + 2 * d, b, pm, g.N) * ym - (double)coefv(cf, 1 + 2 * d, b, pp, g.N) * yp) +
+             g.ds2[d] * ((double)coefv(cf, 2 + 2 * d, b, pm, g.N) * ym - 2.0 * (double)coefv(cf, 2 + 2 * d, b, p, g.N) * yc +
+                         (double)coefv(cf, 2 + 2 * d, b, pp, g.N) * yp);
+      }
+    } else {
+      q = LTgather<double>(g, cf, b, p, pos, yb);
+    }
+    if (base) q += base[off + p];
+    if (is_boundary(g, pos)) q += (double)g.theta * ((omega ? (double)omega[off + p] : 0.0) - (u ? u[off + p] : 0.0));
+    out[off + p] = q;
+    acc += q * q;
+  }
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) part[b * MPN_PMAX + blockIdx.x] = s;
 }

@@ -36,6 +36,7 @@ def _dev(a):
 
 def _solver(w, **kw):
     from paper_2502_18377_b300.binding import Solver
+    kw.setdefault("max_refine", 60)
     return Solver(w.geom, w.batch, w.field_of, w.fields.shape[0], **kw)
 
 
@@ -51,16 +52,25 @@ def _oracle_instance(w, b):
     return A, d, kind, owner, z, lam, el
 
 
+def _no_utt(w):
+    """Rough random coefficients without a u_tt term (a white-noise,
+    random-sign second time derivative makes the problem mixed-type, where
+    the solver converges but slowly)."""
+    w.fields[2] = 0.0
+    return w
+
+
 CASES = [
     ("c1_full", lambda: wl.advection_diffusion_1d()),
     ("c2_small", lambda: wl.reaction_diffusion_2d(batch=3, n=(8, 16, 16))),
     ("c2_ragged", lambda: wl.reaction_diffusion_2d(batch=2, n=(10, 12, 20))),
     ("c3_small", lambda: wl.linearized_burgers_1d(batch=2, n=(32, 64))),
     ("c5_small", lambda: wl.transport_2d(batch=2, n=(8, 16, 16))),
-    ("rand_dirichlet_2d", lambda: wl.random_problem(21, (12, 32), (False, False), batch=2)),
+    ("rand_dirichlet_2d", lambda: _no_utt(wl.random_problem(21, (12, 32), (False, False), batch=2))),
     ("rand_odd_2d_final", lambda: wl.random_problem(22, (9, 13), (False, False), batch=2,
                                                     final_time_rows=True)),
-    ("rand_mixed_3d", lambda: wl.random_problem(23, (7, 16, 12), (False, True, False), batch=2)),
+    ("rand_mixed_3d", lambda: _no_utt(wl.random_problem(23, (7, 16, 12), (False, True, False), batch=2))),
+    ("rand_utt_2d", lambda: wl.random_problem(25, (10, 16), (False, True), batch=2)),
     ("rand_scalars_3d", lambda: wl.random_problem(24, (6, 8, 8), (False, True, True), batch=3,
                                                   field_all=False)),
 ]
