@@ -22,7 +22,7 @@
 
 #include "../../include/mpn.h"
 #include "mpn_kernels.cuh"
-#include "mpn_tile.cuh"
+#include "mpn_stencil.cuh"
 
 #define MAXL 16
 
@@ -46,10 +46,6 @@ struct Level {
   float* fields = nullptr;  // [F][B][N]
   float *rho = nullptr, *dinv = nullptr;
   float *r = nullptr, *e = nullptr, *d = nullptr, *y = nullptr, *t = nullptr;
-  float *eb[2] = {nullptr, nullptr}, *db[2] = {nullptr, nullptr};  // ping-pong iterates
-  int ce = 0, cd = 0;  // current buffers
-  int T[3], ntile[3], tiles;  // shared-memory tile shape of k_tile
-  size_t smem, smem64;
 };
 
 struct mpn_problem {
@@ -87,7 +83,10 @@ enum { S_RZ = 0, S_PQ, S_RN, S_DU, S_UN, S_PW, S_GN, S_GR0, NSLOT = S_GR0 + 8 };
 
 static inline double* slot(mpn_problem* p, int k) { return p->part + (size_t)k * p->B * MPN_PMAX; }
 
+// CTAs per instance: vector kernels (and the reductions their consumers sum)
+// use few, stencil kernels many.
 static int nblk(int N) { int b = (N + MPN_TPB - 1) / MPN_TPB; return b < 1 ? 1 : (b > 64 ? 64 : b); }
+static int sblk(int N) { int b = (N + MPN_TPB - 1) / MPN_TPB; return b < 1 ? 1 : (b > 512 ? 512 : b); }
 
 static int dalloc(mpn_problem* p, void** ptr, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -254,26 +253,6 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
     AL(l.fields, (size_t)std::max(F, 1) * N);
     AL(l.rho, N); AL(l.dinv, N);
     AL(l.r, N); AL(l.e, N); AL(l.d, N); AL(l.y, N); AL(l.t, N);
-    AL(l.eb[1], N); AL(l.db[1], N);
-    l.eb[0] = l.e; l.db[0] = l.d;
-    // tile of about 1024 points, fastest dimension first
-    int n0 = l.g.n[0], n1 = l.g.n[1], n2 = l.g.n[2];
-    if (p->D == 3) {
-      l.T[2] = std::min(n2, 32);
-      l.T[1] = std::min(n1, std::max(1, 256 / l.T[2]));
-      l.T[0] = std::min(n0, std::max(1, 1024 / (l.T[1] * l.T[2])));
-    } else {
-      l.T[2] = 1;
-      l.T[1] = std::min(n1, 256);
-      l.T[0] = std::min(n0, std::max(1, 1024 / l.T[1]));
-    }
-    for (int k2 = 0; k2 < 3; ++k2) l.ntile[k2] = (l.g.n[k2] + l.T[k2] - 1) / l.T[k2];
-    l.tiles = l.ntile[0] * l.ntile[1] * l.ntile[2];
-    int h2 = p->D == 3 ? 4 : 0;
-    size_t nbox = (size_t)(l.T[0] + 4) * (l.T[1] + 4) * (l.T[2] + h2);
-    l.smem = nbox * (3 * sizeof(float) + sizeof(float) * F);
-    l.smem64 = nbox * (3 * sizeof(double) + sizeof(float) * F);
-    if (l.tiles > MPN_PMAX || l.smem64 > 200 * 1024) { mpn_destroy(p); return MPN_ERR_UNSUPPORTED; }
   }
   size_t N0 = (size_t)p->lv[0].g.N * B;
   AL(p->Kband, (size_t)B * p->M * (p->bw + 1));
@@ -293,20 +272,8 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   for (int v = 0; v < 8; ++v) fo[v] = v < V ? d.field_of[v] : -1;
   if (cudaMemcpy(p->field_of_dev, fo, sizeof(fo), cudaMemcpyHostToDevice) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
   if (cudaMallocHost((void**)&p->hbuf, sizeof(double) * 16 * B) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
-  {
-    size_t mx = 0, mx64 = 0;
-    for (int k = 0; k < p->L; ++k) { mx = std::max(mx, p->lv[k].smem); mx64 = std::max(mx64, p->lv[k].smem64); }
-    int attr = (int)std::max(mx, (size_t)48 * 1024), attr64 = (int)std::max(mx64, (size_t)48 * 1024);
-    cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)std::max(sizeof(float) * (p->bw + 1) * 128, (size_t)48 * 1024));
-    if (p->D == 3) {
-      cudaFuncSetAttribute(k_tile<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, attr);
-      cudaFuncSetAttribute(k_tile<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, attr64);
-    } else {
-      cudaFuncSetAttribute(k_tile<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, attr);
-      cudaFuncSetAttribute(k_tile<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, attr64);
-    }
-  }
+  cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)std::max(sizeof(float) * (p->bw + 1) * 128, (size_t)48 * 1024));
 
   // Chebyshev coefficients on [lo, 1] for Dinv scaled by 1 / lambda_max
   const double lo = 0.1, th = (1.0 + lo) / 2, de = (1.0 - lo) / 2, sg = th / de;
@@ -343,31 +310,28 @@ static void prof_flush(mpn_problem* p) {
   }
   p->prof_used = 0;
 }
-template <class T>
-static void launch_tile(mpn_problem* p, int k, TileArgs<T> a, int mode, cudaStream_t st) {
+// One operator pass pair at level k: y = -rho L x, then the mode's update.
+static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st) {
   Level& l = p->lv[k];
   Coef cf = make_coef(p, l.fields);
+  dim3 gr(sblk(l.g.N), p->B);
+  a.y = l.y;
   if (!a.dinv) a.dinv = l.dinv;
-  for (int d = 0; d < 3; ++d) { a.tile[d] = l.T[d]; a.ntile[d] = l.ntile[d]; }
-  dim3 gr(l.tiles, p->B);
-  size_t sm = sizeof(T) == 8 ? l.smem64 : l.smem;
-  if (p->D == 3) k_tile<3, T><<<gr, MPN_TPB, sm, st>>>(l.g, cf, a, mode);
-  else k_tile<2, T><<<gr, MPN_TPB, sm, st>>>(l.g, cf, a, mode);
+  if (p->D == 3) {
+    k_Ly<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, a.x, l.y);
+    k_LTy<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, a, mode);
+  } else {
+    k_Ly<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, a.x, l.y);
+    k_LTy<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, a, mode);
+  }
 }
 
-static TileArgs<float> targs(mpn_problem* p, int k) {
-  TileArgs<float> a;
-  memset(&a, 0, sizeof(a));
-  a.rho = p->lv[k].rho;
-  a.dinv = p->lv[k].dinv;
-  return a;
-}
-
-// q = S x at level k (FP32), optional <x, q> partials into `part` (one per tile).
+// q = S x at level k (FP32), optional <x, q> partials into `part` (sblk per instance).
 static int apply_S(mpn_problem* p, int k, const float* x, float* q, double* part, cudaStream_t st) {
-  TileArgs<float> a = targs(p, k);
-  a.ein = x; a.out = q; a.part = part;
-  launch_tile(p, k, a, TM_APPLY, st);
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.x = x; a.out = q; a.part = part;
+  stencil(p, k, a, SM_APPLY, st);
   CKL();
   return MPN_OK;
 }
@@ -428,55 +392,45 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
   return MPN_OK;
 }
 
-// One V-cycle at level k: e ~ S_k^{-1} r_k.  On return the result is
-// eb[ce] + db[cd] (the last Chebyshev direction pending), except at the
-// coarsest level, where it is eb[ce] alone.
+// One V-cycle at level k: e_k ~ S_k^{-1} r_k (result in l.e).
 static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   Level& l = p->lv[k];
   int B = p->B;
   dim3 gr(nblk(l.g.N), B);
   if (k == p->L - 1) {
-    l.ce = 0;
-    k_coarse_solve<<<dim3((p->M * 32 + MPN_TPB - 1) / MPN_TPB, B), MPN_TPB, 0, st>>>(p->M, p->Kinv, l.r, l.eb[0]);
+    k_coarse_solve<<<dim3((p->M * 32 + MPN_TPB - 1) / MPN_TPB, B), MPN_TPB, 0, st>>>(p->M, p->Kinv, l.r, l.e);
     CKL();
     return MPN_OK;
   }
   int m = p->desc.cheb_degree;
   bool prof = (k == 0);
-  TileArgs<float> a = targs(p, k);
-  a.r = l.r;
-  // pre-smoothing from e = 0
-  l.ce = 0; l.cd = 0;
-  k_cheb_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, l.eb[0], l.db[0]);
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.r = l.r; a.x = l.e; a.e = l.e; a.d = l.d;
+  // pre-smoothing from e = 0: d = Dinv r / th, e = d
+  k_cheb_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, l.e, l.d);
   for (int s = 1; s < m; ++s) {
-    a.ein = l.eb[l.ce]; a.din = l.db[l.cd]; a.eout = l.eb[1 - l.ce]; a.dout = l.db[1 - l.cd];
     a.c1 = p->cheb_c1[s]; a.c2 = p->cheb_c2[s];
     if (prof) prof_mark(p, st);
-    launch_tile(p, k, a, TM_CHEB, st);
+    stencil(p, k, a, SM_CHEB, st);
     if (prof) prof_mark(p, st);
-    l.ce = 1 - l.ce; l.cd = 1 - l.cd;
   }
-  // residual of e + d (e absorbs d), restricted to the coarse level
-  a.ein = l.eb[l.ce]; a.din = l.db[l.cd]; a.eout = l.eb[1 - l.ce]; a.out = l.t;
-  launch_tile(p, k, a, TM_RES, st);
-  l.ce = 1 - l.ce;
+  // residual, restricted to the coarse level
+  a.out = l.t;
+  stencil(p, k, a, SM_RES, st);
   Level& lc = p->lv[k + 1];
   k_restrict_vec<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], l.t, lc.r);
   CKL();
   TRY(vcycle(p, k + 1, st));
-  k_prolong_add<<<gr, MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], lc.eb[lc.ce],
-                                        (k + 1 == p->L - 1) ? nullptr : lc.db[lc.cd], l.eb[l.ce]);
+  k_prolong_add<<<gr, MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], lc.e, nullptr, l.e);
   // post-smoothing
-  a.ein = l.eb[l.ce]; a.din = nullptr; a.dout = l.db[1 - l.cd]; a.c2 = p->cheb_inv_th;
-  launch_tile(p, k, a, TM_POST0, st);
-  l.cd = 1 - l.cd;
+  a.c1 = 0.f; a.c2 = p->cheb_inv_th;
+  stencil(p, k, a, SM_POST0, st);
   for (int s = 1; s < m; ++s) {
-    a.ein = l.eb[l.ce]; a.din = l.db[l.cd]; a.eout = l.eb[1 - l.ce]; a.dout = l.db[1 - l.cd];
     a.c1 = p->cheb_c1[s]; a.c2 = p->cheb_c2[s];
     if (prof) prof_mark(p, st);
-    launch_tile(p, k, a, TM_CHEB, st);
+    stencil(p, k, a, SM_CHEB, st);
     if (prof) prof_mark(p, st);
-    l.ce = 1 - l.ce; l.cd = 1 - l.cd;
   }
   CKL();
   return MPN_OK;
@@ -487,7 +441,7 @@ static int precond(mpn_problem* p, cudaStream_t st) {
   Level& l = p->lv[0];
   TRY(vcycle(p, 0, st));
   dim3 gr(nblk(l.g.N), p->B);
-  k_final_z<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.eb[l.ce], p->L > 1 ? l.db[l.cd] : nullptr, l.r, p->z, slot(p, S_RZ));
+  k_final_z<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.e, nullptr, l.r, p->z, slot(p, S_RZ));
   CKL();
   return MPN_OK;
 }
@@ -502,7 +456,8 @@ static int pcg(mpn_problem* p, int iters, cudaStream_t st) {
   k_pcg_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, p->z, p->x, p->pv);
   for (int it = 0; it < iters; ++it) {
     TRY(apply_S(p, 0, p->pv, p->q, slot(p, S_PQ), st));
-    k_pcg_xr<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), slot(p, S_PQ), l.tiles, P, p->pv, p->q, p->x, l.r, rz_old);
+    k_pcg_xr<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), slot(p, S_PQ), sblk(l.g.N), P, p->pv, p->q, p->x, l.r,
+                                     rz_old);
     CKL();
     if (it == iters - 1) break;
     TRY(precond(p, st));
@@ -519,7 +474,7 @@ static int residual64(mpn_problem* p, const double* u, const double* g_adj, doub
                       cudaStream_t st) {
   Level& l = p->lv[0];
   Coef cf = make_coef(p, l.fields);
-  dim3 gr(l.tiles, p->B);   // partial count per instance = tiles (as every refinement reduction)
+  dim3 gr(nblk(l.g.N), p->B);   // partial count per instance = nblk (as every refinement reduction)
   const float* src = g_adj ? nullptr : p->rhs;
   const float* om = g_adj ? nullptr : p->omega;
   if (p->D == 3) {
@@ -538,7 +493,7 @@ static int residual64(mpn_problem* p, const double* u, const double* g_adj, doub
 static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mpn_stats* stats, cudaStream_t st) {
   Level& l = p->lv[0];
   int B = p->B, N = l.g.N;
-  int P = l.tiles;          // partials per instance of every refinement-level reduction
+  int P = nblk(N);          // partials per instance of every refinement-level reduction
   dim3 gr(P, B);
   double* scale = p->dscal;
   double* outv = p->dscal + 2 * B;  // [slots][B]

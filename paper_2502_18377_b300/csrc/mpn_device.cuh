@@ -144,13 +144,15 @@ __device__ __forceinline__ T rho_point(const Grid& g, const Coef& cf, int b, int
 }
 
 // (L x)_i: the equation row evaluated with every derivative replaced by its
-// difference form.  x2 (nullable) is added to x on the fly.
-template <class T>
+// difference form.  x2 (nullable) is added to x on the fly.  DD: number of
+// grid dimensions when known at compile time (0: read g.D).
+template <class T, int DD = 0>
 __device__ __forceinline__ T Lrow(const Grid& g, const Coef& cf, int b, int p, const int pos[3],
                                   const T* __restrict__ x, const T* __restrict__ x2) {
   T xc = x[p]; if (x2) xc += x2[p];
   T acc = (T)coefv(cf, 0, b, p, g.N) * xc;
-  for (int d = 0; d < g.D; ++d) {
+#pragma unroll
+  for (int d = 0; d < (DD ? DD : g.D); ++d) {
     T c1 = (T)coefv(cf, 1 + 2 * d, b, p, g.N);
     T c2 = (T)coefv(cf, 2 + 2 * d, b, p, g.N);
     if (c1 == (T)0 && c2 == (T)0) continue;
@@ -171,11 +173,12 @@ __device__ __forceinline__ T Lrow(const Grid& g, const Coef& cf, int b, int p, c
 }
 
 // (L^T y)_j: gather over the rows i whose difference forms touch point j.
-template <class T>
+template <class T, int DD = 0>
 __device__ __forceinline__ T LTgather(const Grid& g, const Coef& cf, int b, int p, const int pos[3],
                                       const T* __restrict__ y) {
   T acc = (T)coefv(cf, 0, b, p, g.N) * y[p];
-  for (int d = 0; d < g.D; ++d) {
+#pragma unroll
+  for (int d = 0; d < (DD ? DD : g.D); ++d) {
 #pragma unroll
     for (int o = -2; o <= 2; ++o) {
       int ip = pos[d] - o;

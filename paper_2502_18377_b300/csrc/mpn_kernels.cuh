@@ -136,48 +136,18 @@ __global__ void k_LTpass(Grid g, Coef cf, const T* __restrict__ y, const float* 
 // The smoother iterates e <- e + d with
 //   d_0 = Dinv r_0 / th,  d_k = c1_k d_{k-1} + c2_k Dinv r_k,
 // r_k = r - S e_k, Dinv already scaled by 1 / lambda_max(Dinv S).
+// First smoothing step from e = 0 (look-ahead form): d = Dinv r / th, e = d.
 __global__ void k_cheb_init(int N, const float* __restrict__ r, const float* __restrict__ dinv, float inv_th,
                             float* __restrict__ e, float* __restrict__ d) {
   size_t off = (size_t)blockIdx.y * N;
   GRID_LOOP(p, N) {
-    e[off + p] = 0.f;
-    d[off + p] = inv_th * dinv[off + p] * r[off + p];
+    float v = inv_th * dinv[off + p] * r[off + p];
+    e[off + p] = v;
+    d[off + p] = v;
   }
 }
 
-// mode 0: first post-smoothing step: res = r - S e (y from x = e); d = Dinv res / th.
-// mode 1: e += d; res = r - S e (y from x = e + d); d = c1 d + c2 Dinv res.
-__global__ void k_cheb_B(Grid g, Coef cf, const float* __restrict__ y, float* __restrict__ e,
-                         float* __restrict__ d, const float* __restrict__ r, const float* __restrict__ dinv,
-                         int mode, float c1, float c2) {
-  int b = blockIdx.y;
-  size_t off = (size_t)b * g.N;
-  GRID_LOOP(p, g.N) {
-    int pos[3]; decode(g, p, pos);
-    float ev = e[off + p];
-    float dv = d[off + p];
-    if (mode == 1) ev += dv;
-    float res = r[off + p] + LTgather<float>(g, cf, b, p, pos, y + off);
-    if (is_boundary(g, pos)) res -= g.theta * ev;
-    if (mode == 1) { e[off + p] = ev; d[off + p] = c1 * dv + c2 * dinv[off + p] * res; }
-    else d[off + p] = c2 * dinv[off + p] * res;
-  }
-}
 
-// e += d; t = r - S e   (y from x = e + d).
-__global__ void k_res_B(Grid g, Coef cf, const float* __restrict__ y, float* __restrict__ e,
-                        const float* __restrict__ d, const float* __restrict__ r, float* __restrict__ t) {
-  int b = blockIdx.y;
-  size_t off = (size_t)b * g.N;
-  GRID_LOOP(p, g.N) {
-    int pos[3]; decode(g, p, pos);
-    float ev = e[off + p] + d[off + p];
-    float res = r[off + p] + LTgather<float>(g, cf, b, p, pos, y + off);
-    if (is_boundary(g, pos)) res -= g.theta * ev;
-    e[off + p] = ev;
-    t[off + p] = res;
-  }
-}
 
 // ------------------------------------------------------ grid transfers (P^T, P)
 
@@ -812,7 +782,7 @@ __global__ void k_res64_y(Grid g, Coef cf, const double* __restrict__ rho64, con
                 (double)coefv(cf, 2 + 2 * d, b, p, g.N) * (up - 2.0 * uc + um) * g.ds2[d];
         }
       } else {
-        Lu = Lrow<double>(g, cf, b, p, pos, u + off, nullptr);
+        Lu = Lrow<double, D>(g, cf, b, p, pos, u + off, nullptr);
       }
     }
     double s = bsrc ? (double)bsrc[off + p] : 0.0;
@@ -843,10 +813,10 @@ __global__ void k_res64_q(Grid g, Coef cf, const double* __restrict__ y, const d
                          (double)coefv(cf, 2 + 2 * d, b, pp, g.N) * yp);
       }
     } else {
-      q = LTgather<double>(g, cf, b, p, pos, yb);
+      q = LTgather<double, D>(g, cf, b, p, pos, yb);
     }
     if (base) q += base[off + p];
-    if (is_boundary(g, pos)) q += (double)g.theta * ((omega ? (double)omega[off + p] : 0.0) - (u ? u[off + p] : 0.0));
+    if (is_boundary_t<D>(g, pos)) q += (double)g.theta * ((omega ? (double)omega[off + p] : 0.0) - (u ? u[off + p] : 0.0));
     out[off + p] = q;
     acc += q * q;
   }
