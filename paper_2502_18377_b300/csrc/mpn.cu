@@ -126,6 +126,14 @@ static Coef make_coef(const mpn_problem* p, const float* fields) {
   for (int v = 0; v < 7; ++v) c.field_of[v] = v < p->V ? p->desc.field_of[v] : -1;
   c.fields = fields;
   c.scalars = p->scalars;
+  // per-level point count from the field pointer's level (fields are [F][B][N])
+  int N = 0;
+  for (int k = 0; k < p->L; ++k) if (p->lv[k].fields == fields) N = p->lv[k].g.N;
+  for (int v = 0; v < 7; ++v) {
+    int f = v < p->V ? p->desc.field_of[v] : -1;
+    if (f >= 0) { c.ptr[v] = fields + (size_t)f * p->B * N; c.bstride[v] = N; c.pstride[v] = 1; }
+    else { c.ptr[v] = p->scalars + (size_t)(v < p->V ? v : 0) * p->B; c.bstride[v] = 1; c.pstride[v] = 0; }
+  }
   return c;
 }
 
@@ -317,13 +325,23 @@ static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st
   dim3 gr(sblk(l.g.N), p->B);
   a.y = l.y;
   if (!a.dinv) a.dinv = l.dinv;
+#define LTY(DD, MM) k_LTy<DD, MM><<<gr, MPN_TPB, 0, st>>>(l.g, cf, a)
+#define LTY_D(DD)                                   \
+  switch (mode) {                                   \
+    case SM_POST0: LTY(DD, SM_POST0); break;        \
+    case SM_CHEB: LTY(DD, SM_CHEB); break;          \
+    case SM_RES: LTY(DD, SM_RES); break;            \
+    default: LTY(DD, SM_APPLY); break;              \
+  }
   if (p->D == 3) {
     k_Ly<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, a.x, l.y);
-    k_LTy<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, a, mode);
+    LTY_D(3)
   } else {
     k_Ly<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, a.x, l.y);
-    k_LTy<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, a, mode);
+    LTY_D(2)
   }
+#undef LTY_D
+#undef LTY
 }
 
 // q = S x at level k (FP32), optional <x, q> partials into `part` (sblk per instance).

@@ -43,12 +43,30 @@ struct Coef {
   int field_of[7];
   const float* fields;   // [F][B][N] at this level
   const float* scalars;  // [V][B]
+  // c_v at (b, p) = ptr[v][b * bstride[v] + p * pstride[v]]: a field has
+  // strides (N, 1), a per-instance scalar (1, 0).
+  const float* ptr[7];
+  int bstride[7], pstride[7];
 };
 
 __device__ __forceinline__ float coefv(const Coef& c, int v, int b, int p, int N) {
-  int f = c.field_of[v];
-  return f >= 0 ? __ldg(c.fields + ((size_t)f * c.B + b) * N + p) : __ldg(c.scalars + v * c.B + b);
+  (void)N;
+  return __ldg(c.ptr[v] + (size_t)b * c.bstride[v] + (size_t)p * c.pstride[v]);
 }
+
+// Coefficient access with the instance offset hoisted out of point loops.
+struct CoefB {
+  const float* base[7];
+  int ps[7];
+  __device__ __forceinline__ CoefB(const Coef& c, int b, int V) {
+#pragma unroll
+    for (int v = 0; v < 7; ++v) {
+      base[v] = v < V ? c.ptr[v] + (size_t)b * c.bstride[v] : nullptr;
+      ps[v] = v < V ? c.pstride[v] : 0;
+    }
+  }
+  __device__ __forceinline__ float operator()(int v, int p) const { return __ldg(base[v] + p * ps[v]); }
+};
 
 __device__ __forceinline__ void decode(const Grid& g, int p, int pos[3]) {
   pos[2] = p % g.n[2];

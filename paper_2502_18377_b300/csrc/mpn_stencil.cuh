@@ -62,17 +62,17 @@ __global__ void __launch_bounds__(256) k_Ly(Grid g, Coef cf, const float* __rest
   const size_t off = (size_t)b * g.N;
   const float* xb = x + off;
   const float inv12 = 1.f / (float)(g.n[1] * g.n[2]), inv2 = 1.f / (float)g.n[2];
+  const CoefB C(cf, b, 1 + 2 * D);
   GRID_LOOP(p, g.N) {
     int pos[3]; decode_f(g, p, inv12, inv2, pos);
     float xc = xb[p];
     float Lx;
     if (!edge_any<D>(g, pos)) {
-      Lx = coefv(cf, 0, b, p, g.N) * xc;
+      Lx = C(0, p) * xc;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         float xm = xb[nb1(g, p, pos, d, -1)], xp = xb[nb1(g, p, pos, d, 1)];
-        Lx += coefv(cf, 1 + 2 * d, b, p, g.N) * (0.5f * (xp - xm)) * g.is1[d] +
-              coefv(cf, 2 + 2 * d, b, p, g.N) * (xp - 2.f * xc + xm) * g.is2[d];
+        Lx += C(1 + 2 * d, p) * (0.5f * (xp - xm)) * g.is1[d] + C(2 + 2 * d, p) * (xp - 2.f * xc + xm) * g.is2[d];
       }
     } else {
       Lx = Lrow<float, D>(g, cf, b, p, pos, xb, nullptr);
@@ -81,25 +81,25 @@ __global__ void __launch_bounds__(256) k_Ly(Grid g, Coef cf, const float* __rest
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(256) k_LTy(Grid g, Coef cf, StepArgs a, int mode) {
+template <int D, int MODE>
+__global__ void __launch_bounds__(256) k_LTy(Grid g, Coef cf, StepArgs a) {
   const int b = blockIdx.y;
   const size_t off = (size_t)b * g.N;
   const float* yb = a.y + off;
   const float inv12 = 1.f / (float)(g.n[1] * g.n[2]), inv2 = 1.f / (float)g.n[2];
-  double acc = 0;
+  const CoefB C(cf, b, 1 + 2 * D);
+  float acc = 0.f;   // one or two points per thread; the block sum is FP64
   GRID_LOOP(p, g.N) {
     int pos[3]; decode_f(g, p, inv12, inv2, pos);
     float yc = yb[p];
-    float q = coefv(cf, 0, b, p, g.N) * yc;
+    float q = C(0, p) * yc;
     if (!edge_any<D>(g, pos)) {
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         int pm = nb1(g, p, pos, d, -1), pp = nb1(g, p, pos, d, 1);
         float ym = yb[pm], yp = yb[pp];
-        q += 0.5f * g.is1[d] * (coefv(cf, 1 + 2 * d, b, pm, g.N) * ym - coefv(cf, 1 + 2 * d, b, pp, g.N) * yp) +
-             g.is2[d] * (coefv(cf, 2 + 2 * d, b, pm, g.N) * ym - 2.f * coefv(cf, 2 + 2 * d, b, p, g.N) * yc +
-                         coefv(cf, 2 + 2 * d, b, pp, g.N) * yp);
+        q += 0.5f * g.is1[d] * (C(1 + 2 * d, pm) * ym - C(1 + 2 * d, pp) * yp) +
+             g.is2[d] * (C(2 + 2 * d, pm) * ym - 2.f * C(2 + 2 * d, p) * yc + C(2 + 2 * d, pp) * yp);
       }
     } else {
       q = LTgather<float, D>(g, cf, b, p, pos, yb);
@@ -108,20 +108,20 @@ __global__ void __launch_bounds__(256) k_LTy(Grid g, Coef cf, StepArgs a, int mo
     if (is_boundary_t<D>(g, pos)) q -= g.theta * xj;
     // q = -(S x)_j
     const size_t j = off + p;
-    if (mode == SM_APPLY) {
+    if (MODE == SM_APPLY) {
       a.out[j] = -q;
-      acc -= (double)q * (double)xj;
-    } else if (mode == SM_RES) {
+      acc -= q * xj;
+    } else if (MODE == SM_RES) {
       a.out[j] = a.r[j] + q;
     } else {
       float res = a.r[j] + q;
-      float dn = (mode == SM_CHEB ? a.c1 * a.d[j] : 0.f) + a.c2 * a.dinv[j] * res;
+      float dn = (MODE == SM_CHEB ? a.c1 * a.d[j] : 0.f) + a.c2 * a.dinv[j] * res;
       a.d[j] = dn;
       a.e[j] = xj + dn;
     }
   }
-  if (mode == SM_APPLY && a.part) {
-    double s = block_sum(acc);
+  if (MODE == SM_APPLY && a.part) {
+    double s = block_sum((double)acc);
     if (threadIdx.x == 0) a.part[b * MPN_PMAX + blockIdx.x] = s;
   }
 }
