@@ -42,6 +42,8 @@ static thread_local char g_cuda_err[256] = "";
 
 struct Level {
   Grid g;
+  int vec4 = 0;        // float4 stencil kernels apply (D = 3, n_y % 4 == 0)
+  int papply = 0;      // partial sums per instance written by an operator apply
   int cz[3];           // dims halved from this level to the next
   float* fields = nullptr;  // [F][B][N]
   float *rho = nullptr, *dinv = nullptr;
@@ -243,6 +245,11 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
       }
     theta *= (float)(1 << nd);
   }
+  for (int k = 0; k < p->L; ++k) {
+    Level& l = p->lv[k];
+    l.vec4 = (p->D == 3 && l.g.n[2] % 4 == 0 && l.g.n[2] >= 8) ? 1 : 0;
+    l.papply = l.vec4 ? sblk(l.g.N / 4) : sblk(l.g.N);
+  }
   Level& lc = p->lv[p->L - 1];
   p->M = lc.g.N;
   int plane = lc.g.n[1] * lc.g.n[2];
@@ -322,9 +329,20 @@ static void prof_flush(mpn_problem* p) {
 static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st) {
   Level& l = p->lv[k];
   Coef cf = make_coef(p, l.fields);
-  dim3 gr(sblk(l.g.N), p->B);
   a.y = l.y;
   if (!a.dinv) a.dinv = l.dinv;
+  if (l.vec4) {
+    dim3 g4(sblk(l.g.N / 4), p->B);
+    k_Ly4<<<g4, MPN_TPB, 0, st>>>(l.g, cf, l.rho, a.x, l.y);
+    switch (mode) {
+      case SM_POST0: k_LTy4<SM_POST0><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
+      case SM_CHEB: k_LTy4<SM_CHEB><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
+      case SM_RES: k_LTy4<SM_RES><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
+      default: k_LTy4<SM_APPLY><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
+    }
+    return;
+  }
+  dim3 gr(sblk(l.g.N), p->B);
 #define LTY(DD, MM) k_LTy<DD, MM><<<gr, MPN_TPB, 0, st>>>(l.g, cf, a)
 #define LTY_D(DD)                                   \
   switch (mode) {                                   \
@@ -474,7 +492,7 @@ static int pcg(mpn_problem* p, int iters, cudaStream_t st) {
   k_pcg_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, p->z, p->x, p->pv);
   for (int it = 0; it < iters; ++it) {
     TRY(apply_S(p, 0, p->pv, p->q, slot(p, S_PQ), st));
-    k_pcg_xr<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), slot(p, S_PQ), sblk(l.g.N), P, p->pv, p->q, p->x, l.r,
+    k_pcg_xr<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), slot(p, S_PQ), l.papply, P, p->pv, p->q, p->x, l.r,
                                      rz_old);
     CKL();
     if (it == iters - 1) break;

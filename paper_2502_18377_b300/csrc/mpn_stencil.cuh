@@ -125,3 +125,170 @@ __global__ void __launch_bounds__(256) k_LTy(Grid g, Coef cf, StepArgs a) {
     if (threadIdx.x == 0) a.part[b * MPN_PMAX + blockIdx.x] = s;
   }
 }
+
+// ------------------------------------------------------------ float4 versions
+// D = 3 and n_y % 4 == 0: one thread owns 4 consecutive points along y.
+// Along t and x the four points share their position class, so the
+// (possibly one-sided) weights are uniform and neighbours come as float4;
+// along y the neighbours come from the same float4 plus one value on each
+// side.  A group that touches a non-periodic y-edge falls back to the scalar
+// formulas point by point.
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
+__device__ __forceinline__ float4 operator+(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float4 operator-(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+__device__ __forceinline__ float4 operator*(float4 a, float4 b) { return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
+__device__ __forceinline__ float4 operator*(float a, float4 b) { return make_float4(a * b.x, a * b.y, a * b.z, a * b.w); }
+__device__ __forceinline__ float get(const float4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); }
+
+struct CoefB4 {
+  const float* base[7];
+  int ps[7];
+  __device__ __forceinline__ CoefB4(const Coef& c, int b) {
+#pragma unroll
+    for (int v = 0; v < 7; ++v) { base[v] = c.ptr[v] + (size_t)b * c.bstride[v]; ps[v] = c.pstride[v]; }
+  }
+  __device__ __forceinline__ float4 at4(int v, int p) const { return ps[v] ? ld4(base[v] + p) : f4(__ldg(base[v])); }
+  __device__ __forceinline__ float at(int v, int p) const { return __ldg(base[v] + p * ps[v]); }
+};
+
+// group (it, ix, iy0) of p0 = first point; returns false if the group needs
+// the scalar fallback (touches a non-periodic y edge region)
+__device__ __forceinline__ void group_pos(const Grid& g, int q, int pos[3]) {
+  int ng = g.n[2] >> 2;
+  int row = q / ng;
+  pos[2] = (q - row * ng) << 2;
+  pos[1] = row % g.n[1];
+  pos[0] = row / g.n[1];
+}
+
+__global__ void __launch_bounds__(256) k_Ly4(Grid g, Coef cf, const float* __restrict__ rho, const float* __restrict__ x,
+                                             float* __restrict__ y) {
+  const int b = blockIdx.y;
+  const size_t off = (size_t)b * g.N;
+  const float* xb = x + off;
+  const CoefB4 C(cf, b);
+  const int NG = g.N >> 2;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < NG; q += gridDim.x * blockDim.x) {
+    int pos[3]; group_pos(g, q, pos);
+    const int p0 = q << 2;
+    const int n2 = g.n[2];
+    bool yedge = !g.per[2] && (pos[2] < 3 || pos[2] + 3 > n2 - 4);
+    if (yedge) {
+      for (int k = 0; k < 4; ++k) {
+        int pk[3] = {pos[0], pos[1], pos[2] + k};
+        y[off + p0 + k] = -rho[off + p0 + k] * Lrow<float, 3>(g, cf, b, p0 + k, pk, xb, nullptr);
+      }
+      continue;
+    }
+    float4 xc = ld4(xb + p0);
+    float4 Lx = C.at4(0, p0) * xc;
+    // t and x: uniform position class
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      float4 a1 = f4(0.f), a2 = f4(0.f);
+#pragma unroll
+      for (int o = -2; o <= 2; ++o) {
+        float w1 = dweight(1, pos[d], g.n[d], g.per[d], o), w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
+        if (w1 == 0.f && w2 == 0.f) continue;
+        float4 xv = o == 0 ? xc : ld4(xb + nbr(g, p0, pos, d, o));
+        a1 = a1 + w1 * xv; a2 = a2 + w2 * xv;
+      }
+      Lx = Lx + (g.is1[d] * C.at4(1 + 2 * d, p0)) * a1 + (g.is2[d] * C.at4(2 + 2 * d, p0)) * a2;
+    }
+    // y: central, neighbours from the group plus one value each side
+    {
+      int row0 = p0 - pos[2];
+      float xl = xb[row0 + (pos[2] == 0 ? n2 - 1 : pos[2] - 1)];
+      float xr = xb[row0 + (pos[2] + 4 == n2 ? 0 : pos[2] + 4)];
+      float4 xm = make_float4(xl, xc.x, xc.y, xc.z), xp = make_float4(xc.y, xc.z, xc.w, xr);
+      Lx = Lx + (0.5f * g.is1[2]) * (C.at4(5, p0) * (xp - xm)) + g.is2[2] * (C.at4(6, p0) * (xp - 2.f * xc + xm));
+    }
+    float4 r4 = ld4(rho + off + p0);
+    *reinterpret_cast<float4*>(y + off + p0) = make_float4(-r4.x * Lx.x, -r4.y * Lx.y, -r4.z * Lx.z, -r4.w * Lx.w);
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_LTy4(Grid g, Coef cf, StepArgs a) {
+  const int b = blockIdx.y;
+  const size_t off = (size_t)b * g.N;
+  const float* yb = a.y + off;
+  const CoefB4 C(cf, b);
+  const int NG = g.N >> 2;
+  float acc = 0.f;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < NG; q += gridDim.x * blockDim.x) {
+    int pos[3]; group_pos(g, q, pos);
+    const int p0 = q << 2;
+    const int n2 = g.n[2];
+    float4 qv;
+    bool yedge = !g.per[2] && (pos[2] < 3 || pos[2] + 3 > n2 - 4);
+    if (yedge) {
+      float t[4];
+      for (int k = 0; k < 4; ++k) {
+        int pk[3] = {pos[0], pos[1], pos[2] + k};
+        t[k] = LTgather<float, 3>(g, cf, b, p0 + k, pk, yb);
+      }
+      qv = make_float4(t[0], t[1], t[2], t[3]);
+    } else {
+      float4 yc = ld4(yb + p0);
+      qv = C.at4(0, p0) * yc;
+      // t and x: rows i = j - o e_d share their position class across the group
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+#pragma unroll
+        for (int o = -2; o <= 2; ++o) {
+          int ip = pos[d] - o;
+          if (g.per[d]) { if (ip < 0) ip += g.n[d]; else if (ip >= g.n[d]) ip -= g.n[d]; }
+          else if (ip < 0 || ip >= g.n[d]) continue;
+          float w1 = dweight(1, ip, g.n[d], g.per[d], o), w2 = dweight(2, ip, g.n[d], g.per[d], o);
+          if (w1 == 0.f && w2 == 0.f) continue;
+          int pi = p0 + (ip - pos[d]) * g.stride[d];
+          float4 yv = o == 0 ? yc : ld4(yb + pi);
+          qv = qv + yv * ((w1 * g.is1[d]) * C.at4(1 + 2 * d, pi) + (w2 * g.is2[d]) * C.at4(2 + 2 * d, pi));
+        }
+      }
+      // y: central rows j-1, j, j+1
+      int row0 = p0 - pos[2];
+      int pl = row0 + (pos[2] == 0 ? n2 - 1 : pos[2] - 1), pr = row0 + (pos[2] + 4 == n2 ? 0 : pos[2] + 4);
+      float4 c1 = C.at4(5, p0), c2 = C.at4(6, p0);
+      float yl = yb[pl], yr = yb[pr], c1l = C.at(5, pl), c1r = C.at(5, pr), c2l = C.at(6, pl), c2r = C.at(6, pr);
+      float4 ym = make_float4(yl, yc.x, yc.y, yc.z), yp = make_float4(yc.y, yc.z, yc.w, yr);
+      float4 c1m = make_float4(c1l, c1.x, c1.y, c1.z), c1p = make_float4(c1.y, c1.z, c1.w, c1r);
+      float4 c2m = make_float4(c2l, c2.x, c2.y, c2.z), c2p = make_float4(c2.y, c2.z, c2.w, c2r);
+      qv = qv + (0.5f * g.is1[2]) * (c1m * ym - c1p * yp) + g.is2[2] * (c2m * ym - 2.f * (c2 * yc) + c2p * yp);
+    }
+    float4 xj = ld4(a.x + off + p0);
+    // Dirichlet rows: t and x faces are shared by the group, y faces per point
+    bool bnd_tx = pos[0] == 0 || (g.final_rows && pos[0] == g.n[0] - 1) ||
+                  (!g.per[1] && (pos[1] == 0 || pos[1] == g.n[1] - 1));
+    if (bnd_tx) {
+      qv = qv - g.theta * xj;
+    } else if (!g.per[2]) {
+      float t4[4] = {qv.x, qv.y, qv.z, qv.w};
+      for (int k = 0; k < 4; ++k) {
+        int iy = pos[2] + k;
+        if (iy == 0 || iy == n2 - 1) t4[k] -= g.theta * get(xj, k);
+      }
+      qv = make_float4(t4[0], t4[1], t4[2], t4[3]);
+    }
+    // qv = -(S x) on the group
+    const size_t j = off + p0;
+    if (MODE == SM_APPLY) {
+      *reinterpret_cast<float4*>(a.out + j) = make_float4(-qv.x, -qv.y, -qv.z, -qv.w);
+      acc -= qv.x * xj.x + qv.y * xj.y + qv.z * xj.z + qv.w * xj.w;
+    } else if (MODE == SM_RES) {
+      *reinterpret_cast<float4*>(a.out + j) = ld4(a.r + j) + qv;
+    } else {
+      float4 res = ld4(a.r + j) + qv;
+      float4 dn = a.c2 * (ld4(a.dinv + j) * res);
+      if (MODE == SM_CHEB) dn = dn + a.c1 * ld4(a.d + j);
+      *reinterpret_cast<float4*>(a.d + j) = dn;
+      *reinterpret_cast<float4*>(a.e + j) = xj + dn;
+    }
+  }
+  if (MODE == SM_APPLY && a.part) {
+    double s = block_sum((double)acc);
+    if (threadIdx.x == 0) a.part[b * MPN_PMAX + blockIdx.x] = s;
+  }
+}
