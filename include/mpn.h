@@ -148,6 +148,26 @@ int mpn_apply_reduced(mpn_problem* p, const float* fields, const float* scalars,
  * switches timing on (1) or off (0) and resets the totals. */
 int mpn_profile(mpn_problem* p, int enable, double* ms_total, long long* launches, double* bytes);
 
+/* Allocation-free variant of mpn_apply_reduced.  The paper has no
+ * counterpart: it exists for callers that cannot allocate device memory
+ * (device memory owned by another allocator, or paths where the failure or
+ * implicit synchronisation of cudaMalloc/cudaFree is unacceptable).  It takes
+ * the descriptor instead of a problem object and allocates nothing: the
+ * intermediate of the two-pass apply lives in a fixed device array of
+ * MPN_NOALLOC_MAX_POINTS floats (16 MB, held by every GPU that loads the
+ * library until exit), and the point weights are computed inline.
+ *   desc     host; grid, batch, coefficient layout (solver fields unused)
+ *   fields   device [F][B][N], scalars device [V][B], u device [B][N]
+ *   q        device [B][N] output, q = S u
+ * B * N above MPN_NOALLOC_MAX_POINTS returns MPN_ERR_UNSUPPORTED.  The first
+ * call on a device resolves the array's device address for that device
+ * (with that device current); make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race.
+ * Asynchronous on `stream`. */
+#define MPN_NOALLOC_MAX_POINTS 4194304
+int mpn_apply_reduced_noalloc(const mpn_desc* desc, const float* fields, const float* scalars,
+                              const float* u, float* q, void* stream);
+
 void mpn_destroy(mpn_problem* p);
 const char* mpn_strerror(int status);
 const char* mpn_last_cuda_error(void);

@@ -52,6 +52,7 @@ EXPORTS = {
     "mpn_apply_reduced": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "mpn_profile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
+    "mpn_apply_reduced_noalloc": (ctypes.c_int, [ctypes.POINTER(MpnDesc), _P, _P, _P, _P, _P]),
     "mpn_destroy": (None, [_P]),
     "mpn_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mpn_last_cuda_error": (ctypes.c_char_p, []),
@@ -105,6 +106,40 @@ def _check_f32(name, t, shape):
         raise ValueError(f"{name} must be float32")
     if tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+NOALLOC_MAX_POINTS = 4194304
+
+
+def make_desc(geom: dict, batch: int, field_of, nfields: int) -> MpnDesc:
+    """Descriptor for a grid / batch / coefficient layout (solver defaults)."""
+    lib = load()
+    d = MpnDesc()
+    lib.mpn_default_desc(ctypes.byref(d))
+    n = tuple(geom["n"])
+    D = len(n)
+    d.ndim = D
+    for k in range(3):
+        d.n[k] = n[k] if k < D else 1
+        d.step[k] = geom["step"][k] if k < D else 1.0
+        d.periodic[k] = int(geom["periodic"][k]) if k < D else 0
+    d.stencil = int(geom.get("stencil", 3))
+    d.final_time_rows = int(geom.get("final_time_rows", False))
+    d.batch = batch
+    d.nfields = nfields
+    for v in range(7):
+        d.field_of[v] = field_of[v] if v < len(field_of) else -1
+    return d
+
+
+def apply_reduced_noalloc(desc: MpnDesc, fields, scalars, u, q):
+    """q = S u through the allocation-free entry point (q preallocated)."""
+    lib = load()
+    s = lib.mpn_apply_reduced_noalloc(ctypes.byref(desc), _ptr(fields) if desc.nfields else None, _ptr(scalars),
+                                      _ptr(u), _ptr(q), _stream())
+    if s != 0:
+        raise MpnError(s, "mpn_apply_reduced_noalloc")
+    return q
 
 
 class Solver:
