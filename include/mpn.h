@@ -168,6 +168,57 @@ int mpn_profile(mpn_problem* p, int enable, double* ms_total, long long* launche
 int mpn_apply_reduced_noalloc(const mpn_desc* desc, const float* fields, const float* scalars,
                               const float* u, float* q, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start: a 3x3x3 convolutional network on the (t, x, y) grid
+ * that predicts u from the coefficient fields and the right-hand side; its
+ * prediction is passed as u0 to mpn_forward, and the solver iterates it to
+ * the same tolerance as a cold start.  The paper has no such network; the
+ * layer operations below are its inference and training kernels.
+ * Activations are channels-last BF16 [B][N][C]; weights BF16 [27][Cout][Cin]
+ * with tap = (dt+1)*9 + (dx+1)*3 + (dy+1); biases FP32 [Cout]; all device
+ * memory owned by the caller.  Supported (Cin, Cout): (16, 32), (32, 32),
+ * (32, 16).  Time is zero-padded; x, y wrap when periodic, else zero-padded.
+ * ------------------------------------------------------------------------ */
+typedef struct mpn_conv_desc {
+  int n[3];          /* n_t, n_x, n_y */
+  int periodic[3];   /* periodic[0] must be 0 */
+  int batch;
+  int cin, cout;     /* padded channel counts */
+} mpn_conv_desc;
+
+#define MPN_CONV_RELU 1   /* y = max(., 0) */
+#define MPN_CONV_F32 2    /* FP32 output (else BF16) */
+#define MPN_CONV_BIAS 4   /* add bias */
+#define MPN_WGRAD_CHUNK 2048
+#define MPN_MSE_BLOCKS 64
+
+/* y = act(conv(x, W) + b): BF16 tensor-core (mma.sync m16n8k16) implicit GEMM, FP32 accumulation. */
+int mpn_conv3d_forward(const mpn_conv_desc* d, const void* x, const void* w, const float* bias, void* y,
+                       int flags, void* stream);
+/* g_in [B][N][cin] FP32 = transposed convolution of g_out [B][N][cout] (BF16) with W;
+ * wt_scratch: 27*cin*cout BF16 (flipped, transposed W).  Requires cin = 32. */
+int mpn_conv3d_backward_data(const mpn_conv_desc* d, const void* g_out, const void* w, void* wt_scratch,
+                             float* g_in, void* stream);
+/* Bytes of FP32 scratch mpn_conv3d_backward_weights needs. */
+size_t mpn_conv3d_wgrad_scratch_bytes(const mpn_conv_desc* d);
+/* dW [27][cout][cin] = sum_p g_out[p][co] x[nbr(p, tap)][ci], db [cout] = sum_p g_out[p][co]
+ * (FP32 accumulation, deterministic two-stage reduction). */
+int mpn_conv3d_backward_weights(const mpn_conv_desc* d, const void* g_out, const void* x, float* scratch,
+                                float* dw, float* db, void* stream);
+/* out (BF16) = g * (y > 0) elementwise (y BF16, nullable: no mask), n elements. */
+int mpn_relu_mask(long long n, const float* g, const void* y, void* out, void* stream);
+/* Adam on FP32 master weights w with moments m, v (step >= 1); w_bf16 (nullable) gets the BF16 copy. */
+int mpn_adam_step(long long n, float* w, const float* g, float* m, float* v, float lr, float beta1, float beta2,
+                  float eps, int step, void* w_bf16, void* stream);
+/* x0 [B][N][16] BF16 = (fields[0..F), rhs) * scale[c], channels zero-padded. */
+int mpn_pack_inputs(const mpn_conv_desc* d, int nfields, const float* fields, const float* rhs, const float* scale,
+                    void* x0, void* stream);
+/* MSE of channel 0 of y [B][N][16] (FP32) against target [B][N]: g (same shape as y) and
+ * per-block partial sums of squares loss_part [B][MPN_MSE_BLOCKS]. */
+int mpn_mse_u(const mpn_conv_desc* d, const float* y, const float* target, float* g, float* loss_part, void* stream);
+/* u0 [B][N] = scale * y[., ., 0]. */
+int mpn_unpack_u(const mpn_conv_desc* d, const float* y, float scale, float* u0, void* stream);
+
 void mpn_destroy(mpn_problem* p);
 const char* mpn_strerror(int status);
 const char* mpn_last_cuda_error(void);

@@ -30,6 +30,11 @@ class MpnDesc(ctypes.Structure):
                 ("max_coarse", ctypes.c_int)]
 
 
+class MpnConvDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("periodic", ctypes.c_int * 3), ("batch", ctypes.c_int),
+                ("cin", ctypes.c_int), ("cout", ctypes.c_int)]
+
+
 class MpnStats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("pcg_iters", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("rel_update", ctypes.c_double),
@@ -53,6 +58,16 @@ EXPORTS = {
     "mpn_profile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
     "mpn_apply_reduced_noalloc": (ctypes.c_int, [ctypes.POINTER(MpnDesc), _P, _P, _P, _P, _P]),
+    "mpn_conv3d_forward": (ctypes.c_int, [ctypes.POINTER(MpnConvDesc), _P, _P, _P, _P, ctypes.c_int, _P]),
+    "mpn_conv3d_backward_data": (ctypes.c_int, [ctypes.POINTER(MpnConvDesc), _P, _P, _P, _P, _P]),
+    "mpn_conv3d_wgrad_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(MpnConvDesc)]),
+    "mpn_conv3d_backward_weights": (ctypes.c_int, [ctypes.POINTER(MpnConvDesc), _P, _P, _P, _P, _P, _P]),
+    "mpn_relu_mask": (ctypes.c_int, [ctypes.c_longlong, _P, _P, _P, _P]),
+    "mpn_adam_step": (ctypes.c_int, [ctypes.c_longlong, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_float, ctypes.c_int, _P, _P]),
+    "mpn_pack_inputs": (ctypes.c_int, [ctypes.POINTER(MpnConvDesc), ctypes.c_int, _P, _P, _P, _P, _P]),
+    "mpn_mse_u": (ctypes.c_int, [ctypes.POINTER(MpnConvDesc), _P, _P, _P, _P, _P]),
+    "mpn_unpack_u": (ctypes.c_int, [ctypes.POINTER(MpnConvDesc), _P, ctypes.c_float, _P, _P]),
     "mpn_destroy": (None, [_P]),
     "mpn_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mpn_last_cuda_error": (ctypes.c_char_p, []),

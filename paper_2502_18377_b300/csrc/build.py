@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 PKG = os.path.dirname(HERE)
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libmpn.so")
-SOURCES = [os.path.join(HERE, "mpn.cu"), os.path.join(HERE, "mpn_noalloc.cu")]
+SOURCES = [os.path.join(HERE, "mpn.cu"), os.path.join(HERE, "mpn_noalloc.cu"), os.path.join(HERE, "mpn_conv.cu")]
 DEPS = SOURCES + [os.path.join(HERE, f) for f in os.listdir(HERE) if f.endswith(".cuh")] + \
     [os.path.join(ROOT, "include", "mpn.h")]
 

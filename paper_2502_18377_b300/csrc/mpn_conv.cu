@@ -1,0 +1,414 @@
+// Learned warm start: kernels of a small 3x3x3 convolutional network on the
+// (t, x, y) grid, BF16 activations and weights with FP32 accumulation.
+//
+// Layout: activations channels-last [B][N][C] (C = 16 or 32, zero-padded
+// channels), weights [27][Cout][Cin] (tap = (dt+1)*9 + (dx+1)*3 + (dy+1)),
+// biases FP32 [Cout].  Time is zero-padded; x and y wrap when periodic and are
+// zero-padded otherwise.
+//
+//   mpn_conv3d_forward        y = act(conv(x, W) + b)      tensor cores (mma.sync m16n8k16 bf16)
+//   mpn_conv3d_backward_data  dx = conv^T(dy, W)            same kernel on flipped, transposed W
+//   mpn_conv3d_backward_weights dW, db from dy and x       FP32 CUDA-core reduction, two stages
+//   mpn_relu_mask             g = dx * (y > 0) -> BF16
+//   mpn_adam_step             FP32 masters + BF16 copy
+//   mpn_pack_inputs / mpn_mse_u  data plumbing of the net
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstring>
+#include <cstdint>
+
+#include "../../include/mpn.h"
+
+namespace {
+
+struct CGrid {
+  int n[3], per[3], N;
+};
+
+CGrid make_cgrid(const mpn_conv_desc* d) {
+  CGrid g;
+  for (int k = 0; k < 3; ++k) { g.n[k] = d->n[k]; g.per[k] = d->periodic[k]; }
+  g.N = d->n[0] * d->n[1] * d->n[2];
+  return g;
+}
+
+__device__ __forceinline__ void cdecode(const CGrid& g, int p, int pos[3]) {
+  pos[2] = p % g.n[2];
+  int q = p / g.n[2];
+  pos[1] = q % g.n[1];
+  pos[0] = q / g.n[1];
+}
+
+// neighbour index of a point at offset (dt, dx, dy), or -1 (zero padding)
+__device__ __forceinline__ int cnbr(const CGrid& g, const int pos[3], int dt, int dx, int dy) {
+  int t = pos[0] + dt, x = pos[1] + dx, y = pos[2] + dy;
+  if (t < 0 || t >= g.n[0]) return -1;
+  if (x < 0 || x >= g.n[1]) { if (!g.per[1]) return -1; x = x < 0 ? x + g.n[1] : x - g.n[1]; }
+  if (y < 0 || y >= g.n[2]) { if (!g.per[2]) return -1; y = y < 0 ? y + g.n[2] : y - g.n[2]; }
+  return (t * g.n[1] + x) * g.n[2] + y;
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// Implicit-GEMM convolution: one warp computes 32 points x CO channels; the
+// A fragments (points x input channels of one tap) are gathered from the
+// channels-last input, the B fragments (input x output channels) from W.
+// FLAGS: bit 0 ReLU, bit 1 FP32 output (else BF16), bit 2 add bias.
+template <int CI, int CO, int FLAGS>
+__global__ void __launch_bounds__(128) k_conv(CGrid g, const __nv_bfloat16* __restrict__ x,
+                                              const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias,
+                                              void* __restrict__ out) {
+  constexpr int NT = CO / 8;   // n-tiles
+  constexpr int KS = CI / 16;  // k-steps per tap
+  extern __shared__ __align__(16) __nv_bfloat16 ws[];   // 27 * CO * CI weights
+  for (int i = threadIdx.x; i < 27 * CO * CI / 2; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(ws)[i] = reinterpret_cast<const uint32_t*>(w)[i];
+  __syncthreads();
+  const int b = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  const int base = (blockIdx.x * 4 + warp) * 32;
+  const __nv_bfloat16* xb = x + (size_t)b * g.N * CI;
+  // the four points of this thread: rows gid and gid+8 of m-tiles 0 and 1
+  int pt[4], pos[4][3];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    pt[r] = base + (r >> 1) * 16 + (r & 1) * 8 + gid;
+    if (pt[r] < g.N) cdecode(g, pt[r], pos[r]); else { pos[r][0] = -100; pos[r][1] = pos[r][2] = 0; }
+  }
+  float acc[2][NT][4];
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int n = 0; n < NT; ++n)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[m][n][k] = 0.f;
+  for (int tap = 0; tap < 27; ++tap) {
+    int dt = tap / 9 - 1, dx = (tap / 3) % 3 - 1, dy = tap % 3 - 1;
+    int nb[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) nb[r] = pos[r][0] < 0 ? -1 : cnbr(g, pos[r], dt, dx, dy);
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      uint32_t a[2][4];
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        int r0 = nb[2 * m], r1 = nb[2 * m + 1];
+        int c0 = ks * 16 + tig * 2;
+        a[m][0] = r0 >= 0 ? ld_pair(xb + (size_t)r0 * CI + c0) : 0u;
+        a[m][1] = r1 >= 0 ? ld_pair(xb + (size_t)r1 * CI + c0) : 0u;
+        a[m][2] = r0 >= 0 ? ld_pair(xb + (size_t)r0 * CI + c0 + 8) : 0u;
+        a[m][3] = r1 >= 0 ? ld_pair(xb + (size_t)r1 * CI + c0 + 8) : 0u;
+      }
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        const __nv_bfloat16* wr = ws + ((size_t)tap * CO + n * 8 + gid) * CI + ks * 16 + tig * 2;
+        uint32_t bb[2] = {ld_pair(wr), ld_pair(wr + 8)};
+        mma_bf16(acc[0][n], a[0], bb);
+        mma_bf16(acc[1][n], a[1], bb);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int p = pt[2 * m + h];
+      if (p >= g.N) continue;
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        int co = n * 8 + tig * 2;
+        float v0 = acc[m][n][2 * h], v1 = acc[m][n][2 * h + 1];
+        if (FLAGS & 4) { v0 += bias[co]; v1 += bias[co + 1]; }
+        if (FLAGS & 1) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+        size_t o = ((size_t)b * g.N + p) * CO + co;
+        if (FLAGS & 2) {
+          reinterpret_cast<float*>(out)[o] = v0;
+          reinterpret_cast<float*>(out)[o + 1] = v1;
+        } else {
+          __nv_bfloat162 pr = __floats2bfloat162_rn(v0, v1);
+          *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(out) + o) = pr;
+        }
+      }
+    }
+}
+
+// W'[tap][ci][co] = W[26 - tap][co][ci]: weights of the transposed convolution
+__global__ void k_flip_transpose(int CI, int CO, const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ wt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 27 * CI * CO) return;
+  int ci = i % CI, co = (i / CI) % CO, tap = i / (CI * CO);
+  wt[((size_t)(26 - tap) * CI + ci) * CO + co] = w[i];
+}
+
+// Weight gradient, stage 1: per (chunk of points, tap) partial sums
+// dW[tap][co][ci] = sum_p g[p][co] x[nbr(p, tap)][ci]   (FP32 accumulation)
+// and, for the centre tap, db[co] = sum_p g[p][co].
+template <int CI, int CO>
+__global__ void __launch_bounds__(256) k_wgrad_part(CGrid g, int B, int chunk, const __nv_bfloat16* __restrict__ gr,
+                                                    const __nv_bfloat16* __restrict__ x, float* __restrict__ part,
+                                                    float* __restrict__ bpart) {
+  constexpr int CPT = CI * CO / 256 > 0 ? CI * CO / 256 : 1;   // (co, ci) pairs per thread
+  constexpr int TPC = CI / CPT;                                  // threads per co
+  const int tap = blockIdx.y;
+  const int dt = tap / 9 - 1, dx = (tap / 3) % 3 - 1, dy = tap % 3 - 1;
+  const int t = threadIdx.x;
+  const int co = t / TPC, ci0 = (t % TPC) * CPT;
+  const bool active = co < CO;
+  float acc[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) acc[k] = 0.f;
+  float bacc = 0.f;
+  long long total = (long long)B * g.N;
+  long long p0 = (long long)blockIdx.x * chunk, p1 = p0 + chunk < total ? p0 + chunk : total;
+  for (long long pp = p0; pp < p1; ++pp) {
+    int b = (int)(pp / g.N), p = (int)(pp - (long long)b * g.N);
+    int pos[3]; cdecode(g, p, pos);
+    int q = cnbr(g, pos, dt, dx, dy);
+    if (!active) continue;
+    float gv = __bfloat162float(gr[((size_t)b * g.N + p) * CO + co]);
+    bacc += gv;
+    if (q < 0) continue;
+    const __nv_bfloat16* xr = x + ((size_t)b * g.N + q) * CI + ci0;
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) acc[k] += gv * __bfloat162float(xr[k]);
+  }
+  if (active) {
+    float* o = part + (((size_t)blockIdx.x * 27 + tap) * CO + co) * CI + ci0;
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) o[k] = acc[k];
+    if (tap == 13 && ci0 == 0) bpart[(size_t)blockIdx.x * CO + co] = bacc;
+  }
+}
+
+// stage 2: sum of the chunk partials in a fixed order
+__global__ void k_wgrad_reduce(int nchunk, int n, const float* __restrict__ part, float* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.f;
+  for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * n + i];
+  out[i] = s;
+}
+
+__global__ void k_relu_mask(long long n, const float* __restrict__ g, const __nv_bfloat16* __restrict__ y,
+                            __nv_bfloat16* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float v = g[i];
+  if (y && !(__bfloat162float(y[i]) > 0.f)) v = 0.f;
+  out[i] = __float2bfloat16_rn(v);
+}
+
+__global__ void k_adam(long long n, float* __restrict__ w, const float* __restrict__ gr, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2,
+                       __nv_bfloat16* __restrict__ wb) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float g = gr[i];
+  float mi = b1 * m[i] + (1.f - b1) * g;
+  float vi = b2 * v[i] + (1.f - b2) * g * g;
+  m[i] = mi; v[i] = vi;
+  float wi = w[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+  w[i] = wi;
+  if (wb) wb[i] = __float2bfloat16_rn(wi);
+}
+
+// x0[b][p][c] = channels (fields..., rhs) scaled, zero-padded to 16, BF16
+__global__ void k_pack(int N, int F, const float* __restrict__ fields, const float* __restrict__ rhs,
+                       const float* __restrict__ scale, __nv_bfloat16* __restrict__ x0, int B) {
+  int b = blockIdx.y;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+    __nv_bfloat16* o = x0 + ((size_t)b * N + p) * 16;
+    for (int c = 0; c < 16; ++c) {
+      float v = 0.f;
+      if (c < F) v = fields[((size_t)c * B + b) * N + p] * scale[c];
+      else if (c == F) v = rhs[(size_t)b * N + p] * scale[c];
+      o[c] = __float2bfloat16_rn(v);
+    }
+  }
+}
+
+// MSE on channel 0 of the FP32 output y [B][N][16] against target t [B][N]
+// (already divided by the output scale): g = 2 (y - t) / (B N) on channel 0,
+// and per-block partial losses.
+__global__ void k_mse_u(int N, const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ g,
+                        float* __restrict__ lpart, int B) {
+  __shared__ float sh[256];
+  int b = blockIdx.y;
+  float acc = 0.f;
+  float sc = 2.f / ((float)N * (float)B);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+    size_t o = ((size_t)b * N + p) * 16;
+    float r = y[o] - t[(size_t)b * N + p];
+    acc += r * r;
+    g[o] = sc * r;
+    for (int c = 1; c < 16; ++c) g[o + c] = 0.f;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) lpart[(size_t)b * gridDim.x + blockIdx.x] = sh[0];
+}
+
+// u0[b][p] = scale * y[b][p][0]
+__global__ void k_unpack_u(int N, const float* __restrict__ y, float scale, float* __restrict__ u0, int B) {
+  int b = blockIdx.y;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x)
+    u0[(size_t)b * N + p] = scale * y[((size_t)b * N + p) * 16];
+}
+
+int check(const mpn_conv_desc* d) {
+  if (!d || d->batch < 1) return MPN_ERR_INVALID_ARG;
+  for (int k = 0; k < 3; ++k) if (d->n[k] < 2) return MPN_ERR_INVALID_ARG;
+  if (d->periodic[0]) return MPN_ERR_INVALID_ARG;
+  if (!((d->cin == 16 && d->cout == 32) || (d->cin == 32 && (d->cout == 32 || d->cout == 16))))
+    return MPN_ERR_UNSUPPORTED;
+  return MPN_OK;
+}
+
+template <int CI, int CO, int FL>
+void launch_conv1(const CGrid& g, int B, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias, void* y,
+                  cudaStream_t st) {
+  const int smem = 27 * CI * CO * (int)sizeof(__nv_bfloat16);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv<CI, CO, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  dim3 gr((g.N + 127) / 128, B);
+  k_conv<CI, CO, FL><<<gr, 128, smem, st>>>(g, x, w, bias, y);
+}
+
+template <int CI, int CO>
+void launch_conv(const CGrid& g, int B, int flags, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias,
+                 void* y, cudaStream_t st) {
+  switch (flags) {
+    case 2: launch_conv1<CI, CO, 2>(g, B, x, w, bias, y, st); break;
+    case 5: launch_conv1<CI, CO, 5>(g, B, x, w, bias, y, st); break;
+    case 6: launch_conv1<CI, CO, 6>(g, B, x, w, bias, y, st); break;
+    default: launch_conv1<CI, CO, 0>(g, B, x, w, bias, y, st); break;
+  }
+}
+
+void conv_dispatch(const CGrid& g, int B, int ci, int co, int flags, const __nv_bfloat16* x, const __nv_bfloat16* w,
+                   const float* bias, void* y, cudaStream_t st) {
+  if (ci == 16 && co == 32) launch_conv<16, 32>(g, B, flags, x, w, bias, y, st);
+  else if (ci == 32 && co == 32) launch_conv<32, 32>(g, B, flags, x, w, bias, y, st);
+  else if (ci == 32 && co == 16) launch_conv<32, 16>(g, B, flags, x, w, bias, y, st);
+}
+
+}  // namespace
+
+extern "C" int mpn_conv3d_forward(const mpn_conv_desc* d, const void* x, const void* w, const float* bias, void* y,
+                                  int flags, void* stream) {
+  int s = check(d);
+  if (s) return s;
+  if (!x || !w || !y || ((flags & MPN_CONV_BIAS) && !bias)) return MPN_ERR_INVALID_ARG;
+  CGrid g = make_cgrid(d);
+  conv_dispatch(g, d->batch, d->cin, d->cout, flags & 7, (const __nv_bfloat16*)x, (const __nv_bfloat16*)w, bias, y,
+                (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
+}
+
+extern "C" int mpn_conv3d_backward_data(const mpn_conv_desc* d, const void* g_out, const void* w, void* wt_scratch,
+                                        float* g_in, void* stream) {
+  int s = check(d);
+  if (s) return s;
+  if (!g_out || !w || !wt_scratch || !g_in) return MPN_ERR_INVALID_ARG;
+  if (d->cin != 32) return MPN_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  CGrid g = make_cgrid(d);
+  int n = 27 * d->cin * d->cout;
+  k_flip_transpose<<<(n + 255) / 256, 256, 0, st>>>(d->cin, d->cout, (const __nv_bfloat16*)w,
+                                                    (__nv_bfloat16*)wt_scratch);
+  // transposed convolution = convolution of g_out (channels cout) with W'
+  if (d->cout == 32) launch_conv<32, 32>(g, d->batch, MPN_CONV_F32, (const __nv_bfloat16*)g_out,
+                                         (const __nv_bfloat16*)wt_scratch, nullptr, g_in, st);
+  else launch_conv<16, 32>(g, d->batch, MPN_CONV_F32, (const __nv_bfloat16*)g_out, (const __nv_bfloat16*)wt_scratch,
+                           nullptr, g_in, st);
+  return cudaGetLastError() == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
+}
+
+extern "C" size_t mpn_conv3d_wgrad_scratch_bytes(const mpn_conv_desc* d) {
+  if (check(d)) return 0;
+  long long total = (long long)d->batch * d->n[0] * d->n[1] * d->n[2];
+  long long nchunk = (total + MPN_WGRAD_CHUNK - 1) / MPN_WGRAD_CHUNK;
+  return (size_t)nchunk * (27 * d->cin * d->cout + d->cout) * sizeof(float);
+}
+
+extern "C" int mpn_conv3d_backward_weights(const mpn_conv_desc* d, const void* g_out, const void* x, float* scratch,
+                                           float* dw, float* db, void* stream) {
+  int s = check(d);
+  if (s) return s;
+  if (!g_out || !x || !scratch || !dw || !db) return MPN_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CGrid g = make_cgrid(d);
+  long long total = (long long)d->batch * g.N;
+  int nchunk = (int)((total + MPN_WGRAD_CHUNK - 1) / MPN_WGRAD_CHUNK);
+  int nw = 27 * d->cin * d->cout;
+  float* part = scratch;
+  float* bpart = scratch + (size_t)nchunk * nw;
+  dim3 gr(nchunk, 27);
+  const __nv_bfloat16* go = (const __nv_bfloat16*)g_out;
+  const __nv_bfloat16* xx = (const __nv_bfloat16*)x;
+  if (d->cin == 16 && d->cout == 32) k_wgrad_part<16, 32><<<gr, 256, 0, st>>>(g, d->batch, MPN_WGRAD_CHUNK, go, xx, part, bpart);
+  else if (d->cin == 32 && d->cout == 32) k_wgrad_part<32, 32><<<gr, 256, 0, st>>>(g, d->batch, MPN_WGRAD_CHUNK, go, xx, part, bpart);
+  else if (d->cin == 32 && d->cout == 16) k_wgrad_part<32, 16><<<gr, 256, 0, st>>>(g, d->batch, MPN_WGRAD_CHUNK, go, xx, part, bpart);
+  else return MPN_ERR_UNSUPPORTED;
+  k_wgrad_reduce<<<(nw + 255) / 256, 256, 0, st>>>(nchunk, nw, part, dw);
+  k_wgrad_reduce<<<(d->cout + 255) / 256, 256, 0, st>>>(nchunk, d->cout, bpart, db);
+  return cudaGetLastError() == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
+}
+
+extern "C" int mpn_relu_mask(long long n, const float* g, const void* y, void* out, void* stream) {
+  if (!g || !out || n < 0) return MPN_ERR_INVALID_ARG;
+  k_relu_mask<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, g, (const __nv_bfloat16*)y,
+                                                                            (__nv_bfloat16*)out);
+  return cudaGetLastError() == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
+}
+
+extern "C" int mpn_adam_step(long long n, float* w, const float* g, float* m, float* v, float lr, float beta1,
+                             float beta2, float eps, int step, void* w_bf16, void* stream) {
+  if (!w || !g || !m || !v || n < 0 || step < 1) return MPN_ERR_INVALID_ARG;
+  float c1 = 1.f / (1.f - powf(beta1, (float)step)), c2 = 1.f / (1.f - powf(beta2, (float)step));
+  k_adam<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, w, g, m, v, lr, beta1, beta2, eps, c1, c2,
+                                                                       (__nv_bfloat16*)w_bf16);
+  return cudaGetLastError() == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
+}
+
+extern "C" int mpn_pack_inputs(const mpn_conv_desc* d, int nfields, const float* fields, const float* rhs,
+                               const float* scale, void* x0, void* stream) {
+  if (!d || nfields < 0 || nfields > 15 || !rhs || !scale || !x0 || (nfields > 0 && !fields)) return MPN_ERR_INVALID_ARG;
+  int N = d->n[0] * d->n[1] * d->n[2];
+  dim3 gr((N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024, d->batch);
+  k_pack<<<gr, 256, 0, (cudaStream_t)stream>>>(N, nfields, fields, rhs, scale, (__nv_bfloat16*)x0, d->batch);
+  return cudaGetLastError() == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
+}
+
+extern "C" int mpn_mse_u(const mpn_conv_desc* d, const float* y, const float* target, float* g, float* loss_part,
+                         void* stream) {
+  if (!d || !y || !target || !g || !loss_part) return MPN_ERR_INVALID_ARG;
+  int N = d->n[0] * d->n[1] * d->n[2];
+  dim3 gr(MPN_MSE_BLOCKS, d->batch);
+  k_mse_u<<<gr, 256, 0, (cudaStream_t)stream>>>(N, y, target, g, loss_part, d->batch);
+  return cudaGetLastError() == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
+}
+
+extern "C" int mpn_unpack_u(const mpn_conv_desc* d, const float* y, float scale, float* u0, void* stream) {
+  if (!d || !y || !u0) return MPN_ERR_INVALID_ARG;
+  int N = d->n[0] * d->n[1] * d->n[2];
+  dim3 gr((N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024, d->batch);
+  k_unpack_u<<<gr, 256, 0, (cudaStream_t)stream>>>(N, y, scale, u0, d->batch);
+  return cudaGetLastError() == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
+}
