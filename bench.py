@@ -188,7 +188,7 @@ def run_ours(args):
         ev[k][1].record()
         stats.append((sf, sa))
     torch.cuda.synchronize()
-    prof_ms, prof_n, prof_bytes = s.profile(0)
+    prof_ms, prof_n, prof_bytes, kernels = s.profile(0)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
@@ -198,6 +198,7 @@ def run_ours(args):
     clk = clocks.stop()
 
     # end to end: host buffers through the public API (pinned H2D, D2H of the gradients)
+    e2e = None
     pin = lambda a: torch.from_numpy(a).pin_memory()
     hF, hS, hR, hO, hT = pin(fields), pin(scal), pin(rhs), pin(om), pin(tgt)
     h_out = [torch.empty((s.F, B, N)).pin_memory(), torch.empty((V, B)).pin_memory(),
@@ -214,19 +215,21 @@ def run_ours(args):
             dst.copy_(src, non_blocking=True)
         torch.cuda.current_stream().synchronize()
 
-    e2e_step()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e2e_ms = []
-    for k in range(max(1, min(args.steps, 5))):
-        flush.fill_(float(k))
-        e0.record()
+    if not args.no_e2e:
         e2e_step()
-        e1.record()
         torch.cuda.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-    e2e_v = world * B * N / (statistics.mean(e2e_ms) / 1e3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2e_ms = []
+        for k in range(max(1, min(args.steps, 5))):
+            flush.fill_(float(k))
+            e0.record()
+            e2e_step()
+            e1.record()
+            torch.cuda.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+        e2e = {"value": world * B * N / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank != 0:
         if world > 1:
@@ -235,8 +238,6 @@ def run_ours(args):
     peaks, src = _peaks()
     hbm = float(peaks["hbm_gbs"])
     achieved = (prof_bytes / prof_n) / (prof_ms / prof_n / 1e3) / 1e9 if prof_n else None
-    # kernels launched per step: count from the solver's structure
-    launches = int(os.environ.get("MPN_LAUNCHES_PER_STEP", "0")) or None
     value = world * B * N / (ms / 1e3)
     cpu = None
     if not args.no_cpu_baseline:
@@ -258,8 +259,9 @@ def run_ours(args):
                      "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.4 TB/s",
                      "launches": prof_n, "avg_launch_us": 1e3 * prof_ms / prof_n if prof_n else None},
         "clocks": clk,
-        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches,
+        "e2e": e2e,
+        "gpu_launches": kernels,
+        "gpu_launches_per_step": kernels / args.steps,
         "solver": {"forward": sf, "adjoint": sa},
         "cpu_baseline": cpu,
     }
@@ -275,6 +277,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

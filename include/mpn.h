@@ -144,9 +144,11 @@ int mpn_apply_reduced(mpn_problem* p, const float* fields, const float* scalars,
  * dominant kernel work): CUDA events around each of its launches on the
  * solve stream.  Reads the totals accumulated since the last reset (time in
  * ms, launches, algorithmic bytes = 4 (7 + F) N B per launch: e, d, r, Dinv,
- * rho and the F fields read once, e and d written); then, if enable >= 0,
- * switches timing on (1) or off (0) and resets the totals. */
-int mpn_profile(mpn_problem* p, int enable, double* ms_total, long long* launches, double* bytes);
+ * rho and the F fields read once, e and d written) and the number of kernels
+ * this problem launched; then, if enable >= 0, switches timing on (1) or off
+ * (0) and resets the totals.  Outputs are host pointers (nullable). */
+int mpn_profile(mpn_problem* p, int enable, double* ms_total, long long* launches, double* bytes,
+                long long* kernels);
 
 /* Allocation-free variant of mpn_apply_reduced.  The paper has no
  * counterpart: it exists for callers that cannot allocate device memory

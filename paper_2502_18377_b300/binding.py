@@ -56,7 +56,8 @@ EXPORTS = {
     "mpn_mse_grad": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "mpn_apply_reduced": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "mpn_profile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
-                                   ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
+                                   ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_longlong)]),
     "mpn_apply_reduced_noalloc": (ctypes.c_int, [ctypes.POINTER(MpnDesc), _P, _P, _P, _P, _P]),
     "mpn_conv3d_forward": (ctypes.c_int, [ctypes.POINTER(MpnConvDesc), _P, _P, _P, _P, ctypes.c_int, _P]),
     "mpn_conv3d_backward_data": (ctypes.c_int, [ctypes.POINTER(MpnConvDesc), _P, _P, _P, _P, _P]),
@@ -260,11 +261,12 @@ class Solver:
         return g_z
 
     def profile(self, enable=-1):
-        """Returns (ms, launches, bytes) of the timed smoothing steps since the
-        last reset; enable=1/0 then switches timing on/off and resets."""
-        ms, n, by = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
-        self.lib.mpn_profile(self._h, enable, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by))
-        return ms.value, n.value, by.value
+        """Returns (ms, launches, bytes, kernels): the timed smoothing steps and
+        the kernels launched since the last reset; enable=1/0 then switches
+        timing on/off and resets."""
+        ms, n, by, k = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_longlong()
+        self.lib.mpn_profile(self._h, enable, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by), ctypes.byref(k))
+        return ms.value, n.value, by.value, k.value
 
     def apply_reduced(self, fields, scalars, u):
         q = torch.empty_like(u)

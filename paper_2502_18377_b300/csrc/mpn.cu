@@ -79,6 +79,7 @@ struct mpn_problem {
   std::vector<cudaEvent_t> prof_ev;
   double prof_ms = 0, prof_bytes = 0;
   long long prof_n = 0;
+  long long nlaunch = 0;   // kernels launched since the last mpn_profile reset
 };
 
 enum { S_RZ = 0, S_PQ, S_RN, S_DU, S_UN, S_PW, S_GN, S_GR0, NSLOT = S_GR0 + 8 };
@@ -333,17 +334,17 @@ static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st
   if (!a.dinv) a.dinv = l.dinv;
   if (l.vec4) {
     dim3 g4(sblk(l.g.N / 4), p->B);
-    k_Ly4<<<g4, MPN_TPB, 0, st>>>(l.g, cf, l.rho, a.x, l.y);
+    ++p->nlaunch, k_Ly4<<<g4, MPN_TPB, 0, st>>>(l.g, cf, l.rho, a.x, l.y);
     switch (mode) {
-      case SM_POST0: k_LTy4<SM_POST0><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
-      case SM_CHEB: k_LTy4<SM_CHEB><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
-      case SM_RES: k_LTy4<SM_RES><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
-      default: k_LTy4<SM_APPLY><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
+      case SM_POST0: ++p->nlaunch, k_LTy4<SM_POST0><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
+      case SM_CHEB: ++p->nlaunch, k_LTy4<SM_CHEB><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
+      case SM_RES: ++p->nlaunch, k_LTy4<SM_RES><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
+      default: ++p->nlaunch, k_LTy4<SM_APPLY><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
     }
     return;
   }
   dim3 gr(sblk(l.g.N), p->B);
-#define LTY(DD, MM) k_LTy<DD, MM><<<gr, MPN_TPB, 0, st>>>(l.g, cf, a)
+#define LTY(DD, MM) ++p->nlaunch, k_LTy<DD, MM><<<gr, MPN_TPB, 0, st>>>(l.g, cf, a)
 #define LTY_D(DD)                                   \
   switch (mode) {                                   \
     case SM_POST0: LTY(DD, SM_POST0); break;        \
@@ -352,10 +353,10 @@ static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st
     default: LTY(DD, SM_APPLY); break;              \
   }
   if (p->D == 3) {
-    k_Ly<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, a.x, l.y);
+    ++p->nlaunch, k_Ly<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, a.x, l.y);
     LTY_D(3)
   } else {
-    k_Ly<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, a.x, l.y);
+    ++p->nlaunch, k_Ly<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, a.x, l.y);
     LTY_D(2)
   }
 #undef LTY_D
@@ -381,7 +382,7 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
   CK(cudaMemcpyAsync(p->scalars, scalars, sizeof(float) * (size_t)V * B, cudaMemcpyDeviceToDevice, st));
   {
     Coef cf = make_coef(p, l0.fields);
-    k_rho_fine<<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, p->rho64);
+    ++p->nlaunch, k_rho_fine<<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, p->rho64);
     CKL();
   }
   for (int k = 1; k < p->L; ++k) {
@@ -390,8 +391,8 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
     int nd = lf.cz[0] + lf.cz[1] + lf.cz[2];
     dim3 gf(nblk(lc.g.N), F * B);
     if (F > 0)
-      k_restrict_field<<<gf, MPN_TPB, 0, st>>>(lf.g, lc.g, lf.cz[0], lf.cz[1], lf.cz[2], lf.fields, lc.fields, 1.f);
-    k_restrict_field<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(lf.g, lc.g, lf.cz[0], lf.cz[1], lf.cz[2], lf.rho,
+      ++p->nlaunch, k_restrict_field<<<gf, MPN_TPB, 0, st>>>(lf.g, lc.g, lf.cz[0], lf.cz[1], lf.cz[2], lf.fields, lc.fields, 1.f);
+    ++p->nlaunch, k_restrict_field<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(lf.g, lc.g, lf.cz[0], lf.cz[1], lf.cz[2], lf.rho,
                                                                lc.rho, (float)(1 << nd));
     CKL();
   }
@@ -399,29 +400,29 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
     Level& l = p->lv[k];
     Coef cf = make_coef(p, l.fields);
     dim3 gr(nblk(l.g.N), B);
-    k_diag_inv<<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.dinv);
+    ++p->nlaunch, k_diag_inv<<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.dinv);
     CKL();
     if (k == p->L - 1) break;
     // power method for lambda_max(Dinv S)
-    k_fill_hash<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.t);
+    ++p->nlaunch, k_fill_hash<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.t);
     double* pw = slot(p, S_PW);
     for (int it = 0; it < 12; ++it) {
       TRY(apply_S(p, k, l.t, l.d, nullptr, st));
-      k_power_w<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.dinv, l.d, l.e, pw);
-      if (it < 11) k_power_norm<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.e, l.t, pw, gr.x);
+      ++p->nlaunch, k_power_w<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.dinv, l.d, l.e, pw);
+      if (it < 11) ++p->nlaunch, k_power_norm<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.e, l.t, pw, gr.x);
     }
-    k_scale_dinv<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.dinv, pw, gr.x, 1.1f, p->lam + k * B);
+    ++p->nlaunch, k_scale_dinv<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.dinv, pw, gr.x, 1.1f, p->lam + k * B);
     CKL();
   }
   // coarsest: banded assembly, Cholesky, explicit inverse
   Level& lc = p->lv[p->L - 1];
   Coef cfc = make_coef(p, lc.fields);
   CK(cudaMemsetAsync(p->ferr, 0, sizeof(int) * B, st));
-  k_coarse_assemble<<<dim3(nblk(p->M), B), MPN_TPB, 0, st>>>(lc.g, cfc, lc.rho, p->bw, p->Kband);
+  ++p->nlaunch, k_coarse_assemble<<<dim3(nblk(p->M), B), MPN_TPB, 0, st>>>(lc.g, cfc, lc.rho, p->bw, p->Kband);
   size_t smem = sizeof(float) * (size_t)p->M * (p->bw + 1);
   CK(cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_coarse_factor<<<B, 512, smem, st>>>(p->M, p->bw, p->Kband, p->ferr);
-  k_coarse_inverse<<<dim3((p->M + 127) / 128, B), 128, sizeof(float) * (p->bw + 1) * 128, st>>>(p->M, p->bw, p->Kband,
+  ++p->nlaunch, k_coarse_factor<<<B, 512, smem, st>>>(p->M, p->bw, p->Kband, p->ferr);
+  ++p->nlaunch, k_coarse_inverse<<<dim3((p->M + 127) / 128, B), 128, sizeof(float) * (p->bw + 1) * 128, st>>>(p->M, p->bw, p->Kband,
                                                                                                 p->Kinv);
   CKL();
   p->setup_ok = true;
@@ -434,7 +435,7 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   int B = p->B;
   dim3 gr(nblk(l.g.N), B);
   if (k == p->L - 1) {
-    k_coarse_solve<<<dim3((p->M * 32 + MPN_TPB - 1) / MPN_TPB, B), MPN_TPB, 0, st>>>(p->M, p->Kinv, l.r, l.e);
+    ++p->nlaunch, k_coarse_solve<<<dim3((p->M * 32 + MPN_TPB - 1) / MPN_TPB, B), MPN_TPB, 0, st>>>(p->M, p->Kinv, l.r, l.e);
     CKL();
     return MPN_OK;
   }
@@ -444,7 +445,7 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   memset(&a, 0, sizeof(a));
   a.r = l.r; a.x = l.e; a.e = l.e; a.d = l.d;
   // pre-smoothing from e = 0: d = Dinv r / th, e = d
-  k_cheb_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, l.e, l.d);
+  ++p->nlaunch, k_cheb_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, l.e, l.d);
   for (int s = 1; s < m; ++s) {
     a.c1 = p->cheb_c1[s]; a.c2 = p->cheb_c2[s];
     if (prof) prof_mark(p, st);
@@ -455,10 +456,10 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   a.out = l.t;
   stencil(p, k, a, SM_RES, st);
   Level& lc = p->lv[k + 1];
-  k_restrict_vec<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], l.t, lc.r);
+  ++p->nlaunch, k_restrict_vec<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], l.t, lc.r);
   CKL();
   TRY(vcycle(p, k + 1, st));
-  k_prolong_add<<<gr, MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], lc.e, nullptr, l.e);
+  ++p->nlaunch, k_prolong_add<<<gr, MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], lc.e, nullptr, l.e);
   // post-smoothing
   a.c1 = 0.f; a.c2 = p->cheb_inv_th;
   stencil(p, k, a, SM_POST0, st);
@@ -477,7 +478,7 @@ static int precond(mpn_problem* p, cudaStream_t st) {
   Level& l = p->lv[0];
   TRY(vcycle(p, 0, st));
   dim3 gr(nblk(l.g.N), p->B);
-  k_final_z<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.e, nullptr, l.r, p->z, slot(p, S_RZ));
+  ++p->nlaunch, k_final_z<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.e, nullptr, l.r, p->z, slot(p, S_RZ));
   CKL();
   return MPN_OK;
 }
@@ -489,15 +490,15 @@ static int pcg(mpn_problem* p, int iters, cudaStream_t st) {
   int P = gr.x;
   double* rz_old = p->dscal + p->B;
   TRY(precond(p, st));
-  k_pcg_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, p->z, p->x, p->pv);
+  ++p->nlaunch, k_pcg_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, p->z, p->x, p->pv);
   for (int it = 0; it < iters; ++it) {
     TRY(apply_S(p, 0, p->pv, p->q, slot(p, S_PQ), st));
-    k_pcg_xr<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), slot(p, S_PQ), l.papply, P, p->pv, p->q, p->x, l.r,
+    ++p->nlaunch, k_pcg_xr<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), slot(p, S_PQ), l.papply, P, p->pv, p->q, p->x, l.r,
                                      rz_old);
     CKL();
     if (it == iters - 1) break;
     TRY(precond(p, st));
-    k_pcg_p<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), P, rz_old, p->z, p->pv);
+    ++p->nlaunch, k_pcg_p<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), P, rz_old, p->z, p->pv);
     CKL();
   }
   return MPN_OK;
@@ -514,11 +515,11 @@ static int residual64(mpn_problem* p, const double* u, const double* g_adj, doub
   const float* src = g_adj ? nullptr : p->rhs;
   const float* om = g_adj ? nullptr : p->omega;
   if (p->D == 3) {
-    k_res64_y<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
-    k_res64_q<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
+    ++p->nlaunch, k_res64_y<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    ++p->nlaunch, k_res64_q<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
   } else {
-    k_res64_y<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
-    k_res64_q<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
+    ++p->nlaunch, k_res64_y<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    ++p->nlaunch, k_res64_q<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
   }
   CKL();
   return MPN_OK;
@@ -544,17 +545,17 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
   int iters = p->desc.inner_iters, total_iters = 0;
   for (int sweep = 0; sweep < p->desc.max_refine; ++sweep) {
     TRY(residual64(p, p->u64, g_adj, p->r64, slot(p, S_RN), st));
-    k_to32<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN), P, l.r, scale);
+    ++p->nlaunch, k_to32<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN), P, l.r, scale);
     CKL();
     TRY(pcg(p, iters, st));
     total_iters += iters;
-    k_update64<<<gr, MPN_TPB, 0, st>>>(N, p->x, scale, p->u64, slot(p, S_DU), slot(p, S_UN));
+    ++p->nlaunch, k_update64<<<gr, MPN_TPB, 0, st>>>(N, p->x, scale, p->u64, slot(p, S_DU), slot(p, S_UN));
     {
       // correction and solution sizes measured on every unknown of z
-      k_znorm<<<gr, MPN_TPB, 0, st>>>(l.g, p->u64, p->x, scale, slot(p, S_DU), slot(p, S_UN));
+      ++p->nlaunch, k_znorm<<<gr, MPN_TPB, 0, st>>>(l.g, p->u64, p->x, scale, slot(p, S_DU), slot(p, S_UN));
     }
     // slots S_RN, S_DU, S_UN, (S_PW unused), S_GN -> outv
-    k_collect<<<B, 64, 0, st>>>(B, 5, slot(p, S_RN), P, outv);
+    ++p->nlaunch, k_collect<<<B, 64, 0, st>>>(B, 5, slot(p, S_RN), P, outv);
     CKL();
     CK(cudaMemcpyAsync(p->hbuf, outv, sizeof(double) * 5 * B, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -603,13 +604,13 @@ static int forward_impl(mpn_problem* p, const float* fields, const float* scalar
   CK(cudaMemcpyAsync(p->rhs, rhs, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(p->omega, omega, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
   dim3 gr(nblk(l.g.N), B);
-  k_set_u<<<gr, MPN_TPB, 0, st>>>(l.g.N, u0, p->u64);
+  ++p->nlaunch, k_set_u<<<gr, MPN_TPB, 0, st>>>(l.g.N, u0, p->u64);
   CKL();
   p->zd_valid = false;
   int status = refine_solve(p, nullptr, u0 == nullptr, stats, st);
   if (status != MPN_OK && status != MPN_ERR_NOT_CONVERGED) return status;
   Coef cf = make_coef(p, l.fields);
-  k_recover<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
+  ++p->nlaunch, k_recover<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
   CKL();
   CK(cudaMemcpyAsync(p->uf64, p->u64, sizeof(double) * N0, cudaMemcpyDeviceToDevice, st));
   p->zd_valid = true;
@@ -648,15 +649,15 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
   }
   Coef cf = make_coef(p, l.fields);
   // reduced right-hand side g_u - M_{u zeta} M_{zeta zeta}^{-1} g_zeta (FP64)
-  k_adj_kappa<<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
-  k_adj_rhs<<<gr, MPN_TPB, 0, st>>>(l.g, g_z, p->kap, p->g64);
-  k_set_u<<<gr, MPN_TPB, 0, st>>>(l.g.N, nullptr, p->u64);
+  ++p->nlaunch, k_adj_kappa<<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
+  ++p->nlaunch, k_adj_rhs<<<gr, MPN_TPB, 0, st>>>(l.g, g_z, p->kap, p->g64);
+  ++p->nlaunch, k_set_u<<<gr, MPN_TPB, 0, st>>>(l.g.N, nullptr, p->u64);
   CKL();
   int status = refine_solve(p, p->g64, true, stats, st);
   if (status != MPN_OK && status != MPN_ERR_NOT_CONVERGED) return status;
   double* gp = slot(p, S_GR0);
-  k_gradients<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->rhs, p->uf64, p->u64, g_z, dfields, drhs, domega, dz, gp);
-  k_scalar_grads<<<B, 64, 0, st>>>(V, B, p->field_of_dev, gp, gr.x, dscalars);
+  ++p->nlaunch, k_gradients<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->rhs, p->uf64, p->u64, g_z, dfields, drhs, domega, dz, gp);
+  ++p->nlaunch, k_scalar_grads<<<B, 64, 0, st>>>(V, B, p->field_of_dev, gp, gr.x, dscalars);
   CKL();
   CK(cudaStreamSynchronize(st));
   return status;
@@ -665,7 +666,7 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
 extern "C" int mpn_mse_grad(mpn_problem* p, const float* z, const float* target, float* g_z, void* stream) {
   if (!p || !z || !target || !g_z) return MPN_ERR_INVALID_ARG;
   Level& l = p->lv[0];
-  k_mse_grad<<<dim3(nblk(l.g.N), p->B), MPN_TPB, 0, (cudaStream_t)stream>>>(l.g.N, p->V, p->B, z, target, g_z);
+  ++p->nlaunch, k_mse_grad<<<dim3(nblk(l.g.N), p->B), MPN_TPB, 0, (cudaStream_t)stream>>>(l.g.N, p->V, p->B, z, target, g_z);
   CKL();
   return MPN_OK;
 }
@@ -681,11 +682,13 @@ extern "C" int mpn_apply_reduced(mpn_problem* p, const float* fields, const floa
   return MPN_OK;
 }
 
-extern "C" int mpn_profile(mpn_problem* p, int enable, double* ms_total, long long* launches, double* bytes) {
+extern "C" int mpn_profile(mpn_problem* p, int enable, double* ms_total, long long* launches, double* bytes,
+                           long long* kernels) {
   if (!p) return MPN_ERR_INVALID_ARG;
   if (ms_total) *ms_total = p->prof_ms;
   if (launches) *launches = p->prof_n;
   if (bytes) *bytes = p->prof_bytes;
+  if (kernels) *kernels = p->nlaunch;
   if (enable >= 0) {
     if (enable && p->prof_ev.empty()) {
       p->prof_ev.resize(2 * PROF_PAIRS);
@@ -694,6 +697,7 @@ extern "C" int mpn_profile(mpn_problem* p, int enable, double* ms_total, long lo
     p->prof_on = enable;
     p->prof_used = 0;
     p->prof_ms = 0; p->prof_n = 0; p->prof_bytes = 0;
+    p->nlaunch = 0;
   }
   return MPN_OK;
 }

@@ -1,0 +1,80 @@
+"""Full-size checks in the benchmark's launch configuration.
+
+* Linearized Burgers at its full size (B = 32, 128 x 256): the oracle solves
+  sampled instances exactly; forward z and the gradients must match (1e-6 /
+  1e-5 relative L2).
+* Reaction-diffusion at the benchmark size (B = 16, 32 x 64 x 64): a direct
+  solve per instance is out of the oracle's reach, so the check is a property
+  that holds at any size: the oracle assembles A and d of sampled instances
+  and evaluates the FP64 normal-equation residual ||A^T (d - A z)|| / ||A^T d||
+  of the solver's FP64 output (Eq. 9), and the dual lambda = d - A z must be
+  orthogonal to the columns of A in the same sense (it is the same quantity).
+  Bound: the refinement stops at a predicted relative error of 1e-7 in z; with
+  ||A^T A|| ||z|| / ||A^T d|| of order 1e2..1e3 for these instances, the
+  residual of a 1e-6-accurate z is below 1e-6 — the test requires 1e-7.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import assemble as asm
+from oracle import grad as og
+from oracle import solve as osv
+from paper_2502_18377_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _round(w):
+    r = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    return wl.Workload(w.name, w.geom, list(w.field_of), r(w.scalars), r(w.fields), r(w.rhs), r(w.omega),
+                       None if w.target is None else r(w.target))
+
+
+def _dev(a):
+    return torch.tensor(np.asarray(a, dtype=np.float32), device="cuda").contiguous()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_burgers_full_size_sampled_instances():
+    from paper_2502_18377_b300.binding import Solver
+    w = _round(wl.linearized_burgers_1d())          # B = 32, 128 x 256
+    s = Solver(w.geom, w.batch, w.field_of, w.fields.shape[0])
+    args = (_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega))
+    z = s.forward(*args)
+    tgt = _dev(w.target)
+    gz = s.mse_grad(z, tgt)
+    dfields, dscal, drhs, dom = s.adjoint(*args, z, gz, reuse_setup=True)
+    zc, gzc = z.cpu().numpy(), gz.cpu().numpy().astype(np.float64)
+    dfields, drhs, dom = dfields.cpu().numpy(), drhs.cpu().numpy(), dom.cpu().numpy()
+    V, N = 5, w.npoints
+    for b in (0, 17, 31):
+        A, d, kind, owner = asm.assemble(w.geom, w.full_coeff()[:, b], w.rhs[b], w.omega[b])
+        zr, lam, el = osv.solve_lsq_elim(A, d, V)
+        assert _rel(zc[b].ravel(), zr) <= 1e-6, (b, _rel(zc[b].ravel(), zr))
+        dz, dlam = og.adjoint_elim(el, gzc[b].ravel())
+        dc, db, dw = og.gradients(w.geom, A, d, kind, owner, zr, lam, dz, dlam)
+        assert _rel(dfields[0, b], dc[3]) <= 1e-5
+        assert _rel(drhs[b], db) <= 1e-5
+        assert _rel(dom[b], dw) <= 1e-5
+
+
+def test_reaction_diffusion_bench_size_residual():
+    from paper_2502_18377_b300.binding import Solver
+    w = _round(wl.reaction_diffusion_2d())          # B = 16, 32 x 64 x 64
+    s = Solver(w.geom, w.batch, w.field_of, w.fields.shape[0])
+    args = (_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega))
+    z64 = torch.empty((w.batch, 7, w.npoints), device="cuda", dtype=torch.float64)
+    z = s.forward(*args, z64=z64)
+    stats = dict(s.last_stats)
+    z64c = z64.cpu().numpy()
+    zc = z.cpu().numpy()
+    for b in (0, 7, 15):
+        A, d, kind, owner = asm.assemble(w.geom, w.full_coeff()[:, b], w.rhs[b], w.omega[b])
+        res = osv.normal_residual(A, d, z64c[b].ravel())
+        assert res <= 1e-7, (b, res, stats)
+        # the FP32 output is the FP64 one rounded
+        assert _rel(zc[b].ravel(), z64c[b].ravel()) <= 1e-7
