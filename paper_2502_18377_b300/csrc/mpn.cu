@@ -75,11 +75,18 @@ struct mpn_problem {
   float cheb_c1[32], cheb_c2[32], cheb_inv_th;
   std::vector<void*> allocs;
   // live timing of the finest-level smoothing step (events on the solve stream)
-  int prof_on = 0, prof_used = 0;
+  int prof_on = 0;
   std::vector<cudaEvent_t> prof_ev;
   double prof_ms = 0, prof_bytes = 0;
   long long prof_n = 0;
   long long nlaunch = 0;   // kernels launched since the last mpn_profile reset
+  int prof_next = 0;       // next free event of the pool (graphs keep theirs)
+  // one CUDA graph per (solve kind, inner iterations, profiling): a whole
+  // refinement sweep, replayed on an internal stream
+  struct SweepGraph { int adjoint, iters, prof; cudaGraphExec_t exec; long long kernels; int ev0, ev1; };
+  std::vector<SweepGraph> graphs;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_user = nullptr;
 };
 
 enum { S_RZ = 0, S_PQ, S_RN, S_DU, S_UN, S_PW, S_GN, S_GR0, NSLOT = S_GR0 + 8 };
@@ -176,6 +183,9 @@ extern "C" const char* mpn_last_cuda_error(void) { return g_cuda_err; }
 
 extern "C" void mpn_destroy(mpn_problem* p) {
   if (!p) return;
+  for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+  if (p->gstream) cudaStreamDestroy(p->gstream);
+  if (p->ev_user) cudaEventDestroy(p->ev_user);
   for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
   for (void* a : p->allocs) cudaFree(a);
   if (p->hbuf) cudaFreeHost(p->hbuf);
@@ -255,7 +265,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   p->M = lc.g.N;
   int plane = lc.g.n[1] * lc.g.n[2];
   p->bw = std::min(p->M - 1, 3 * plane - 1);
-  if (p->M > d.max_coarse || (size_t)p->M * (p->bw + 1) * sizeof(float) > 200 * 1024) {
+  if (p->M > d.max_coarse || p->bw >= 256 || (size_t)p->M * (p->bw + 1) * sizeof(float) > 200 * 1024) {
     delete p;
     return MPN_ERR_UNSUPPORTED;
   }
@@ -288,8 +298,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   for (int v = 0; v < 8; ++v) fo[v] = v < V ? d.field_of[v] : -1;
   if (cudaMemcpy(p->field_of_dev, fo, sizeof(fo), cudaMemcpyHostToDevice) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
   if (cudaMallocHost((void**)&p->hbuf, sizeof(double) * 16 * B) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
-  cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)std::max(sizeof(float) * (p->bw + 1) * 128, (size_t)48 * 1024));
+  cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 
   // Chebyshev coefficients on [lo, 1] for Dinv scaled by 1 / lambda_max
   const double lo = 0.1, th = (1.0 + lo) / 2, de = (1.0 - lo) / 2, sg = th / de;
@@ -307,24 +316,30 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
 
 // ------------------------------------------------------------------ pieces
 #define PROF_PAIRS 1024
+// Events are recorded only while a sweep graph is being captured; each graph
+// owns the range of the pool it recorded into.
 static void prof_mark(mpn_problem* p, cudaStream_t st) {
-  if (!p->prof_on || p->prof_used >= 2 * PROF_PAIRS) return;
-  cudaEventRecord(p->prof_ev[p->prof_used++], st);
+  if (!p->prof_on || p->prof_next >= 2 * PROF_PAIRS) return;
+  // inside stream capture a timing event must be an external event-record node
+  if (cudaEventRecordWithFlags(p->prof_ev[p->prof_next], st, cudaEventRecordExternal) == cudaSuccess)
+    ++p->prof_next;
+  else
+    (void)cudaGetLastError();
 }
-// Accumulates the recorded (start, end) pairs; the stream has been synchronised.
-static void prof_flush(mpn_problem* p) {
+// Accumulates the (start, end) pairs of events [e0, e1); the graph that
+// recorded them has completed.
+static void prof_flush(mpn_problem* p, int e0, int e1) {
   if (!p->prof_on) return;
   const Level& l = p->lv[0];
   // algorithmic bytes of one smoothing step on the finest grid: read e, d, r,
   // dinv, rho and the F coefficient fields once, write e and d (FP32)
   double bytes = 4.0 * (7 + p->F) * (double)l.g.N * p->B;
-  for (int k = 0; k + 1 < p->prof_used; k += 2) {
+  for (int k = e0; k + 1 < e1; k += 2) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, p->prof_ev[k], p->prof_ev[k + 1]) == cudaSuccess) {
       p->prof_ms += ms; p->prof_n += 1; p->prof_bytes += bytes;
     }
   }
-  p->prof_used = 0;
 }
 // One operator pass pair at level k: y = -rho L x, then the mode's update.
 static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st) {
@@ -422,8 +437,15 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
   size_t smem = sizeof(float) * (size_t)p->M * (p->bw + 1);
   CK(cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ++p->nlaunch, k_coarse_factor<<<B, 512, smem, st>>>(p->M, p->bw, p->Kband, p->ferr);
-  ++p->nlaunch, k_coarse_inverse<<<dim3((p->M + 127) / 128, B), 128, sizeof(float) * (p->bw + 1) * 128, st>>>(p->M, p->bw, p->Kband,
-                                                                                                p->Kinv);
+  {
+    const int nt = 64;
+    int ws = 64;
+    while (ws <= p->bw) ws *= 2;
+    size_t band = sizeof(float) * (size_t)p->M * (p->bw + 1), win = sizeof(float) * ws * nt;
+    int in_smem = band + win <= 200 * 1024;
+    ++p->nlaunch, k_coarse_inverse<<<dim3((p->M + nt - 1) / nt, B), nt, win + (in_smem ? band : 0), st>>>(
+        p->M, p->bw, ws - 1, in_smem, p->Kband, p->Kinv);
+  }
   CKL();
   p->setup_ok = true;
   return MPN_OK;
@@ -525,41 +547,84 @@ static int residual64(mpn_problem* p, const double* u, const double* g_adj, doub
   return MPN_OK;
 }
 
+// The work of one refinement sweep on stream `st`: FP64 residual, inner PCG,
+// FP64 update, the sizes the stop rule needs, and their copy to the host.
+static int sweep_body(mpn_problem* p, const double* g_adj, int iters, int P, cudaStream_t st) {
+  Level& l = p->lv[0];
+  int B = p->B, N = l.g.N;
+  dim3 gr(P, B);
+  double* scale = p->dscal;
+  double* outv = p->dscal + 2 * B;  // [slots][B]
+  TRY(residual64(p, p->u64, g_adj, p->r64, slot(p, S_RN), st));
+  ++p->nlaunch, k_to32<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN), P, l.r, scale);
+  CKL();
+  TRY(pcg(p, iters, st));
+  ++p->nlaunch, k_update64<<<gr, MPN_TPB, 0, st>>>(N, p->x, scale, p->u64, slot(p, S_DU), slot(p, S_UN));
+  // correction and solution sizes measured on every unknown of z
+  ++p->nlaunch, k_znorm<<<gr, MPN_TPB, 0, st>>>(l.g, p->u64, p->x, scale, slot(p, S_DU), slot(p, S_UN));
+  // slots S_RN, S_DU, S_UN, (S_PW unused), S_GN -> outv
+  ++p->nlaunch, k_collect<<<B, 64, 0, st>>>(B, 5, slot(p, S_RN), P, outv);
+  CKL();
+  CK(cudaMemcpyAsync(p->hbuf, outv, sizeof(double) * 5 * B, cudaMemcpyDeviceToHost, st));
+  return MPN_OK;
+}
+
+// One refinement sweep, as a CUDA graph replayed on the problem's internal
+// stream (captured on first use for this solve kind, inner-iteration count and
+// profiling state).  Ordered after the caller's stream; returns once the
+// sweep's scalars are on the host.
+static int run_sweep(mpn_problem* p, const double* g_adj, int iters, int P, cudaStream_t st) {
+  if (!p->gstream) {
+    CK(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&p->ev_user, cudaEventDisableTiming));
+  }
+  int adj = g_adj ? 1 : 0;
+  mpn_problem::SweepGraph* g = nullptr;
+  for (auto& x : p->graphs)
+    if (x.adjoint == adj && x.iters == iters && x.prof == p->prof_on) g = &x;
+  if (!g) {
+    long long nl0 = p->nlaunch;
+    int ev0 = p->prof_next;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
+    int s = sweep_body(p, g_adj, iters, P, p->gstream);
+    cudaError_t ec = cudaStreamEndCapture(p->gstream, &graph);
+    if (s != MPN_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+    CK(ec);
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ei);
+    p->graphs.push_back({adj, iters, p->prof_on, exec, p->nlaunch - nl0, ev0, p->prof_next});
+    p->nlaunch = nl0;
+    g = &p->graphs.back();
+  }
+  CK(cudaEventRecord(p->ev_user, st));
+  CK(cudaStreamWaitEvent(p->gstream, p->ev_user, 0));
+  CK(cudaGraphLaunch(g->exec, p->gstream));
+  p->nlaunch += g->kernels;
+  CK(cudaStreamSynchronize(p->gstream));
+  prof_flush(p, g->ev0, g->ev1);
+  return MPN_OK;
+}
+
 // Solve S u = rhs (forward: g_adj null; adjoint: the FP64 rhs g_adj) by FP64
 // refinement around FP32 MG-PCG.  u64 holds the initial guess on entry.
 static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mpn_stats* stats, cudaStream_t st) {
   Level& l = p->lv[0];
   int B = p->B, N = l.g.N;
   int P = nblk(N);          // partials per instance of every refinement-level reduction
-  dim3 gr(P, B);
-  double* scale = p->dscal;
-  double* outv = p->dscal + 2 * B;  // [slots][B]
   std::vector<double> prev_upd(B, 1.0);
   mpn_stats sres;
   memset(&sres, 0, sizeof(sres));
   int status = MPN_ERR_NOT_CONVERGED;
-  // ||rhs|| for the relative residual
   // ||rhs|| for the relative residual: the first residual when starting from 0
   if (!zero_start) TRY(residual64(p, nullptr, g_adj, p->r64, slot(p, S_GN), st));
   std::vector<double> gnorm(B, 0.0);
   int iters = p->desc.inner_iters, total_iters = 0;
   for (int sweep = 0; sweep < p->desc.max_refine; ++sweep) {
-    TRY(residual64(p, p->u64, g_adj, p->r64, slot(p, S_RN), st));
-    ++p->nlaunch, k_to32<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN), P, l.r, scale);
-    CKL();
-    TRY(pcg(p, iters, st));
+    TRY(run_sweep(p, g_adj, iters, P, st));
     total_iters += iters;
-    ++p->nlaunch, k_update64<<<gr, MPN_TPB, 0, st>>>(N, p->x, scale, p->u64, slot(p, S_DU), slot(p, S_UN));
-    {
-      // correction and solution sizes measured on every unknown of z
-      ++p->nlaunch, k_znorm<<<gr, MPN_TPB, 0, st>>>(l.g, p->u64, p->x, scale, slot(p, S_DU), slot(p, S_UN));
-    }
-    // slots S_RN, S_DU, S_UN, (S_PW unused), S_GN -> outv
-    ++p->nlaunch, k_collect<<<B, 64, 0, st>>>(B, 5, slot(p, S_RN), P, outv);
-    CKL();
-    CK(cudaMemcpyAsync(p->hbuf, outv, sizeof(double) * 5 * B, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    prof_flush(p);
     const double* h = p->hbuf;
     double maxpred = 0, maxupd = 0, maxres = 0, maxrate = 0;
     bool bad = false, grew = false;
@@ -695,7 +760,6 @@ extern "C" int mpn_profile(mpn_problem* p, int enable, double* ms_total, long lo
       for (auto& e : p->prof_ev) CK(cudaEventCreate(&e));
     }
     p->prof_on = enable;
-    p->prof_used = 0;
     p->prof_ms = 0; p->prof_n = 0; p->prof_bytes = 0;
     p->nlaunch = 0;
   }

@@ -314,49 +314,56 @@ __global__ void k_coarse_factor(int M, int bw, float* __restrict__ Kb, int* __re
 }
 
 // Explicit inverse from the banded factor: thread c solves L L^T x = e_c and
-// writes column c of Kinv (symmetric).  The last bw values of the running
-// substitution live in a shared-memory window, so the dependency chain never
-// waits on global memory.
-__global__ void k_coarse_inverse(int M, int bw, const float* __restrict__ Lb, float* __restrict__ Kinv) {
-  extern __shared__ float win[];
-  int b = blockIdx.y;
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const float* L = Lb + (size_t)b * M * (bw + 1);
-  float* X = Kinv + (size_t)b * M * M;
+// writes column c of Kinv (symmetric).  The band is staged in shared memory
+// (when it fits; `band_in_smem`), and the last values of the running
+// substitution live in a shared-memory window of wmask+1 slots (a power of
+// two > bw), so the dependency chain never waits on global memory; two
+// partial sums halve the chain length.
+__global__ void k_coarse_inverse(int M, int bw, int wmask, int band_in_smem, const float* __restrict__ Lb,
+                                 float* __restrict__ Kinv) {
+  extern __shared__ float sm[];
+  const int b = blockIdx.y;
   const int W = bw + 1;
-  const int tx = threadIdx.x, nt = blockDim.x;
-  if (c >= M) return;
-  for (int i = 0; i < c; ++i) X[(size_t)i * M + c] = 0.f;
-  // forward: window slot of y_j is j mod W, tracked incrementally
-  int si = c % W;
-  for (int i = c; i < M; ++i) {
-    float s = (i == c) ? 1.f : 0.f;
-    int j0 = max(c, i - bw);
-    int sj = si - (i - j0); if (sj < 0) sj += W;
-    const float* Li = L + (size_t)i * W + (i - j0);
-    for (int j = j0; j < i; ++j) {
-      s -= *Li-- * win[sj * nt + tx];
-      if (++sj == W) sj = 0;
-    }
-    float y = s / L[(size_t)i * W];
-    win[si * nt + tx] = y;
-    X[(size_t)i * M + c] = y;
-    if (++si == W) si = 0;
+  const float* Lg = Lb + (size_t)b * M * W;
+  float* win = sm;                                  // [wmask + 1][blockDim.x]
+  float* Ls = sm + (wmask + 1) * blockDim.x;        // [M][W] when staged
+  if (band_in_smem) {
+    for (int t = threadIdx.x; t < M * W; t += blockDim.x) Ls[t] = Lg[t];
+    __syncthreads();
   }
-  // backward: x_i needs x_{i+1..i+bw}
-  si = (M - 1) % W;
-  for (int i = M - 1; i >= 0; --i) {
-    float s = X[(size_t)i * M + c];
-    int j1 = min(M - 1, i + bw);
-    int sj = si + 1; if (sj == W) sj = 0;
-    for (int j = i + 1; j <= j1; ++j) {
-      s -= L[(size_t)j * W + (j - i)] * win[sj * nt + tx];
-      if (++sj == W) sj = 0;
+  const float* L = band_in_smem ? Ls : Lg;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= M) return;
+  float* X = Kinv + (size_t)b * M * M;
+  const int tx = threadIdx.x, nt = blockDim.x;
+  for (int i = 0; i < c; ++i) X[(size_t)i * M + c] = 0.f;
+  for (int i = c; i < M; ++i) {
+    int j0 = max(c, i - bw);
+    float s0 = (i == c) ? 1.f : 0.f, s1 = 0.f;
+    const float* Li = L + (size_t)i * W + (i - j0);
+    int j = j0;
+    for (; j + 1 < i; j += 2) {
+      s0 -= Li[0] * win[(j & wmask) * nt + tx];
+      s1 -= Li[-1] * win[((j + 1) & wmask) * nt + tx];
+      Li -= 2;
     }
-    float xv = s / L[(size_t)i * W];
-    win[si * nt + tx] = xv;
+    if (j < i) s0 -= Li[0] * win[(j & wmask) * nt + tx];
+    float y = (s0 + s1) / L[(size_t)i * W];
+    win[(i & wmask) * nt + tx] = y;
+    X[(size_t)i * M + c] = y;
+  }
+  for (int i = M - 1; i >= 0; --i) {
+    int j1 = min(M - 1, i + bw);
+    float s0 = X[(size_t)i * M + c], s1 = 0.f;
+    int j = i + 1;
+    for (; j + 1 <= j1; j += 2) {
+      s0 -= L[(size_t)j * W + (j - i)] * win[(j & wmask) * nt + tx];
+      s1 -= L[(size_t)(j + 1) * W + (j + 1 - i)] * win[((j + 1) & wmask) * nt + tx];
+    }
+    if (j <= j1) s0 -= L[(size_t)j * W + (j - i)] * win[(j & wmask) * nt + tx];
+    float xv = (s0 + s1) / L[(size_t)i * W];
+    win[(i & wmask) * nt + tx] = xv;
     X[(size_t)i * M + c] = xv;
-    if (--si < 0) si = W - 1;
   }
 }
 
