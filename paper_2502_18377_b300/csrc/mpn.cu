@@ -298,7 +298,6 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   for (int v = 0; v < 8; ++v) fo[v] = v < V ? d.field_of[v] : -1;
   if (cudaMemcpy(p->field_of_dev, fo, sizeof(fo), cudaMemcpyHostToDevice) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
   if (cudaMallocHost((void**)&p->hbuf, sizeof(double) * 16 * B) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
-  cudaFuncSetAttribute(k_coarse_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 
   // Chebyshev coefficients on [lo, 1] for Dinv scaled by 1 / lambda_max
   const double lo = 0.1, th = (1.0 + lo) / 2, de = (1.0 - lo) / 2, sg = th / de;
@@ -437,15 +436,15 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
   size_t smem = sizeof(float) * (size_t)p->M * (p->bw + 1);
   CK(cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ++p->nlaunch, k_coarse_factor<<<B, 512, smem, st>>>(p->M, p->bw, p->Kband, p->ferr);
+  // one warp per column of the inverse
   {
-    const int nt = 64;
-    int ws = 64;
-    while (ws <= p->bw) ws *= 2;
-    size_t band = sizeof(float) * (size_t)p->M * (p->bw + 1), win = sizeof(float) * ws * nt;
-    int in_smem = band + win <= 200 * 1024;
-    ++p->nlaunch, k_coarse_inverse<<<dim3((p->M + nt - 1) / nt, B), nt, win + (in_smem ? band : 0), st>>>(
-        p->M, p->bw, ws - 1, in_smem, p->Kband, p->Kinv);
+    dim3 gi((p->M * 32 + MPN_TPB - 1) / MPN_TPB, B);
+    if (p->bw < 32) ++p->nlaunch, k_coarse_inverse<1><<<gi, MPN_TPB, 0, st>>>(p->M, p->bw, p->Kband, p->Kinv);
+    else if (p->bw < 64) ++p->nlaunch, k_coarse_inverse<2><<<gi, MPN_TPB, 0, st>>>(p->M, p->bw, p->Kband, p->Kinv);
+    else if (p->bw < 128) ++p->nlaunch, k_coarse_inverse<4><<<gi, MPN_TPB, 0, st>>>(p->M, p->bw, p->Kband, p->Kinv);
+    else ++p->nlaunch, k_coarse_inverse<8><<<gi, MPN_TPB, 0, st>>>(p->M, p->bw, p->Kband, p->Kinv);
   }
+
   CKL();
   p->setup_ok = true;
   return MPN_OK;
@@ -481,7 +480,10 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   ++p->nlaunch, k_restrict_vec<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], l.t, lc.r);
   CKL();
   TRY(vcycle(p, k + 1, st));
-  ++p->nlaunch, k_prolong_add<<<gr, MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], lc.e, nullptr, l.e);
+  if (!l.cz[0] && l.cz[1] && l.cz[2] && l.g.per[1] && l.g.per[2] && l.g.n[2] % 4 == 0)
+    ++p->nlaunch, k_prolong_add4<<<dim3(sblk(l.g.N / 4), B), MPN_TPB, 0, st>>>(l.g, lc.g, lc.e, l.e);
+  else
+    ++p->nlaunch, k_prolong_add<<<gr, MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], lc.e, nullptr, l.e);
   // post-smoothing
   a.c1 = 0.f; a.c2 = p->cheb_inv_th;
   stencil(p, k, a, SM_POST0, st);

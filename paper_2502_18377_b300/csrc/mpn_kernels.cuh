@@ -63,11 +63,11 @@ __global__ void k_diag_inv(Grid g, Coef cf, const float* __restrict__ rho, float
   GRID_LOOP(p, g.N) {
     int pos[3]; decode(g, p, pos);
     // own row: L_jj
-    double Ljj = coefv(cf, 0, b, p, g.N);
+    float Ljj = coefv(cf, 0, b, p, g.N);
     for (int d = 0; d < g.D; ++d)
-      Ljj += (double)coefv(cf, 1 + 2 * d, b, p, g.N) * dweight(1, pos[d], g.n[d], g.per[d], 0) * g.ds1[d] +
-             (double)coefv(cf, 2 + 2 * d, b, p, g.N) * dweight(2, pos[d], g.n[d], g.per[d], 0) * g.ds2[d];
-    double acc = (double)rh[p] * Ljj * Ljj;
+      Ljj += coefv(cf, 1 + 2 * d, b, p, g.N) * dweight(1, pos[d], g.n[d], g.per[d], 0) * g.is1[d] +
+             coefv(cf, 2 + 2 * d, b, p, g.N) * dweight(2, pos[d], g.n[d], g.per[d], 0) * g.is2[d];
+    float acc = rh[p] * Ljj * Ljj;
     for (int d = 0; d < g.D; ++d)
       for (int o = -2; o <= 2; ++o) {
         if (o == 0) continue;
@@ -77,12 +77,11 @@ __global__ void k_diag_inv(Grid g, Coef cf, const float* __restrict__ rho, float
         float w1 = dweight(1, ip, g.n[d], g.per[d], o), w2 = dweight(2, ip, g.n[d], g.per[d], o);
         if (w1 == 0.f && w2 == 0.f) continue;
         int q = p + (ip - pos[d]) * g.stride[d];
-        double Lij = (double)coefv(cf, 1 + 2 * d, b, q, g.N) * w1 * g.ds1[d] +
-                     (double)coefv(cf, 2 + 2 * d, b, q, g.N) * w2 * g.ds2[d];
-        acc += (double)rh[q] * Lij * Lij;
+        float Lij = coefv(cf, 1 + 2 * d, b, q, g.N) * w1 * g.is1[d] + coefv(cf, 2 + 2 * d, b, q, g.N) * w2 * g.is2[d];
+        acc += rh[q] * Lij * Lij;
       }
     if (is_boundary(g, pos)) acc += g.theta;
-    dinv[(size_t)b * g.N + p] = acc > 0 ? (float)(1.0 / acc) : 0.f;
+    dinv[(size_t)b * g.N + p] = acc > 0 ? 1.f / acc : 0.f;
   }
 }
 
@@ -219,6 +218,34 @@ __global__ void k_prolong_add(Grid gf, Grid gc, int c0, int c1, int c2, const fl
   }
 }
 
+// e_f += P e_c for the common case: t kept, x and y periodic and halved,
+// n_y % 4 == 0.  One thread owns 4 fine points along y (= coarse y 2q, 2q+1
+// and the next one, wrapping).
+__global__ void k_prolong_add4(Grid gf, Grid gc, const float* __restrict__ ec, float* __restrict__ ef) {
+  const int b = blockIdx.y;
+  const float* E = ec + (size_t)b * gc.N;
+  float* Fo = ef + (size_t)b * gf.N;
+  const int ng = gf.n[2] >> 2;
+  const int NG = gf.N >> 2;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < NG; q += gridDim.x * blockDim.x) {
+    int row = q / ng;
+    int j = (q - row * ng) * 2;                  // coarse y of the group's first point
+    int ix = row % gf.n[1], it = row / gf.n[1];
+    int jn = j + 2 == gc.n[2] ? 0 : j + 2;
+    int cx0 = ix >> 1, cx1 = (ix & 1) ? ((cx0 + 1 == gc.n[1]) ? 0 : cx0 + 1) : cx0;
+    float wx = (ix & 1) ? 0.5f : 1.f;
+    const float* r0 = E + ((size_t)it * gc.n[1] + cx0) * gc.n[2];
+    const float* r1 = E + ((size_t)it * gc.n[1] + cx1) * gc.n[2];
+    float a0 = r0[j], a1 = r0[j + 1], a2 = r0[jn];
+    if (ix & 1) { a0 += r1[j]; a1 += r1[j + 1]; a2 += r1[jn]; }
+    a0 *= wx; a1 *= wx; a2 *= wx;
+    float4* dst = reinterpret_cast<float4*>(Fo + (size_t)q * 4);
+    float4 v = *dst;
+    v.x += a0; v.y += 0.5f * (a0 + a1); v.z += a1; v.w += 0.5f * (a1 + a2);
+    *dst = v;
+  }
+}
+
 // ------------------------------------------------------ coarsest-level solve
 // Banded lower storage: Kb[b][j][j - k] = S[j][k] for 0 <= j - k <= bw.
 __global__ void k_coarse_assemble(Grid g, Coef cf, const float* __restrict__ rho, int bw, float* __restrict__ Kb) {
@@ -313,57 +340,68 @@ __global__ void k_coarse_factor(int M, int bw, float* __restrict__ Kb, int* __re
   for (int t = threadIdx.x; t < M * W; t += blockDim.x) K[t] = sb[t];
 }
 
-// Explicit inverse from the banded factor: thread c solves L L^T x = e_c and
-// writes column c of Kinv (symmetric).  The band is staged in shared memory
-// (when it fits; `band_in_smem`), and the last values of the running
-// substitution live in a shared-memory window of wmask+1 slots (a power of
-// two > bw), so the dependency chain never waits on global memory; two
-// partial sums halve the chain length.
-__global__ void k_coarse_inverse(int M, int bw, int wmask, int band_in_smem, const float* __restrict__ Lb,
-                                 float* __restrict__ Kinv) {
-  extern __shared__ float sm[];
+// Explicit inverse from the banded factor (bw < 32 NW): one warp per column c
+// solves L L^T x = e_c and writes column c of Kinv (symmetric).  At step i the
+// band row (or column) is split across the lanes and the dot product reduced
+// by shuffles; the last 32 NW values of the substitution live in NW registers
+// per lane and shift by one lane per step.
+template <int NW>
+__global__ void k_coarse_inverse(int M, int bw, const float* __restrict__ Lb, float* __restrict__ Kinv) {
   const int b = blockIdx.y;
   const int W = bw + 1;
-  const float* Lg = Lb + (size_t)b * M * W;
-  float* win = sm;                                  // [wmask + 1][blockDim.x]
-  float* Ls = sm + (wmask + 1) * blockDim.x;        // [M][W] when staged
-  if (band_in_smem) {
-    for (int t = threadIdx.x; t < M * W; t += blockDim.x) Ls[t] = Lg[t];
-    __syncthreads();
-  }
-  const float* L = band_in_smem ? Ls : Lg;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const float* L = Lb + (size_t)b * M * W;
+  const int lane = threadIdx.x & 31;
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (c >= M) return;
   float* X = Kinv + (size_t)b * M * M;
-  const int tx = threadIdx.x, nt = blockDim.x;
-  for (int i = 0; i < c; ++i) X[(size_t)i * M + c] = 0.f;
+  float w[NW];
+  // forward: y_i = (delta_ic - sum_{j<i} L_ij y_j) / L_ii; w[k] on lane l holds
+  // y_{i-1-32k-l}
+#pragma unroll
+  for (int k = 0; k < NW; ++k) w[k] = 0.f;
   for (int i = c; i < M; ++i) {
-    int j0 = max(c, i - bw);
-    float s0 = (i == c) ? 1.f : 0.f, s1 = 0.f;
-    const float* Li = L + (size_t)i * W + (i - j0);
-    int j = j0;
-    for (; j + 1 < i; j += 2) {
-      s0 -= Li[0] * win[(j & wmask) * nt + tx];
-      s1 -= Li[-1] * win[((j + 1) & wmask) * nt + tx];
-      Li -= 2;
+    const float* Li = L + (size_t)i * W;
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      int o = 1 + 32 * k + lane;                // offset i - j
+      if (o <= bw && i - o >= c) s += Li[o] * w[k];
     }
-    if (j < i) s0 -= Li[0] * win[(j & wmask) * nt + tx];
-    float y = (s0 + s1) / L[(size_t)i * W];
-    win[(i & wmask) * nt + tx] = y;
-    X[(size_t)i * M + c] = y;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    float y = ((i == c ? 1.f : 0.f) - s) / Li[0];
+#pragma unroll
+    for (int k = NW - 1; k >= 0; --k) {
+      float carry = k > 0 ? __shfl_sync(0xffffffffu, w[k - 1], 31) : y;
+      w[k] = __shfl_up_sync(0xffffffffu, w[k], 1);
+      if (lane == 0) w[k] = carry;
+    }
+    if (lane == 0) X[(size_t)i * M + c] = y;
   }
+  __syncwarp();
+  // backward: x_i = (y_i - sum_{j>i} L_ji x_j) / L_ii; w[k] on lane l holds
+  // x_{i+1+32k+l}
+#pragma unroll
+  for (int k = 0; k < NW; ++k) w[k] = 0.f;
   for (int i = M - 1; i >= 0; --i) {
-    int j1 = min(M - 1, i + bw);
-    float s0 = X[(size_t)i * M + c], s1 = 0.f;
-    int j = i + 1;
-    for (; j + 1 <= j1; j += 2) {
-      s0 -= L[(size_t)j * W + (j - i)] * win[(j & wmask) * nt + tx];
-      s1 -= L[(size_t)(j + 1) * W + (j + 1 - i)] * win[((j + 1) & wmask) * nt + tx];
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      int o = 1 + 32 * k + lane, j = i + o;
+      if (o <= bw && j < M) s += L[(size_t)j * W + o] * w[k];
     }
-    if (j <= j1) s0 -= L[(size_t)j * W + (j - i)] * win[(j & wmask) * nt + tx];
-    float xv = (s0 + s1) / L[(size_t)i * W];
-    win[(i & wmask) * nt + tx] = xv;
-    X[(size_t)i * M + c] = xv;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    float yi = i >= c ? X[(size_t)i * M + c] : 0.f;
+    float x = (yi - s) / L[(size_t)i * W];
+#pragma unroll
+    for (int k = NW - 1; k >= 0; --k) {
+      float carry = k > 0 ? __shfl_sync(0xffffffffu, w[k - 1], 31) : x;
+      w[k] = __shfl_up_sync(0xffffffffu, w[k], 1);
+      if (lane == 0) w[k] = carry;
+    }
+    __syncwarp();
+    if (lane == 0) X[(size_t)i * M + c] = x;
   }
 }
 
@@ -757,9 +795,9 @@ __global__ void k_mse_grad(int N, int V, int B, const float* __restrict__ z, con
 // Points away from non-periodic edges use the central weights directly.
 __device__ __forceinline__ void decode_fast(const Grid& g, int p, int pos[3]) {
   int n12 = g.n[1] * g.n[2];
-  int i0 = __float2int_rz(((float)p + 0.5f) / (float)n12);
+  int i0 = __float2int_rz(((float)p + 0.5f) * __frcp_rn((float)n12));
   int rem = p - i0 * n12;
-  int i1 = __float2int_rz(((float)rem + 0.5f) / (float)g.n[2]);
+  int i1 = __float2int_rz(((float)rem + 0.5f) * __frcp_rn((float)g.n[2]));
   pos[0] = i0; pos[1] = i1; pos[2] = rem - i1 * g.n[2];
 }
 

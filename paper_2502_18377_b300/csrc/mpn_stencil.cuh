@@ -184,17 +184,27 @@ __global__ void __launch_bounds__(256) k_Ly4(Grid g, Coef cf, const float* __res
     float4 xc = ld4(xb + p0);
     float4 Lx = C.at4(0, p0) * xc;
     // t and x: uniform position class
+    bool txin = pos[0] > 0 && pos[0] < g.n[0] - 1 && (g.per[1] || (pos[1] > 0 && pos[1] < g.n[1] - 1));
+    if (txin) {
 #pragma unroll
-    for (int d = 0; d < 2; ++d) {
-      float4 a1 = f4(0.f), a2 = f4(0.f);
-#pragma unroll
-      for (int o = -2; o <= 2; ++o) {
-        float w1 = dweight(1, pos[d], g.n[d], g.per[d], o), w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
-        if (w1 == 0.f && w2 == 0.f) continue;
-        float4 xv = o == 0 ? xc : ld4(xb + nbr(g, p0, pos, d, o));
-        a1 = a1 + w1 * xv; a2 = a2 + w2 * xv;
+      for (int d = 0; d < 2; ++d) {
+        float4 xm = ld4(xb + nb1(g, p0, pos, d, -1)), xp = ld4(xb + nb1(g, p0, pos, d, 1));
+        Lx = Lx + ((0.5f * g.is1[d]) * C.at4(1 + 2 * d, p0)) * (xp - xm) +
+             (g.is2[d] * C.at4(2 + 2 * d, p0)) * (xp - 2.f * xc + xm);
       }
-      Lx = Lx + (g.is1[d] * C.at4(1 + 2 * d, p0)) * a1 + (g.is2[d] * C.at4(2 + 2 * d, p0)) * a2;
+    } else {
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        float4 a1 = f4(0.f), a2 = f4(0.f);
+#pragma unroll
+        for (int o = -2; o <= 2; ++o) {
+          float w1 = dweight(1, pos[d], g.n[d], g.per[d], o), w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
+          if (w1 == 0.f && w2 == 0.f) continue;
+          float4 xv = o == 0 ? xc : ld4(xb + nbr(g, p0, pos, d, o));
+          a1 = a1 + w1 * xv; a2 = a2 + w2 * xv;
+        }
+        Lx = Lx + (g.is1[d] * C.at4(1 + 2 * d, p0)) * a1 + (g.is2[d] * C.at4(2 + 2 * d, p0)) * a2;
+      }
     }
     // y: central, neighbours from the group plus one value each side
     {
@@ -234,6 +244,16 @@ __global__ void __launch_bounds__(256) k_LTy4(Grid g, Coef cf, StepArgs a) {
       float4 yc = ld4(yb + p0);
       qv = C.at4(0, p0) * yc;
       // t and x: rows i = j - o e_d share their position class across the group
+      bool txin = pos[0] > 2 && pos[0] < g.n[0] - 3 && (g.per[1] || (pos[1] > 2 && pos[1] < g.n[1] - 3));
+      if (txin) {
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+          int pm = nb1(g, p0, pos, d, -1), pp = nb1(g, p0, pos, d, 1);
+          float4 ym = ld4(yb + pm), yp = ld4(yb + pp);
+          qv = qv + (0.5f * g.is1[d]) * (C.at4(1 + 2 * d, pm) * ym - C.at4(1 + 2 * d, pp) * yp) +
+               g.is2[d] * (C.at4(2 + 2 * d, pm) * ym - 2.f * (C.at4(2 + 2 * d, p0) * yc) + C.at4(2 + 2 * d, pp) * yp);
+        }
+      } else
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
 #pragma unroll
