@@ -78,6 +78,9 @@ typedef struct mpn_desc {
   int cheb_degree;        /* Chebyshev-Jacobi smoothing steps, pre and post */
   int coarse_min;         /* spatial dims are halved while the half is >= this */
   int max_coarse;         /* largest coarsest-level system (unknowns per instance) */
+  int fused_coarse;       /* 1: the coarse levels whose data fit in one thread-block cluster's shared
+                             memory per instance run as one kernel per V-cycle; 0: one kernel per
+                             operator pass at every level (same arithmetic) */
 } mpn_desc;
 
 typedef struct mpn_stats {
@@ -92,7 +95,7 @@ typedef struct mpn_stats {
 typedef struct mpn_problem mpn_problem;
 
 /* Fills *desc with defaults (tol 1e-7, max_refine 12, inner_iters 6,
- * cheb_degree 4, coarse_min 4, max_coarse 2048, stencil 3). */
+ * cheb_degree 4, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1). */
 int mpn_default_desc(mpn_desc* desc);
 
 /* Validates the descriptor, builds the grid hierarchy (spatial halving, time
@@ -105,6 +108,12 @@ size_t mpn_workspace_bytes(const mpn_problem* p);
 
 /* Number of multigrid levels and their grid shapes (host array [levels][3]). */
 int mpn_levels(const mpn_problem* p, int* nlevels, int* shapes /* host, 3 * 16 ints */);
+
+/* First multigrid level of the fused coarse end of the V-cycle (that level
+ * and all coarser ones run as one kernel launch per V-cycle), or -1 when
+ * every level runs pass by pass (fused_coarse = 0, fewer than two levels
+ * fit, or the thread-block cluster cannot be resident).  Host-side query. */
+int mpn_fused_level(const mpn_problem* p);
 
 /* Forward pass (Eqs. 9-10): writes z* [B][V][N] and, if z64 is non-null, the
  * FP64 solution [B][V][N] (double).  u0 is an optional warm start.  stats is

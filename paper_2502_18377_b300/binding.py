@@ -27,7 +27,7 @@ class MpnDesc(ctypes.Structure):
                 ("nfields", ctypes.c_int), ("field_of", ctypes.c_int * 7), ("tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("inner_iters", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("coarse_min", ctypes.c_int),
-                ("max_coarse", ctypes.c_int)]
+                ("max_coarse", ctypes.c_int), ("fused_coarse", ctypes.c_int)]
 
 
 class MpnConvDesc(ctypes.Structure):
@@ -50,6 +50,7 @@ EXPORTS = {
     "mpn_create": (ctypes.c_int, [ctypes.POINTER(MpnDesc), ctypes.POINTER(_P)]),
     "mpn_workspace_bytes": (ctypes.c_size_t, [_P]),
     "mpn_levels": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "mpn_fused_level": (ctypes.c_int, [_P]),
     "mpn_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(MpnStats), _P]),
     "mpn_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int,
                                    ctypes.POINTER(MpnStats), _P]),
@@ -162,7 +163,7 @@ class Solver:
     """One problem object (grid, batch, coefficient layout) of the C ABI."""
 
     def __init__(self, geom: dict, batch: int, field_of, nfields: int, tol=1e-7, max_refine=12,
-                 inner_iters=6, cheb_degree=4, coarse_min=4, max_coarse=2048):
+                 inner_iters=6, cheb_degree=4, coarse_min=4, max_coarse=2048, fused_coarse=True):
         lib = load()
         d = MpnDesc()
         lib.mpn_default_desc(ctypes.byref(d))
@@ -181,6 +182,7 @@ class Solver:
             d.field_of[v] = field_of[v] if v < len(field_of) else -1
         d.tol, d.max_refine, d.inner_iters = tol, max_refine, inner_iters
         d.cheb_degree, d.coarse_min, d.max_coarse = cheb_degree, coarse_min, max_coarse
+        d.fused_coarse = int(bool(fused_coarse))
         h = ctypes.c_void_p()
         s = lib.mpn_create(ctypes.byref(d), ctypes.byref(h))
         if s != 0:
@@ -204,6 +206,10 @@ class Solver:
     @property
     def workspace_bytes(self):
         return int(self.lib.mpn_workspace_bytes(self._h))
+
+    def fused_level(self):
+        """First level of the fused coarse end of the V-cycle, or -1."""
+        return int(self.lib.mpn_fused_level(self._h))
 
     def levels(self):
         nl = ctypes.c_int()

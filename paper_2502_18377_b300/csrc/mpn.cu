@@ -23,6 +23,7 @@
 #include "../../include/mpn.h"
 #include "mpn_kernels.cuh"
 #include "mpn_stencil.cuh"
+#include "mpn_tail.cuh"
 
 #define MAXL 16
 
@@ -73,6 +74,11 @@ struct mpn_problem {
   bool setup_ok = false;
   bool zd_valid = false;   // uf64 holds the FP64 u of the last forward
   float cheb_c1[32], cheb_c2[32], cheb_inv_th;
+  // fused coarse end of the V-cycle: first level (-1: none), cluster size,
+  // dynamic shared memory per CTA, kernel arguments
+  int tail_k0 = -1, tail_cs = 0;
+  size_t tail_smem = 0;
+  TailArgs tail;
   std::vector<void*> allocs;
   // live timing of the finest-level smoothing step (events on the solve stream)
   int prof_on = 0;
@@ -162,6 +168,7 @@ extern "C" int mpn_default_desc(mpn_desc* d) {
   d->cheb_degree = 4;
   d->coarse_min = 4;
   d->max_coarse = 2048;
+  d->fused_coarse = 1;
   return MPN_OK;
 }
 
@@ -202,6 +209,102 @@ extern "C" int mpn_levels(const mpn_problem* p, int* nl, int* shapes) {
       for (int d = 0; d < 3; ++d) shapes[3 * k + d] = p->lv[k].g.n[d];
   return MPN_OK;
 }
+
+// Fused coarse end (mpn_tail.cuh): the finest level k0 with at most two
+// points per thread and CTA from which all coarser levels fit, per CTA, in
+// shared memory, with the cluster size and the shared-memory layout.  Left at -1 when fewer than two levels would be fused
+// or the cluster cannot be resident on this device.
+static void plan_tail(mpn_problem* p) {
+  p->tail_k0 = -1;
+  if (!p->desc.fused_coarse || p->L < 2) return;
+  const int n0 = p->lv[0].g.n[0];
+  int cs = 1;
+  while (cs * 2 <= std::min(TAIL_MAX_CLUSTER, n0)) cs *= 2;
+  const int P = (n0 + cs - 1) / cs;
+  const size_t budget = 200 * 1024;
+  for (int k0 = 0; k0 + 1 < p->L; ++k0) {
+    if (p->L - k0 > TAIL_MAXL) continue;
+    // a level with more than two points per thread and CTA runs better pass
+    // by pass over the whole GPU (vectorised kernels, full occupancy)
+    if ((size_t)P * p->lv[k0].g.n[1] * p->lv[k0].g.n[2] > 2 * TAIL_TPB) continue;
+    TailArgs& ta = p->tail;
+    memset(&ta, 0, sizeof(ta));
+    size_t off = 0;
+    for (int k = k0; k < p->L; ++k) {
+      const Level& l = p->lv[k];
+      TailLevel& T = ta.lv[k - k0];
+      T.g = l.g;
+      for (int d = 0; d < 3; ++d) T.cz[d] = l.cz[d];
+      T.plane = l.g.n[1] * l.g.n[2];
+      T.cap = P * T.plane;
+      T.fields = l.fields; T.rho = l.rho; T.dinv = l.dinv;
+      const int c = T.cap;
+      T.o_r = (int)off; T.o_e = (int)off + c;
+      if (k + 1 < p->L) {
+        T.o_d = (int)off + 2 * c; T.o_y = (int)off + 3 * c; T.o_rho = (int)off + 4 * c; T.o_dinv = (int)off + 5 * c;
+        T.o_f = (int)off + 6 * c;
+        off += (size_t)(6 + p->F) * c;
+      } else {
+        T.o_d = T.o_y = T.o_rho = T.o_dinv = T.o_f = T.o_r;
+        off += (size_t)2 * c;
+      }
+      off = (off + 3) & ~(size_t)3;
+    }
+    ta.o_g = (int)off;
+    off += (size_t)p->M;
+    ta.o_tw = (int)off;
+    off += (size_t)P * TW_STRIDE;
+    const size_t smem = off * sizeof(float);
+    if (smem > budget) continue;
+    ta.nl = p->L - k0;
+    ta.V = p->V; ta.F = p->F; ta.B = p->B; ta.M = p->M; ta.m = p->desc.cheb_degree; ta.P = P;
+    ta.invP = 1.f / (float)P;
+    for (int v = 0; v < 7; ++v) ta.field_of[v] = v < p->V ? p->desc.field_of[v] : -1;
+    ta.scalars = p->scalars;
+    for (int k = 0; k < 32; ++k) { ta.c1[k] = p->cheb_c1[k]; ta.c2[k] = p->cheb_c2[k]; }
+    ta.inv_th = p->cheb_inv_th;
+    ta.Kinv = p->Kinv;
+    ta.rin = p->lv[k0].r;
+    ta.eout = p->lv[k0].e;
+    const void* fn = p->D == 3 ? (const void*)k_vtail<3> : (const void*)k_vtail<2>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, p->B);
+    cfg.blockDim = dim3(TAIL_TPB);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+    cfg.attrs = at; cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) != cudaSuccess || ncl < 1) {
+      (void)cudaGetLastError();
+      return;
+    }
+    p->tail_k0 = k0; p->tail_cs = cs; p->tail_smem = smem;
+    return;
+  }
+}
+
+static void launch_tail(mpn_problem* p, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p->tail_cs, p->B);
+  cfg.blockDim = dim3(TAIL_TPB);
+  cfg.dynamicSmemBytes = p->tail_smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = p->tail_cs; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+  cfg.attrs = at; cfg.numAttrs = 1;
+  ++p->nlaunch;
+  if (p->D == 3) cudaLaunchKernelEx(&cfg, k_vtail<3>, p->tail);
+  else cudaLaunchKernelEx(&cfg, k_vtail<2>, p->tail);
+}
+
+extern "C" int mpn_fused_level(const mpn_problem* p) { return p ? p->tail_k0 : -1; }
 
 extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   if (!desc || !out) return MPN_ERR_INVALID_ARG;
@@ -309,6 +412,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
     p->cheb_c2[k] = (float)(2 * r1 / de);
     r0 = r1;
   }
+  plan_tail(p);
   *out = p;
   return MPN_OK;
 }
@@ -455,6 +559,11 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   Level& l = p->lv[k];
   int B = p->B;
   dim3 gr(nblk(l.g.N), B);
+  if (k == p->tail_k0) {
+    launch_tail(p, st);
+    CKL();
+    return MPN_OK;
+  }
   if (k == p->L - 1) {
     ++p->nlaunch, k_coarse_solve<<<dim3((p->M * 32 + MPN_TPB - 1) / MPN_TPB, B), MPN_TPB, 0, st>>>(p->M, p->Kinv, l.r, l.e);
     CKL();
