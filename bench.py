@@ -33,6 +33,11 @@ BATCH, GRID = 16, (32, 64, 64)
 L2_BYTES = 126 * 2 ** 20
 
 
+# DRAM bytes of one finest-level smoothing step (k_Ly4 + k_LTy4<1>) from one
+# ncu capture of this workload; None once those kernels change.
+PAIR_TRAFFIC_BYTES = 92.6e6
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -255,7 +260,8 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MB write outside the step events)"},
         "roofline": {"bound": "hbm", "kernel": "finest-level Chebyshev smoothing step (L pass + L^T pass)",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "frac": (achieved / hbm) if achieved else None, "traffic": PAIR_TRAFFIC_BYTES,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_Ly4 + k_LTy4<1> at the finest level, one capture, bytes per pair (profiles/finest_smoothing_pair_reaction_diffusion_2d_B16_32x64x64.md)",
                      "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.4 TB/s",
                      "launches": prof_n, "avg_launch_us": 1e3 * prof_ms / prof_n if prof_n else None},
         "clocks": clk,
