@@ -33,9 +33,9 @@ BATCH, GRID = 16, (32, 64, 64)
 L2_BYTES = 126 * 2 ** 20
 
 
-# DRAM bytes of one finest-level smoothing step (k_Ly4 + k_LTy4<1>) from one
-# ncu capture of this workload; None once those kernels change.
-PAIR_TRAFFIC_BYTES = 92.6e6
+# DRAM bytes of one finest-level smoothing step (k_step3<CHEB>) from one ncu
+# capture of this workload; None once that kernel changes.
+PAIR_TRAFFIC_BYTES = 59.6e6
 
 
 def _peaks():
@@ -258,10 +258,10 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "batch_per_gpu": B, "grid": list(GRID), "periodic": [0, 1, 1],
                    "unknowns_per_instance": V * N, "tol": 1e-7, "parallelism": f"replicas{world}",
                    "l2": "flushed between timed steps (256 MB write outside the step events)"},
-        "roofline": {"bound": "hbm", "kernel": "finest-level Chebyshev smoothing step (L pass + L^T pass)",
+        "roofline": {"bound": "hbm", "kernel": "finest-level Chebyshev smoothing step (k_step3: L and L^T passes fused through shared memory)",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": PAIR_TRAFFIC_BYTES,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_Ly4 + k_LTy4<1> at the finest level, one capture, bytes per pair (profiles/finest_smoothing_pair_reaction_diffusion_2d_B16_32x64x64.md)",
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the finest-level smoothing step kernel, one capture, bytes per step (profiles/finest_smoothing_step_reaction_diffusion_2d_B16_32x64x64.md)",
                      "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.4 TB/s",
                      "launches": prof_n, "avg_launch_us": 1e3 * prof_ms / prof_n if prof_n else None},
         "clocks": clk,

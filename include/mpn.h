@@ -81,6 +81,10 @@ typedef struct mpn_desc {
   int fused_coarse;       /* 1: the coarse levels whose data fit in one thread-block cluster's shared
                              memory per instance run as one kernel per V-cycle; 0: one kernel per
                              operator pass at every level (same arithmetic) */
+  int fused_step;         /* 1: on levels with float4 rows (D = 3, n_y % 4 == 0, 8 <= n_y <= 128,
+                             n_x % 4 == 0, n_t % 4 == 0) both operator passes of a smoothing step,
+                             residual or apply run as one kernel through shared memory; 0: two kernels
+                             (same arithmetic) */
 } mpn_desc;
 
 typedef struct mpn_stats {
@@ -95,7 +99,7 @@ typedef struct mpn_stats {
 typedef struct mpn_problem mpn_problem;
 
 /* Fills *desc with defaults (tol 1e-7, max_refine 12, inner_iters 6,
- * cheb_degree 4, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1). */
+ * cheb_degree 4, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 1). */
 int mpn_default_desc(mpn_desc* desc);
 
 /* Validates the descriptor, builds the grid hierarchy (spatial halving, time

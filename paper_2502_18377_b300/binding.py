@@ -27,7 +27,8 @@ class MpnDesc(ctypes.Structure):
                 ("nfields", ctypes.c_int), ("field_of", ctypes.c_int * 7), ("tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("inner_iters", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("coarse_min", ctypes.c_int),
-                ("max_coarse", ctypes.c_int), ("fused_coarse", ctypes.c_int)]
+                ("max_coarse", ctypes.c_int), ("fused_coarse", ctypes.c_int),
+                ("fused_step", ctypes.c_int)]
 
 
 class MpnConvDesc(ctypes.Structure):
@@ -163,7 +164,8 @@ class Solver:
     """One problem object (grid, batch, coefficient layout) of the C ABI."""
 
     def __init__(self, geom: dict, batch: int, field_of, nfields: int, tol=1e-7, max_refine=12,
-                 inner_iters=6, cheb_degree=4, coarse_min=4, max_coarse=2048, fused_coarse=True):
+                 inner_iters=6, cheb_degree=4, coarse_min=4, max_coarse=2048, fused_coarse=True,
+                 fused_step=True):
         lib = load()
         d = MpnDesc()
         lib.mpn_default_desc(ctypes.byref(d))
@@ -183,6 +185,7 @@ class Solver:
         d.tol, d.max_refine, d.inner_iters = tol, max_refine, inner_iters
         d.cheb_degree, d.coarse_min, d.max_coarse = cheb_degree, coarse_min, max_coarse
         d.fused_coarse = int(bool(fused_coarse))
+        d.fused_step = int(bool(fused_step))
         h = ctypes.c_void_p()
         s = lib.mpn_create(ctypes.byref(d), ctypes.byref(h))
         if s != 0:

@@ -24,6 +24,7 @@
 #include "mpn_kernels.cuh"
 #include "mpn_stencil.cuh"
 #include "mpn_tail.cuh"
+#include "mpn_fused.cuh"
 
 #define MAXL 16
 
@@ -46,6 +47,8 @@ struct Level {
   int vec4 = 0;        // float4 stencil kernels apply (D = 3, n_y % 4 == 0)
   int papply = 0;      // partial sums per instance written by an operator apply
   int cz[3];           // dims halved from this level to the next
+  int fs_tt = 0;       // > 0: operator steps as one fused kernel with TT-plane tiles (k_step3)
+  float* e2 = nullptr; // second iterate buffer of the fused smoother (the operand is read with a halo)
   float* fields = nullptr;  // [F][B][N]
   float *rho = nullptr, *dinv = nullptr;
   float *r = nullptr, *e = nullptr, *d = nullptr, *y = nullptr, *t = nullptr;
@@ -169,6 +172,7 @@ extern "C" int mpn_default_desc(mpn_desc* d) {
   d->coarse_min = 4;
   d->max_coarse = 2048;
   d->fused_coarse = 1;
+  d->fused_step = 1;
   return MPN_OK;
 }
 
@@ -208,6 +212,24 @@ extern "C" int mpn_levels(const mpn_problem* p, int* nl, int* shapes) {
     for (int k = 0; k < p->L; ++k)
       for (int d = 0; d < 3; ++d) shapes[3 * k + d] = p->lv[k].g.n[d];
   return MPN_OK;
+}
+
+#define FS_MAX_NY 128
+static size_t fs_smem(int tt, int ny) { return sizeof(float) * (size_t)(fs_rows_x(tt) + fs_rows_y(tt)) * ny; }
+// Opt the fused step kernels into the shared memory of the largest tile.
+static int fs_set_smem() {
+  int bytes = (int)fs_smem(8, FS_MAX_NY);
+  cudaError_t e = cudaSuccess;
+#define FS_ATTR(M, T, P1, P2) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<M, T, P1, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+#define FS_ATTR_M(T, P1, P2) FS_ATTR(SM_POST0, T, P1, P2); FS_ATTR(SM_CHEB, T, P1, P2); FS_ATTR(SM_RES, T, P1, P2); FS_ATTR(SM_APPLY, T, P1, P2)
+#define FS_ATTR_P(T) FS_ATTR_M(T, true, true); FS_ATTR_M(T, true, false); FS_ATTR_M(T, false, true); FS_ATTR_M(T, false, false)
+  FS_ATTR_P(8);
+  FS_ATTR_P(4);
+#undef FS_ATTR_P
+#undef FS_ATTR_M
+#undef FS_ATTR
+  return e == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
 }
 
 // Fused coarse end (mpn_tail.cuh): the finest level k0 with at most two
@@ -363,6 +385,12 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
     Level& l = p->lv[k];
     l.vec4 = (p->D == 3 && l.g.n[2] % 4 == 0 && l.g.n[2] >= 8) ? 1 : 0;
     l.papply = l.vec4 ? sblk(l.g.N / 4) : sblk(l.g.N);
+    // fused operator step: whole y rows of at most FS_MAX_NY points in shared
+    // memory, tiles that divide the t and x extents
+    if (d.fused_step && l.vec4 && l.g.n[2] <= FS_MAX_NY && l.g.n[1] % FS_TX == 0) {
+      l.fs_tt = l.g.n[0] % 8 == 0 ? 8 : (l.g.n[0] % 4 == 0 ? 4 : 0);
+      if (l.fs_tt) l.papply = (l.g.n[0] / l.fs_tt) * (l.g.n[1] / FS_TX);
+    }
   }
   Level& lc = p->lv[p->L - 1];
   p->M = lc.g.N;
@@ -382,6 +410,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
     AL(l.fields, (size_t)std::max(F, 1) * N);
     AL(l.rho, N); AL(l.dinv, N);
     AL(l.r, N); AL(l.e, N); AL(l.d, N); AL(l.y, N); AL(l.t, N);
+    if (l.fs_tt) AL(l.e2, N);
   }
   size_t N0 = (size_t)p->lv[0].g.N * B;
   AL(p->Kband, (size_t)B * p->M * (p->bw + 1));
@@ -412,6 +441,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
     p->cheb_c2[k] = (float)(2 * r1 / de);
     r0 = r1;
   }
+  if (fs_set_smem() != MPN_OK) { mpn_destroy(p); return MPN_ERR_CUDA; }
   plan_tail(p);
   *out = p;
   return MPN_OK;
@@ -450,6 +480,25 @@ static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st
   Coef cf = make_coef(p, l.fields);
   a.y = l.y;
   if (!a.dinv) a.dinv = l.dinv;
+  if (l.fs_tt) {
+    dim3 gs((l.g.n[0] / l.fs_tt) * (l.g.n[1] / FS_TX), p->B);
+    size_t sm = fs_smem(l.fs_tt, l.g.n[2]);
+#define FS_LAUNCH(T, P1, P2)                                                                                  \
+  switch (mode) {                                                                                             \
+    case SM_POST0: ++p->nlaunch, k_step3<SM_POST0, T, P1, P2><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break; \
+    case SM_CHEB: ++p->nlaunch, k_step3<SM_CHEB, T, P1, P2><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;   \
+    case SM_RES: ++p->nlaunch, k_step3<SM_RES, T, P1, P2><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;     \
+    default: ++p->nlaunch, k_step3<SM_APPLY, T, P1, P2><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;     \
+  }
+#define FS_LAUNCH_T(P1, P2) if (l.fs_tt == 8) { FS_LAUNCH(8, P1, P2) } else { FS_LAUNCH(4, P1, P2) }
+    if (l.g.per[1] && l.g.per[2]) { FS_LAUNCH_T(true, true) }
+    else if (l.g.per[1]) { FS_LAUNCH_T(true, false) }
+    else if (l.g.per[2]) { FS_LAUNCH_T(false, true) }
+    else { FS_LAUNCH_T(false, false) }
+#undef FS_LAUNCH_T
+#undef FS_LAUNCH
+    return;
+  }
   if (l.vec4) {
     dim3 g4(sblk(l.g.N / 4), p->B);
     ++p->nlaunch, k_Ly4<<<g4, MPN_TPB, 0, st>>>(l.g, cf, l.rho, a.x, l.y);
@@ -571,18 +620,27 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   }
   int m = p->desc.cheb_degree;
   bool prof = (k == 0);
+  // Iterate buffers: a fused level reads the operand with a halo and writes
+  // the updated iterate to the other buffer.  The 2m - 1 halo-reading updates
+  // of a V-cycle flip the buffer an odd number of times, so starting in e2
+  // ends in e.
+  float* cur = l.fs_tt ? l.e2 : l.e;
+  auto other = [&](float* e) { return !l.fs_tt ? e : (e == l.e ? l.e2 : l.e); };
   StepArgs a;
   memset(&a, 0, sizeof(a));
-  a.r = l.r; a.x = l.e; a.e = l.e; a.d = l.d;
+  a.r = l.r; a.d = l.d;
   // pre-smoothing from e = 0: d = Dinv r / th, e = d
-  ++p->nlaunch, k_cheb_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, l.e, l.d);
+  ++p->nlaunch, k_cheb_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, cur, l.d);
   for (int s = 1; s < m; ++s) {
     a.c1 = p->cheb_c1[s]; a.c2 = p->cheb_c2[s];
+    a.x = cur; a.e = other(cur);
     if (prof) prof_mark(p, st);
     stencil(p, k, a, SM_CHEB, st);
     if (prof) prof_mark(p, st);
+    cur = other(cur);
   }
   // residual, restricted to the coarse level
+  a.x = cur; a.e = cur;
   a.out = l.t;
   stencil(p, k, a, SM_RES, st);
   Level& lc = p->lv[k + 1];
@@ -590,17 +648,21 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   CKL();
   TRY(vcycle(p, k + 1, st));
   if (!l.cz[0] && l.cz[1] && l.cz[2] && l.g.per[1] && l.g.per[2] && l.g.n[2] % 4 == 0)
-    ++p->nlaunch, k_prolong_add4<<<dim3(sblk(l.g.N / 4), B), MPN_TPB, 0, st>>>(l.g, lc.g, lc.e, l.e);
+    ++p->nlaunch, k_prolong_add4<<<dim3(sblk(l.g.N / 4), B), MPN_TPB, 0, st>>>(l.g, lc.g, lc.e, cur);
   else
-    ++p->nlaunch, k_prolong_add<<<gr, MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], lc.e, nullptr, l.e);
+    ++p->nlaunch, k_prolong_add<<<gr, MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], lc.e, nullptr, cur);
   // post-smoothing
   a.c1 = 0.f; a.c2 = p->cheb_inv_th;
+  a.x = cur; a.e = other(cur);
   stencil(p, k, a, SM_POST0, st);
+  cur = other(cur);
   for (int s = 1; s < m; ++s) {
     a.c1 = p->cheb_c1[s]; a.c2 = p->cheb_c2[s];
+    a.x = cur; a.e = other(cur);
     if (prof) prof_mark(p, st);
     stencil(p, k, a, SM_CHEB, st);
     if (prof) prof_mark(p, st);
+    cur = other(cur);
   }
   CKL();
   return MPN_OK;

@@ -68,6 +68,17 @@ struct CoefB {
   __device__ __forceinline__ float operator()(int v, int p) const { return __ldg(base[v] + p * ps[v]); }
 };
 
+// a = q / n, r = q mod n (0 <= q, 1 <= n) without an integer division: a
+// float estimate that is off by at most one while the quotient is below 2^21,
+// corrected by one step.
+__device__ __forceinline__ int fdivmod(int q, int n, float inv_n, int& r) {
+  int a = __float2int_rz(((float)q + 0.5f) * inv_n);
+  r = q - a * n;
+  if (r < 0) { --a; r += n; }
+  else if (r >= n) { ++a; r -= n; }
+  return a;
+}
+
 __device__ __forceinline__ void decode(const Grid& g, int p, int pos[3]) {
   pos[2] = p % g.n[2];
   int q = p / g.n[2];

@@ -794,13 +794,11 @@ __global__ void k_mse_grad(int N, int V, int B, const float* __restrict__ z, con
 //   k_res64_q:  r = base + L^T y + theta 1_B (omega - u), partials of ||r||^2
 // Points away from non-periodic edges use the central weights directly.
 __device__ __forceinline__ void decode_fast(const Grid& g, int p, int pos[3]) {
-  int n12 = g.n[1] * g.n[2];
-  int i0 = __float2int_rz(((float)p + 0.5f) * __frcp_rn((float)n12));
-  int rem = p - i0 * n12;
-  int i1 = __float2int_rz(((float)rem + 0.5f) * __frcp_rn((float)g.n[2]));
-  pos[0] = i0; pos[1] = i1; pos[2] = rem - i1 * g.n[2];
+  int rem, i2;
+  pos[0] = fdivmod(p, g.n[1] * g.n[2], __frcp_rn((float)(g.n[1] * g.n[2])), rem);
+  pos[1] = fdivmod(rem, g.n[2], __frcp_rn((float)g.n[2]), i2);
+  pos[2] = i2;
 }
-
 __device__ __forceinline__ bool any_edge(const Grid& g, const int pos[3]) {
   bool e = pos[0] < 3 || pos[0] > g.n[0] - 4;
   for (int d = 1; d < 3; ++d)

@@ -29,13 +29,12 @@ struct StepArgs {
   float c1, c2;
 };
 
-// p -> (t, x, y) without integer division (exact for p < 2^21).
+// p -> (t, x, y) without integer division.
 __device__ __forceinline__ void decode_f(const Grid& g, int p, float inv12, float inv2, int pos[3]) {
-  int n12 = g.n[1] * g.n[2];
-  int i0 = __float2int_rz(((float)p + 0.5f) * inv12);
-  int rem = p - i0 * n12;
-  int i1 = __float2int_rz(((float)rem + 0.5f) * inv2);
-  pos[0] = i0; pos[1] = i1; pos[2] = rem - i1 * g.n[2];
+  int rem, i2;
+  pos[0] = fdivmod(p, g.n[1] * g.n[2], inv12, rem);
+  pos[1] = fdivmod(rem, g.n[2], inv2, i2);
+  pos[2] = i2;
 }
 
 // Neighbour at offset +-1 along d for an interior/periodic coordinate.
@@ -154,23 +153,22 @@ struct CoefB4 {
 
 // group (it, ix, iy0) of p0 = first point; returns false if the group needs
 // the scalar fallback (touches a non-periodic y edge region)
-__device__ __forceinline__ void group_pos(const Grid& g, int q, int pos[3]) {
-  int ng = g.n[2] >> 2;
-  int row = q / ng;
-  pos[2] = (q - row * ng) << 2;
-  pos[1] = row % g.n[1];
-  pos[0] = row / g.n[1];
+__device__ __forceinline__ void group_pos(const Grid& g, int q, float inv_ng, float inv_n1, int pos[3]) {
+  int ng = g.n[2] >> 2, r;
+  int row = fdivmod(q, ng, inv_ng, r);
+  pos[2] = r << 2;
+  pos[0] = fdivmod(row, g.n[1], inv_n1, pos[1]);
 }
-
-__global__ void __launch_bounds__(256) k_Ly4(Grid g, Coef cf, const float* __restrict__ rho, const float* __restrict__ x,
+__global__ void __launch_bounds__(256, 6) k_Ly4(Grid g, Coef cf, const float* __restrict__ rho, const float* __restrict__ x,
                                              float* __restrict__ y) {
   const int b = blockIdx.y;
   const size_t off = (size_t)b * g.N;
   const float* xb = x + off;
   const CoefB4 C(cf, b);
   const int NG = g.N >> 2;
+  const float inv_ng = 1.f / (float)(g.n[2] >> 2), inv_n1 = 1.f / (float)g.n[1];
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < NG; q += gridDim.x * blockDim.x) {
-    int pos[3]; group_pos(g, q, pos);
+    int pos[3]; group_pos(g, q, inv_ng, inv_n1, pos);
     const int p0 = q << 2;
     const int n2 = g.n[2];
     bool yedge = !g.per[2] && (pos[2] < 3 || pos[2] + 3 > n2 - 4);
@@ -220,15 +218,16 @@ __global__ void __launch_bounds__(256) k_Ly4(Grid g, Coef cf, const float* __res
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256) k_LTy4(Grid g, Coef cf, StepArgs a) {
+__global__ void __launch_bounds__(256, 5) k_LTy4(Grid g, Coef cf, StepArgs a) {
   const int b = blockIdx.y;
   const size_t off = (size_t)b * g.N;
   const float* yb = a.y + off;
   const CoefB4 C(cf, b);
   const int NG = g.N >> 2;
+  const float inv_ng = 1.f / (float)(g.n[2] >> 2), inv_n1 = 1.f / (float)g.n[1];
   float acc = 0.f;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < NG; q += gridDim.x * blockDim.x) {
-    int pos[3]; group_pos(g, q, pos);
+    int pos[3]; group_pos(g, q, inv_ng, inv_n1, pos);
     const int p0 = q << 2;
     const int n2 = g.n[2];
     float4 qv;

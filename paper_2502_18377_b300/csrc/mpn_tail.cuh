@@ -76,12 +76,12 @@ struct TailLv {
 template <int D>
 __device__ __forceinline__ void tl_pos(const Grid& g, int plane, float invpl, float inv2, int t0, int j, int pos[3],
                                        int& rem) {
-  int lt = __float2int_rz(((float)j + 0.5f) * invpl);
-  rem = j - lt * plane;
+  int lt = fdivmod(j, plane, invpl, rem);
   pos[0] = t0 + lt;
   if (D == 3) {
-    int i1 = __float2int_rz(((float)rem + 0.5f) * inv2);
-    pos[1] = i1; pos[2] = rem - i1 * g.n[2];
+    int i2;
+    pos[1] = fdivmod(rem, g.n[2], inv2, i2);
+    pos[2] = i2;
   } else {
     pos[1] = rem; pos[2] = 0;
   }

@@ -73,6 +73,11 @@ CASES = [
     ("rand_utt_2d", lambda: wl.random_problem(25, (10, 16), (False, True), batch=2)),
     ("rand_scalars_3d", lambda: wl.random_problem(24, (6, 8, 8), (False, True, True), batch=3,
                                                   field_all=False)),
+    # float4 levels run the fused operator step; these two put Dirichlet x and
+    # y faces, one-sided edge rows and final-time rows inside its tiles
+    ("rand_dirichlet_3d", lambda: _no_utt(wl.random_problem(26, (8, 16, 12), (False, False, False), batch=2))),
+    ("rand_final_3d", lambda: _no_utt(wl.random_problem(27, (12, 8, 16), (False, False, True), batch=2,
+                                                        final_time_rows=True))),
 ]
 
 
@@ -90,11 +95,12 @@ def test_forward_matches_oracle(name, make):
 
 @pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
 def test_forward_passwise_levels_match_oracle(name, make):
-    """The same solve with every multigrid level run pass by pass (no fused
-    coarse end): both V-cycle schedules meet the oracle, and the fused one is
-    in use by default wherever two or more levels fit."""
+    """The same solve with every operator pass a kernel of its own (no fused
+    coarse end, no fused operator step): both schedules meet the oracle, and
+    the fused coarse end is in use by default wherever two or more levels
+    fit."""
     w = _round(make())
-    s = _solver(w, fused_coarse=False)
+    s = _solver(w, fused_coarse=False, fused_step=False)
     assert s.fused_level() == -1
     z = s.forward(_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega)).cpu().numpy()
     for b in range(w.batch):
@@ -145,16 +151,19 @@ def test_reduced_operator_matches_oracle_schur():
     """S u (FP32 kernels) against the oracle's Schur complement of A^T A."""
     for w in (wl.random_problem(31, (9, 20), (False, True), batch=2),
               wl.random_problem(32, (6, 10, 12), (False, False, True), batch=2, final_time_rows=True),
-              _round(wl.reaction_diffusion_2d(batch=2, n=(8, 16, 16)))):
+              _round(wl.reaction_diffusion_2d(batch=2, n=(8, 16, 16))),
+              wl.random_problem(33, (8, 12, 16), (False, False, False), batch=2, final_time_rows=True)):
         w = _round(w)
-        s = _solver(w)
         rng = np.random.default_rng(0)
         u = rng.normal(size=(w.batch, w.npoints)).astype(np.float32)
-        q = s.apply_reduced(_dev(w.fields), _dev(w.scalars), _dev(u)).cpu().numpy()
-        for b in range(w.batch):
-            A, d, kind, owner, zr, lam, el = _oracle_instance(w, b)
-            ref = el.S @ u[b].astype(np.float64)
-            assert _rel(q[b], ref) <= 2e-5, _rel(q[b], ref)
+        # the last two run the fused operator step at the finest level
+        for fused in (True, False):
+            s = _solver(w, fused_step=fused)
+            q = s.apply_reduced(_dev(w.fields), _dev(w.scalars), _dev(u)).cpu().numpy()
+            for b in range(w.batch):
+                A, d, kind, owner, zr, lam, el = _oracle_instance(w, b)
+                ref = el.S @ u[b].astype(np.float64)
+                assert _rel(q[b], ref) <= 2e-5, (fused, _rel(q[b], ref))
 
 
 def test_forward_is_deterministic():
