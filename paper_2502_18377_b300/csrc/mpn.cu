@@ -106,6 +106,14 @@ static inline double* slot(mpn_problem* p, int k) { return p->part + (size_t)k *
 // use few, stencil kernels many.
 static int nblk(int N) { int b = (N + MPN_TPB - 1) / MPN_TPB; return b < 1 ? 1 : (b > 64 ? 64 : b); }
 static int sblk(int N) { int b = (N + MPN_TPB - 1) / MPN_TPB; return b < 1 ? 1 : (b > 512 ? 512 : b); }
+// PCG vector kernels: one float4 group (or one value) per thread, up to
+// MPN_PMAX blocks per instance (each block writes one partial sum).
+static bool vec4_len(int N) { return N % 4 == 0; }
+static int vgrid(int N) {
+  int n = vec4_len(N) ? N / 4 : N;
+  int b = (n + MPN_TPB - 1) / MPN_TPB;
+  return b < 1 ? 1 : (b > MPN_PMAX ? MPN_PMAX : b);
+}
 
 static int dalloc(mpn_problem* p, void** ptr, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -248,7 +256,7 @@ static void plan_tail(mpn_problem* p) {
     if (p->L - k0 > TAIL_MAXL) continue;
     // a level with more than two points per thread and CTA runs better pass
     // by pass over the whole GPU (vectorised kernels, full occupancy)
-    if ((size_t)P * p->lv[k0].g.n[1] * p->lv[k0].g.n[2] > 2 * TAIL_TPB) continue;
+    if ((size_t)P * p->lv[k0].g.n[1] * p->lv[k0].g.n[2] > TAIL_MAX_PPT * TAIL_TPB) continue;
     TailArgs& ta = p->tail;
     memset(&ta, 0, sizeof(ta));
     size_t off = 0;
@@ -630,13 +638,18 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   memset(&a, 0, sizeof(a));
   a.r = l.r; a.d = l.d;
   // pre-smoothing from e = 0: d = Dinv r / th, e = d
-  ++p->nlaunch, k_cheb_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, cur, l.d);
+  if (vec4_len(l.g.N))
+    ++p->nlaunch, k_cheb_init<true><<<dim3(vgrid(l.g.N), B), MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, cur, l.d);
+  else
+    ++p->nlaunch, k_cheb_init<false><<<dim3(vgrid(l.g.N), B), MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, cur, l.d);
   for (int s = 1; s < m; ++s) {
     a.c1 = p->cheb_c1[s]; a.c2 = p->cheb_c2[s];
     a.x = cur; a.e = other(cur);
-    if (prof) prof_mark(p, st);
+    // profiling brackets one smoothing step per V-cycle (each event is a
+    // graph node of its own, so bracketing every step would slow the sweep)
+    if (prof && s == 1) prof_mark(p, st);
     stencil(p, k, a, SM_CHEB, st);
-    if (prof) prof_mark(p, st);
+    if (prof && s == 1) prof_mark(p, st);
     cur = other(cur);
   }
   // residual, restricted to the coarse level
@@ -659,9 +672,7 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   for (int s = 1; s < m; ++s) {
     a.c1 = p->cheb_c1[s]; a.c2 = p->cheb_c2[s];
     a.x = cur; a.e = other(cur);
-    if (prof) prof_mark(p, st);
     stencil(p, k, a, SM_CHEB, st);
-    if (prof) prof_mark(p, st);
     cur = other(cur);
   }
   CKL();
@@ -672,8 +683,9 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
 static int precond(mpn_problem* p, cudaStream_t st) {
   Level& l = p->lv[0];
   TRY(vcycle(p, 0, st));
-  dim3 gr(nblk(l.g.N), p->B);
-  ++p->nlaunch, k_final_z<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.e, nullptr, l.r, p->z, slot(p, S_RZ));
+  dim3 gv(vgrid(l.g.N), p->B);
+  if (vec4_len(l.g.N)) ++p->nlaunch, k_final_z<true><<<gv, MPN_TPB, 0, st>>>(l.g.N, l.e, l.r, p->z, slot(p, S_RZ));
+  else ++p->nlaunch, k_final_z<false><<<gv, MPN_TPB, 0, st>>>(l.g.N, l.e, l.r, p->z, slot(p, S_RZ));
   CKL();
   return MPN_OK;
 }
@@ -681,19 +693,27 @@ static int precond(mpn_problem* p, cudaStream_t st) {
 // Inner FP32 PCG on S x = r (r = lv[0].r), fixed iteration count, x = p->x.
 static int pcg(mpn_problem* p, int iters, cudaStream_t st) {
   Level& l = p->lv[0];
-  dim3 gr(nblk(l.g.N), p->B);
-  int P = gr.x;
+  const int N = l.g.N;
+  dim3 gv(vgrid(N), p->B);
+  const int P = gv.x;
+  const bool v4 = vec4_len(N);
   double* rz_old = p->dscal + p->B;
   TRY(precond(p, st));
-  ++p->nlaunch, k_pcg_init<<<gr, MPN_TPB, 0, st>>>(l.g.N, p->z, p->x, p->pv);
+  if (v4) ++p->nlaunch, k_pcg_init<true><<<gv, MPN_TPB, 0, st>>>(N, p->z, p->x, p->pv);
+  else ++p->nlaunch, k_pcg_init<false><<<gv, MPN_TPB, 0, st>>>(N, p->z, p->x, p->pv);
   for (int it = 0; it < iters; ++it) {
     TRY(apply_S(p, 0, p->pv, p->q, slot(p, S_PQ), st));
-    ++p->nlaunch, k_pcg_xr<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), slot(p, S_PQ), l.papply, P, p->pv, p->q, p->x, l.r,
-                                     rz_old);
+    if (v4)
+      ++p->nlaunch, k_pcg_xr<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, P, p->pv, p->q,
+                                                            p->x, l.r, rz_old);
+    else
+      ++p->nlaunch, k_pcg_xr<false><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, P, p->pv, p->q,
+                                                             p->x, l.r, rz_old);
     CKL();
     if (it == iters - 1) break;
     TRY(precond(p, st));
-    ++p->nlaunch, k_pcg_p<<<gr, MPN_TPB, 0, st>>>(l.g.N, slot(p, S_RZ), P, rz_old, p->z, p->pv);
+    if (v4) ++p->nlaunch, k_pcg_p<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), P, rz_old, p->z, p->pv);
+    else ++p->nlaunch, k_pcg_p<false><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), P, rz_old, p->z, p->pv);
     CKL();
   }
   return MPN_OK;

@@ -132,21 +132,34 @@ __global__ void k_LTpass(Grid g, Coef cf, const T* __restrict__ y, const float* 
 }
 
 // --------------------------------------------------- Chebyshev-Jacobi smoother
+// PCG vector kernels.  V4: the instance length is a multiple of 4 and every
+// thread handles float4 groups (grid from vgrid()).
+template <bool V4>
+__device__ __forceinline__ float4 vld(const float* a, int i) {
+  if (V4) return __ldg(reinterpret_cast<const float4*>(a) + i);
+  return make_float4(__ldg(a + i), 0.f, 0.f, 0.f);
+}
+template <bool V4>
+__device__ __forceinline__ void vst(float* a, int i, float4 v) {
+  if (V4) reinterpret_cast<float4*>(a)[i] = v;
+  else a[i] = v.x;
+}
+
 // The smoother iterates e <- e + d with
 //   d_0 = Dinv r_0 / th,  d_k = c1_k d_{k-1} + c2_k Dinv r_k,
 // r_k = r - S e_k, Dinv already scaled by 1 / lambda_max(Dinv S).
 // First smoothing step from e = 0 (look-ahead form): d = Dinv r / th, e = d.
+template <bool V4>
 __global__ void k_cheb_init(int N, const float* __restrict__ r, const float* __restrict__ dinv, float inv_th,
                             float* __restrict__ e, float* __restrict__ d) {
-  size_t off = (size_t)blockIdx.y * N;
-  GRID_LOOP(p, N) {
-    float v = inv_th * dinv[off + p] * r[off + p];
-    e[off + p] = v;
-    d[off + p] = v;
+  const size_t off = (size_t)blockIdx.y * N;
+  const int n = V4 ? N >> 2 : N;
+  GRID_LOOP(i, n) {
+    float4 v = inv_th * (vld<V4>(dinv + off, i) * vld<V4>(r + off, i));
+    vst<V4>(e + off, i, v);
+    vst<V4>(d + off, i, v);
   }
 }
-
-
 
 // ------------------------------------------------------ grid transfers (P^T, P)
 
@@ -467,66 +480,56 @@ __global__ void k_scale_dinv(int N, float* __restrict__ dinv, const double* __re
 
 // --------------------------------------------------------------------- PCG
 // z = e + d (d nullable); partial <r, z>.
-__global__ void k_final_z(int N, const float* __restrict__ e, const float* __restrict__ d,
-                          const float* __restrict__ r, float* __restrict__ z, double* __restrict__ part) {
-  int b = blockIdx.y;
-  size_t off = (size_t)b * N;
-  double acc = 0;
-  GRID_LOOP(p, N) {
-    float v = e[off + p];
-    if (d) v += d[off + p];
-    z[off + p] = v;
-    acc += (double)v * r[off + p];
+// z = e, partial <z, r> per block.
+template <bool V4>
+__global__ void k_final_z(int N, const float* __restrict__ e, const float* __restrict__ r, float* __restrict__ z,
+                          double* __restrict__ part) {
+  const int b = blockIdx.y;
+  const size_t off = (size_t)b * N;
+  const int n = V4 ? N >> 2 : N;
+  float acc = 0.f;
+  GRID_LOOP(i, n) {
+    float4 v = vld<V4>(e + off, i), rr = vld<V4>(r + off, i);
+    vst<V4>(z + off, i, v);
+    acc += v.x * rr.x + v.y * rr.y + v.z * rr.z + v.w * rr.w;
   }
-  double s = block_sum(acc);
+  double s = block_sum((double)acc);
   if (threadIdx.x == 0) part[b * MPN_PMAX + blockIdx.x] = s;
 }
-
-// x = 0; p = z   (start of PCG; <r, z> partials already produced)
+template <bool V4>
 __global__ void k_pcg_init(int N, const float* __restrict__ z, float* __restrict__ x, float* __restrict__ pv) {
-  size_t off = (size_t)blockIdx.y * N;
-  GRID_LOOP(p, N) { x[off + p] = 0.f; pv[off + p] = z[off + p]; }
+  const size_t off = (size_t)blockIdx.y * N;
+  const int n = V4 ? N >> 2 : N;
+  GRID_LOOP(i, n) { vst<V4>(x + off, i, make_float4(0.f, 0.f, 0.f, 0.f)); vst<V4>(pv + off, i, vld<V4>(z + off, i)); }
 }
-
-// alpha = <r,z> / <p,q>; x += alpha p; r -= alpha q; saves <r,z> in rz_old.
+template <bool V4>
 __global__ void k_pcg_xr(int N, const double* __restrict__ part_rz, const double* __restrict__ part_pq, int P,
                          int Prz, const float* __restrict__ pv, const float* __restrict__ q, float* __restrict__ x,
                          float* __restrict__ r, double* __restrict__ rz_old) {
-  int b = blockIdx.y;
-  double rz = sum_partials(part_rz, b, Prz);
-  double pq = sum_partials(part_pq, b, P);
-  float alpha = (pq > 0 && rz > 0) ? (float)(rz / pq) : 0.f;
+  const int b = blockIdx.y;
+  const double rz = sum_partials(part_rz, b, Prz);
+  const double pq = sum_partials(part_pq, b, P);
+  const float alpha = (pq > 0 && rz > 0) ? (float)(rz / pq) : 0.f;
   if (blockIdx.x == 0 && threadIdx.x == 0) rz_old[b] = rz;
-  size_t off = (size_t)b * N;
-  GRID_LOOP(p, N) {
-    x[off + p] += alpha * pv[off + p];
-    r[off + p] -= alpha * q[off + p];
+  const size_t off = (size_t)b * N;
+  const int n = V4 ? N >> 2 : N;
+  GRID_LOOP(i, n) {
+    float4 xv = vld<V4>(x + off, i), pp = vld<V4>(pv + off, i), rv = vld<V4>(r + off, i), qq = vld<V4>(q + off, i);
+    vst<V4>(x + off, i, xv + alpha * pp);
+    vst<V4>(r + off, i, rv - alpha * qq);
   }
 }
-
-// beta = <r,z>_new / <r,z>_old; p = z + beta p
+template <bool V4>
 __global__ void k_pcg_p(int N, const double* __restrict__ part_rz, int P, const double* __restrict__ rz_old,
                         const float* __restrict__ z, float* __restrict__ pv) {
-  int b = blockIdx.y;
-  double rz = sum_partials(part_rz, b, P);
-  double ro = rz_old[b];
-  float beta = (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f;
-  size_t off = (size_t)b * N;
-  GRID_LOOP(p, N) pv[off + p] = z[off + p] + beta * pv[off + p];
+  const int b = blockIdx.y;
+  const double rz = sum_partials(part_rz, b, P);
+  const double ro = rz_old[b];
+  const float beta = (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f;
+  const size_t off = (size_t)b * N;
+  const int n = V4 ? N >> 2 : N;
+  GRID_LOOP(i, n) vst<V4>(pv + off, i, vld<V4>(z + off, i) + beta * vld<V4>(pv + off, i));
 }
-
-// ------------------------------------------------------- FP64 refinement glue
-// partial ||v||^2 (double input)
-__global__ void k_norm2_d(int N, const double* __restrict__ v, double* __restrict__ part) {
-  int b = blockIdx.y;
-  size_t off = (size_t)b * N;
-  double acc = 0;
-  GRID_LOOP(p, N) { double t = v[off + p]; acc += t * t; }
-  double s = block_sum(acc);
-  if (threadIdx.x == 0) part[b * MPN_PMAX + blockIdx.x] = s;
-}
-
-// r32 = r64 / ||r64|| ; the norm is saved in scale[b]
 __global__ void k_to32(int N, const double* __restrict__ r64, const double* __restrict__ part, int P,
                        float* __restrict__ r32, double* __restrict__ scale) {
   int b = blockIdx.y;

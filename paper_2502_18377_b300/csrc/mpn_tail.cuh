@@ -21,7 +21,13 @@ namespace cg = cooperative_groups;
 
 #define TAIL_TPB 512
 #define TAIL_MAXL 16
-#define TAIL_MAX_CLUSTER 8
+// first fused level: at most TAIL_MAX_PPT points per thread and CTA
+#ifndef TAIL_MAX_PPT
+#define TAIL_MAX_PPT 4
+#endif
+#ifndef TAIL_MAX_CLUSTER
+#define TAIL_MAX_CLUSTER 4
+#endif
 
 struct TailLevel {
   Grid g;
