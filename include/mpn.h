@@ -98,8 +98,8 @@ typedef struct mpn_stats {
 
 typedef struct mpn_problem mpn_problem;
 
-/* Fills *desc with defaults (tol 1e-7, max_refine 12, inner_iters 6,
- * cheb_degree 4, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 1). */
+/* Fills *desc with defaults (tol 1e-7, max_refine 12, inner_iters 5,
+ * cheb_degree 5, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 1). */
 int mpn_default_desc(mpn_desc* desc);
 
 /* Validates the descriptor, builds the grid hierarchy (spatial halving, time

@@ -164,7 +164,7 @@ class Solver:
     """One problem object (grid, batch, coefficient layout) of the C ABI."""
 
     def __init__(self, geom: dict, batch: int, field_of, nfields: int, tol=1e-7, max_refine=12,
-                 inner_iters=6, cheb_degree=4, coarse_min=4, max_coarse=2048, fused_coarse=True,
+                 inner_iters=5, cheb_degree=5, coarse_min=4, max_coarse=2048, fused_coarse=True,
                  fused_step=True):
         lib = load()
         d = MpnDesc()

@@ -63,6 +63,7 @@ struct mpn_problem {
   float *Kband = nullptr, *Kinv = nullptr;
   int* ferr = nullptr;
   float *scalars = nullptr, *rhs = nullptr, *omega = nullptr;
+  float* scal4 = nullptr;  // scalars replicated 4 times, [V][B][4]
   int* field_of_dev = nullptr;
   float *x = nullptr, *pv = nullptr, *q = nullptr, *z = nullptr;
   double *u64 = nullptr, *r64 = nullptr, *y64 = nullptr, *g64 = nullptr;
@@ -158,8 +159,13 @@ static Coef make_coef(const mpn_problem* p, const float* fields) {
   for (int k = 0; k < p->L; ++k) if (p->lv[k].fields == fields) N = p->lv[k].g.N;
   for (int v = 0; v < 7; ++v) {
     int f = v < p->V ? p->desc.field_of[v] : -1;
-    if (f >= 0) { c.ptr[v] = fields + (size_t)f * p->B * N; c.bstride[v] = N; c.pstride[v] = 1; }
-    else { c.ptr[v] = p->scalars + (size_t)(v < p->V ? v : 0) * p->B; c.bstride[v] = 1; c.pstride[v] = 0; }
+    if (f >= 0) {
+      c.ptr[v] = c.ptr4[v] = fields + (size_t)f * p->B * N;
+      c.bstride[v] = c.bstride4[v] = N; c.pstride[v] = 1;
+    } else {
+      c.ptr[v] = p->scalars + (size_t)(v < p->V ? v : 0) * p->B; c.bstride[v] = 1; c.pstride[v] = 0;
+      c.ptr4[v] = p->scal4 + (size_t)(v < p->V ? v : 0) * p->B * 4; c.bstride4[v] = 4;
+    }
   }
   return c;
 }
@@ -175,8 +181,8 @@ extern "C" int mpn_default_desc(mpn_desc* d) {
   for (int v = 0; v < 7; ++v) d->field_of[v] = -1;
   d->tol = 1e-7;
   d->max_refine = 12;
-  d->inner_iters = 6;
-  d->cheb_degree = 4;
+  d->inner_iters = 5;
+  d->cheb_degree = 5;
   d->coarse_min = 4;
   d->max_coarse = 2048;
   d->fused_coarse = 1;
@@ -425,6 +431,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   AL(p->Kinv, (size_t)B * p->M * p->M);
   AL(p->ferr, B);
   AL(p->scalars, (size_t)V * B);
+  AL(p->scal4, (size_t)V * B * 4);
   AL(p->rhs, N0); AL(p->omega, N0);
   AL(p->field_of_dev, 8);
   AL(p->x, N0); AL(p->pv, N0); AL(p->q, N0); AL(p->z, N0);
@@ -555,9 +562,11 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
   Level& l0 = p->lv[0];
   if (F > 0) CK(cudaMemcpyAsync(l0.fields, fields, sizeof(float) * (size_t)F * B * l0.g.N, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(p->scalars, scalars, sizeof(float) * (size_t)V * B, cudaMemcpyDeviceToDevice, st));
+  ++p->nlaunch, k_rep4<<<(V * B + MPN_TPB - 1) / MPN_TPB, MPN_TPB, 0, st>>>(V * B, p->scalars, p->scal4);
   {
     Coef cf = make_coef(p, l0.fields);
-    ++p->nlaunch, k_rho_fine<<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, p->rho64);
+    if (p->D == 3) ++p->nlaunch, k_rho_fine<3><<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, p->rho64);
+    else ++p->nlaunch, k_rho_fine<2><<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, p->rho64);
     CKL();
   }
   for (int k = 1; k < p->L; ++k) {
@@ -868,7 +877,8 @@ static int forward_impl(mpn_problem* p, const float* fields, const float* scalar
   int status = refine_solve(p, nullptr, u0 == nullptr, stats, st);
   if (status != MPN_OK && status != MPN_ERR_NOT_CONVERGED) return status;
   Coef cf = make_coef(p, l.fields);
-  ++p->nlaunch, k_recover<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
+  if (p->D == 3) ++p->nlaunch, k_recover<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
+  else ++p->nlaunch, k_recover<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
   CKL();
   CK(cudaMemcpyAsync(p->uf64, p->u64, sizeof(double) * N0, cudaMemcpyDeviceToDevice, st));
   p->zd_valid = true;
@@ -907,14 +917,24 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
   }
   Coef cf = make_coef(p, l.fields);
   // reduced right-hand side g_u - M_{u zeta} M_{zeta zeta}^{-1} g_zeta (FP64)
-  ++p->nlaunch, k_adj_kappa<<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
-  ++p->nlaunch, k_adj_rhs<<<gr, MPN_TPB, 0, st>>>(l.g, g_z, p->kap, p->g64);
+  if (p->D == 3) {
+    ++p->nlaunch, k_adj_kappa<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
+    ++p->nlaunch, k_adj_rhs<3><<<gr, MPN_TPB, 0, st>>>(l.g, g_z, p->kap, p->g64);
+  } else {
+    ++p->nlaunch, k_adj_kappa<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
+    ++p->nlaunch, k_adj_rhs<2><<<gr, MPN_TPB, 0, st>>>(l.g, g_z, p->kap, p->g64);
+  }
   ++p->nlaunch, k_set_u<<<gr, MPN_TPB, 0, st>>>(l.g.N, nullptr, p->u64);
   CKL();
   int status = refine_solve(p, p->g64, true, stats, st);
   if (status != MPN_OK && status != MPN_ERR_NOT_CONVERGED) return status;
   double* gp = slot(p, S_GR0);
-  ++p->nlaunch, k_gradients<<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->rhs, p->uf64, p->u64, g_z, dfields, drhs, domega, dz, gp);
+  if (p->D == 3)
+    ++p->nlaunch, k_gradients<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->rhs, p->uf64, p->u64, g_z, dfields, drhs,
+                                                         domega, dz, gp);
+  else
+    ++p->nlaunch, k_gradients<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->rhs, p->uf64, p->u64, g_z, dfields, drhs,
+                                                         domega, dz, gp);
   ++p->nlaunch, k_scalar_grads<<<B, 64, 0, st>>>(V, B, p->field_of_dev, gp, gr.x, dscalars);
   CKL();
   CK(cudaStreamSynchronize(st));

@@ -47,6 +47,11 @@ struct Coef {
   // strides (N, 1), a per-instance scalar (1, 0).
   const float* ptr[7];
   int bstride[7], pstride[7];
+  // the same with per-instance scalars stored 4 times ([V][B][4]), so that a
+  // float4 load at stride 0 reads a scalar: c_v as float4 at (b, p) =
+  // ptr4[v][b * bstride4[v] + p * pstride[v]]
+  const float* ptr4[7];
+  int bstride4[7];
 };
 
 __device__ __forceinline__ float coefv(const Coef& c, int v, int b, int p, int N) {
@@ -84,6 +89,21 @@ __device__ __forceinline__ void decode(const Grid& g, int p, int pos[3]) {
   int q = p / g.n[2];
   pos[1] = q % g.n[1];
   pos[0] = q / g.n[1];
+}
+
+// decode() without integer division; any_edge: the point is within 2 of a
+// time edge or of a non-periodic spatial edge (one-sided forms nearby).
+__device__ __forceinline__ void decode_fast(const Grid& g, int p, int pos[3]) {
+  int rem, i2;
+  pos[0] = fdivmod(p, g.n[1] * g.n[2], __frcp_rn((float)(g.n[1] * g.n[2])), rem);
+  pos[1] = fdivmod(rem, g.n[2], __frcp_rn((float)g.n[2]), i2);
+  pos[2] = i2;
+}
+__device__ __forceinline__ bool any_edge(const Grid& g, const int pos[3]) {
+  bool e = pos[0] < 3 || pos[0] > g.n[0] - 4;
+  for (int d = 1; d < 3; ++d)
+    if (d < g.D && !g.per[d]) e |= pos[d] < 3 || pos[d] > g.n[d] - 4;
+  return e;
 }
 
 // Point index of the neighbour at offset o along d (wrapping when periodic).
@@ -156,10 +176,11 @@ template <> __device__ __forceinline__ float is2_of<float>(const Grid& g, int d)
 template <> __device__ __forceinline__ double is2_of<double>(const Grid& g, int d) { return g.ds2[d]; }
 
 // Point weight rho_i = 1 / (1 + sum_d beta_d^T W_d^{-1} beta_d).
-template <class T>
+template <class T, int DD = 0>
 __device__ __forceinline__ T rho_point(const Grid& g, const Coef& cf, int b, int p, const int pos[3]) {
   T gam = 0;
-  for (int d = 0; d < g.D; ++d) {
+#pragma unroll
+  for (int d = 0; d < (DD ? DD : g.D); ++d) {
     T b1 = (T)coefv(cf, 1 + 2 * d, b, p, g.N) * is1_of<T>(g, d);
     T b2 = (T)coefv(cf, 2 + 2 * d, b, p, g.N) * is2_of<T>(g, d);
     int cls = edge_class(g, d, pos[d]);

@@ -51,21 +51,17 @@ __device__ __forceinline__ void dforms1(int cls, float xm2, float xm1, float x0,
   else { a1 = 1.5f * x0 - 2.f * xm1 + 0.5f * xm2; a2 = x0 - 2.f * xm1 + xm2; }
 }
 
-// Coefficient access with per-instance scalars held in registers.
-struct CoefR4 {
-  const float* base[7];   // field data of this instance, or nullptr for a scalar
-  float sv[7];
-  __device__ __forceinline__ CoefR4(const Coef& c, int b) {
+// Branch-free coefficient access: fields at stride 1, per-instance scalars
+// (stored 4 times) at stride 0, both as one float4 or scalar load.
+struct CoefU4 {
+  const float* base[7];
+  int ps[7];
+  __device__ __forceinline__ CoefU4(const Coef& c, int b) {
 #pragma unroll
-    for (int v = 0; v < 7; ++v) {
-      const float* q = c.ptr[v] ? c.ptr[v] + (size_t)b * c.bstride[v] : nullptr;
-      const bool fld = q && c.pstride[v];
-      base[v] = fld ? q : nullptr;
-      sv[v] = (!fld && q) ? __ldg(q) : 0.f;
-    }
+    for (int v = 0; v < 7; ++v) { base[v] = c.ptr4[v] + (size_t)b * c.bstride4[v]; ps[v] = c.pstride[v]; }
   }
-  __device__ __forceinline__ float4 at4(int v, int p) const { return base[v] ? ld4(base[v] + p) : f4(sv[v]); }
-  __device__ __forceinline__ float at(int v, int p) const { return base[v] ? __ldg(base[v] + p) : sv[v]; }
+  __device__ __forceinline__ float4 at4(int v, int p) const { return ld4(base[v] + p * ps[v]); }
+  __device__ __forceinline__ float at(int v, int p) const { return __ldg(base[v] + p * ps[v]); }
 };
 
 template <int MODE, int TT, bool PER1, bool PER2>
@@ -83,7 +79,7 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
   float* xs = fsm;
   float* ys = fsm + fs_rows_x(TT) * n2;
   const float* X = a.x + off;
-  const CoefR4 C(cf, b);
+  const CoefU4 C(cf, b);
   const float h1t = 0.5f * g.is1[0], h1x = 0.5f * g.is1[1], h1y = 0.5f * g.is1[2];
   const float i2t = g.is2[0], i2x = g.is2[1], i2y = g.is2[2];
 

@@ -9,11 +9,12 @@
 
 // ------------------------------------------------------------------- setup
 // rho at the finest level from the coefficients.
+template <int D>
 __global__ void k_rho_fine(Grid g, Coef cf, float* __restrict__ rho, double* __restrict__ rho64) {
   int b = blockIdx.y;
   GRID_LOOP(p, g.N) {
-    int pos[3]; decode(g, p, pos);
-    double r = rho_point<double>(g, cf, b, p, pos);
+    int pos[3]; decode_fast(g, p, pos);
+    double r = rho_point<double, D>(g, cf, b, p, pos);
     rho[(size_t)b * g.N + p] = (float)r;
     rho64[(size_t)b * g.N + p] = r;
   }
@@ -134,6 +135,12 @@ __global__ void k_LTpass(Grid g, Coef cf, const T* __restrict__ y, const float* 
 // --------------------------------------------------- Chebyshev-Jacobi smoother
 // PCG vector kernels.  V4: the instance length is a multiple of 4 and every
 // thread handles float4 groups (grid from vgrid()).
+// out[4 i + k] = in[i], k < 4 (per-instance scalars for stride-0 float4 loads).
+__global__ void k_rep4(int n, const float* __restrict__ in, float* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) reinterpret_cast<float4*>(out)[i] = f4(in[i]);
+}
+
 template <bool V4>
 __device__ __forceinline__ float4 vld(const float* a, int i) {
   if (V4) return __ldg(reinterpret_cast<const float4*>(a) + i);
@@ -502,19 +509,24 @@ __global__ void k_pcg_init(int N, const float* __restrict__ z, float* __restrict
   const int n = V4 ? N >> 2 : N;
   GRID_LOOP(i, n) { vst<V4>(x + off, i, make_float4(0.f, 0.f, 0.f, 0.f)); vst<V4>(pv + off, i, vld<V4>(z + off, i)); }
 }
+// The vector loads of a thread's first group are issued before the block
+// sums the partial dot products, so their latency overlaps the reduction.
 template <bool V4>
 __global__ void k_pcg_xr(int N, const double* __restrict__ part_rz, const double* __restrict__ part_pq, int P,
                          int Prz, const float* __restrict__ pv, const float* __restrict__ q, float* __restrict__ x,
                          float* __restrict__ r, double* __restrict__ rz_old) {
   const int b = blockIdx.y;
+  const size_t off = (size_t)b * N;
+  const int n = V4 ? N >> 2 : N;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  float4 xv, pp, rv, qq;
+  if (i0 < n) { xv = vld<V4>(x + off, i0); pp = vld<V4>(pv + off, i0); rv = vld<V4>(r + off, i0); qq = vld<V4>(q + off, i0); }
   const double rz = sum_partials(part_rz, b, Prz);
   const double pq = sum_partials(part_pq, b, P);
   const float alpha = (pq > 0 && rz > 0) ? (float)(rz / pq) : 0.f;
   if (blockIdx.x == 0 && threadIdx.x == 0) rz_old[b] = rz;
-  const size_t off = (size_t)b * N;
-  const int n = V4 ? N >> 2 : N;
-  GRID_LOOP(i, n) {
-    float4 xv = vld<V4>(x + off, i), pp = vld<V4>(pv + off, i), rv = vld<V4>(r + off, i), qq = vld<V4>(q + off, i);
+  for (int i = i0; i < n; i += stride) {
+    if (i != i0) { xv = vld<V4>(x + off, i); pp = vld<V4>(pv + off, i); rv = vld<V4>(r + off, i); qq = vld<V4>(q + off, i); }
     vst<V4>(x + off, i, xv + alpha * pp);
     vst<V4>(r + off, i, rv - alpha * qq);
   }
@@ -523,12 +535,18 @@ template <bool V4>
 __global__ void k_pcg_p(int N, const double* __restrict__ part_rz, int P, const double* __restrict__ rz_old,
                         const float* __restrict__ z, float* __restrict__ pv) {
   const int b = blockIdx.y;
+  const size_t off = (size_t)b * N;
+  const int n = V4 ? N >> 2 : N;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  float4 zz, pp;
+  if (i0 < n) { zz = vld<V4>(z + off, i0); pp = vld<V4>(pv + off, i0); }
   const double rz = sum_partials(part_rz, b, P);
   const double ro = rz_old[b];
   const float beta = (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f;
-  const size_t off = (size_t)b * N;
-  const int n = V4 ? N >> 2 : N;
-  GRID_LOOP(i, n) vst<V4>(pv + off, i, vld<V4>(z + off, i) + beta * vld<V4>(pv + off, i));
+  for (int i = i0; i < n; i += stride) {
+    if (i != i0) { zz = vld<V4>(z + off, i); pp = vld<V4>(pv + off, i); }
+    vst<V4>(pv + off, i, zz + beta * pp);
+  }
 }
 __global__ void k_to32(int N, const double* __restrict__ r64, const double* __restrict__ part, int P,
                        float* __restrict__ r32, double* __restrict__ scale) {
@@ -582,15 +600,17 @@ __global__ void k_set_u(int N, const float* __restrict__ u0, double* __restrict_
 // the (small) equation-row residual.  The duals follow from it:
 // lambda_E = -rho E* (forward, bE = b) and d_lambda_E = -rho E* (adjoint).
 // Returns rho E*.
+template <int D>
 __device__ __forceinline__ double recover_point(const Grid& g, const Coef& cf, int b, int p, const int pos[3],
                                                 const double* __restrict__ u, double rho, double bE,
                                                 const float* __restrict__ gz, double* zo) {
-  int V = 1 + 2 * g.D;
+  constexpr int V = 1 + 2 * D;
   size_t off = (size_t)b * g.N;
   double uc = u[off + p];
   double Est = (double)coefv(cf, 0, b, p, g.N) * uc - bE;
   double a[3][2], hw[3][2], qb[3][2];
-  for (int d = 0; d < g.D; ++d) {
+  #pragma unroll
+    for (int d = 0; d < D; ++d) {
     double a1 = 0, a2 = 0;
     for (int o = -2; o <= 2; ++o) {
       float w1 = dweight(1, pos[d], g.n[d], g.per[d], o), w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
@@ -614,7 +634,8 @@ __device__ __forceinline__ double recover_point(const Grid& g, const Coef& cf, i
   }
   double rE = rho * Est;
   zo[0] = uc;
-  for (int d = 0; d < g.D; ++d) {
+  #pragma unroll
+    for (int d = 0; d < D; ++d) {
     zo[1 + 2 * d] = (a[d][0] + hw[d][0] - rE * qb[d][0]) * g.ds1[d];
     zo[2 + 2 * d] = (a[d][1] + hw[d][1] - rE * qb[d][1]) * g.ds2[d];
   }
@@ -622,16 +643,17 @@ __device__ __forceinline__ double recover_point(const Grid& g, const Coef& cf, i
 }
 
 // z (FP32 and/or FP64) from u.
+template <int D>
 __global__ void k_recover(Grid g, Coef cf, const double* __restrict__ rho64, const double* __restrict__ u,
                           const float* __restrict__ bE, const float* __restrict__ gz, float* __restrict__ zf,
                           double* __restrict__ zd) {
   int b = blockIdx.y;
-  int V = 1 + 2 * g.D;
+  constexpr int V = 1 + 2 * D;
   size_t off = (size_t)b * g.N;
   GRID_LOOP(p, g.N) {
-    int pos[3]; decode(g, p, pos);
+    int pos[3]; decode_fast(g, p, pos);
     double zo[7];
-    recover_point(g, cf, b, p, pos, u, rho64[off + p], bE ? (double)bE[off + p] : 0.0, gz, zo);
+    recover_point<D>(g, cf, b, p, pos, u, rho64[off + p], bE ? (double)bE[off + p] : 0.0, gz, zo);
     size_t zb = (size_t)b * V * g.N;
     for (int v = 0; v < V; ++v) {
       if (zf) zf[zb + (size_t)v * g.N + p] = (float)zo[v];
@@ -649,78 +671,61 @@ __global__ void k_recover(Grid g, Coef cf, const double* __restrict__ rho64, con
 // z and d_z are recovered on the fly.  Field
 // gradients sum over the unknowns sharing a field; scalar gradients are
 // reduced per instance (partials in part[v]).
+template <int D>
 __global__ void k_gradients(Grid g, Coef cf, const double* __restrict__ rho64, const float* __restrict__ rhs,
                             const double* __restrict__ uf, const double* __restrict__ du, const float* __restrict__ gz,
                             float* __restrict__ dfields, float* __restrict__ drhs, float* __restrict__ domega,
                             float* __restrict__ dz_out, double* __restrict__ part) {
   int b = blockIdx.y;
-  int V = 1 + 2 * g.D;
+  constexpr int V = 1 + 2 * D;
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   size_t off = (size_t)b * g.N;
   GRID_LOOP(p, g.N) {
-    int pos[3]; decode(g, p, pos);
+    int pos[3]; decode_fast(g, p, pos);
     double zv[7], dv[7];
     double r = rho64[off + p];
-    double lam = -recover_point(g, cf, b, p, pos, uf, r, (double)rhs[off + p], nullptr, zv);
-    double dlam = -recover_point(g, cf, b, p, pos, du, r, 0.0, gz, dv);
-    for (int f = 0; f < cf.F; ++f) {
+    double lam = -recover_point<D>(g, cf, b, p, pos, uf, r, (double)rhs[off + p], nullptr, zv);
+    double dlam = -recover_point<D>(g, cf, b, p, pos, du, r, 0.0, gz, dv);
+    double cv[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      cv[v] = dlam * zv[v] + lam * dv[v];
+      if (cf.field_of[v] < 0) acc[v] += cv[v];
+    }
+#pragma unroll
+    for (int f = 0; f < 7; ++f) {
+      if (f >= cf.F) break;
       double s = 0;
-      for (int v = 0; v < V; ++v) if (cf.field_of[v] == f) s += dlam * zv[v] + lam * dv[v];
+#pragma unroll
+      for (int v = 0; v < V; ++v) if (cf.field_of[v] == f) s += cv[v];
       dfields[((size_t)f * cf.B + b) * g.N + p] = (float)s;
     }
-    for (int v = 0; v < V; ++v) if (cf.field_of[v] < 0) acc[v] += dlam * zv[v] + lam * dv[v];
     drhs[off + p] = (float)(-dlam);
     domega[off + p] = is_boundary(g, pos) ? (float)dv[0] : 0.f;
-    if (dz_out) for (int v = 0; v < V; ++v) dz_out[((size_t)b * V + v) * g.N + p] = (float)dv[v];
+    if (dz_out) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) dz_out[((size_t)b * V + v) * g.N + p] = (float)dv[v];
+    }
   }
+#pragma unroll
   for (int v = 0; v < V; ++v) {
     double s = block_sum(acc[v]);
     if (threadIdx.x == 0) part[((size_t)v * cf.B + b) * MPN_PMAX + blockIdx.x] = s;
   }
 }
 
-// Partials of the size of z(u) and of the last correction measured on every
-// unknown: u itself plus, per dimension, its first and second difference
-// quotients (the derivative unknowns up to their small point-local
-// correction).  Only a couple of digits are needed, so FP32.
-__global__ void k_znorm(Grid g, const double* __restrict__ u, const float* __restrict__ x,
-                        const double* __restrict__ scale, double* __restrict__ part_dz, double* __restrict__ part_z) {
-  int b = blockIdx.y;
-  float sc = (float)scale[b];
-  size_t off = (size_t)b * g.N;
-  float a1 = 0, a2 = 0;
-  GRID_LOOP(p, g.N) {
-    int pos[3]; decode(g, p, pos);
-    float uc = (float)u[off + p], xc = sc * x[off + p];
-    a2 += uc * uc; a1 += xc * xc;
-    for (int d = 0; d < g.D; ++d) {
-      float u1 = 0, u2 = 0, x1 = 0, x2 = 0;
-      for (int o = -2; o <= 2; ++o) {
-        float w1 = dweight(1, pos[d], g.n[d], g.per[d], o), w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
-        if (w1 == 0.f && w2 == 0.f) continue;
-        int q = o == 0 ? p : nbr(g, p, pos, d, o);
-        float uv = (float)u[off + q], xv = sc * x[off + q];
-        u1 += w1 * uv; u2 += w2 * uv; x1 += w1 * xv; x2 += w2 * xv;
-      }
-      u1 *= g.is1[d]; u2 *= g.is2[d]; x1 *= g.is1[d]; x2 *= g.is2[d];
-      a2 += u1 * u1 + u2 * u2; a1 += x1 * x1 + x2 * x2;
-    }
-  }
-  double s1 = block_sum((double)a1);
-  double s2 = block_sum((double)a2);
-  if (threadIdx.x == 0) { part_dz[b * MPN_PMAX + blockIdx.x] = s1; part_z[b * MPN_PMAX + blockIdx.x] = s2; }
-}
-
 // Adjoint right-hand side, part 1: per point psi = (W + beta beta^T)^{-1} S^{-1} g_zeta
 // and the coefficients of M_{u zeta} M_{zeta zeta}^{-1} g_zeta as a scatter through
 // the difference forms: kap[0] = c_0 beta.psi (center), kap[1+2d], kap[2+2d] = -(W_d psi_d).
+template <int D>
 __global__ void k_adj_kappa(Grid g, Coef cf, const float* __restrict__ gz, double* __restrict__ kap) {
   int b = blockIdx.y;
-  int V = 1 + 2 * g.D;
+  constexpr int V = 1 + 2 * D;
   GRID_LOOP(p, g.N) {
-    int pos[3]; decode(g, p, pos);
+    int pos[3]; decode_fast(g, p, pos);
     double hw[3][2], be[3][2], bwh = 0, gam = 0;
-    for (int d = 0; d < g.D; ++d) {
+    #pragma unroll
+    for (int d = 0; d < D; ++d) {
       int cls = edge_class(g, d, pos[d]);
       double b1 = coefv(cf, 1 + 2 * d, b, p, g.N) * g.ds1[d];
       double b2 = coefv(cf, 2 + 2 * d, b, p, g.N) * g.ds2[d];
@@ -734,7 +739,8 @@ __global__ void k_adj_kappa(Grid g, Coef cf, const float* __restrict__ gz, doubl
     }
     double fac = bwh / (1.0 + gam);
     double bpsi = 0;
-    for (int d = 0; d < g.D; ++d) {
+    #pragma unroll
+    for (int d = 0; d < D; ++d) {
       int cls = edge_class(g, d, pos[d]);
       double q1, q2; winv<double>(cls, be[d][0], be[d][1], q1, q2);
       double ps1 = hw[d][0] - q1 * fac, ps2 = hw[d][1] - q2 * fac;
@@ -748,14 +754,16 @@ __global__ void k_adj_kappa(Grid g, Coef cf, const float* __restrict__ gz, doubl
 }
 
 // Adjoint right-hand side, part 2: rhs_u = g_u - scatter(kap)  (FP64).
+template <int D>
 __global__ void k_adj_rhs(Grid g, const float* __restrict__ gz, const double* __restrict__ kap,
                           double* __restrict__ out) {
   int b = blockIdx.y;
   int V = 1 + 2 * g.D, B = gridDim.y;
   GRID_LOOP(p, g.N) {
-    int pos[3]; decode(g, p, pos);
+    int pos[3]; decode_fast(g, p, pos);
     double acc = kap[(size_t)b * g.N + p];
-    for (int d = 0; d < g.D; ++d)
+    #pragma unroll
+    for (int d = 0; d < D; ++d)
       for (int o = -2; o <= 2; ++o) {
         int ip = pos[d] - o;
         if (g.per[d]) { ip %= g.n[d]; if (ip < 0) ip += g.n[d]; }
@@ -790,25 +798,55 @@ __global__ void k_mse_grad(int N, int V, int B, const float* __restrict__ z, con
   }
 }
 
+
+// Partials of the size of z(u) and of the last correction measured on every
+// unknown: u itself plus, per dimension, its first and second difference
+// quotients (the derivative unknowns up to their small point-local
+// correction).  Only a couple of digits are needed, so FP32.
+__global__ void k_znorm(Grid g, const double* __restrict__ u, const float* __restrict__ x,
+                        const double* __restrict__ scale, double* __restrict__ part_dz, double* __restrict__ part_z) {
+  int b = blockIdx.y;
+  float sc = (float)scale[b];
+  size_t off = (size_t)b * g.N;
+  const double* ub = u + off;
+  const float* xb = x + off;
+  float a1 = 0, a2 = 0;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode_fast(g, p, pos);
+    float uc = (float)ub[p], xc = sc * xb[p];
+    a2 += uc * uc; a1 += xc * xc;
+    const bool edge = any_edge(g, pos);
+    for (int d = 0; d < g.D; ++d) {
+      float u1 = 0, u2 = 0, x1 = 0, x2 = 0;
+      if (!edge) {
+        int qm = nbr(g, p, pos, d, -1), qp = nbr(g, p, pos, d, 1);
+        float um = (float)ub[qm], up = (float)ub[qp], xm = sc * xb[qm], xp = sc * xb[qp];
+        u1 = 0.5f * (up - um); u2 = up - 2.f * uc + um;
+        x1 = 0.5f * (xp - xm); x2 = xp - 2.f * xc + xm;
+      } else {
+        for (int o = -2; o <= 2; ++o) {
+          float w1 = dweight(1, pos[d], g.n[d], g.per[d], o), w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
+          if (w1 == 0.f && w2 == 0.f) continue;
+          int q = o == 0 ? p : nbr(g, p, pos, d, o);
+          float uv = (float)ub[q], xv = sc * xb[q];
+          u1 += w1 * uv; u2 += w2 * uv; x1 += w1 * xv; x2 += w2 * xv;
+        }
+      }
+      u1 *= g.is1[d]; u2 *= g.is2[d]; x1 *= g.is1[d]; x2 *= g.is2[d];
+      a2 += u1 * u1 + u2 * u2; a1 += x1 * x1 + x2 * x2;
+    }
+  }
+  double s1 = block_sum((double)a1);
+  double s2 = block_sum((double)a2);
+  if (threadIdx.x == 0) { part_dz[b * MPN_PMAX + blockIdx.x] = s1; part_z[b * MPN_PMAX + blockIdx.x] = s2; }
+}
+
 // ------------------------------------------------- FP64 refinement residual
 // Two passes so that every FP64 operation is done once per point (FP64
 // throughput, not memory, bounds these):
 //   k_res64_y:  y = rho (b - L u)              (b, u nullable => 0)
 //   k_res64_q:  r = base + L^T y + theta 1_B (omega - u), partials of ||r||^2
 // Points away from non-periodic edges use the central weights directly.
-__device__ __forceinline__ void decode_fast(const Grid& g, int p, int pos[3]) {
-  int rem, i2;
-  pos[0] = fdivmod(p, g.n[1] * g.n[2], __frcp_rn((float)(g.n[1] * g.n[2])), rem);
-  pos[1] = fdivmod(rem, g.n[2], __frcp_rn((float)g.n[2]), i2);
-  pos[2] = i2;
-}
-__device__ __forceinline__ bool any_edge(const Grid& g, const int pos[3]) {
-  bool e = pos[0] < 3 || pos[0] > g.n[0] - 4;
-  for (int d = 1; d < 3; ++d)
-    if (d < g.D && !g.per[d]) e |= pos[d] < 3 || pos[d] > g.n[d] - 4;
-  return e;
-}
-
 template <int D>
 __global__ void k_res64_y(Grid g, Coef cf, const double* __restrict__ rho64, const double* __restrict__ u,
                           const float* __restrict__ bsrc, double* __restrict__ y) {

@@ -121,6 +121,7 @@ extern "C" int mpn_apply_reduced_noalloc(const mpn_desc* desc, const float* fiel
     cf.field_of[v] = f;
     if (f >= 0) { cf.ptr[v] = fields + (size_t)f * d.batch * N; cf.bstride[v] = (int)N; cf.pstride[v] = 1; }
     else { cf.ptr[v] = scalars + (size_t)(v < V ? v : 0) * d.batch; cf.bstride[v] = 1; cf.pstride[v] = 0; }
+    cf.ptr4[v] = nullptr; cf.bstride4[v] = 0;   // float4 scalar copies: not used here
   }
 
   cudaStream_t st = (cudaStream_t)stream;
