@@ -97,9 +97,12 @@ struct mpn_problem {
   std::vector<SweepGraph> graphs;
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_user = nullptr;
+  // setup: one stream per level for the independent power iterations
+  cudaStream_t aux[MAXL] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[MAXL] = {};
 };
 
-enum { S_RZ = 0, S_PQ, S_RN, S_DU, S_UN, S_PW, S_GN, S_GR0, NSLOT = S_GR0 + 8 };
+enum { S_RZ = 0, S_PQ, S_RN, S_DU, S_UN, S_PW, S_GN, S_GR0, S_PW0 = S_GR0 + 8, NSLOT = S_PW0 + MAXL };
 
 static inline double* slot(mpn_problem* p, int k) { return p->part + (size_t)k * p->B * MPN_PMAX; }
 
@@ -211,6 +214,11 @@ extern "C" void mpn_destroy(mpn_problem* p) {
   for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
   if (p->gstream) cudaStreamDestroy(p->gstream);
   if (p->ev_user) cudaEventDestroy(p->ev_user);
+  for (int k = 0; k < MAXL; ++k) {
+    if (p->aux[k]) cudaStreamDestroy(p->aux[k]);
+    if (p->ev_join[k]) cudaEventDestroy(p->ev_join[k]);
+  }
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
   for (void* a : p->allocs) cudaFree(a);
   if (p->hbuf) cudaFreeHost(p->hbuf);
@@ -580,23 +588,37 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
                                                                lc.rho, (float)(1 << nd));
     CKL();
   }
+  // Jacobi diagonals and lambda_max(Dinv S) per level: the levels are
+  // independent, so each runs its power iteration on a stream of its own
+  // while the coarsest system is factorised on st.
+  if (!p->ev_fork) {
+    CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    for (int k = 0; k < MAXL; ++k) {
+      CK(cudaStreamCreateWithFlags(&p->aux[k], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&p->ev_join[k], cudaEventDisableTiming));
+    }
+  }
+  CK(cudaEventRecord(p->ev_fork, st));
   for (int k = 0; k < p->L; ++k) {
     Level& l = p->lv[k];
     Coef cf = make_coef(p, l.fields);
     dim3 gr(nblk(l.g.N), B);
-    ++p->nlaunch, k_diag_inv<<<gr, MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.dinv);
+    cudaStream_t sk = k == p->L - 1 ? st : p->aux[k];
+    if (sk != st) CK(cudaStreamWaitEvent(sk, p->ev_fork, 0));
+    ++p->nlaunch, k_diag_inv<<<gr, MPN_TPB, 0, sk>>>(l.g, cf, l.rho, l.dinv);
     CKL();
     if (k == p->L - 1) break;
     // power method for lambda_max(Dinv S)
-    ++p->nlaunch, k_fill_hash<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.t);
-    double* pw = slot(p, S_PW);
+    ++p->nlaunch, k_fill_hash<<<gr, MPN_TPB, 0, sk>>>(l.g.N, l.t);
+    double* pw = slot(p, S_PW0 + k);
     for (int it = 0; it < 12; ++it) {
-      TRY(apply_S(p, k, l.t, l.d, nullptr, st));
-      ++p->nlaunch, k_power_w<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.dinv, l.d, l.e, pw);
-      if (it < 11) ++p->nlaunch, k_power_norm<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.e, l.t, pw, gr.x);
+      TRY(apply_S(p, k, l.t, l.d, nullptr, sk));
+      ++p->nlaunch, k_power_w<<<gr, MPN_TPB, 0, sk>>>(l.g.N, l.dinv, l.d, l.e, pw);
+      if (it < 11) ++p->nlaunch, k_power_norm<<<gr, MPN_TPB, 0, sk>>>(l.g.N, l.e, l.t, pw, gr.x);
     }
-    ++p->nlaunch, k_scale_dinv<<<gr, MPN_TPB, 0, st>>>(l.g.N, l.dinv, pw, gr.x, 1.1f, p->lam + k * B);
+    ++p->nlaunch, k_scale_dinv<<<gr, MPN_TPB, 0, sk>>>(l.g.N, l.dinv, pw, gr.x, 1.1f, p->lam + k * B);
     CKL();
+    CK(cudaEventRecord(p->ev_join[k], sk));
   }
   // coarsest: banded assembly, Cholesky, explicit inverse
   Level& lc = p->lv[p->L - 1];
@@ -616,6 +638,7 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
   }
 
   CKL();
+  for (int k = 0; k + 1 < p->L; ++k) CK(cudaStreamWaitEvent(st, p->ev_join[k], 0));
   p->setup_ok = true;
   return MPN_OK;
 }
@@ -666,7 +689,10 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   a.out = l.t;
   stencil(p, k, a, SM_RES, st);
   Level& lc = p->lv[k + 1];
-  ++p->nlaunch, k_restrict_vec<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], l.t, lc.r);
+  if (!l.cz[0] && l.cz[1] && l.cz[2] && l.g.per[1] && l.g.per[2] && l.g.n[2] % 8 == 0)
+    ++p->nlaunch, k_restrict_vec4<<<dim3(sblk(lc.g.N / 4), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.t, lc.r);
+  else
+    ++p->nlaunch, k_restrict_vec<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], l.t, lc.r);
   CKL();
   TRY(vcycle(p, k + 1, st));
   if (!l.cz[0] && l.cz[1] && l.cz[2] && l.g.per[1] && l.g.per[2] && l.g.n[2] % 4 == 0)

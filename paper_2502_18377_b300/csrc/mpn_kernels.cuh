@@ -266,6 +266,38 @@ __global__ void k_prolong_add4(Grid gf, Grid gc, const float* __restrict__ ec, f
   }
 }
 
+// r_c = P^T r_f for the same case with n_y % 8 == 0: one thread owns 4
+// coarse points along y, i.e. fine y 2j-1 .. 2j+7 of three fine x rows.
+__global__ void k_restrict_vec4(Grid gf, Grid gc, const float* __restrict__ fine, float* __restrict__ coarse) {
+  const int b = blockIdx.y;
+  const float* Fi = fine + (size_t)b * gf.N;
+  float* Co = coarse + (size_t)b * gc.N;
+  const int n1c = gc.n[1], n2c = gc.n[2], n1f = gf.n[1], n2f = gf.n[2];
+  const int G = n2c >> 2;
+  const float invG = 1.f / (float)G, inv1 = 1.f / (float)n1c;
+  const int NG = gc.N >> 2;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < NG; q += gridDim.x * blockDim.x) {
+    int gq, X;
+    const int row = fdivmod(q, G, invG, gq);
+    const int t = fdivmod(row, n1c, inv1, X);
+    const int fy = 8 * gq;                        // fine y of the group's first coarse point
+    float4 acc = f4(0.f);
+#pragma unroll
+    for (int r = -1; r <= 1; ++r) {
+      int xf = 2 * X + r;
+      if (xf < 0) xf += n1f;
+      const float w = r == 0 ? 1.f : 0.5f;
+      const float* base = Fi + ((size_t)t * n1f + xf) * n2f;
+      const float4 a = ld4(base + fy), c = ld4(base + fy + 4);
+      const float l = __ldg(base + (fy == 0 ? n2f - 1 : fy - 1));
+      const float4 o = make_float4(a.x + 0.5f * (a.y + l), a.z + 0.5f * (a.w + a.y), c.x + 0.5f * (c.y + a.w),
+                                   c.z + 0.5f * (c.w + c.y));
+      acc = acc + w * o;
+    }
+    *reinterpret_cast<float4*>(Co + (size_t)q * 4) = acc;
+  }
+}
+
 // ------------------------------------------------------ coarsest-level solve
 // Banded lower storage: Kb[b][j][j - k] = S[j][k] for 0 <= j - k <= bw.
 __global__ void k_coarse_assemble(Grid g, Coef cf, const float* __restrict__ rho, int bw, float* __restrict__ Kb) {
