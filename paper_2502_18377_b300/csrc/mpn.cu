@@ -64,6 +64,7 @@ struct mpn_problem {
   int* ferr = nullptr;
   float *scalars = nullptr, *rhs = nullptr, *omega = nullptr;
   float* scal4 = nullptr;  // scalars replicated 4 times, [V][B][4]
+  int field_mask = 0;      // bit v: c_v is a field
   int* field_of_dev = nullptr;
   float *x = nullptr, *pv = nullptr, *q = nullptr, *z = nullptr;
   double *u64 = nullptr, *r64 = nullptr, *y64 = nullptr, *g64 = nullptr;
@@ -237,15 +238,17 @@ extern "C" int mpn_levels(const mpn_problem* p, int* nl, int* shapes) {
 }
 
 #define FS_MAX_NY 128
+// c_0, c_xx and c_yy fields, every other coefficient a per-instance scalar
+#define FS_MASK_RD ((1 << 0) | (1 << 4) | (1 << 6))
 static size_t fs_smem(int tt, int ny) { return sizeof(float) * (size_t)(fs_rows_x(tt) + fs_rows_y(tt)) * ny; }
 // Opt the fused step kernels into the shared memory of the largest tile.
 static int fs_set_smem() {
   int bytes = (int)fs_smem(8, FS_MAX_NY);
   cudaError_t e = cudaSuccess;
-#define FS_ATTR(M, T, P1, P2) \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<M, T, P1, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-#define FS_ATTR_M(T, P1, P2) FS_ATTR(SM_POST0, T, P1, P2); FS_ATTR(SM_CHEB, T, P1, P2); FS_ATTR(SM_RES, T, P1, P2); FS_ATTR(SM_APPLY, T, P1, P2)
-#define FS_ATTR_P(T) FS_ATTR_M(T, true, true); FS_ATTR_M(T, true, false); FS_ATTR_M(T, false, true); FS_ATTR_M(T, false, false)
+#define FS_ATTR(M, T, P1, P2, MK) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<M, T, P1, P2, MK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+#define FS_ATTR_M(T, P1, P2, MK) FS_ATTR(SM_POST0, T, P1, P2, MK); FS_ATTR(SM_CHEB, T, P1, P2, MK); FS_ATTR(SM_RES, T, P1, P2, MK); FS_ATTR(SM_APPLY, T, P1, P2, MK)
+#define FS_ATTR_P(T) FS_ATTR_M(T, true, true, FS_ANY); FS_ATTR_M(T, true, false, FS_ANY); FS_ATTR_M(T, false, true, FS_ANY); FS_ATTR_M(T, false, false, FS_ANY); FS_ATTR_M(T, true, true, FS_MASK_RD)
   FS_ATTR_P(8);
   FS_ATTR_P(4);
 #undef FS_ATTR_P
@@ -375,6 +378,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   mpn_problem* p = new mpn_problem();
   p->desc = d;
   p->D = d.ndim; p->V = V; p->F = d.nfields; p->B = d.batch;
+  for (int v = 0; v < V; ++v) if (d.field_of[v] >= 0) p->field_mask |= 1 << v;
   if (p->D == 2) p->desc.n[2] = 1;
 
   // hierarchy: halve spatial dims (t kept) while the half is >= coarse_min
@@ -506,18 +510,21 @@ static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st
   if (l.fs_tt) {
     dim3 gs((l.g.n[0] / l.fs_tt) * (l.g.n[1] / FS_TX), p->B);
     size_t sm = fs_smem(l.fs_tt, l.g.n[2]);
-#define FS_LAUNCH(T, P1, P2)                                                                                  \
-  switch (mode) {                                                                                             \
-    case SM_POST0: ++p->nlaunch, k_step3<SM_POST0, T, P1, P2><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break; \
-    case SM_CHEB: ++p->nlaunch, k_step3<SM_CHEB, T, P1, P2><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;   \
-    case SM_RES: ++p->nlaunch, k_step3<SM_RES, T, P1, P2><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;     \
-    default: ++p->nlaunch, k_step3<SM_APPLY, T, P1, P2><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;     \
+#define FS_LAUNCH(T, P1, P2, MK)                                                                     \
+  switch (mode) {                                                                                    \
+    case SM_POST0: ++p->nlaunch, k_step3<SM_POST0, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break; \
+    case SM_CHEB: ++p->nlaunch, k_step3<SM_CHEB, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;   \
+    case SM_RES: ++p->nlaunch, k_step3<SM_RES, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;     \
+    default: ++p->nlaunch, k_step3<SM_APPLY, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;     \
   }
-#define FS_LAUNCH_T(P1, P2) if (l.fs_tt == 8) { FS_LAUNCH(8, P1, P2) } else { FS_LAUNCH(4, P1, P2) }
-    if (l.g.per[1] && l.g.per[2]) { FS_LAUNCH_T(true, true) }
-    else if (l.g.per[1]) { FS_LAUNCH_T(true, false) }
-    else if (l.g.per[2]) { FS_LAUNCH_T(false, true) }
-    else { FS_LAUNCH_T(false, false) }
+#define FS_LAUNCH_T(P1, P2, MK) if (l.fs_tt == 8) { FS_LAUNCH(8, P1, P2, MK) } else { FS_LAUNCH(4, P1, P2, MK) }
+    // compile-time coefficient layout for the common case of a reaction term
+    // and an isotropic diffusion field with scalar first-order and time terms
+    if (l.g.per[1] && l.g.per[2] && p->field_mask == FS_MASK_RD) { FS_LAUNCH_T(true, true, FS_MASK_RD) }
+    else if (l.g.per[1] && l.g.per[2]) { FS_LAUNCH_T(true, true, FS_ANY) }
+    else if (l.g.per[1]) { FS_LAUNCH_T(true, false, FS_ANY) }
+    else if (l.g.per[2]) { FS_LAUNCH_T(false, true, FS_ANY) }
+    else { FS_LAUNCH_T(false, false, FS_ANY) }
 #undef FS_LAUNCH_T
 #undef FS_LAUNCH
     return;

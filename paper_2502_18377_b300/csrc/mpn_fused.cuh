@@ -51,20 +51,35 @@ __device__ __forceinline__ void dforms1(int cls, float xm2, float xm1, float x0,
   else { a1 = 1.5f * x0 - 2.f * xm1 + 0.5f * xm2; a2 = x0 - 2.f * xm1 + xm2; }
 }
 
-// Branch-free coefficient access: fields at stride 1, per-instance scalars
-// (stored 4 times) at stride 0, both as one float4 or scalar load.
+// Coefficient access.  MASK = FS_ANY: fields at stride 1 and per-instance
+// scalars (stored four times) at stride 0, one load either way.  Otherwise
+// bit v of MASK says that c_v is a field (the problem's layout is fixed at
+// compile time): scalars are loaded once into registers and fields per group.
+#define FS_ANY 0x80
+template <int MASK>
 struct CoefU4 {
   const float* base[7];
   int ps[7];
+  float sv[7];
   __device__ __forceinline__ CoefU4(const Coef& c, int b) {
 #pragma unroll
-    for (int v = 0; v < 7; ++v) { base[v] = c.ptr4[v] + (size_t)b * c.bstride4[v]; ps[v] = c.pstride[v]; }
+    for (int v = 0; v < 7; ++v) {
+      base[v] = c.ptr4[v] + (size_t)b * c.bstride4[v];
+      ps[v] = c.pstride[v];
+      sv[v] = (MASK != FS_ANY && !((MASK >> v) & 1)) ? __ldg(base[v]) : 0.f;
+    }
   }
-  __device__ __forceinline__ float4 at4(int v, int p) const { return ld4(base[v] + p * ps[v]); }
-  __device__ __forceinline__ float at(int v, int p) const { return __ldg(base[v] + p * ps[v]); }
+  __device__ __forceinline__ float4 at4(int v, int p) const {
+    if (MASK == FS_ANY) return ld4(base[v] + p * ps[v]);
+    return ((MASK >> v) & 1) ? ld4(base[v] + p) : f4(sv[v]);
+  }
+  __device__ __forceinline__ float at(int v, int p) const {
+    if (MASK == FS_ANY) return __ldg(base[v] + p * ps[v]);
+    return ((MASK >> v) & 1) ? __ldg(base[v] + p) : sv[v];
+  }
 };
 
-template <int MODE, int TT, bool PER1, bool PER2>
+template <int MODE, int TT, bool PER1, bool PER2, int MASK>
 __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* __restrict__ rho, StepArgs a) {
   extern __shared__ __align__(16) float fsm[];
   constexpr int RXW = FS_TX + 4, RYW = FS_TX + 2;
@@ -79,7 +94,7 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
   float* xs = fsm;
   float* ys = fsm + fs_rows_x(TT) * n2;
   const float* X = a.x + off;
-  const CoefU4 C(cf, b);
+  const CoefU4<MASK> C(cf, b);
   const float h1t = 0.5f * g.is1[0], h1x = 0.5f * g.is1[1], h1y = 0.5f * g.is1[2];
   const float i2t = g.is2[0], i2x = g.is2[1], i2y = g.is2[2];
 
