@@ -257,6 +257,13 @@ static int fs_set_smem() {
   return e == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
 }
 
+// Instantiation of the fused coarse end for this problem's dimension and
+// coefficient layout.
+static const void* tail_fn(const mpn_problem* p) {
+  if (p->D == 3) return p->field_mask == FS_MASK_RD ? (const void*)k_vtail<3, FS_MASK_RD> : (const void*)k_vtail<3, FS_ANY>;
+  return (const void*)k_vtail<2, FS_ANY>;
+}
+
 // Fused coarse end (mpn_tail.cuh): the finest level k0 with at most two
 // points per thread and CTA from which all coarser levels fit, per CTA, in
 // shared memory, with the cluster size and the shared-memory layout.  Left at -1 when fewer than two levels would be fused
@@ -313,7 +320,7 @@ static void plan_tail(mpn_problem* p) {
     ta.Kinv = p->Kinv;
     ta.rin = p->lv[k0].r;
     ta.eout = p->lv[k0].e;
-    const void* fn = p->D == 3 ? (const void*)k_vtail<3> : (const void*)k_vtail<2>;
+    const void* fn = tail_fn(p);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       (void)cudaGetLastError();
       return;
@@ -347,8 +354,8 @@ static void launch_tail(mpn_problem* p, cudaStream_t st) {
   at[0].val.clusterDim.x = p->tail_cs; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
   cfg.attrs = at; cfg.numAttrs = 1;
   ++p->nlaunch;
-  if (p->D == 3) cudaLaunchKernelEx(&cfg, k_vtail<3>, p->tail);
-  else cudaLaunchKernelEx(&cfg, k_vtail<2>, p->tail);
+  void* args[] = {&p->tail};
+  cudaLaunchKernelExC(&cfg, tail_fn(p), args);
 }
 
 extern "C" int mpn_fused_level(const mpn_problem* p) { return p ? p->tail_k0 : -1; }

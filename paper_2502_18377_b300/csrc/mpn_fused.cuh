@@ -55,7 +55,9 @@ __device__ __forceinline__ void dforms1(int cls, float xm2, float xm1, float x0,
 // scalars (stored four times) at stride 0, one load either way.  Otherwise
 // bit v of MASK says that c_v is a field (the problem's layout is fixed at
 // compile time): scalars are loaded once into registers and fields per group.
+#ifndef FS_ANY
 #define FS_ANY 0x80
+#endif
 template <int MASK>
 struct CoefU4 {
   const float* base[7];

@@ -20,6 +20,9 @@
 namespace cg = cooperative_groups;
 
 #define TAIL_TPB 512
+#ifndef FS_ANY
+#define FS_ANY 0x80
+#endif
 #define TAIL_MAXL 16
 // first fused level: at most TAIL_MAX_PPT points per thread and CTA
 #ifndef TAIL_MAX_PPT
@@ -101,6 +104,9 @@ __device__ __forceinline__ int tl_off(const Grid& g, const int pos[3], int d, in
   return (c - pos[d]) * g.stride[d];
 }
 
+// MASK: FS_ANY (coefficient kind read at run time) or bit v set when c_v is a
+// field (layout fixed at compile time).
+template <int MASK>
 struct TailView {
   TailLv L;
   int fo[7];
@@ -115,12 +121,13 @@ struct TailView {
     return r == myr ? *a : dsm_ld(a, r);
   }
   // coefficient v at CTA-local point j
+  __device__ __forceinline__ bool is_field(int v) const { return MASK == FS_ANY ? fo[v] >= 0 : ((MASK >> v) & 1); }
   __device__ __forceinline__ float c(int v, int j) const {
-    return fo[v] >= 0 ? tail_sm[L.o_f + fo[v] * L.cap + j] : scal[v];
+    return is_field(v) ? tail_sm[L.o_f + fo[v] * L.cap + j] : scal[v];
   }
   // coefficient v at (time plane tp, in-plane index rem), any CTA
   __device__ __forceinline__ float cr(int v, int tp, int rem) const {
-    return fo[v] >= 0 ? ld(L.o_f + fo[v] * L.cap, tp, rem) : scal[v];
+    return is_field(v) ? ld(L.o_f + fo[v] * L.cap, tp, rem) : scal[v];
   }
 };
 
@@ -132,8 +139,8 @@ struct TailView {
 #define TW_STRIDE 20
 
 // Spatial part (dims 1 .. D-1) of (L x)_j.
-template <int D>
-__device__ __forceinline__ float ly_space(const TailView& v, const float* X, int j, const int pos[3], float xc) {
+template <int D, int MASK>
+__device__ __forceinline__ float ly_space(const TailView<MASK>& v, const float* X, int j, const int pos[3], float xc) {
   const Grid& g = v.L.g;
   float acc = 0.f;
 #pragma unroll
@@ -158,8 +165,8 @@ __device__ __forceinline__ float ly_space(const TailView& v, const float* X, int
 }
 
 // y = -rho L e on this CTA's points.
-template <int D>
-__device__ void tail_Ly(const TailView& v, int o_tw) {
+template <int D, int MASK>
+__device__ void tail_Ly(const TailView<MASK>& v, int o_tw) {
   const Grid& g = v.L.g;
   const int n0 = g.n[0];
   const int cnt = v.ntp * v.L.plane;
@@ -189,15 +196,15 @@ __device__ void tail_Ly(const TailView& v, int o_tw) {
         a1 += w1 * xv; a2 += w2 * xv;
       }
     }
-    float Lx = v.c(0, j) * xc + v.c(1, j) * a1 * is1t + v.c(2, j) * a2 * is2t + ly_space<D>(v, X, j, pos, xc);
+    float Lx = v.c(0, j) * xc + v.c(1, j) * a1 * is1t + v.c(2, j) * a2 * is2t + ly_space<D, MASK>(v, X, j, pos, xc);
     Y[j] = -RHO[j] * Lx;
   }
 }
 
 // q = L^T y - theta 1_B e = -(S e) on this CTA's points, then the mode's
 // update (SM_CHEB / SM_POST0: Chebyshev step on e, d; SM_RES: d = r - S e).
-template <int D, int MODE>
-__device__ void tail_LTy(const TailView& v, int o_tw, float c1, float c2) {
+template <int D, int MODE, int MASK>
+__device__ void tail_LTy(const TailView<MASK>& v, int o_tw, float c1, float c2) {
   const Grid& g = v.L.g;
   const int n0 = g.n[0];
   const int cnt = v.ntp * v.L.plane;
@@ -363,7 +370,7 @@ __device__ void tail_prolong(const TailLv& F, const TailLv& C, int ntp) {
   }
 }
 
-template <int D>
+template <int D, int MASK>
 __global__ void __launch_bounds__(TAIL_TPB, 1) k_vtail(const __grid_constant__ TailArgs ta) {
   float* sm = tail_sm;
   cg::cluster_group cl = cg::this_cluster();
@@ -396,7 +403,7 @@ __global__ void __launch_bounds__(TAIL_TPB, 1) k_vtail(const __grid_constant__ T
     const size_t base = (size_t)b * L.g.N + (size_t)t0 * L.plane;
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) sm[o_r + j] = rin[base + j];
   }
-  TailView v0{TailLv(ta.lv[0]), {}, {}, myr, t0, ntp, ta.P, ta.invP};
+  TailView<MASK> v0{TailLv(ta.lv[0]), {}, {}, myr, t0, ntp, ta.P, ta.invP};
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
     v0.fo[q] = ta.field_of[q];
@@ -421,7 +428,7 @@ __global__ void __launch_bounds__(TAIL_TPB, 1) k_vtail(const __grid_constant__ T
 
   // down: pre-smoothing from e = 0, residual, restriction
   for (int k = 0; k + 1 < nl; ++k) {
-    TailView v = v0;
+    TailView<MASK> v = v0;
     v.L = TailLv(ta.lv[k]);
     {
       const int cnt = ntp * v.L.plane, o_e = v.L.o_e, o_d = v.L.o_d, o_r = v.L.o_r, o_di = v.L.o_dinv;
@@ -433,14 +440,14 @@ __global__ void __launch_bounds__(TAIL_TPB, 1) k_vtail(const __grid_constant__ T
     }
     cl.sync();
     for (int s = 1; s < m; ++s) {
-      tail_Ly<D>(v, o_tw);
+      tail_Ly<D, MASK>(v, o_tw);
       cl.sync();
-      tail_LTy<D, SM_CHEB>(v, o_tw, ta.c1[s], ta.c2[s]);
+      tail_LTy<D, SM_CHEB, MASK>(v, o_tw, ta.c1[s], ta.c2[s]);
       cl.sync();
     }
-    tail_Ly<D>(v, o_tw);
+    tail_Ly<D, MASK>(v, o_tw);
     cl.sync();
-    tail_LTy<D, SM_RES>(v, o_tw, 0.f, 0.f);
+    tail_LTy<D, SM_RES, MASK>(v, o_tw, 0.f, 0.f);
     __syncthreads();
     tail_restrict<D>(v.L, TailLv(ta.lv[k + 1]), ntp);
     __syncthreads();
@@ -476,18 +483,18 @@ __global__ void __launch_bounds__(TAIL_TPB, 1) k_vtail(const __grid_constant__ T
 
   // up: prolongation, post-smoothing
   for (int k = nl - 2; k >= 0; --k) {
-    TailView v = v0;
+    TailView<MASK> v = v0;
     v.L = TailLv(ta.lv[k]);
     tail_prolong<D>(v.L, TailLv(ta.lv[k + 1]), ntp);
     cl.sync();
-    tail_Ly<D>(v, o_tw);
+    tail_Ly<D, MASK>(v, o_tw);
     cl.sync();
-    tail_LTy<D, SM_POST0>(v, o_tw, 0.f, inv_th);
+    tail_LTy<D, SM_POST0, MASK>(v, o_tw, 0.f, inv_th);
     cl.sync();
     for (int s = 1; s < m; ++s) {
-      tail_Ly<D>(v, o_tw);
+      tail_Ly<D, MASK>(v, o_tw);
       cl.sync();
-      tail_LTy<D, SM_CHEB>(v, o_tw, ta.c1[s], ta.c2[s]);
+      tail_LTy<D, SM_CHEB, MASK>(v, o_tw, ta.c1[s], ta.c2[s]);
       cl.sync();
     }
   }
