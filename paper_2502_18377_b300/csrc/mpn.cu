@@ -238,6 +238,8 @@ extern "C" int mpn_levels(const mpn_problem* p, int* nl, int* shapes) {
 }
 
 #define FS_MAX_NY 128
+// shared memory of the coarsest-inverse kernel (floats)
+#define INV_SMEM_FLOATS (224 * 1024 / 4)
 // c_0, c_xx and c_yy fields, every other coefficient a per-instance scalar
 #define FS_MASK_RD ((1 << 0) | (1 << 4) | (1 << 6))
 static size_t fs_smem(int tt, int ny) { return sizeof(float) * (size_t)(fs_rows_x(tt) + fs_rows_y(tt)) * ny; }
@@ -429,7 +431,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   p->M = lc.g.N;
   int plane = lc.g.n[1] * lc.g.n[2];
   p->bw = std::min(p->M - 1, 3 * plane - 1);
-  if (p->M > d.max_coarse || p->bw >= 256 || (size_t)p->M * (p->bw + 1) * sizeof(float) > 200 * 1024) {
+  if (p->M > d.max_coarse || p->bw >= 256 || ((size_t)p->M * (p->bw + 1) + p->bw) * sizeof(float) > 200 * 1024) {
     delete p;
     return MPN_ERR_UNSUPPORTED;
   }
@@ -639,16 +641,26 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
   Coef cfc = make_coef(p, lc.fields);
   CK(cudaMemsetAsync(p->ferr, 0, sizeof(int) * B, st));
   ++p->nlaunch, k_coarse_assemble<<<dim3(nblk(p->M), B), MPN_TPB, 0, st>>>(lc.g, cfc, lc.rho, p->bw, p->Kband);
-  size_t smem = sizeof(float) * (size_t)p->M * (p->bw + 1);
+  size_t smem = sizeof(float) * ((size_t)p->M * (p->bw + 1) + p->bw);
   CK(cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ++p->nlaunch, k_coarse_factor<<<B, 512, smem, st>>>(p->M, p->bw, p->Kband, p->ferr);
-  // one warp per column of the inverse
+  // one warp per column of the inverse; the CTA stages the band, the
+  // reciprocal diagonal and one forward-solution vector per warp
   {
-    dim3 gi((p->M * 32 + MPN_TPB - 1) / MPN_TPB, B);
-    if (p->bw < 32) ++p->nlaunch, k_coarse_inverse<1><<<gi, MPN_TPB, 0, st>>>(p->M, p->bw, p->Kband, p->Kinv);
-    else if (p->bw < 64) ++p->nlaunch, k_coarse_inverse<2><<<gi, MPN_TPB, 0, st>>>(p->M, p->bw, p->Kband, p->Kinv);
-    else if (p->bw < 128) ++p->nlaunch, k_coarse_inverse<4><<<gi, MPN_TPB, 0, st>>>(p->M, p->bw, p->Kband, p->Kinv);
-    else ++p->nlaunch, k_coarse_inverse<8><<<gi, MPN_TPB, 0, st>>>(p->M, p->bw, p->Kband, p->Kinv);
+    const size_t fixed = (size_t)p->M * (p->bw + 1) + p->M;
+    int nwarps = (int)std::min<size_t>(32, (INV_SMEM_FLOATS - fixed) / p->M);
+    dim3 gi((p->M + nwarps - 1) / nwarps, B);
+    size_t sm = sizeof(float) * (fixed + (size_t)nwarps * p->M);
+#define INV_LAUNCH(NW)                                                                                 \
+  do {                                                                                                 \
+    CK(cudaFuncSetAttribute(k_coarse_inverse<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+    ++p->nlaunch, k_coarse_inverse<NW><<<gi, 32 * nwarps, sm, st>>>(p->M, p->bw, p->Kband, p->Kinv);      \
+  } while (0)
+    if (p->bw < 32) INV_LAUNCH(1);
+    else if (p->bw < 64) INV_LAUNCH(2);
+    else if (p->bw < 128) INV_LAUNCH(4);
+    else INV_LAUNCH(8);
+#undef INV_LAUNCH
   }
 
   CKL();

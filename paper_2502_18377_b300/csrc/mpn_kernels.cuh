@@ -357,35 +357,34 @@ __global__ void k_coarse_assemble(Grid g, Coef cf, const float* __restrict__ rho
 
 // Banded Cholesky, one block per instance, band held in shared memory.
 // A non-positive pivot is replaced by 1 and flagged in err[b].
+// Right-looking band Cholesky of one instance's coarsest system in shared
+// memory (the band, then a column buffer of bw floats).  Step k: threads
+// ii < bw scale l_ik (i = k + 1 + ii) into the column buffer; after a barrier
+// the block, as 32 columns x (blockDim / 32) rows, updates the lower triangle
+// S_ij -= l_ik l_jk, k < j <= i <= k + bw.  blockDim.x >= bw, a multiple of 32.
 __global__ void k_coarse_factor(int M, int bw, float* __restrict__ Kb, int* __restrict__ err) {
   extern __shared__ float sb[];
-  int b = blockIdx.x;
+  const int b = blockIdx.x;
   float* K = Kb + (size_t)b * M * (bw + 1);
-  int W = bw + 1;
+  const int W = bw + 1;
+  float* colk = sb + (size_t)M * W;
   for (int t = threadIdx.x; t < M * W; t += blockDim.x) sb[t] = K[t];
   __syncthreads();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
   for (int k = 0; k < M; ++k) {
-    if (threadIdx.x == 0) {
-      float a = sb[k * W];
-      if (!(a > 0.f)) { a = 1.f; err[b] = 1; }
-      sb[k * W] = sqrtf(a);
-    }
+    float a = sb[k * W];
+    if (!(a > 0.f)) { a = 1.f; if (threadIdx.x == 0) err[b] = 1; }
+    const float piv = sqrtf(a), ipiv = 1.f / piv;
+    const int nr = min(bw, M - k - 1);
+    const int ii = threadIdx.x;
+    if (ii < nr) colk[ii] = sb[(k + 1 + ii) * W + ii + 1] * ipiv;
     __syncthreads();
-    float piv = sb[k * W];
-    for (int t = threadIdx.x; t < bw; t += blockDim.x) {
-      int i = k + 1 + t;
-      if (i < M) sb[i * W + (i - k)] /= piv;
-    }
-    __syncthreads();
-    int npair = bw * (bw + 1) / 2;
-    for (int t = threadIdx.x; t < npair; t += blockDim.x) {
-      // enumerate (ii, jj) with 0 <= jj <= ii < bw: i = k+1+ii, j = k+1+jj
-      int ii = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
-      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-      while (ii * (ii + 1) / 2 > t) --ii;
-      int jj = t - ii * (ii + 1) / 2;
-      int i = k + 1 + ii, j = k + 1 + jj;
-      if (i < M) sb[i * W + (i - j)] -= sb[i * W + (i - k)] * sb[j * W + (j - k)];
+    if (threadIdx.x == 0) sb[k * W] = piv;
+    if (ii < nr) sb[(k + 1 + ii) * W + ii + 1] = colk[ii];
+    for (int i2 = ty; i2 < nr; i2 += nty) {
+      const float li = colk[i2];
+      float* row = sb + (k + 1 + i2) * W + i2;   // row[-jj] is entry (k+1+i2, k+1+jj)
+      for (int jj = tx; jj <= i2; jj += 32) row[-jj] -= li * colk[jj];
     }
     __syncthreads();
   }
@@ -393,18 +392,32 @@ __global__ void k_coarse_factor(int M, int bw, float* __restrict__ Kb, int* __re
 }
 
 // Explicit inverse from the banded factor (bw < 32 NW): one warp per column c
-// solves L L^T x = e_c and writes column c of Kinv (symmetric).  At step i the
+// solves L L^T x = e_c for the rows i >= c and writes them to column and row c
+// of the symmetric Kinv.  The CTA stages the band and the reciprocal diagonal
+// in shared memory, plus one forward-solution vector per warp.  At step i the
 // band row (or column) is split across the lanes and the dot product reduced
 // by shuffles; the last 32 NW values of the substitution live in NW registers
 // per lane and shift by one lane per step.
 template <int NW>
 __global__ void k_coarse_inverse(int M, int bw, const float* __restrict__ Lb, float* __restrict__ Kinv) {
+  extern __shared__ float sL[];
   const int b = blockIdx.y;
   const int W = bw + 1;
-  const float* L = Lb + (size_t)b * M * W;
-  const int lane = threadIdx.x & 31;
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (c >= M) return;
+  float* rd = sL + (size_t)M * W;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* Y = rd + M + (size_t)wid * M;       // this warp's forward solution
+  {
+    const float* src = Lb + (size_t)b * M * W;
+    for (int t = threadIdx.x; t < M * W; t += blockDim.x) sL[t] = src[t];
+    __syncthreads();
+    for (int t = threadIdx.x; t < M; t += blockDim.x) rd[t] = 1.f / sL[t * W];
+    __syncthreads();
+  }
+  const float* L = sL;
+  // column of this warp: long (small c) and short (large c) columns alternate
+  const int idx = blockIdx.x * (blockDim.x >> 5) + wid;
+  if (idx >= M) return;
+  const int c = (idx & 1) ? M - 1 - (idx >> 1) : (idx >> 1);
   float* X = Kinv + (size_t)b * M * M;
   float w[NW];
   // forward: y_i = (delta_ic - sum_{j<i} L_ij y_j) / L_ii; w[k] on lane l holds
@@ -421,21 +434,22 @@ __global__ void k_coarse_inverse(int M, int bw, const float* __restrict__ Lb, fl
     }
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-    float y = ((i == c ? 1.f : 0.f) - s) / Li[0];
+    float y = ((i == c ? 1.f : 0.f) - s) * rd[i];
 #pragma unroll
     for (int k = NW - 1; k >= 0; --k) {
       float carry = k > 0 ? __shfl_sync(0xffffffffu, w[k - 1], 31) : y;
       w[k] = __shfl_up_sync(0xffffffffu, w[k], 1);
       if (lane == 0) w[k] = carry;
     }
-    if (lane == 0) X[(size_t)i * M + c] = y;
+    if (lane == 0) Y[i] = y;
   }
   __syncwarp();
-  // backward: x_i = (y_i - sum_{j>i} L_ji x_j) / L_ii; w[k] on lane l holds
-  // x_{i+1+32k+l}
+  // backward: x_i = (y_i - sum_{j>i} L_ji x_j) / L_ii down to i = c (the
+  // rest of the column is the mirror of rows already computed by other
+  // warps); w[k] on lane l holds x_{i+1+32k+l}
 #pragma unroll
   for (int k = 0; k < NW; ++k) w[k] = 0.f;
-  for (int i = M - 1; i >= 0; --i) {
+  for (int i = M - 1; i >= c; --i) {
     float s = 0.f;
 #pragma unroll
     for (int k = 0; k < NW; ++k) {
@@ -444,16 +458,14 @@ __global__ void k_coarse_inverse(int M, int bw, const float* __restrict__ Lb, fl
     }
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-    float yi = i >= c ? X[(size_t)i * M + c] : 0.f;
-    float x = (yi - s) / L[(size_t)i * W];
+    float x = (Y[i] - s) * rd[i];
 #pragma unroll
     for (int k = NW - 1; k >= 0; --k) {
       float carry = k > 0 ? __shfl_sync(0xffffffffu, w[k - 1], 31) : x;
       w[k] = __shfl_up_sync(0xffffffffu, w[k], 1);
       if (lane == 0) w[k] = carry;
     }
-    __syncwarp();
-    if (lane == 0) X[(size_t)i * M + c] = x;
+    if (lane == 0) { X[(size_t)i * M + c] = x; X[(size_t)c * M + i] = x; }
   }
 }
 
