@@ -790,12 +790,15 @@ static int residual64(mpn_problem* p, const double* u, const double* g_adj, doub
   dim3 gr(nblk(l.g.N), p->B);   // partial count per instance = nblk (as every refinement reduction)
   const float* src = g_adj ? nullptr : p->rhs;
   const float* om = g_adj ? nullptr : p->omega;
-  if (p->D == 3) {
-    ++p->nlaunch, k_res64_y<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
-    ++p->nlaunch, k_res64_q<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
+  if (p->D == 3 && p->field_mask == FS_MASK_RD) {
+    ++p->nlaunch, k_res64_y<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    ++p->nlaunch, k_res64_q<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
+  } else if (p->D == 3) {
+    ++p->nlaunch, k_res64_y<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    ++p->nlaunch, k_res64_q<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
   } else {
-    ++p->nlaunch, k_res64_y<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
-    ++p->nlaunch, k_res64_q<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
+    ++p->nlaunch, k_res64_y<2, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    ++p->nlaunch, k_res64_q<2, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
   }
   CKL();
   return MPN_OK;

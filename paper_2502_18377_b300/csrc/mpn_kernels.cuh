@@ -891,23 +891,42 @@ __global__ void k_znorm(Grid g, const double* __restrict__ u, const float* __res
 //   k_res64_y:  y = rho (b - L u)              (b, u nullable => 0)
 //   k_res64_q:  r = base + L^T y + theta 1_B (omega - u), partials of ||r||^2
 // Points away from non-periodic edges use the central weights directly.
-template <int D>
+// FP64 coefficient access.  MASK = RES_ANY: every c_v read and converted per
+// use.  Otherwise bit v of MASK says c_v is a field; the per-instance scalars
+// are converted once per thread and the difference forms they multiply are
+// formed before the product (fewer FP64 operations: this pass is bound by the
+// FP64 pipe).
+#define RES_ANY 0x80
+template <int MASK>
+struct Coef64 {
+  const Coef& cf;
+  int b;
+  double sv[7];
+  __device__ __forceinline__ Coef64(const Coef& c, int b_) : cf(c), b(b_) {
+#pragma unroll
+    for (int v = 0; v < 7; ++v) sv[v] = scal(v) ? (double)__ldg(c.ptr[v] + (size_t)b_ * c.bstride[v]) : 0.0;
+  }
+  __device__ __forceinline__ static constexpr bool scal(int v) { return MASK != RES_ANY && !((MASK >> v) & 1); }
+  __device__ __forceinline__ double at(int v, int p) const { return scal(v) ? sv[v] : (double)coefv(cf, v, b, p, 0); }
+};
+
+template <int D, int MASK>
 __global__ void k_res64_y(Grid g, Coef cf, const double* __restrict__ rho64, const double* __restrict__ u,
                           const float* __restrict__ bsrc, double* __restrict__ y) {
   int b = blockIdx.y;
   size_t off = (size_t)b * g.N;
+  const Coef64<MASK> C(cf, b);
   GRID_LOOP(p, g.N) {
     int pos[3]; decode_fast(g, p, pos);
     double Lu = 0;
     if (u) {
       double uc = u[off + p];
-      Lu = (double)coefv(cf, 0, b, p, g.N) * uc;
       if (!any_edge(g, pos)) {
+        Lu = C.at(0, p) * uc;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
           double um = u[off + nbr(g, p, pos, d, -1)], up = u[off + nbr(g, p, pos, d, 1)];
-          Lu += (double)coefv(cf, 1 + 2 * d, b, p, g.N) * (0.5 * (up - um)) * g.ds1[d] +
-                (double)coefv(cf, 2 + 2 * d, b, p, g.N) * (up - 2.0 * uc + um) * g.ds2[d];
+          Lu += C.at(1 + 2 * d, p) * (0.5 * g.ds1[d]) * (up - um) + C.at(2 + 2 * d, p) * g.ds2[d] * (up - 2.0 * uc + um);
         }
       } else {
         Lu = Lrow<double, D>(g, cf, b, p, pos, u + off, nullptr);
@@ -918,12 +937,13 @@ __global__ void k_res64_y(Grid g, Coef cf, const double* __restrict__ rho64, con
   }
 }
 
-template <int D>
+template <int D, int MASK>
 __global__ void k_res64_q(Grid g, Coef cf, const double* __restrict__ y, const double* __restrict__ base,
                           const float* __restrict__ omega, const double* __restrict__ u, double* __restrict__ out,
                           double* __restrict__ part) {
   int b = blockIdx.y;
   size_t off = (size_t)b * g.N;
+  const Coef64<MASK> C(cf, b);
   double acc = 0;
   GRID_LOOP(p, g.N) {
     int pos[3]; decode_fast(g, p, pos);
@@ -931,14 +951,16 @@ __global__ void k_res64_q(Grid g, Coef cf, const double* __restrict__ y, const d
     const double* yb = y + off;
     if (!any_edge(g, pos)) {
       double yc = yb[p];
-      q = (double)coefv(cf, 0, b, p, g.N) * yc;
+      q = C.at(0, p) * yc;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         int pm = nbr(g, p, pos, d, -1), pp = nbr(g, p, pos, d, 1);
         double ym = yb[pm], yp = yb[pp];
-        q += 0.5 * g.ds1[d] * ((double)coefv(cf, 1 + 2 * d, b, pm, g.N) * ym - (double)coefv(cf, 1 + 2 * d, b, pp, g.N) * yp) +
-             g.ds2[d] * ((double)coefv(cf, 2 + 2 * d, b, pm, g.N) * ym - 2.0 * (double)coefv(cf, 2 + 2 * d, b, p, g.N) * yc +
-                         (double)coefv(cf, 2 + 2 * d, b, pp, g.N) * yp);
+        const int v1 = 1 + 2 * d, v2 = 2 + 2 * d;
+        if (Coef64<MASK>::scal(v1)) q += (0.5 * g.ds1[d] * C.sv[v1]) * (ym - yp);
+        else q += 0.5 * g.ds1[d] * (C.at(v1, pm) * ym - C.at(v1, pp) * yp);
+        if (Coef64<MASK>::scal(v2)) q += (g.ds2[d] * C.sv[v2]) * (ym - 2.0 * yc + yp);
+        else q += g.ds2[d] * (C.at(v2, pm) * ym - 2.0 * C.at(v2, p) * yc + C.at(v2, pp) * yp);
       }
     } else {
       q = LTgather<double, D>(g, cf, b, p, pos, yb);
