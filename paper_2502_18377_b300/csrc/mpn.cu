@@ -932,8 +932,12 @@ static int forward_impl(mpn_problem* p, const float* fields, const float* scalar
   int status = refine_solve(p, nullptr, u0 == nullptr, stats, st);
   if (status != MPN_OK && status != MPN_ERR_NOT_CONVERGED) return status;
   Coef cf = make_coef(p, l.fields);
-  if (p->D == 3) ++p->nlaunch, k_recover<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
-  else ++p->nlaunch, k_recover<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
+  if (p->D == 3 && p->field_mask == FS_MASK_RD)
+    ++p->nlaunch, k_recover<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
+  else if (p->D == 3)
+    ++p->nlaunch, k_recover<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
+  else
+    ++p->nlaunch, k_recover<2, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
   CKL();
   CK(cudaMemcpyAsync(p->uf64, p->u64, sizeof(double) * N0, cudaMemcpyDeviceToDevice, st));
   p->zd_valid = true;
@@ -973,10 +977,11 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
   Coef cf = make_coef(p, l.fields);
   // reduced right-hand side g_u - M_{u zeta} M_{zeta zeta}^{-1} g_zeta (FP64)
   if (p->D == 3) {
-    ++p->nlaunch, k_adj_kappa<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
+    if (p->field_mask == FS_MASK_RD) ++p->nlaunch, k_adj_kappa<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
+    else ++p->nlaunch, k_adj_kappa<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
     ++p->nlaunch, k_adj_rhs<3><<<gr, MPN_TPB, 0, st>>>(l.g, g_z, p->kap, p->g64);
   } else {
-    ++p->nlaunch, k_adj_kappa<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
+    ++p->nlaunch, k_adj_kappa<2, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
     ++p->nlaunch, k_adj_rhs<2><<<gr, MPN_TPB, 0, st>>>(l.g, g_z, p->kap, p->g64);
   }
   ++p->nlaunch, k_set_u<<<gr, MPN_TPB, 0, st>>>(l.g.N, nullptr, p->u64);
@@ -984,12 +989,13 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
   int status = refine_solve(p, p->g64, true, stats, st);
   if (status != MPN_OK && status != MPN_ERR_NOT_CONVERGED) return status;
   double* gp = slot(p, S_GR0);
-  if (p->D == 3)
-    ++p->nlaunch, k_gradients<3><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->rhs, p->uf64, p->u64, g_z, dfields, drhs,
-                                                         domega, dz, gp);
-  else
-    ++p->nlaunch, k_gradients<2><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->rhs, p->uf64, p->u64, g_z, dfields, drhs,
-                                                         domega, dz, gp);
+#define GRAD_LAUNCH(DD, MK)                                                                              \
+  ++p->nlaunch, k_gradients<DD, MK><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->rhs, p->uf64, p->u64, g_z, dfields, \
+                                                           drhs, domega, dz, gp)
+  if (p->D == 3 && p->field_mask == FS_MASK_RD) GRAD_LAUNCH(3, FS_MASK_RD);
+  else if (p->D == 3) GRAD_LAUNCH(3, RES_ANY);
+  else GRAD_LAUNCH(2, RES_ANY);
+#undef GRAD_LAUNCH
   ++p->nlaunch, k_scalar_grads<<<B, 64, 0, st>>>(V, B, p->field_of_dev, gp, gr.x, dscalars);
   CKL();
   CK(cudaStreamSynchronize(st));

@@ -7,6 +7,26 @@
 
 #define GRID_LOOP(p, N) for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (N); p += gridDim.x * blockDim.x)
 
+// FP64 coefficient access.  MASK = RES_ANY: every c_v read and converted per
+// use.  Otherwise bit v of MASK says c_v is a field; the per-instance scalars
+// are converted once per thread and the difference forms they multiply are
+// formed before the product (fewer FP64 operations: this pass is bound by the
+// FP64 pipe).
+#define RES_ANY 0x80
+template <int MASK>
+struct Coef64 {
+  const Coef& cf;
+  int b;
+  double sv[7];
+  __device__ __forceinline__ Coef64(const Coef& c, int b_) : cf(c), b(b_) {
+#pragma unroll
+    for (int v = 0; v < 7; ++v) sv[v] = scal(v) ? (double)__ldg(c.ptr[v] + (size_t)b_ * c.bstride[v]) : 0.0;
+  }
+  __device__ __forceinline__ static constexpr bool scal(int v) { return MASK != RES_ANY && !((MASK >> v) & 1); }
+  __device__ __forceinline__ double at(int v, int p) const { return scal(v) ? sv[v] : (double)coefv(cf, v, b, p, 0); }
+};
+
+
 // ------------------------------------------------------------------- setup
 // rho at the finest level from the coefficients.
 template <int D>
@@ -644,27 +664,33 @@ __global__ void k_set_u(int N, const float* __restrict__ u0, double* __restrict_
 // the (small) equation-row residual.  The duals follow from it:
 // lambda_E = -rho E* (forward, bE = b) and d_lambda_E = -rho E* (adjoint).
 // Returns rho E*.
-template <int D>
-__device__ __forceinline__ double recover_point(const Grid& g, const Coef& cf, int b, int p, const int pos[3],
+template <int D, int MASK>
+__device__ __forceinline__ double recover_point(const Grid& g, const Coef64<MASK>& C, int b, int p, const int pos[3],
                                                 const double* __restrict__ u, double rho, double bE,
                                                 const float* __restrict__ gz, double* zo) {
   constexpr int V = 1 + 2 * D;
   size_t off = (size_t)b * g.N;
   double uc = u[off + p];
-  double Est = (double)coefv(cf, 0, b, p, g.N) * uc - bE;
+  double Est = C.at(0, p) * uc - bE;
   double a[3][2], hw[3][2], qb[3][2];
-  #pragma unroll
-    for (int d = 0; d < D; ++d) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
     double a1 = 0, a2 = 0;
-    for (int o = -2; o <= 2; ++o) {
-      float w1 = dweight(1, pos[d], g.n[d], g.per[d], o), w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
-      if (w1 == 0.f && w2 == 0.f) continue;
-      double xv = o == 0 ? uc : u[off + nbr(g, p, pos, d, o)];
-      a1 += (double)w1 * xv; a2 += (double)w2 * xv;
+    if (g.per[d] || (pos[d] > 0 && pos[d] < g.n[d] - 1)) {
+      const double um = u[off + nbr(g, p, pos, d, -1)], up = u[off + nbr(g, p, pos, d, 1)];
+      a1 = 0.5 * (up - um); a2 = up - 2.0 * uc + um;
+    } else {
+#pragma unroll
+      for (int o = -2; o <= 2; ++o) {
+        float w1 = dweight(1, pos[d], g.n[d], g.per[d], o), w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
+        if (w1 == 0.f && w2 == 0.f) continue;
+        double xv = o == 0 ? uc : u[off + nbr(g, p, pos, d, o)];
+        a1 += (double)w1 * xv; a2 += (double)w2 * xv;
+      }
     }
     int cls = edge_class(g, d, pos[d]);
-    double b1 = (double)coefv(cf, 1 + 2 * d, b, p, g.N) * g.ds1[d];
-    double b2 = (double)coefv(cf, 2 + 2 * d, b, p, g.N) * g.ds2[d];
+    double b1 = C.at(1 + 2 * d, p) * g.ds1[d];
+    double b2 = C.at(2 + 2 * d, p) * g.ds2[d];
     a[d][0] = a1; a[d][1] = a2;
     Est += b1 * a1 + b2 * a2;
     winv<double>(cls, b1, b2, qb[d][0], qb[d][1]);    // W^{-1} beta
@@ -678,8 +704,8 @@ __device__ __forceinline__ double recover_point(const Grid& g, const Coef& cf, i
   }
   double rE = rho * Est;
   zo[0] = uc;
-  #pragma unroll
-    for (int d = 0; d < D; ++d) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
     zo[1 + 2 * d] = (a[d][0] + hw[d][0] - rE * qb[d][0]) * g.ds1[d];
     zo[2 + 2 * d] = (a[d][1] + hw[d][1] - rE * qb[d][1]) * g.ds2[d];
   }
@@ -687,17 +713,18 @@ __device__ __forceinline__ double recover_point(const Grid& g, const Coef& cf, i
 }
 
 // z (FP32 and/or FP64) from u.
-template <int D>
+template <int D, int MASK>
 __global__ void k_recover(Grid g, Coef cf, const double* __restrict__ rho64, const double* __restrict__ u,
                           const float* __restrict__ bE, const float* __restrict__ gz, float* __restrict__ zf,
                           double* __restrict__ zd) {
   int b = blockIdx.y;
+  const Coef64<MASK> C(cf, b);
   constexpr int V = 1 + 2 * D;
   size_t off = (size_t)b * g.N;
   GRID_LOOP(p, g.N) {
     int pos[3]; decode_fast(g, p, pos);
     double zo[7];
-    recover_point<D>(g, cf, b, p, pos, u, rho64[off + p], bE ? (double)bE[off + p] : 0.0, gz, zo);
+    recover_point<D, MASK>(g, C, b, p, pos, u, rho64[off + p], bE ? (double)bE[off + p] : 0.0, gz, zo);
     size_t zb = (size_t)b * V * g.N;
     for (int v = 0; v < V; ++v) {
       if (zf) zf[zb + (size_t)v * g.N + p] = (float)zo[v];
@@ -715,12 +742,13 @@ __global__ void k_recover(Grid g, Coef cf, const double* __restrict__ rho64, con
 // z and d_z are recovered on the fly.  Field
 // gradients sum over the unknowns sharing a field; scalar gradients are
 // reduced per instance (partials in part[v]).
-template <int D>
+template <int D, int MASK>
 __global__ void k_gradients(Grid g, Coef cf, const double* __restrict__ rho64, const float* __restrict__ rhs,
                             const double* __restrict__ uf, const double* __restrict__ du, const float* __restrict__ gz,
                             float* __restrict__ dfields, float* __restrict__ drhs, float* __restrict__ domega,
                             float* __restrict__ dz_out, double* __restrict__ part) {
   int b = blockIdx.y;
+  const Coef64<MASK> C(cf, b);
   constexpr int V = 1 + 2 * D;
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   size_t off = (size_t)b * g.N;
@@ -728,8 +756,8 @@ __global__ void k_gradients(Grid g, Coef cf, const double* __restrict__ rho64, c
     int pos[3]; decode_fast(g, p, pos);
     double zv[7], dv[7];
     double r = rho64[off + p];
-    double lam = -recover_point<D>(g, cf, b, p, pos, uf, r, (double)rhs[off + p], nullptr, zv);
-    double dlam = -recover_point<D>(g, cf, b, p, pos, du, r, 0.0, gz, dv);
+    double lam = -recover_point<D, MASK>(g, C, b, p, pos, uf, r, (double)rhs[off + p], nullptr, zv);
+    double dlam = -recover_point<D, MASK>(g, C, b, p, pos, du, r, 0.0, gz, dv);
     double cv[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -761,9 +789,10 @@ __global__ void k_gradients(Grid g, Coef cf, const double* __restrict__ rho64, c
 // Adjoint right-hand side, part 1: per point psi = (W + beta beta^T)^{-1} S^{-1} g_zeta
 // and the coefficients of M_{u zeta} M_{zeta zeta}^{-1} g_zeta as a scatter through
 // the difference forms: kap[0] = c_0 beta.psi (center), kap[1+2d], kap[2+2d] = -(W_d psi_d).
-template <int D>
+template <int D, int MASK>
 __global__ void k_adj_kappa(Grid g, Coef cf, const float* __restrict__ gz, double* __restrict__ kap) {
   int b = blockIdx.y;
+  const Coef64<MASK> C(cf, b);
   constexpr int V = 1 + 2 * D;
   GRID_LOOP(p, g.N) {
     int pos[3]; decode_fast(g, p, pos);
@@ -771,8 +800,8 @@ __global__ void k_adj_kappa(Grid g, Coef cf, const float* __restrict__ gz, doubl
     #pragma unroll
     for (int d = 0; d < D; ++d) {
       int cls = edge_class(g, d, pos[d]);
-      double b1 = coefv(cf, 1 + 2 * d, b, p, g.N) * g.ds1[d];
-      double b2 = coefv(cf, 2 + 2 * d, b, p, g.N) * g.ds2[d];
+      double b1 = C.at(1 + 2 * d, p) * g.ds1[d];
+      double b2 = C.at(2 + 2 * d, p) * g.ds2[d];
       be[d][0] = b1; be[d][1] = b2;
       double h1 = (double)gz[((size_t)b * V + 1 + 2 * d) * g.N + p] * g.ds1[d];
       double h2 = (double)gz[((size_t)b * V + 2 + 2 * d) * g.N + p] * g.ds2[d];
@@ -793,7 +822,7 @@ __global__ void k_adj_kappa(Grid g, Coef cf, const float* __restrict__ gz, doubl
       kap[((size_t)(1 + 2 * d) * gridDim.y + b) * g.N + p] = -(w11 * ps1 + w12 * ps2);
       kap[((size_t)(2 + 2 * d) * gridDim.y + b) * g.N + p] = -(w12 * ps1 + w22 * ps2);
     }
-    kap[(size_t)b * g.N + p] = coefv(cf, 0, b, p, g.N) * bpsi;
+    kap[(size_t)b * g.N + p] = C.at(0, p) * bpsi;
   }
 }
 
@@ -891,25 +920,6 @@ __global__ void k_znorm(Grid g, const double* __restrict__ u, const float* __res
 //   k_res64_y:  y = rho (b - L u)              (b, u nullable => 0)
 //   k_res64_q:  r = base + L^T y + theta 1_B (omega - u), partials of ||r||^2
 // Points away from non-periodic edges use the central weights directly.
-// FP64 coefficient access.  MASK = RES_ANY: every c_v read and converted per
-// use.  Otherwise bit v of MASK says c_v is a field; the per-instance scalars
-// are converted once per thread and the difference forms they multiply are
-// formed before the product (fewer FP64 operations: this pass is bound by the
-// FP64 pipe).
-#define RES_ANY 0x80
-template <int MASK>
-struct Coef64 {
-  const Coef& cf;
-  int b;
-  double sv[7];
-  __device__ __forceinline__ Coef64(const Coef& c, int b_) : cf(c), b(b_) {
-#pragma unroll
-    for (int v = 0; v < 7; ++v) sv[v] = scal(v) ? (double)__ldg(c.ptr[v] + (size_t)b_ * c.bstride[v]) : 0.0;
-  }
-  __device__ __forceinline__ static constexpr bool scal(int v) { return MASK != RES_ANY && !((MASK >> v) & 1); }
-  __device__ __forceinline__ double at(int v, int p) const { return scal(v) ? sv[v] : (double)coefv(cf, v, b, p, 0); }
-};
-
 template <int D, int MASK>
 __global__ void k_res64_y(Grid g, Coef cf, const double* __restrict__ rho64, const double* __restrict__ u,
                           const float* __restrict__ bsrc, double* __restrict__ y) {
