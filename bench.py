@@ -161,7 +161,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w, fields, scal, rhs, om, tgt = make_inputs(rank)
-    s = Solver(w.geom, w.batch, w.field_of, fields.shape[0])
+    s = Solver(w.geom, w.batch, w.field_of, fields.shape[0], krylov=args.krylov)
     D = lambda a: torch.from_numpy(a).to(dev)
     F_, S_, R_, O_, T_ = D(fields), D(scal), D(rhs), D(om), D(tgt)
     V, N, B = s.V, s.N, s.B
@@ -256,6 +256,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64-refinement", "data": "synthetic",
         "config": {"workload": WORKLOAD, "batch_per_gpu": B, "grid": list(GRID), "periodic": [0, 1, 1],
+                   "krylov": args.krylov,
                    "unknowns_per_instance": V * N, "tol": 1e-7, "parallelism": f"replicas{world}",
                    "l2": "flushed between timed steps (256 MB write outside the step events)"},
         "roofline": {"bound": "hbm", "kernel": "finest-level Chebyshev smoothing step (k_step3: L and L^T passes fused through shared memory)",
@@ -284,6 +285,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--krylov", default="cg", choices=["cg", "fgmres"],
+                    help="inner FP32 solver of each refinement sweep (flexible GMRES is the solver of Section 3.1)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -85,7 +85,13 @@ typedef struct mpn_desc {
                              n_x % 4 == 0, n_t % 4 == 0) both operator passes of a smoothing step,
                              residual or apply run as one kernel through shared memory; 0: two kernels
                              (same arithmetic) */
+  int krylov;             /* inner FP32 solver of each refinement sweep: MPN_KRYLOV_CG (conjugate
+                             gradients) or MPN_KRYLOV_FGMRES (flexible GMRES(m), m = the sweep's
+                             iteration count, with the same V-cycle as right preconditioner, the
+                             solver of Section 3.1) */
 } mpn_desc;
+
+enum { MPN_KRYLOV_CG = 0, MPN_KRYLOV_FGMRES = 1 };
 
 typedef struct mpn_stats {
   int sweeps;             /* FP64 refinement sweeps done */
@@ -99,7 +105,7 @@ typedef struct mpn_stats {
 typedef struct mpn_problem mpn_problem;
 
 /* Fills *desc with defaults (tol 1e-7, max_refine 12, inner_iters 5,
- * cheb_degree 5, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 1). */
+ * cheb_degree 5, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 1, krylov CG). */
 int mpn_default_desc(mpn_desc* desc);
 
 /* Validates the descriptor, builds the grid hierarchy (spatial halving, time

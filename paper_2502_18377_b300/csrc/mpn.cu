@@ -65,6 +65,11 @@ struct mpn_problem {
   float *scalars = nullptr, *rhs = nullptr, *omega = nullptr;
   float* scal4 = nullptr;  // scalars replicated 4 times, [V][B][4]
   int field_mask = 0;      // bit v: c_v is a field
+  // FGMRES workspace: basis V[mk + 1], preconditioned Z[mk], dot partials,
+  // Hessenberg / rotations / rhs / solution per instance
+  int mk = 0;
+  float *fgV = nullptr, *fgZ = nullptr;
+  double *fgpart = nullptr, *fgH = nullptr, *fgc = nullptr, *fgs = nullptr, *fgg = nullptr, *fgy = nullptr, *fgh = nullptr;
   int* field_of_dev = nullptr;
   float *x = nullptr, *pv = nullptr, *q = nullptr, *z = nullptr;
   double *u64 = nullptr, *r64 = nullptr, *y64 = nullptr, *g64 = nullptr;
@@ -191,6 +196,7 @@ extern "C" int mpn_default_desc(mpn_desc* d) {
   d->max_coarse = 2048;
   d->fused_coarse = 1;
   d->fused_step = 1;
+  d->krylov = MPN_KRYLOV_CG;
   return MPN_OK;
 }
 
@@ -373,6 +379,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   if (d.stencil != 3) return MPN_ERR_INVALID_ARG;
   if (d.inner_iters < 1 || d.max_refine < 1 || d.cheb_degree < 1 || d.cheb_degree > 30) return MPN_ERR_INVALID_ARG;
   if (d.coarse_min < 3 || !(d.tol > 0)) return MPN_ERR_INVALID_ARG;
+  if (d.krylov != MPN_KRYLOV_CG && d.krylov != MPN_KRYLOV_FGMRES) return MPN_ERR_INVALID_ARG;
   int V = 1 + 2 * d.ndim;
   for (int k = 0; k < d.ndim; ++k) {
     if (d.n[k] < 3 || !(d.step[k] > 0)) return MPN_ERR_INVALID_ARG;
@@ -461,6 +468,16 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   AL(p->part, (size_t)NSLOT * B * MPN_PMAX);
   AL(p->dscal, (size_t)16 * B);
   AL(p->lam, (size_t)MAXL * B);
+  if (d.krylov == MPN_KRYLOV_FGMRES) {
+    p->mk = std::min(FG_MMAX, 8 * d.inner_iters);
+    const int mk = p->mk;
+    AL(p->fgV, (size_t)(mk + 1) * N0);
+    AL(p->fgZ, (size_t)mk * N0);
+    AL(p->fgpart, (size_t)(mk + 2) * B * MPN_PMAX);
+    AL(p->fgH, (size_t)B * mk * (mk + 1));
+    AL(p->fgc, (size_t)B * mk); AL(p->fgs, (size_t)B * mk); AL(p->fgy, (size_t)B * mk);
+    AL(p->fgg, (size_t)B * (mk + 1)); AL(p->fgh, (size_t)B);
+  }
 #undef AL
   int fo[8];
   for (int v = 0; v < 8; ++v) fo[v] = v < V ? d.field_of[v] : -1;
@@ -780,6 +797,43 @@ static int pcg(mpn_problem* p, int iters, cudaStream_t st) {
   return MPN_OK;
 }
 
+// Inner FP32 FGMRES(m) on S x = r (r = lv[0].r, overwritten by the basis
+// vectors), m = iters capped at the workspace, x = p->x.  The V-cycle reads
+// its right-hand side from lv[0].r and leaves z_j in lv[0].e.
+static int fgmres(mpn_problem* p, int iters, cudaStream_t st) {
+  Level& l = p->lv[0];
+  const int N = l.g.N, B = p->B;
+  const int m = std::min(iters, p->mk);
+  const size_t vs = (size_t)N * B;          // vector stride
+  dim3 gv(vgrid(N), B);
+  const int P = gv.x;
+  const bool v4 = vec4_len(N);
+  double* dots = p->fgpart;                 // slots 0..m
+  double* nrm = p->fgpart + (size_t)(p->mk + 1) * B * MPN_PMAX;
+#define FG_V4(K, ...) do { if (v4) ++p->nlaunch, K<true><<<gv, MPN_TPB, 0, st>>>(__VA_ARGS__); \
+                           else ++p->nlaunch, K<false><<<gv, MPN_TPB, 0, st>>>(__VA_ARGS__); } while (0)
+  // beta = |r|, v_0 = r / beta
+  FG_V4(k_fg_dots, N, l.r, l.r, (size_t)0, 1, dots);
+  ++p->nlaunch, k_fg_init<<<B, 32, 0, st>>>(p->mk + 1, dots, P, p->fgg, p->fgh);
+  FG_V4(k_fg_scale, N, l.r, p->fgh, p->fgV, l.r);
+  CKL();
+  for (int j = 0; j < m; ++j) {
+    TRY(vcycle(p, 0, st));                                        // z_j in lv[0].e
+    CK(cudaMemcpyAsync(p->fgZ + j * vs, l.e, sizeof(float) * vs, cudaMemcpyDeviceToDevice, st));
+    TRY(apply_S(p, 0, l.e, p->q, nullptr, st));                   // w = S z_j
+    FG_V4(k_fg_dots, N, p->q, p->fgV, vs, j + 1, dots);
+    FG_V4(k_fg_orth, N, p->q, p->fgV, vs, j + 1, dots, P, nrm);
+    ++p->nlaunch, k_fg_hess<<<B, 32, 0, st>>>(j, p->mk, dots, P, nrm, p->fgH, p->fgc, p->fgs, p->fgg, p->fgh);
+    if (j + 1 < m) FG_V4(k_fg_scale, N, p->q, p->fgh, p->fgV + (j + 1) * vs, l.r);
+    CKL();
+  }
+  ++p->nlaunch, k_fg_ysolve<<<(B + 63) / 64, 64, 0, st>>>(B, m, p->mk, p->fgH, p->fgg, p->fgy);
+  FG_V4(k_fg_update, N, p->fgZ, vs, m, p->mk, p->fgy, p->x);
+#undef FG_V4
+  CKL();
+  return MPN_OK;
+}
+
 // FP64 residual out = rhs_vec - S u (u nullable => 0) where rhs_vec is either
 // the forward right-hand side L^T rho b + theta 1_B omega (g_adj null) or
 // g_adj; partials of ||out||^2 into `part` (one per tile).
@@ -815,7 +869,8 @@ static int sweep_body(mpn_problem* p, const double* g_adj, int iters, int P, cud
   TRY(residual64(p, p->u64, g_adj, p->r64, slot(p, S_RN), st));
   ++p->nlaunch, k_to32<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN), P, l.r, scale);
   CKL();
-  TRY(pcg(p, iters, st));
+  if (p->desc.krylov == MPN_KRYLOV_FGMRES) TRY(fgmres(p, iters, st));
+  else TRY(pcg(p, iters, st));
   ++p->nlaunch, k_update64<<<gr, MPN_TPB, 0, st>>>(N, p->x, scale, p->u64, slot(p, S_DU), slot(p, S_UN));
   // correction and solution sizes measured on every unknown of z
   ++p->nlaunch, k_znorm<<<gr, MPN_TPB, 0, st>>>(l.g, p->u64, p->x, scale, slot(p, S_DU), slot(p, S_UN));
@@ -871,7 +926,7 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
   Level& l = p->lv[0];
   int B = p->B, N = l.g.N;
   int P = nblk(N);          // partials per instance of every refinement-level reduction
-  std::vector<double> prev_upd(B, 1.0);
+  std::vector<double> prev_upd(B, 1.0), prev_q(B, 0.0);
   mpn_stats sres;
   memset(&sres, 0, sizeof(sres));
   int status = MPN_ERR_NOT_CONVERGED;
@@ -890,8 +945,15 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
       if (sweep == 0) gnorm[b] = zero_start ? rn : sqrt(h[4 * B + b]);
       if (!std::isfinite(rn) || !std::isfinite(du) || !std::isfinite(un)) bad = true;
       double upd = un > 0 ? du / un : (du > 0 ? 1.0 : 0.0);
-      // the first update is the whole solution; contraction is measured from sweep 2 on
-      double pred = sweep < 2 ? upd : upd * std::min(1.0, upd / std::max(prev_upd[b], 1e-300));
+      // the first update is the whole solution; contraction is measured from
+      // sweep 2 on, as the larger of the last two update ratios (a single
+      // lucky sweep of an erratic inner solve does not end the refinement),
+      // and the remaining error is the geometric tail of the next
+      // corrections: upd (q + q^2 + ...) = upd q / (1 - q)
+      const double q1 = upd / std::max(prev_upd[b], 1e-300);
+      const double q = sweep >= 1 ? std::max(q1, prev_q[b]) : q1;
+      if (sweep >= 1) prev_q[b] = q1;
+      double pred = sweep < 2 ? upd : (q < 1.0 ? upd * q / (1.0 - q) : HUGE_VAL);
       if (sweep >= 2 && upd > 10.0 * prev_upd[b] && upd > 1e-3) grew = true;
       if (sweep >= 2) maxrate = std::max(maxrate, upd / std::max(prev_upd[b], 1e-300));
       prev_upd[b] = upd;

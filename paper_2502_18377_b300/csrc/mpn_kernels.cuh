@@ -612,6 +612,150 @@ __global__ void k_pcg_p(int N, const double* __restrict__ part_rz, int P, const 
     vst<V4>(pv + off, i, zz + beta * pp);
   }
 }
+// ------------------------------------------------ FGMRES (Section 3.1)
+// Batched right-preconditioned flexible GMRES(m) on S x = r from x = 0, one
+// restart cycle per refinement sweep: Arnoldi basis v_0..v_m (FP32 vectors),
+// preconditioned vectors z_j = V-cycle(v_j), classical Gram-Schmidt (one
+// multi-dot pass, one multi-update pass), Hessenberg matrix, Givens rotations
+// and the small least-squares solve per instance in FP64.
+#define FG_MMAX 64
+
+// partials of <w, V_i>, i < nv (V_i = V + i vstride), one slot per i
+template <bool V4>
+__global__ void k_fg_dots(int N, const float* __restrict__ w, const float* __restrict__ V, size_t vstride, int nv,
+                          double* __restrict__ part) {
+  const int b = blockIdx.y, B = gridDim.y;
+  const size_t off = (size_t)b * N;
+  const int n = V4 ? N >> 2 : N;
+  for (int i = 0; i < nv; ++i) {
+    const float* vi = V + i * vstride + off;
+    float acc = 0.f;
+    GRID_LOOP(q, n) {
+      float4 a = vld<V4>(w + off, q), c = vld<V4>(vi, q);
+      acc += a.x * c.x + a.y * c.y + a.z * c.z + a.w * c.w;
+    }
+    double s = block_sum((double)acc);
+    if (threadIdx.x == 0) part[((size_t)i * B + b) * MPN_PMAX + blockIdx.x] = s;
+  }
+}
+
+// w -= sum_i h_i V_i with h_i the summed partials of slot i; partials of |w|^2
+template <bool V4>
+__global__ void k_fg_orth(int N, float* __restrict__ w, const float* __restrict__ V, size_t vstride, int nv,
+                          const double* __restrict__ part, int P, double* __restrict__ npart) {
+  __shared__ float hs[FG_MMAX + 1];
+  const int b = blockIdx.y, B = gridDim.y;
+  for (int i = 0; i < nv; ++i) {
+    double h = sum_partials(part + (size_t)i * B * MPN_PMAX, b, P);
+    if (threadIdx.x == 0) hs[i] = (float)h;
+  }
+  __syncthreads();
+  const size_t off = (size_t)b * N;
+  const int n = V4 ? N >> 2 : N;
+  float acc = 0.f;
+  GRID_LOOP(q, n) {
+    float4 a = vld<V4>(w + off, q);
+    for (int i = 0; i < nv; ++i) a = a - hs[i] * vld<V4>(V + i * vstride + off, q);
+    vst<V4>(w + off, q, a);
+    acc += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+  }
+  double s = block_sum((double)acc);
+  if (threadIdx.x == 0) npart[b * MPN_PMAX + blockIdx.x] = s;
+}
+
+// beta = |r|: g = beta e_0, hnext = beta (one warp per instance)
+__global__ void k_fg_init(int m1, const double* __restrict__ part, int P, double* __restrict__ g,
+                          double* __restrict__ hnext) {
+  const int b = blockIdx.x;
+  double beta = sqrt(sum_partials(part, b, P));
+  for (int i = threadIdx.x; i < m1; i += blockDim.x) g[(size_t)b * m1 + i] = i == 0 ? beta : 0.0;
+  if (threadIdx.x == 0) hnext[b] = beta;
+}
+
+// Column j of H from the dot partials, rotated by the previous Givens
+// rotations; the new rotation zeroes h_{j+1,j} and updates g.  hnext keeps the
+// unrotated h_{j+1,j} = |w| for normalising v_{j+1}.
+__global__ void k_fg_hess(int j, int m, const double* __restrict__ part, int P, const double* __restrict__ npart,
+                          double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                          double* __restrict__ g, double* __restrict__ hnext) {
+  __shared__ double h[FG_MMAX + 1];
+  const int b = blockIdx.x, B = gridDim.x;
+  for (int i = 0; i <= j; ++i) {
+    double v = sum_partials(part + (size_t)i * B * MPN_PMAX, b, P);
+    if (threadIdx.x == 0) h[i] = v;
+  }
+  double hn = sqrt(sum_partials(npart, b, P));
+  if (threadIdx.x == 0) {
+    double* c = cs + (size_t)b * m;
+    double* s = sn + (size_t)b * m;
+    double* gg = g + (size_t)b * (m + 1);
+    for (int i = 0; i < j; ++i) {
+      double a = c[i] * h[i] + s[i] * h[i + 1];
+      h[i + 1] = -s[i] * h[i] + c[i] * h[i + 1];
+      h[i] = a;
+    }
+    double r = sqrt(h[j] * h[j] + hn * hn);
+    double cj = r > 0 ? h[j] / r : 1.0, sj = r > 0 ? hn / r : 0.0;
+    c[j] = cj; s[j] = sj;
+    h[j] = r;
+    gg[j + 1] = -sj * gg[j];
+    gg[j] = cj * gg[j];
+    double* col = H + ((size_t)b * m + j) * (m + 1);
+    for (int i = 0; i <= j; ++i) col[i] = h[i];
+    hnext[b] = hn;
+  }
+}
+
+// v = w / hnext (zero after a breakdown), also written to the preconditioner's input
+template <bool V4>
+__global__ void k_fg_scale(int N, const float* __restrict__ w, const double* __restrict__ hnext, float* __restrict__ v,
+                           float* __restrict__ r_in) {
+  const int b = blockIdx.y;
+  const double h = hnext[b];
+  const float inv = h > 1e-300 ? (float)(1.0 / h) : 0.f;
+  const size_t off = (size_t)b * N;
+  const int n = V4 ? N >> 2 : N;
+  GRID_LOOP(q, n) {
+    float4 a = inv * vld<V4>(w + off, q);
+    vst<V4>(v + off, q, a);
+    vst<V4>(r_in + off, q, a);
+  }
+}
+
+// y = R^{-1} g over the first k columns (R upper triangular after the
+// rotations); one thread per instance
+__global__ void k_fg_ysolve(int B, int k, int m, const double* __restrict__ H, const double* __restrict__ g,
+                            double* __restrict__ y) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const double* Hb = H + (size_t)b * m * (m + 1);
+  const double* gb = g + (size_t)b * (m + 1);
+  double* yb = y + (size_t)b * m;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = gb[i];
+    for (int c = i + 1; c < k; ++c) s -= Hb[(size_t)c * (m + 1) + i] * yb[c];
+    const double d = Hb[(size_t)i * (m + 1) + i];
+    yb[i] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+// x = sum_j y_j Z_j
+template <bool V4>
+__global__ void k_fg_update(int N, const float* __restrict__ Z, size_t zstride, int k, int m, const double* __restrict__ y,
+                            float* __restrict__ x) {
+  __shared__ float ys[FG_MMAX];
+  const int b = blockIdx.y;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = (float)y[(size_t)b * m + i];
+  __syncthreads();
+  const size_t off = (size_t)b * N;
+  const int n = V4 ? N >> 2 : N;
+  GRID_LOOP(q, n) {
+    float4 a = f4(0.f);
+    for (int j = 0; j < k; ++j) a = a + ys[j] * vld<V4>(Z + j * zstride + off, q);
+    vst<V4>(x + off, q, a);
+  }
+}
+
 __global__ void k_to32(int N, const double* __restrict__ r64, const double* __restrict__ part, int P,
                        float* __restrict__ r32, double* __restrict__ scale) {
   int b = blockIdx.y;
