@@ -89,6 +89,10 @@ typedef struct mpn_desc {
                              gradients) or MPN_KRYLOV_FGMRES (flexible GMRES(m), m = the sweep's
                              iteration count, with the same V-cycle as right preconditioner, the
                              solver of Section 3.1) */
+  int coarsen_time;       /* 1: the multigrid hierarchy halves the first (time) axis too, for problems
+                             that are elliptic in it (no first time derivative, e.g. Laplace's
+                             equation with the first axis as a space axis); 0 (default): time is
+                             kept on every level, as a central first time derivative requires */
 } mpn_desc;
 
 enum { MPN_KRYLOV_CG = 0, MPN_KRYLOV_FGMRES = 1 };
@@ -105,7 +109,7 @@ typedef struct mpn_stats {
 typedef struct mpn_problem mpn_problem;
 
 /* Fills *desc with defaults (tol 1e-7, max_refine 12, inner_iters 5,
- * cheb_degree 5, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 1, krylov CG). */
+ * cheb_degree 5, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 1, krylov CG, coarsen_time 0). */
 int mpn_default_desc(mpn_desc* desc);
 
 /* Validates the descriptor, builds the grid hierarchy (spatial halving, time

@@ -197,6 +197,7 @@ extern "C" int mpn_default_desc(mpn_desc* d) {
   d->fused_coarse = 1;
   d->fused_step = 1;
   d->krylov = MPN_KRYLOV_CG;
+  d->coarsen_time = 0;
   return MPN_OK;
 }
 
@@ -286,6 +287,10 @@ static void plan_tail(mpn_problem* p) {
   const size_t budget = 200 * 1024;
   for (int k0 = 0; k0 + 1 < p->L; ++k0) {
     if (p->L - k0 > TAIL_MAXL) continue;
+    // every fused level keeps the time planes (transfers stay inside a CTA)
+    bool keeps_t = true;
+    for (int k = k0; k + 1 < p->L; ++k) keeps_t = keeps_t && !p->lv[k].cz[0];
+    if (!keeps_t) continue;
     // a level with more than two points per thread and CTA runs better pass
     // by pass over the whole GPU (vectorised kernels, full occupancy)
     if ((size_t)P * p->lv[k0].g.n[1] * p->lv[k0].g.n[2] > TAIL_MAX_PPT * TAIL_TPB) continue;
@@ -397,7 +402,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   for (int v = 0; v < V; ++v) if (d.field_of[v] >= 0) p->field_mask |= 1 << v;
   if (p->D == 2) p->desc.n[2] = 1;
 
-  // hierarchy: halve spatial dims (t kept) while the half is >= coarse_min
+  // hierarchy: halve spatial dims (t kept unless coarsen_time) while the half is >= coarse_min
   int n[3] = {p->desc.n[0], p->desc.n[1], p->desc.n[2]};
   double s[3] = {d.step[0], d.step[1], p->D == 3 ? d.step[2] : 1.0};
   int per[3] = {0, d.periodic[1], p->D == 3 ? d.periodic[2] : 0};
@@ -408,7 +413,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
     l.g = make_grid(p->D, n, s, per, d.final_time_rows, theta);
     int nd = 0;
     for (int k = 0; k < 3; ++k) {
-      l.cz[k] = (k >= 1 && k < p->D && n[k] % 2 == 0 && n[k] / 2 >= d.coarse_min) ? 1 : 0;
+      l.cz[k] = ((k >= 1 || d.coarsen_time) && k < p->D && n[k] % 2 == 0 && n[k] / 2 >= d.coarse_min) ? 1 : 0;
       nd += l.cz[k];
     }
     p->L++;

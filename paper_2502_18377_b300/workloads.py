@@ -265,6 +265,33 @@ def transport_2d(batch=4, n=(32, 256, 256), seed_base=5000, stencil=3):
                     field_of, scal, fields, rhs, np.zeros((batch, N)), tgt)
 
 
+def laplace_2d(batch=32, n=32, seed_base=6000, stencil=3):
+    """Laplace's equation u_yy + u_xx = 0 on the unit square (the solver test
+    of the paper's experiments section and its time / memory table, batch 32).
+
+    The grid's first axis plays y: c_tt = c_xx = 1, every other coefficient 0
+    (per-instance scalars), b = 0, Dirichlet rows on all four faces (the
+    final-plane face included).  Boundary data and the reference solution come
+    from the harmonic function u = sum_{k=1..3} a_k sin(k pi x) sinh(k pi y) /
+    sinh(k pi), a_k ~ U[-1, 1] per instance: sinusoidal on the face y = 1,
+    zero on the other three.  `target` holds u on the whole grid."""
+    (y, x), steps = _coords((n, n), (False, False), (1.0, 1.0))
+    Y, X = np.meshgrid(y, x, indexing="ij")
+    V, N = 5, n * n
+    scal = np.zeros((V, batch))
+    scal[2] = 1.0
+    scal[4] = 1.0
+    om = np.empty((batch, N))
+    for b in range(batch):
+        rng = np.random.default_rng(seed_base + b)
+        a = rng.uniform(-1.0, 1.0, size=3)
+        u = sum(a[k - 1] * np.sin(k * math.pi * X) * np.sinh(k * math.pi * Y) / math.sinh(k * math.pi)
+                for k in (1, 2, 3))
+        om[b] = u.ravel()
+    return Workload("laplace_2d", _geom((n, n), steps, (False, False), stencil, True),
+                    [-1] * V, scal, np.zeros((0, batch, N)), np.zeros((batch, N)), om, om.copy())
+
+
 def random_problem(seed, n, periodic, stencil=3, batch=1, final_time_rows=False,
                    lengths=None, field_all=True):
     """Generic random instance for property tests: every coefficient is a

@@ -78,6 +78,8 @@ CASES = [
     ("rand_dirichlet_3d", lambda: _no_utt(wl.random_problem(26, (8, 16, 12), (False, False, False), batch=2))),
     ("rand_final_3d", lambda: _no_utt(wl.random_problem(27, (12, 8, 16), (False, False, True), batch=2,
                                                         final_time_rows=True))),
+    # Laplace's equation (elliptic in both axes, Dirichlet on all four faces)
+    ("laplace_32", lambda: wl.laplace_2d(batch=2, n=32)),
 ]
 
 
@@ -117,6 +119,19 @@ def test_forward_passwise_levels_match_oracle(name, make):
     if it_p < 100:
         assert abs(it_f - it_p) <= 6, (sf.last_stats, s.last_stats)
     assert _rel(zf.ravel(), z.ravel()) <= 2 * FWD_TOL
+
+
+@pytest.mark.parametrize("krylov", ["cg", "fgmres"])
+def test_laplace_with_time_axis_coarsened_matches_oracle(krylov):
+    """Laplace's equation is elliptic in the first axis as well: the hierarchy
+    that halves it too (coarsen_time) reaches the oracle's solution."""
+    w = _round(wl.laplace_2d(batch=2, n=32))
+    s = _solver(w, coarsen_time=True, krylov=krylov)
+    assert s.levels()[1][0] == 16, s.levels()
+    z = s.forward(_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega)).cpu().numpy()
+    for b in range(w.batch):
+        zr = _oracle_instance(w, b)[4]
+        assert _rel(z[b].ravel(), zr) <= FWD_TOL, (b, _rel(z[b].ravel(), zr), s.last_stats)
 
 
 @pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])

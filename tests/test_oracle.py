@@ -214,6 +214,29 @@ def test_advection_translation_convergence():
     assert math.log2(errs[1] / errs[2]) > 1.5, errs
 
 
+def test_laplace_converges_to_harmonic_solution():
+    """Laplace's equation (the paper's solver unit test), with the grid's first
+    axis as y, Dirichlet data on all four faces from u = sinh(pi y) sin(pi x) /
+    sinh(pi) + 0.5 sinh(2 pi y) sin(2 pi x) / sinh(2 pi): the least-squares
+    solution approaches this harmonic function as the grid is refined."""
+    errs = []
+    for m in (8, 16, 32):
+        g = _geom((m, m), (False, False), final=True)
+        y = np.arange(m) * g["step"][0]
+        x = np.arange(m) * g["step"][1]
+        Y, X = np.meshgrid(y, x, indexing="ij")
+        u = (np.sinh(math.pi * Y) * np.sin(math.pi * X) / math.sinh(math.pi)
+             + 0.5 * np.sinh(2 * math.pi * Y) * np.sin(2 * math.pi * X) / math.sinh(2 * math.pi))
+        N = m * m
+        c = np.zeros((5, N)); c[2] = 1.0; c[4] = 1.0
+        A, d, kind, owner = asm.assemble(g, c, np.zeros(N), u.ravel())
+        z, _, _ = osv.solve_lsq(A, d)
+        errs.append(np.linalg.norm(z[:N] - u.ravel()) / np.linalg.norm(u))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[0] / errs[1] > 4 and errs[1] / errs[2] > 4, errs
+    assert errs[2] < 5e-3, errs
+
+
 # ------------------------------------------------------------- the LS solve
 @pytest.mark.parametrize("n,per,st", [((6, 6), (False, False), 3), ((6, 8), (False, True), 5),
                                       ((4, 5, 6), (False, True, False), 3)])
