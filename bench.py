@@ -98,11 +98,30 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def make_inputs(rank):
+def make_inputs(rank, batch=BATCH, grid=GRID):
+    """This rank's batch: the workload with seeds of its own (instances are
+    independent, so ranks share nothing)."""
     from paper_2502_18377_b300 import workloads as wl
-    w = wl.reaction_diffusion_2d(batch=BATCH, n=GRID, seed_base=2000 + 100_000 * rank)
+    w = wl.reaction_diffusion_2d(batch=batch, n=grid, seed_base=2000 + 100_000 * rank)
     f32 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float32))
     return w, f32(w.fields), f32(w.scalars), f32(w.rhs), f32(w.omega), f32(w.target)
+
+
+def job_time_ms(ms_local, world, device=None):
+    """Per-step time of the job: the maximum over ranks (the slowest rank
+    bounds a data-parallel step)."""
+    if world == 1:
+        return ms_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, batch, npoints, ms):
+    """Whole-job grid points per second: every rank solves its own batch."""
+    return world * batch * npoints / (ms / 1e3)
 
 
 def cpu_oracle_step(seed, n):
@@ -196,10 +215,7 @@ def run_ours(args):
     prof_ms, prof_n, prof_bytes, kernels = s.profile(0)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_time_ms(ms, world, dev)
     clk = clocks.stop()
 
     # end to end: host buffers through the public API (pinned H2D, D2H of the gradients)
@@ -233,7 +249,7 @@ def run_ours(args):
             e1.record()
             torch.cuda.synchronize()
             e2e_ms.append(e0.elapsed_time(e1))
-        e2e = {"value": world * B * N / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT,
+        e2e = {"value": job_throughput(world, B, N, job_time_ms(statistics.mean(e2e_ms), world, dev)), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank != 0:
@@ -243,7 +259,7 @@ def run_ours(args):
     peaks, src = _peaks()
     hbm = float(peaks["hbm_gbs"])
     achieved = (prof_bytes / prof_n) / (prof_ms / prof_n / 1e3) / 1e9 if prof_n else None
-    value = world * B * N / (ms / 1e3)
+    value = job_throughput(world, B, N, ms)
     cpu = None
     if not args.no_cpu_baseline:
         n_s = (16, 32, 32)
