@@ -258,3 +258,29 @@ def test_gradients_match_finite_differences_burgers():
         assert abs(an - fd) <= 1e-3 * scale, (k, kind, an, fd)
         checked += 1
     assert checked == 20
+
+
+def test_error_statuses_without_a_gpu_fault():
+    """Failure handling is host-visible status, never a device fault: NaN in
+    the inputs -> NONFINITE, too few refinement sweeps -> NOT_CONVERGED with
+    the statistics written, and the problem stays usable afterwards."""
+    from paper_2502_18377_b300.binding import MpnError
+    w = _round(wl.reaction_diffusion_2d(batch=2, n=(8, 16, 16)))
+    s = _solver(w)
+    args = [_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega)]
+    bad = args[2].clone()
+    bad[1, 17] = float("nan")
+    with pytest.raises(MpnError) as e:
+        s.forward(args[0], args[1], bad, args[3])
+    assert e.value.status == 4, e.value
+    s1 = _solver(w, max_refine=1)
+    with pytest.raises(MpnError) as e:
+        s1.forward(*args)
+    assert e.value.status == 3
+    assert s1.last_stats["sweeps"] == 1 and s1.last_stats["pcg_iters"] > 0
+    z = s1.forward(*args, allow_not_converged=True)
+    assert torch.isfinite(z).all()
+    # the first problem still solves correctly after the failed call
+    z = s.forward(*args).cpu().numpy()
+    zr = _oracle_instance(w, 0)[4]
+    assert _rel(z[0].ravel(), zr) <= FWD_TOL
