@@ -93,6 +93,10 @@ typedef struct mpn_desc {
                              that are elliptic in it (no first time derivative, e.g. Laplace's
                              equation with the first axis as a space axis); 0 (default): time is
                              kept on every level, as a central first time derivative requires */
+  int direct;             /* 1: batched direct path for small problems: no hierarchy, the whole reduced
+                             system is factorised (banded Cholesky, explicit inverse) once per forward
+                             solve and every refinement sweep applies the inverse (at most 4096 grid
+                             points per instance); 0 (default): multigrid-preconditioned Krylov */
 } mpn_desc;
 
 enum { MPN_KRYLOV_CG = 0, MPN_KRYLOV_FGMRES = 1 };
@@ -109,7 +113,7 @@ typedef struct mpn_stats {
 typedef struct mpn_problem mpn_problem;
 
 /* Fills *desc with defaults (tol 1e-7, max_refine 12, inner_iters 5,
- * cheb_degree 5, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 1, krylov CG, coarsen_time 0). */
+ * cheb_degree 5, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 1, krylov CG, coarsen_time 0, direct 0). */
 int mpn_default_desc(mpn_desc* desc);
 
 /* Validates the descriptor, builds the grid hierarchy (spatial halving, time

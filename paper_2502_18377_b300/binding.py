@@ -28,7 +28,8 @@ class MpnDesc(ctypes.Structure):
                 ("max_refine", ctypes.c_int), ("inner_iters", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("coarse_min", ctypes.c_int),
                 ("max_coarse", ctypes.c_int), ("fused_coarse", ctypes.c_int),
-                ("fused_step", ctypes.c_int), ("krylov", ctypes.c_int), ("coarsen_time", ctypes.c_int)]
+                ("fused_step", ctypes.c_int), ("krylov", ctypes.c_int), ("coarsen_time", ctypes.c_int),
+                ("direct", ctypes.c_int)]
 
 KRYLOV = {"cg": 0, "fgmres": 1}
 
@@ -167,7 +168,7 @@ class Solver:
 
     def __init__(self, geom: dict, batch: int, field_of, nfields: int, tol=1e-7, max_refine=12,
                  inner_iters=5, cheb_degree=5, coarse_min=4, max_coarse=2048, fused_coarse=True,
-                 fused_step=True, krylov="cg", coarsen_time=False):
+                 fused_step=True, krylov="cg", coarsen_time=False, direct=False):
         lib = load()
         d = MpnDesc()
         lib.mpn_default_desc(ctypes.byref(d))
@@ -190,6 +191,7 @@ class Solver:
         d.fused_step = int(bool(fused_step))
         d.krylov = KRYLOV[krylov]
         d.coarsen_time = int(bool(coarsen_time))
+        d.direct = int(bool(direct))
         h = ctypes.c_void_p()
         s = lib.mpn_create(ctypes.byref(d), ctypes.byref(h))
         if s != 0:

@@ -65,6 +65,7 @@ struct mpn_problem {
   float *scalars = nullptr, *rhs = nullptr, *omega = nullptr;
   float* scal4 = nullptr;  // scalars replicated 4 times, [V][B][4]
   int field_mask = 0;      // bit v: c_v is a field
+  bool band_smem = true;   // coarsest band factorised in shared memory
   // FGMRES workspace: basis V[mk + 1], preconditioned Z[mk], dot partials,
   // Hessenberg / rotations / rhs / solution per instance
   int mk = 0;
@@ -198,6 +199,7 @@ extern "C" int mpn_default_desc(mpn_desc* d) {
   d->fused_step = 1;
   d->krylov = MPN_KRYLOV_CG;
   d->coarsen_time = 0;
+  d->direct = 0;
   return MPN_OK;
 }
 
@@ -245,6 +247,8 @@ extern "C" int mpn_levels(const mpn_problem* p, int* nl, int* shapes) {
 }
 
 #define FS_MAX_NY 128
+// largest whole-problem system of the direct path (unknowns per instance)
+#define MPN_DIRECT_MAX 4096
 // shared memory of the coarsest-inverse kernel (floats)
 #define INV_SMEM_FLOATS (224 * 1024 / 4)
 // c_0, c_xx and c_yy fields, every other coefficient a per-instance scalar
@@ -413,7 +417,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
     l.g = make_grid(p->D, n, s, per, d.final_time_rows, theta);
     int nd = 0;
     for (int k = 0; k < 3; ++k) {
-      l.cz[k] = ((k >= 1 || d.coarsen_time) && k < p->D && n[k] % 2 == 0 && n[k] / 2 >= d.coarse_min) ? 1 : 0;
+      l.cz[k] = (!d.direct && (k >= 1 || d.coarsen_time) && k < p->D && n[k] % 2 == 0 && n[k] / 2 >= d.coarse_min) ? 1 : 0;
       nd += l.cz[k];
     }
     p->L++;
@@ -443,7 +447,11 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   p->M = lc.g.N;
   int plane = lc.g.n[1] * lc.g.n[2];
   p->bw = std::min(p->M - 1, 3 * plane - 1);
-  if (p->M > d.max_coarse || p->bw >= 256 || ((size_t)p->M * (p->bw + 1) + p->bw) * sizeof(float) > 200 * 1024) {
+  // the coarsest band is factorised in shared memory when it fits, else in
+  // global memory (the direct path's whole-problem systems)
+  p->band_smem = ((size_t)p->M * (p->bw + 1) + p->bw) * sizeof(float) <= 200 * 1024;
+  const int mmax = d.direct ? MPN_DIRECT_MAX : d.max_coarse;
+  if (p->M > mmax || p->bw >= 256 || (!d.direct && !p->band_smem)) {
     delete p;
     return MPN_ERR_UNSUPPORTED;
   }
@@ -663,25 +671,31 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
   Coef cfc = make_coef(p, lc.fields);
   CK(cudaMemsetAsync(p->ferr, 0, sizeof(int) * B, st));
   ++p->nlaunch, k_coarse_assemble<<<dim3(nblk(p->M), B), MPN_TPB, 0, st>>>(lc.g, cfc, lc.rho, p->bw, p->Kband);
-  size_t smem = sizeof(float) * ((size_t)p->M * (p->bw + 1) + p->bw);
-  CK(cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ++p->nlaunch, k_coarse_factor<<<B, 512, smem, st>>>(p->M, p->bw, p->Kband, p->ferr);
+  if (p->band_smem) {
+    size_t smem = sizeof(float) * ((size_t)p->M * (p->bw + 1) + p->bw);
+    CK(cudaFuncSetAttribute(k_coarse_factor<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ++p->nlaunch, k_coarse_factor<true><<<B, 512, smem, st>>>(p->M, p->bw, p->Kband, p->ferr);
+  } else {
+    ++p->nlaunch, k_coarse_factor<false><<<B, 512, sizeof(float) * p->bw, st>>>(p->M, p->bw, p->Kband, p->ferr);
+  }
   // one warp per column of the inverse; the CTA stages the band, the
   // reciprocal diagonal and one forward-solution vector per warp
   {
-    const size_t fixed = (size_t)p->M * (p->bw + 1) + p->M;
+    const size_t fixed = (p->band_smem ? (size_t)p->M * (p->bw + 1) : 0) + p->M;
     int nwarps = (int)std::min<size_t>(32, (INV_SMEM_FLOATS - fixed) / p->M);
     dim3 gi((p->M + nwarps - 1) / nwarps, B);
     size_t sm = sizeof(float) * (fixed + (size_t)nwarps * p->M);
-#define INV_LAUNCH(NW)                                                                                 \
-  do {                                                                                                 \
-    CK(cudaFuncSetAttribute(k_coarse_inverse<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
-    ++p->nlaunch, k_coarse_inverse<NW><<<gi, 32 * nwarps, sm, st>>>(p->M, p->bw, p->Kband, p->Kinv);      \
+#define INV_LAUNCH2(NW, SM)                                                                                  \
+  do {                                                                                                       \
+    CK(cudaFuncSetAttribute(k_coarse_inverse<NW, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+    ++p->nlaunch, k_coarse_inverse<NW, SM><<<gi, 32 * nwarps, sm, st>>>(p->M, p->bw, p->Kband, p->Kinv);      \
   } while (0)
+#define INV_LAUNCH(NW) do { if (p->band_smem) INV_LAUNCH2(NW, true); else INV_LAUNCH2(NW, false); } while (0)
     if (p->bw < 32) INV_LAUNCH(1);
     else if (p->bw < 64) INV_LAUNCH(2);
     else if (p->bw < 128) INV_LAUNCH(4);
     else INV_LAUNCH(8);
+#undef INV_LAUNCH2
 #undef INV_LAUNCH
   }
 
@@ -938,7 +952,7 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
   // ||rhs|| for the relative residual: the first residual when starting from 0
   if (!zero_start) TRY(residual64(p, nullptr, g_adj, p->r64, slot(p, S_GN), st));
   std::vector<double> gnorm(B, 0.0);
-  int iters = p->desc.inner_iters, total_iters = 0;
+  int iters = p->desc.direct ? 1 : p->desc.inner_iters, total_iters = 0;
   for (int sweep = 0; sweep < p->desc.max_refine; ++sweep) {
     TRY(run_sweep(p, g_adj, iters, P, st));
     total_iters += iters;
@@ -975,7 +989,7 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
     if (grew) { status = MPN_ERR_DIVERGED; break; }
     if ((sweep >= 2 && maxpred <= p->desc.tol) || (sweep >= 1 && maxupd <= p->desc.tol * 0.1)) { status = MPN_OK; break; }
     // a sweep that gained less than a digit: lengthen the inner solve
-    if (sweep >= 1 && maxrate > 0.1 && iters < 8 * p->desc.inner_iters) iters *= 2;
+    if (!p->desc.direct && sweep >= 1 && maxrate > 0.1 && iters < 8 * p->desc.inner_iters) iters *= 2;
   }
   if (stats) *stats = sres;
   return status;

@@ -382,13 +382,19 @@ __global__ void k_coarse_assemble(Grid g, Coef cf, const float* __restrict__ rho
 // ii < bw scale l_ik (i = k + 1 + ii) into the column buffer; after a barrier
 // the block, as 32 columns x (blockDim / 32) rows, updates the lower triangle
 // S_ij -= l_ik l_jk, k < j <= i <= k + bw.  blockDim.x >= bw, a multiple of 32.
+template <bool SMEM>
 __global__ void k_coarse_factor(int M, int bw, float* __restrict__ Kb, int* __restrict__ err) {
-  extern __shared__ float sb[];
+  extern __shared__ float shm[];
   const int b = blockIdx.x;
   float* K = Kb + (size_t)b * M * (bw + 1);
   const int W = bw + 1;
-  float* colk = sb + (size_t)M * W;
-  for (int t = threadIdx.x; t < M * W; t += blockDim.x) sb[t] = K[t];
+  // SMEM: the band is staged in shared memory; else it is factorised in place
+  // in global memory (L2-resident), for bands larger than shared memory
+  float* sb = SMEM ? shm : K;
+  float* colk = SMEM ? shm + (size_t)M * W : shm;
+  if (SMEM) {
+    for (int t = threadIdx.x; t < M * W; t += blockDim.x) sb[t] = K[t];
+  }
   __syncthreads();
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
   for (int k = 0; k < M; ++k) {
@@ -408,7 +414,9 @@ __global__ void k_coarse_factor(int M, int bw, float* __restrict__ Kb, int* __re
     }
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < M * W; t += blockDim.x) K[t] = sb[t];
+  if (SMEM) {
+    for (int t = threadIdx.x; t < M * W; t += blockDim.x) K[t] = sb[t];
+  }
 }
 
 // Explicit inverse from the banded factor (bw < 32 NW): one warp per column c
@@ -418,22 +426,22 @@ __global__ void k_coarse_factor(int M, int bw, float* __restrict__ Kb, int* __re
 // band row (or column) is split across the lanes and the dot product reduced
 // by shuffles; the last 32 NW values of the substitution live in NW registers
 // per lane and shift by one lane per step.
-template <int NW>
+template <int NW, bool SMEM>
 __global__ void k_coarse_inverse(int M, int bw, const float* __restrict__ Lb, float* __restrict__ Kinv) {
   extern __shared__ float sL[];
   const int b = blockIdx.y;
   const int W = bw + 1;
-  float* rd = sL + (size_t)M * W;
+  const float* src = Lb + (size_t)b * M * W;
+  float* rd = SMEM ? sL + (size_t)M * W : sL;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* Y = rd + M + (size_t)wid * M;       // this warp's forward solution
-  {
-    const float* src = Lb + (size_t)b * M * W;
+  if (SMEM) {
     for (int t = threadIdx.x; t < M * W; t += blockDim.x) sL[t] = src[t];
     __syncthreads();
-    for (int t = threadIdx.x; t < M; t += blockDim.x) rd[t] = 1.f / sL[t * W];
-    __syncthreads();
   }
-  const float* L = sL;
+  const float* L = SMEM ? sL : src;        // band rows: shared memory, or global (L2)
+  for (int t = threadIdx.x; t < M; t += blockDim.x) rd[t] = 1.f / L[(size_t)t * W];
+  __syncthreads();
   // column of this warp: long (small c) and short (large c) columns alternate
   const int idx = blockIdx.x * (blockDim.x >> 5) + wid;
   if (idx >= M) return;

@@ -121,6 +121,42 @@ def test_forward_passwise_levels_match_oracle(name, make):
     assert _rel(zf.ravel(), z.ravel()) <= 2 * FWD_TOL
 
 
+DIRECT_CASES = ["c1_full", "c3_small", "rand_dirichlet_2d", "rand_odd_2d_final", "rand_utt_2d",
+                "rand_scalars_3d", "laplace_32"]
+
+
+@pytest.mark.parametrize("name,make", [c for c in CASES if c[0] in DIRECT_CASES],
+                         ids=[c[0] for c in CASES if c[0] in DIRECT_CASES])
+def test_direct_path_matches_oracle(name, make):
+    """Small problems through the direct path (no hierarchy; the reduced
+    system's banded Cholesky factor and explicit inverse, in shared or global
+    memory by band size): forward and adjoint meet the oracle."""
+    w = _round(make())
+    s = _solver(w, direct=True)
+    assert len(s.levels()) == 1
+    args = (_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega))
+    z = s.forward(*args)
+    zc = z.cpu().numpy()
+    rng = np.random.default_rng(7)
+    V, N = asm.n_vars(w.ndim), w.npoints
+    g = rng.normal(size=(w.batch, V, N)).astype(np.float32)
+    _, _, drhs, _, dz = s.adjoint(*args, z, _dev(g), reuse_setup=True, want_dz=True)
+    dz = dz.cpu().numpy()
+    for b in range(w.batch):
+        A, d, kind, owner, zr, lam, el = _oracle_instance(w, b)
+        assert _rel(zc[b].ravel(), zr) <= FWD_TOL, (name, b, _rel(zc[b].ravel(), zr), s.last_stats)
+        dzr, _ = og.adjoint_elim(el, g[b].astype(np.float64).ravel())
+        assert _rel(dz[b].ravel(), dzr) <= FWD_TOL, (name, b, _rel(dz[b].ravel(), dzr))
+
+
+def test_direct_path_rejects_wide_bands():
+    from paper_2502_18377_b300.binding import MpnError
+    w = wl.reaction_diffusion_2d(batch=1, n=(8, 16, 16))      # band 3 * 256 - 1 >= 256
+    with pytest.raises(MpnError) as e:
+        _solver(w, direct=True)
+    assert e.value.status == 2
+
+
 @pytest.mark.parametrize("krylov", ["cg", "fgmres"])
 def test_laplace_with_time_axis_coarsened_matches_oracle(krylov):
     """Laplace's equation is elliptic in the first axis as well: the hierarchy
