@@ -100,7 +100,7 @@ struct mpn_problem {
   int prof_next = 0;       // next free event of the pool (graphs keep theirs)
   // one CUDA graph per (solve kind, inner iterations, profiling): a whole
   // refinement sweep, replayed on an internal stream
-  struct SweepGraph { int adjoint, iters, prof; cudaGraphExec_t exec; long long kernels; int ev0, ev1; };
+  struct SweepGraph { int adjoint, iters, prof; bool from_zero; cudaGraphExec_t exec; long long kernels; int ev0, ev1; };
   std::vector<SweepGraph> graphs;
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_user = nullptr;
@@ -863,6 +863,11 @@ static int residual64(mpn_problem* p, const double* u, const double* g_adj, doub
   dim3 gr(nblk(l.g.N), p->B);   // partial count per instance = nblk (as every refinement reduction)
   const float* src = g_adj ? nullptr : p->rhs;
   const float* om = g_adj ? nullptr : p->omega;
+  if (!u && g_adj) {   // adjoint from zero: the residual is the right-hand side
+    ++p->nlaunch, k_copy_norm64<<<gr, MPN_TPB, 0, st>>>(l.g.N, g_adj, out, part);
+    CKL();
+    return MPN_OK;
+  }
   if (p->D == 3 && p->field_mask == FS_MASK_RD) {
     ++p->nlaunch, k_res64_y<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
     ++p->nlaunch, k_res64_q<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
@@ -879,13 +884,14 @@ static int residual64(mpn_problem* p, const double* u, const double* g_adj, doub
 
 // The work of one refinement sweep on stream `st`: FP64 residual, inner PCG,
 // FP64 update, the sizes the stop rule needs, and their copy to the host.
-static int sweep_body(mpn_problem* p, const double* g_adj, int iters, int P, cudaStream_t st) {
+static int sweep_body(mpn_problem* p, const double* g_adj, int iters, int P, bool from_zero, cudaStream_t st) {
   Level& l = p->lv[0];
   int B = p->B, N = l.g.N;
   dim3 gr(P, B);
   double* scale = p->dscal;
   double* outv = p->dscal + 2 * B;  // [slots][B]
-  TRY(residual64(p, p->u64, g_adj, p->r64, slot(p, S_RN), st));
+  // from a zero iterate the residual needs no operator apply on u
+  TRY(residual64(p, from_zero ? nullptr : p->u64, g_adj, p->r64, slot(p, S_RN), st));
   ++p->nlaunch, k_to32<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN), P, l.r, scale);
   CKL();
   if (p->desc.krylov == MPN_KRYLOV_FGMRES) TRY(fgmres(p, iters, st));
@@ -904,7 +910,7 @@ static int sweep_body(mpn_problem* p, const double* g_adj, int iters, int P, cud
 // stream (captured on first use for this solve kind, inner-iteration count and
 // profiling state).  Ordered after the caller's stream; returns once the
 // sweep's scalars are on the host.
-static int run_sweep(mpn_problem* p, const double* g_adj, int iters, int P, cudaStream_t st) {
+static int run_sweep(mpn_problem* p, const double* g_adj, int iters, int P, bool from_zero, cudaStream_t st) {
   if (!p->gstream) {
     CK(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&p->ev_user, cudaEventDisableTiming));
@@ -912,13 +918,13 @@ static int run_sweep(mpn_problem* p, const double* g_adj, int iters, int P, cuda
   int adj = g_adj ? 1 : 0;
   mpn_problem::SweepGraph* g = nullptr;
   for (auto& x : p->graphs)
-    if (x.adjoint == adj && x.iters == iters && x.prof == p->prof_on) g = &x;
+    if (x.adjoint == adj && x.iters == iters && x.prof == p->prof_on && x.from_zero == from_zero) g = &x;
   if (!g) {
     long long nl0 = p->nlaunch;
     int ev0 = p->prof_next;
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
-    int s = sweep_body(p, g_adj, iters, P, p->gstream);
+    int s = sweep_body(p, g_adj, iters, P, from_zero, p->gstream);
     cudaError_t ec = cudaStreamEndCapture(p->gstream, &graph);
     if (s != MPN_OK) { if (graph) cudaGraphDestroy(graph); return s; }
     CK(ec);
@@ -926,7 +932,7 @@ static int run_sweep(mpn_problem* p, const double* g_adj, int iters, int P, cuda
     cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     CK(ei);
-    p->graphs.push_back({adj, iters, p->prof_on, exec, p->nlaunch - nl0, ev0, p->prof_next});
+    p->graphs.push_back({adj, iters, p->prof_on, from_zero, exec, p->nlaunch - nl0, ev0, p->prof_next});
     p->nlaunch = nl0;
     g = &p->graphs.back();
   }
@@ -954,7 +960,7 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
   std::vector<double> gnorm(B, 0.0);
   int iters = p->desc.direct ? 1 : p->desc.inner_iters, total_iters = 0;
   for (int sweep = 0; sweep < p->desc.max_refine; ++sweep) {
-    TRY(run_sweep(p, g_adj, iters, P, st));
+    TRY(run_sweep(p, g_adj, iters, P, zero_start && sweep == 0, st));
     total_iters += iters;
     const double* h = p->hbuf;
     double maxpred = 0, maxupd = 0, maxres = 0, maxrate = 0;

@@ -764,6 +764,20 @@ __global__ void k_fg_update(int N, const float* __restrict__ Z, size_t zstride, 
   }
 }
 
+// out = g (FP64) with partials of |g|^2: the residual of a solve from zero.
+__global__ void k_copy_norm64(int N, const double* __restrict__ g, double* __restrict__ out, double* __restrict__ part) {
+  const int b = blockIdx.y;
+  const size_t off = (size_t)b * N;
+  double acc = 0;
+  GRID_LOOP(p, N) {
+    const double v = g[off + p];
+    out[off + p] = v;
+    acc += v * v;
+  }
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) part[b * MPN_PMAX + blockIdx.x] = s;
+}
+
 __global__ void k_to32(int N, const double* __restrict__ r64, const double* __restrict__ part, int P,
                        float* __restrict__ r32, double* __restrict__ scale) {
   int b = blockIdx.y;
