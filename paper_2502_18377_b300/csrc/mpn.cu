@@ -62,6 +62,7 @@ struct mpn_problem {
   int M, bw;           // coarsest system size and band width
   float *Kband = nullptr, *Kinv = nullptr;
   int* ferr = nullptr;
+  int* kerr = nullptr;     // device word a kernel sets when a bounded wait gives up (sticky)
   float *scalars = nullptr, *rhs = nullptr, *omega = nullptr;
   float* scal4 = nullptr;  // scalars replicated 4 times, [V][B][4]
   int field_mask = 0;      // bit v: c_v is a field
@@ -471,6 +472,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   AL(p->Kband, (size_t)B * p->M * (p->bw + 1));
   AL(p->Kinv, (size_t)B * p->M * p->M);
   AL(p->ferr, B);
+  AL(p->kerr, 1);
   AL(p->scalars, (size_t)V * B);
   AL(p->scal4, (size_t)V * B * 4);
   AL(p->rhs, N0); AL(p->omega, N0);
@@ -495,6 +497,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   int fo[8];
   for (int v = 0; v < 8; ++v) fo[v] = v < V ? d.field_of[v] : -1;
   if (cudaMemcpy(p->field_of_dev, fo, sizeof(fo), cudaMemcpyHostToDevice) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
+  if (cudaMemset(p->kerr, 0, sizeof(int)) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
   if (cudaMallocHost((void**)&p->hbuf, sizeof(double) * 16 * B) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
 
   // Chebyshev coefficients on [lo, 1] for Dinv scaled by 1 / lambda_max
@@ -546,6 +549,7 @@ static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st
   Coef cf = make_coef(p, l.fields);
   a.y = l.y;
   if (!a.dinv) a.dinv = l.dinv;
+  if (!a.err) a.err = p->kerr;
   if (l.fs_tt) {
     dim3 gs((l.g.n[0] / l.fs_tt) * (l.g.n[1] / FS_TX), p->B);
     size_t sm = fs_smem(l.fs_tt, l.g.n[2]);
@@ -903,6 +907,7 @@ static int sweep_body(mpn_problem* p, const double* g_adj, int iters, int P, boo
   ++p->nlaunch, k_collect<<<B, 64, 0, st>>>(B, 5, slot(p, S_RN), P, outv);
   CKL();
   CK(cudaMemcpyAsync(p->hbuf, outv, sizeof(double) * 5 * B, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(p->hbuf + 5 * B, p->kerr, sizeof(int), cudaMemcpyDeviceToHost, st));
   return MPN_OK;
 }
 
@@ -963,6 +968,7 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
     TRY(run_sweep(p, g_adj, iters, P, zero_start && sweep == 0, st));
     total_iters += iters;
     const double* h = p->hbuf;
+    if (*(const int*)(h + 5 * B)) { status = MPN_ERR_CUDA; break; }   // a kernel's bounded wait gave up
     double maxpred = 0, maxupd = 0, maxres = 0, maxrate = 0;
     bool bad = false, grew = false;
     for (int b = 0; b < B; ++b) {

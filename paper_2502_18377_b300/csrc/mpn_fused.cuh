@@ -31,6 +31,32 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;" ::: "memory");
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
+// Bulk asynchronous copies global -> shared completing on an mbarrier.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(float* dst, const float* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// Waits for phase `parity` of the barrier; gives up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int limit) {
+  const unsigned a = smem_u32(bar);
+  for (int i = 0; i < limit; ++i) {
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+#define FS_WAIT_LIMIT (1 << 22)
+
 __device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
 // Shared-memory floats of the tile for a y extent n2.
@@ -101,18 +127,47 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
   const float i2t = g.is2[0], i2x = g.is2[1], i2y = g.is2[2];
 
   // 1. operand rows t0-2 .. t0+TT+1 x x0-2 .. x0+FS_TX+1 (rows outside a
-  //    non-periodic domain are never read)
-  for (int i = threadIdx.x; i < fs_rows_x(TT) * G; i += FS_TPB) {
-    int gq;
-    const int row = fdivmod(i, G, invG, gq);
-    const int t = t0 - 2 + row / RXW;
-    int x = x0 - 2 + row % RXW;
-    if (t < 0 || t >= n0) continue;
-    if (PER1) { if (x < 0) x += n1; else if (x >= n1) x -= n1; }
-    else if (x < 0 || x >= n1) continue;
-    cp_async16(xs + row * n2 + 4 * gq, X + (size_t)t * pl + x * n2 + 4 * gq);
+  //    non-periodic domain are never read): per time plane one bulk copy of
+  //    the consecutive x rows, split where a periodic x wraps
+  //    Lane rt of warp 0 copies time plane t0-2+rt.
+  __shared__ unsigned long long bar;
+  if (threadIdx.x < 32) {
+    const int rt = threadIdx.x, t = t0 - 2 + rt;
+    const bool plane = rt < TT + 4 && t >= 0 && t < n0;
+    // visits the segments (source row x, tile row, rows) of this lane's plane
+    auto segments = [&](auto&& visit) {
+      int rx = 0;
+      while (plane && rx < RXW) {
+        int x = x0 - 2 + rx, len;
+        if (x < 0) {
+          len = min(-x, RXW - rx);
+          if (!PER1) { rx += len; continue; }
+          x += n1;
+        } else if (x >= n1) {
+          if (!PER1) break;
+          len = RXW - rx;
+          x -= n1;
+        } else {
+          len = min(n1 - x, RXW - rx);
+        }
+        visit(x, rt * RXW + rx, len);
+        rx += len;
+      }
+    };
+    int rows = 0;
+    segments([&](int, int, int len) { rows += len; });
+    rows = __reduce_add_sync(0xffffffffu, rows);
+    if (rt == 0) {
+      mbar_init(&bar, 1);
+      mbar_expect_tx(&bar, (unsigned)(rows * n2 * sizeof(float)));
+    }
+    __syncwarp();
+    segments([&](int x, int r, int len) {
+      bulk_g2s(xs + r * n2, X + (size_t)t * pl + (size_t)x * n2, (unsigned)(len * n2 * sizeof(float)), &bar);
+    });
   }
-  cp_async_wait_all();
+  __syncthreads();
+  if (!mbar_wait(&bar, 0, FS_WAIT_LIMIT) && a.err) atomicExch(a.err, 1);
   __syncthreads();
 
   // each thread keeps one float4 group gi of the rows and strides over rows

@@ -26,6 +26,7 @@ struct StepArgs {
   float* d;           // direction (modes 0, 1)
   float* out;         // mode 2: r - S x;  mode 3: S x
   double* part;       // mode 3: partials of <x, S x> (nullable)
+  int* err;           // set when a bounded wait gives up (fused step; nullable)
   float c1, c2;
 };
 
