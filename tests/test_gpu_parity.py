@@ -60,10 +60,30 @@ def _no_utt(w):
     return w
 
 
+def _rd_fields(w, layout):
+    """Reaction-diffusion with another assignment of its coefficient fields
+    (c_0, c_xx, c_yy stay fields, the fused step's compile-time layout):
+    "three" gives c_yy a field of its own (anisotropic diffusion), "one"
+    makes c_0, c_xx and c_yy one field."""
+    if layout == "three":
+        d2 = w.fields[0] * (1.0 + 0.5 * np.cos(np.linspace(0.0, 3.0, w.npoints)))[None, :]
+        fields = np.concatenate([w.fields, d2[None]], axis=0)
+        field_of = [1, -1, -1, -1, 0, -1, 2]
+    else:
+        fields = w.fields[:1].copy()
+        field_of = [0, -1, -1, -1, 0, -1, 0]
+    return wl.Workload(w.name + "_" + layout, w.geom, field_of, w.scalars, fields, w.rhs, w.omega, w.target)
+
+
 CASES = [
     ("c1_full", lambda: wl.advection_diffusion_1d()),
     ("c2_small", lambda: wl.reaction_diffusion_2d(batch=3, n=(8, 16, 16))),
     ("c2_ragged", lambda: wl.reaction_diffusion_2d(batch=2, n=(10, 12, 20))),
+    # the fused step's compile-time layout with three distinct fields on
+    # 4-plane tiles, with one field, and with 128-point y rows
+    ("c2_three_fields", lambda: _rd_fields(wl.reaction_diffusion_2d(batch=2, n=(12, 16, 32)), "three")),
+    ("c2_one_field", lambda: _rd_fields(wl.reaction_diffusion_2d(batch=2, n=(8, 16, 16)), "one")),
+    ("c2_wide_y", lambda: wl.reaction_diffusion_2d(batch=1, n=(8, 8, 128))),
     ("c3_small", lambda: wl.linearized_burgers_1d(batch=2, n=(32, 64))),
     ("c5_small", lambda: wl.transport_2d(batch=2, n=(8, 16, 16))),
     ("rand_dirichlet_2d", lambda: _no_utt(wl.random_problem(21, (12, 32), (False, False), batch=2))),
