@@ -296,8 +296,8 @@ static void plan_tail(mpn_problem* p) {
     bool keeps_t = true;
     for (int k = k0; k + 1 < p->L; ++k) keeps_t = keeps_t && !p->lv[k].cz[0];
     if (!keeps_t) continue;
-    // a level with more than two points per thread and CTA runs better pass
-    // by pass over the whole GPU (vectorised kernels, full occupancy)
+    // a level with more than TAIL_MAX_PPT points per thread and CTA runs
+    // better pass by pass over the whole GPU (vectorised kernels, full occupancy)
     if ((size_t)P * p->lv[k0].g.n[1] * p->lv[k0].g.n[2] > TAIL_MAX_PPT * TAIL_TPB) continue;
     TailArgs& ta = p->tail;
     memset(&ta, 0, sizeof(ta));

@@ -66,8 +66,8 @@ def test_reaction_diffusion_bench_size_residual():
     from paper_2502_18377_b300.binding import Solver
     w = _round(wl.reaction_diffusion_2d())          # B = 16, 32 x 64 x 64
     s = Solver(w.geom, w.batch, w.field_of, w.fields.shape[0])
-    # levels 32x16x16 and coarser run as one clustered kernel per V-cycle
-    assert s.fused_level() == 2, (s.levels(), s.fused_level())
+    # levels 32x8x8 and coarser run as one clustered kernel per V-cycle
+    assert s.fused_level() == 3, (s.levels(), s.fused_level())
     args = (_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega))
     z64 = torch.empty((w.batch, 7, w.npoints), device="cuda", dtype=torch.float64)
     z = s.forward(*args, z64=z64)
