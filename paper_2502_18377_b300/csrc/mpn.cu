@@ -254,6 +254,8 @@ extern "C" int mpn_levels(const mpn_problem* p, int* nl, int* shapes) {
 #define INV_SMEM_FLOATS (224 * 1024 / 4)
 // c_0, c_xx and c_yy fields, every other coefficient a per-instance scalar
 #define FS_MASK_RD ((1 << 0) | (1 << 4) | (1 << 6))
+// the same with c_xx and c_yy one field
+#define FS_MASK_RDI (FS_MASK_RD | FS_SHARE46)
 static size_t fs_smem(int tt, int ny) { return sizeof(float) * (size_t)(fs_rows_x(tt) + fs_rows_y(tt)) * ny; }
 // Opt the fused step kernels into the shared memory of the largest tile.
 static int fs_set_smem() {
@@ -262,7 +264,7 @@ static int fs_set_smem() {
 #define FS_ATTR(M, T, P1, P2, MK) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<M, T, P1, P2, MK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
 #define FS_ATTR_M(T, P1, P2, MK) FS_ATTR(SM_POST0, T, P1, P2, MK); FS_ATTR(SM_CHEB, T, P1, P2, MK); FS_ATTR(SM_RES, T, P1, P2, MK); FS_ATTR(SM_APPLY, T, P1, P2, MK)
-#define FS_ATTR_P(T) FS_ATTR_M(T, true, true, FS_ANY); FS_ATTR_M(T, true, false, FS_ANY); FS_ATTR_M(T, false, true, FS_ANY); FS_ATTR_M(T, false, false, FS_ANY); FS_ATTR_M(T, true, true, FS_MASK_RD)
+#define FS_ATTR_P(T) FS_ATTR_M(T, true, true, FS_ANY); FS_ATTR_M(T, true, false, FS_ANY); FS_ATTR_M(T, false, true, FS_ANY); FS_ATTR_M(T, false, false, FS_ANY); FS_ATTR_M(T, true, true, FS_MASK_RD); FS_ATTR_M(T, true, true, FS_MASK_RDI)
   FS_ATTR_P(8);
   FS_ATTR_P(4);
 #undef FS_ATTR_P
@@ -563,7 +565,9 @@ static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st
 #define FS_LAUNCH_T(P1, P2, MK) if (l.fs_tt == 8) { FS_LAUNCH(8, P1, P2, MK) } else { FS_LAUNCH(4, P1, P2, MK) }
     // compile-time coefficient layout for the common case of a reaction term
     // and an isotropic diffusion field with scalar first-order and time terms
-    if (l.g.per[1] && l.g.per[2] && p->field_mask == FS_MASK_RD) { FS_LAUNCH_T(true, true, FS_MASK_RD) }
+    if (l.g.per[1] && l.g.per[2] && p->field_mask == FS_MASK_RD && p->desc.field_of[4] == p->desc.field_of[6]) {
+      FS_LAUNCH_T(true, true, FS_MASK_RDI)
+    } else if (l.g.per[1] && l.g.per[2] && p->field_mask == FS_MASK_RD) { FS_LAUNCH_T(true, true, FS_MASK_RD) }
     else if (l.g.per[1] && l.g.per[2]) { FS_LAUNCH_T(true, true, FS_ANY) }
     else if (l.g.per[1]) { FS_LAUNCH_T(true, false, FS_ANY) }
     else if (l.g.per[2]) { FS_LAUNCH_T(false, true, FS_ANY) }

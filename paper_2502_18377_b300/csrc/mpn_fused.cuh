@@ -84,6 +84,9 @@ __device__ __forceinline__ void dforms1(int cls, float xm2, float xm1, float x0,
 #ifndef FS_ANY
 #define FS_ANY 0x80
 #endif
+// with a compile-time layout: c_yy reads the field of c_xx (isotropic
+// diffusion), so the shared loads are issued once
+#define FS_SHARE46 0x100
 template <int MASK>
 struct CoefU4 {
   const float* base[7];
@@ -99,10 +102,12 @@ struct CoefU4 {
   }
   __device__ __forceinline__ float4 at4(int v, int p) const {
     if (MASK == FS_ANY) return ld4(base[v] + p * ps[v]);
+    if ((MASK & FS_SHARE46) && v == 6) v = 4;
     return ((MASK >> v) & 1) ? ld4(base[v] + p) : f4(sv[v]);
   }
   __device__ __forceinline__ float at(int v, int p) const {
     if (MASK == FS_ANY) return __ldg(base[v] + p * ps[v]);
+    if ((MASK & FS_SHARE46) && v == 6) v = 4;
     return ((MASK >> v) & 1) ? __ldg(base[v] + p) : sv[v];
   }
 };
