@@ -156,6 +156,7 @@ static Grid make_grid(int D, const int n[3], const double s[3], const int per[3]
   g.N = g.n[0] * g.n[1] * g.n[2];
   g.final_rows = final_rows;
   g.theta = theta;
+  grid_set_inverses(g);
   return g;
 }
 

@@ -36,7 +36,14 @@ struct Grid {
   float theta;    // weight of the Dirichlet rows at this level
   float is1[3], is2[3];    // 1/s, 1/s^2
   double ds1[3], ds2[3];   // 1/s, 1/s^2 in FP64
+  float inv_pl, inv_n2;    // 1 / (n[1] n[2]), 1 / n[2] (index decoding)
 };
+
+// Host: the reciprocals decode_fast() reads.
+inline void grid_set_inverses(Grid& g) {
+  g.inv_pl = 1.f / (float)(g.n[1] * g.n[2]);
+  g.inv_n2 = 1.f / (float)g.n[2];
+}
 
 struct Coef {
   int V, F, B;
@@ -84,19 +91,12 @@ __device__ __forceinline__ int fdivmod(int q, int n, float inv_n, int& r) {
   return a;
 }
 
-__device__ __forceinline__ void decode(const Grid& g, int p, int pos[3]) {
-  pos[2] = p % g.n[2];
-  int q = p / g.n[2];
-  pos[1] = q % g.n[1];
-  pos[0] = q / g.n[1];
-}
-
-// decode() without integer division; any_edge: the point is within 2 of a
+// Point index -> (t, x, y) without an integer division; any_edge: the point is within 2 of a
 // time edge or of a non-periodic spatial edge (one-sided forms nearby).
 __device__ __forceinline__ void decode_fast(const Grid& g, int p, int pos[3]) {
   int rem, i2;
-  pos[0] = fdivmod(p, g.n[1] * g.n[2], __frcp_rn((float)(g.n[1] * g.n[2])), rem);
-  pos[1] = fdivmod(rem, g.n[2], __frcp_rn((float)g.n[2]), i2);
+  pos[0] = fdivmod(p, g.n[1] * g.n[2], g.inv_pl, rem);
+  pos[1] = fdivmod(rem, g.n[2], g.inv_n2, i2);
   pos[2] = i2;
 }
 __device__ __forceinline__ bool any_edge(const Grid& g, const int pos[3]) {
@@ -106,11 +106,15 @@ __device__ __forceinline__ bool any_edge(const Grid& g, const int pos[3]) {
   return e;
 }
 
+// c wrapped into [0, n) for -n <= c < 2n: every periodic neighbour offset
+// is at most 2 and every extent at least 3, so one add or subtract suffices.
+__device__ __forceinline__ int wrap1(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
+
 // Point index of the neighbour at offset o along d (wrapping when periodic).
 // The caller guarantees the target exists for non-periodic dims.
 __device__ __forceinline__ int nbr(const Grid& g, int p, const int pos[3], int d, int o) {
   int c = pos[d] + o;
-  if (g.per[d]) { c %= g.n[d]; if (c < 0) c += g.n[d]; }
+  if (g.per[d]) c = wrap1(c, g.n[d]);
   return p + (c - pos[d]) * g.stride[d];
 }
 
@@ -232,7 +236,7 @@ __device__ __forceinline__ T LTgather(const Grid& g, const Coef& cf, int b, int 
 #pragma unroll
     for (int o = -2; o <= 2; ++o) {
       int ip = pos[d] - o;
-      if (g.per[d]) { ip %= g.n[d]; if (ip < 0) ip += g.n[d]; }
+      if (g.per[d]) ip = wrap1(ip, g.n[d]);
       else if (ip < 0 || ip >= g.n[d]) continue;
       float w1 = dweight(1, ip, g.n[d], g.per[d], o);
       float w2 = dweight(2, ip, g.n[d], g.per[d], o);

@@ -49,7 +49,7 @@ __global__ void k_restrict_field(Grid gf, Grid gc, int c0, int c1, int c2, const
   int cz[3] = {c0, c1, c2};
   const float* f = fine + (size_t)b * gf.N;
   GRID_LOOP(p, gc.N) {
-    int pos[3]; decode(gc, p, pos);
+    int pos[3]; decode_fast(gc, p, pos);
     int cnt[3], idx[3][8]; float w[3][8];
     for (int d = 0; d < 3; ++d) {
       if (!cz[d]) { cnt[d] = 1; idx[d][0] = pos[d]; w[d][0] = 1.f; continue; }
@@ -57,7 +57,7 @@ __global__ void k_restrict_field(Grid gf, Grid gc, int c0, int c1, int c2, const
       if (gf.per[d]) {
         int c = 2 * pos[d];
         cnt[d] = 3;
-        idx[d][0] = (c - 1 + n) % n; idx[d][1] = c; idx[d][2] = (c + 1) % n;
+        idx[d][0] = wrap1(c - 1, n); idx[d][1] = c; idx[d][2] = wrap1(c + 1, n);
         w[d][0] = 0.25f; w[d][1] = 0.5f; w[d][2] = 0.25f;
       } else {
         cnt[d] = np_restrict_w(pos[d], n, gc.n[d], idx[d], w[d]);
@@ -82,7 +82,7 @@ __global__ void k_diag_inv(Grid g, Coef cf, const float* __restrict__ rho, float
   int b = blockIdx.y;
   const float* rh = rho + (size_t)b * g.N;
   GRID_LOOP(p, g.N) {
-    int pos[3]; decode(g, p, pos);
+    int pos[3]; decode_fast(g, p, pos);
     // own row: L_jj
     float Ljj = coefv(cf, 0, b, p, g.N);
     for (int d = 0; d < g.D; ++d)
@@ -93,7 +93,7 @@ __global__ void k_diag_inv(Grid g, Coef cf, const float* __restrict__ rho, float
       for (int o = -2; o <= 2; ++o) {
         if (o == 0) continue;
         int ip = pos[d] - o;
-        if (g.per[d]) { ip %= g.n[d]; if (ip < 0) ip += g.n[d]; }
+        if (g.per[d]) ip = wrap1(ip, g.n[d]);
         else if (ip < 0 || ip >= g.n[d]) continue;
         float w1 = dweight(1, ip, g.n[d], g.per[d], o), w2 = dweight(2, ip, g.n[d], g.per[d], o);
         if (w1 == 0.f && w2 == 0.f) continue;
@@ -115,7 +115,7 @@ __global__ void k_Lpass(Grid g, Coef cf, const float* __restrict__ rho, const T*
   int b = blockIdx.y;
   size_t off = (size_t)b * g.N;
   GRID_LOOP(p, g.N) {
-    int pos[3]; decode(g, p, pos);
+    int pos[3]; decode_fast(g, p, pos);
     T Lx = x ? Lrow<T>(g, cf, b, p, pos, x + off, x2 ? x2 + off : nullptr) : (T)0;
     T r = rho ? (T)rho[off + p] : rho_point<T>(g, cf, b, p, pos);
     T s = src ? (T)src[off + p] : (T)0;
@@ -133,7 +133,7 @@ __global__ void k_LTpass(Grid g, Coef cf, const T* __restrict__ y, const float* 
   size_t off = (size_t)b * g.N;
   double acc = 0;
   GRID_LOOP(p, g.N) {
-    int pos[3]; decode(g, p, pos);
+    int pos[3]; decode_fast(g, p, pos);
     T v = LTgather<T>(g, cf, b, p, pos, y + off);
     if (base) v += (T)base[off + p];
     if (baseT) v += baseT[off + p];
@@ -200,7 +200,7 @@ __global__ void k_restrict_vec(Grid gf, Grid gc, int c0, int c1, int c2, const f
   int cz[3] = {c0, c1, c2};
   const float* f = fine + (size_t)b * gf.N;
   GRID_LOOP(p, gc.N) {
-    int pos[3]; decode(gc, p, pos);
+    int pos[3]; decode_fast(gc, p, pos);
     int cnt[3], idx[3][8]; float w[3][8];
     for (int d = 0; d < 3; ++d) {
       if (!cz[d]) { cnt[d] = 1; idx[d][0] = pos[d]; w[d][0] = 1.f; continue; }
@@ -231,7 +231,7 @@ __global__ void k_prolong_add(Grid gf, Grid gc, int c0, int c1, int c2, const fl
   const float* E = ec + (size_t)b * gc.N;
   const float* Dd = dc ? dc + (size_t)b * gc.N : nullptr;
   GRID_LOOP(p, gf.N) {
-    int pos[3]; decode(gf, p, pos);
+    int pos[3]; decode_fast(gf, p, pos);
     int cnt[3], idx[3][2]; float w[3][2];
     for (int d = 0; d < 3; ++d) {
       if (!cz[d]) { cnt[d] = 1; idx[d][0] = pos[d]; w[d][0] = 1.f; continue; }
@@ -325,7 +325,7 @@ __global__ void k_coarse_assemble(Grid g, Coef cf, const float* __restrict__ rho
   const float* rh = rho + (size_t)b * g.N;
   float* K = Kb + (size_t)b * g.N * (bw + 1);
   GRID_LOOP(j, g.N) {
-    int pj[3]; decode(g, j, pj);
+    int pj[3]; decode_fast(g, j, pj);
     float* row = K + (size_t)j * (bw + 1);
     for (int k = 0; k <= bw; ++k) row[k] = 0.f;
     if (is_boundary(g, pj)) row[0] += g.theta;
@@ -344,7 +344,7 @@ __global__ void k_coarse_assemble(Grid g, Coef cf, const float* __restrict__ rho
         } else {
           if (o == 0) continue;
           int ip = pj[d0] - o;
-          if (g.per[d0]) { ip %= g.n[d0]; if (ip < 0) ip += g.n[d0]; }
+          if (g.per[d0]) ip = wrap1(ip, g.n[d0]);
           else if (ip < 0 || ip >= g.n[d0]) continue;
           float w1 = dweight(1, ip, g.n[d0], g.per[d0], o), w2 = dweight(2, ip, g.n[d0], g.per[d0], o);
           if (w1 == 0.f && w2 == 0.f) continue;
@@ -1005,7 +1005,7 @@ __global__ void k_adj_rhs(Grid g, const float* __restrict__ gz, const double* __
     for (int d = 0; d < D; ++d)
       for (int o = -2; o <= 2; ++o) {
         int ip = pos[d] - o;
-        if (g.per[d]) { ip %= g.n[d]; if (ip < 0) ip += g.n[d]; }
+        if (g.per[d]) ip = wrap1(ip, g.n[d]);
         else if (ip < 0 || ip >= g.n[d]) continue;
         float w1 = dweight(1, ip, g.n[d], g.per[d], o), w2 = dweight(2, ip, g.n[d], g.per[d], o);
         if (w1 == 0.f && w2 == 0.f) continue;

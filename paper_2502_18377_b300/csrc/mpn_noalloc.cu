@@ -53,7 +53,7 @@ __global__ void k_na_Ly(Grid g, Coef cf, const float* __restrict__ u, float* __r
   const int b = blockIdx.y;
   const size_t off = (size_t)b * g.N;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += gridDim.x * blockDim.x) {
-    int pos[3]; decode(g, p, pos);
+    int pos[3]; decode_fast(g, p, pos);
     float Lx = Lrow<float, D>(g, cf, b, p, pos, u + off, nullptr);
     y[off + p] = -rho_point<float>(g, cf, b, p, pos) * Lx;
   }
@@ -66,7 +66,7 @@ __global__ void k_na_LTy(Grid g, Coef cf, const float* __restrict__ y, const flo
   const int b = blockIdx.y;
   const size_t off = (size_t)b * g.N;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += gridDim.x * blockDim.x) {
-    int pos[3]; decode(g, p, pos);
+    int pos[3]; decode_fast(g, p, pos);
     float v = -LTgather<float, D>(g, cf, b, p, pos, y + off);
     if (is_boundary_t<D>(g, pos)) v += g.theta * u[off + p];
     q[off + p] = v;
@@ -111,6 +111,7 @@ extern "C" int mpn_apply_reduced_noalloc(const mpn_desc* desc, const float* fiel
   g.N = (int)N;
   g.final_rows = d.final_time_rows;
   g.theta = 1.f;
+  grid_set_inverses(g);
 
   Coef cf;
   memset(&cf, 0, sizeof(cf));
