@@ -194,14 +194,21 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
     if (PER1) { if (x < 0) x += n1; else if (x >= n1) x -= n1; }
     else if (x < 0 || x >= n1) continue;
     const int p = t * pl + x * n2 + y0;
+    const float4 r4 = ld4(rho + off + p);                     // issued before the arithmetic
+    // a compile-time layout's coefficients at the point, loaded up front too
+    // (the generic layout loads them where they are used)
+    float4 cpt[7];
+#pragma unroll
+    for (int v = 0; v < 7; ++v) cpt[v] = MASK != FS_ANY ? C.at4(v, p) : f4(0.f);
+    auto cat = [&](int v) { return MASK != FS_ANY ? cpt[v] : C.at4(v, p); };
     const float* xr = xs + ((st + 1) * RXW + sx + 1) * n2;   // operand row of this y row
     const float4 xc = lds4(xr + y0);
-    float4 Lx = C.at4(0, p) * xc;
+    float4 Lx = cat(0) * xc;
     if (t > 0 && t < n0 - 1 && (PER1 || (x > 0 && x < n1 - 1))) {
       const float4 tm = lds4(xr - RXW * n2 + y0), tp = lds4(xr + RXW * n2 + y0);
       const float4 xm = lds4(xr - n2 + y0), xp = lds4(xr + n2 + y0);
-      Lx = Lx + (h1t * C.at4(1, p)) * (tp - tm) + (i2t * C.at4(2, p)) * (tp - 2.f * xc + tm) +
-           (h1x * C.at4(3, p)) * (xp - xm) + (i2x * C.at4(4, p)) * (xp - 2.f * xc + xm);
+      Lx = Lx + (h1t * cat(1)) * (tp - tm) + (i2t * cat(2)) * (tp - 2.f * xc + tm) +
+           (h1x * cat(3)) * (xp - xm) + (i2x * cat(4)) * (xp - 2.f * xc + xm);
     } else {
       float4 a1, a2;
       {
@@ -211,20 +218,20 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
         float4 xm1 = cls != 1 ? lds4(dn + y0) : xc, xp1 = cls != 2 ? lds4(up + y0) : xc;
         float4 xm2 = cls == 2 ? lds4(dn - RXW * n2 + y0) : xc, xp2 = cls == 1 ? lds4(up + RXW * n2 + y0) : xc;
         dforms(cls, xm2, xm1, xc, xp1, xp2, a1, a2);
-        Lx = Lx + (g.is1[0] * C.at4(1, p)) * a1 + (i2t * C.at4(2, p)) * a2;
+        Lx = Lx + (g.is1[0] * cat(1)) * a1 + (i2t * cat(2)) * a2;
       }
       {
         const int cls = PER1 ? 0 : (x == 0 ? 1 : (x == n1 - 1 ? 2 : 0));
         float4 xm1 = cls != 1 ? lds4(xr - n2 + y0) : xc, xp1 = cls != 2 ? lds4(xr + n2 + y0) : xc;
         float4 xm2 = cls == 2 ? lds4(xr - 2 * n2 + y0) : xc, xp2 = cls == 1 ? lds4(xr + 2 * n2 + y0) : xc;
         dforms(cls, xm2, xm1, xc, xp1, xp2, a1, a2);
-        Lx = Lx + (g.is1[1] * C.at4(3, p)) * a1 + (i2x * C.at4(4, p)) * a2;
+        Lx = Lx + (g.is1[1] * cat(3)) * a1 + (i2x * cat(4)) * a2;
       }
     }
     // y: whole row in shared memory
     if (yin2) {
       const float4 ym = make_float4(xr[yl], xc.x, xc.y, xc.z), yp = make_float4(xc.y, xc.z, xc.w, xr[yr4]);
-      Lx = Lx + (h1y * C.at4(5, p)) * (yp - ym) + (i2y * C.at4(6, p)) * (yp - 2.f * xc + ym);
+      Lx = Lx + (h1y * cat(5)) * (yp - ym) + (i2y * cat(6)) * (yp - 2.f * xc + ym);
     } else {
       float l4[4];
 #pragma unroll
@@ -240,7 +247,6 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
       }
       Lx = Lx + make_float4(l4[0], l4[1], l4[2], l4[3]);
     }
-    const float4 r4 = ld4(rho + off + p);
     *reinterpret_cast<float4*>(ys + row * n2 + y0) = make_float4(-r4.x * Lx.x, -r4.y * Lx.y, -r4.z * Lx.z, -r4.w * Lx.w);
   }
   __syncthreads();
@@ -251,25 +257,49 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
     const int ot = row / FS_TX, ox = row % FS_TX;
     const int t = t0 + ot, x = x0 + ox;
     const int p = t * pl + x * n2 + y0;
+    // operands of the update, loaded before the gather so that their latency
+    // overlaps it
+    const size_t j = off + p;
+    float4 ur = make_float4(0.f, 0.f, 0.f, 0.f), udi = ur, ud = ur;
+    if (MODE != SM_APPLY) ur = ld4(a.r + j);
+    if (MODE == SM_POST0 || MODE == SM_CHEB) udi = ld4(a.dinv + j);
+    if (MODE == SM_CHEB) ud = ld4(a.d + j);
     const float* yr = ys + ((ot + 1) * RYW + ox + 1) * n2;
     const float4 yc = lds4(yr + y0);
-    float4 qv = C.at4(0, p) * yc;
     const int pxm = (PER1 && x == 0) ? p + (n1 - 1) * n2 : p - n2;
     const int pxp = (PER1 && x == n1 - 1) ? p - (n1 - 1) * n2 : p + n2;
+    // a compile-time layout's coefficients of the central gathers, loaded up
+    // front (a neighbour index stays at the point where its branch is not
+    // taken); the generic layout loads them where they are used
+    const bool tcen = t >= 3 && t <= n0 - 4, xcen = PER1 || (x >= 3 && x <= n1 - 4);
+    float4 k0, k1m, k1p, k2, k2m, k2p, k3m, k3p, k4, k4m, k4p, k5, k6;
+    float c5l, c5r, c6l, c6r;
+    if (MASK != FS_ANY) {
+      const int ptm = tcen ? p - pl : p, ptp = tcen ? p + pl : p;
+      const int qxm = xcen ? pxm : p, qxp = xcen ? pxp : p;
+      const int prow = p - y0;
+      k0 = C.at4(0, p); k2 = C.at4(2, p); k4 = C.at4(4, p); k5 = C.at4(5, p); k6 = C.at4(6, p);
+      k1m = C.at4(1, ptm); k1p = C.at4(1, ptp); k2m = C.at4(2, ptm); k2p = C.at4(2, ptp);
+      k3m = C.at4(3, qxm); k3p = C.at4(3, qxp); k4m = C.at4(4, qxm); k4p = C.at4(4, qxp);
+      c5l = C.at(5, prow + yl); c5r = C.at(5, prow + yr4); c6l = C.at(6, prow + yl); c6r = C.at(6, prow + yr4);
+    }
+    auto pick = [&](const float4& pre, int v, int q) { return MASK != FS_ANY ? pre : C.at4(v, q); };
+    auto pickf = [&](float pre, int v, int q) { return MASK != FS_ANY ? pre : C.at(v, q); };
+    float4 qv = pick(k0, 0, p) * yc;
     if (t >= 3 && t <= n0 - 4 && (PER1 || (x >= 3 && x <= n1 - 4))) {
       const float4 tm = lds4(yr - RYW * n2 + y0), tp = lds4(yr + RYW * n2 + y0);
       const float4 xm = lds4(yr - n2 + y0), xp = lds4(yr + n2 + y0);
-      const float4 c2t = C.at4(2, p), c2x = C.at4(4, p);
-      qv = qv + h1t * (C.at4(1, p - pl) * tm - C.at4(1, p + pl) * tp) +
-           i2t * (C.at4(2, p - pl) * tm - 2.f * (c2t * yc) + C.at4(2, p + pl) * tp) +
-           h1x * (C.at4(3, pxm) * xm - C.at4(3, pxp) * xp) +
-           i2x * (C.at4(4, pxm) * xm - 2.f * (c2x * yc) + C.at4(4, pxp) * xp);
+      const float4 c2t = pick(k2, 2, p), c2x = pick(k4, 4, p);
+      qv = qv + h1t * (pick(k1m, 1, p - pl) * tm - pick(k1p, 1, p + pl) * tp) +
+           i2t * (pick(k2m, 2, p - pl) * tm - 2.f * (c2t * yc) + pick(k2p, 2, p + pl) * tp) +
+           h1x * (pick(k3m, 3, pxm) * xm - pick(k3p, 3, pxp) * xp) +
+           i2x * (pick(k4m, 4, pxm) * xm - 2.f * (c2x * yc) + pick(k4p, 4, pxp) * xp);
     } else {
       // t
       if (t >= 3 && t <= n0 - 4) {
         const float4 ym = lds4(yr - RYW * n2 + y0), yp = lds4(yr + RYW * n2 + y0);
-        qv = qv + h1t * (C.at4(1, p - pl) * ym - C.at4(1, p + pl) * yp) +
-             i2t * (C.at4(2, p - pl) * ym - 2.f * (C.at4(2, p) * yc) + C.at4(2, p + pl) * yp);
+        qv = qv + h1t * (pick(k1m, 1, p - pl) * ym - pick(k1p, 1, p + pl) * yp) +
+             i2t * (pick(k2m, 2, p - pl) * ym - 2.f * (pick(k2, 2, p) * yc) + pick(k2p, 2, p + pl) * yp);
       } else {
 #pragma unroll
         for (int o = -2; o <= 2; ++o) {
@@ -285,8 +315,8 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
       // x
       if (PER1 || (x >= 3 && x <= n1 - 4)) {
         const float4 ym = lds4(yr - n2 + y0), yp = lds4(yr + n2 + y0);
-        qv = qv + h1x * (C.at4(3, pxm) * ym - C.at4(3, pxp) * yp) +
-             i2x * (C.at4(4, pxm) * ym - 2.f * (C.at4(4, p) * yc) + C.at4(4, pxp) * yp);
+        qv = qv + h1x * (pick(k3m, 3, pxm) * ym - pick(k3p, 3, pxp) * yp) +
+             i2x * (pick(k4m, 4, pxm) * ym - 2.f * (pick(k4, 4, p) * yc) + pick(k4p, 4, pxp) * yp);
       } else {
 #pragma unroll
         for (int o = -2; o <= 2; ++o) {
@@ -303,8 +333,8 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
     // y
     if (yin3) {
       const int prow = p - y0;
-      const float4 c1 = C.at4(5, p), c2 = C.at4(6, p);
-      const float c1l = C.at(5, prow + yl), c1r = C.at(5, prow + yr4), c2l = C.at(6, prow + yl), c2r = C.at(6, prow + yr4);
+      const float4 c1 = pick(k5, 5, p), c2 = pick(k6, 6, p);
+      const float c1l = pickf(c5l, 5, prow + yl), c1r = pickf(c5r, 5, prow + yr4), c2l = pickf(c6l, 6, prow + yl), c2r = pickf(c6r, 6, prow + yr4);
       const float4 ym = make_float4(yr[yl], yc.x, yc.y, yc.z), yp = make_float4(yc.y, yc.z, yc.w, yr[yr4]);
       const float4 c1m = make_float4(c1l, c1.x, c1.y, c1.z), c1p = make_float4(c1.y, c1.z, c1.w, c1r);
       const float4 c2m = make_float4(c2l, c2.x, c2.y, c2.z), c2p = make_float4(c2.y, c2.z, c2.w, c2r);
@@ -336,16 +366,15 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
       if (y0 + 3 == n2 - 1) qv.w -= g.theta * xj.w;
     }
     // qv = -(S x) on the group
-    const size_t j = off + p;
     if (MODE == SM_APPLY) {
       *reinterpret_cast<float4*>(a.out + j) = make_float4(-qv.x, -qv.y, -qv.z, -qv.w);
       acc -= qv.x * xj.x + qv.y * xj.y + qv.z * xj.z + qv.w * xj.w;
     } else if (MODE == SM_RES) {
-      *reinterpret_cast<float4*>(a.out + j) = ld4(a.r + j) + qv;
+      *reinterpret_cast<float4*>(a.out + j) = ur + qv;
     } else {
-      const float4 res = ld4(a.r + j) + qv;
-      float4 dn = a.c2 * (ld4(a.dinv + j) * res);
-      if (MODE == SM_CHEB) dn = dn + a.c1 * ld4(a.d + j);
+      const float4 res = ur + qv;
+      float4 dn = a.c2 * (udi * res);
+      if (MODE == SM_CHEB) dn = dn + a.c1 * ud;
       *reinterpret_cast<float4*>(a.d + j) = dn;
       *reinterpret_cast<float4*>(a.e + j) = xj + dn;
     }
