@@ -105,6 +105,11 @@ struct mpn_problem {
   std::vector<SweepGraph> graphs;
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_user = nullptr;
+  // the setup after the input copies, as one CUDA graph (its buffers are the
+  // problem's own, so one capture serves every call)
+  cudaGraphExec_t setup_exec = nullptr;
+  long long setup_kernels = 0;
+  cudaEvent_t ev_setup = nullptr;
   // setup: one stream per level for the independent power iterations
   cudaStream_t aux[MAXL] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[MAXL] = {};
@@ -224,6 +229,8 @@ extern "C" const char* mpn_last_cuda_error(void) { return g_cuda_err; }
 extern "C" void mpn_destroy(mpn_problem* p) {
   if (!p) return;
   for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+  if (p->setup_exec) cudaGraphExecDestroy(p->setup_exec);
+  if (p->ev_setup) cudaEventDestroy(p->ev_setup);
   if (p->gstream) cudaStreamDestroy(p->gstream);
   if (p->ev_user) cudaEventDestroy(p->ev_user);
   for (int k = 0; k < MAXL; ++k) {
@@ -618,13 +625,57 @@ static int apply_S(mpn_problem* p, int k, const float* x, float* q, double* part
   return MPN_OK;
 }
 
-static int setup(mpn_problem* p, const float* fields, const float* scalars, cudaStream_t st) {
+// Streams and events of the setup and of the sweep graphs (created once).
+static int ensure_streams(mpn_problem* p) {
+  if (!p->gstream) {
+    CK(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&p->ev_user, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&p->ev_setup, cudaEventDisableTiming));
+  }
+  if (!p->ev_fork) {
+    CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    for (int k = 0; k < MAXL; ++k) {
+      CK(cudaStreamCreateWithFlags(&p->aux[k], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&p->ev_join[k], cudaEventDisableTiming));
+    }
+  }
+  return MPN_OK;
+}
+
+// Shared-memory sizes of the coarsest factorisation and inverse, and the
+// inverse's warps per CTA.
+static size_t coarse_factor_smem(const mpn_problem* p) { return sizeof(float) * ((size_t)p->M * (p->bw + 1) + p->bw); }
+static int coarse_inverse_warps(const mpn_problem* p) {
+  const size_t fixed = (p->band_smem ? (size_t)p->M * (p->bw + 1) : 0) + p->M;
+  return (int)std::min<size_t>(32, (INV_SMEM_FLOATS - fixed) / p->M);
+}
+static size_t coarse_inverse_smem(const mpn_problem* p) {
+  const size_t fixed = (p->band_smem ? (size_t)p->M * (p->bw + 1) : 0) + p->M;
+  return sizeof(float) * (fixed + (size_t)coarse_inverse_warps(p) * p->M);
+}
+// Opts the coarsest-level kernels of this problem into their shared memory
+// (host calls, kept out of the captured setup).
+static int coarse_attrs(mpn_problem* p) {
+  if (p->band_smem)
+    CK(cudaFuncSetAttribute(k_coarse_factor<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_factor_smem(p)));
+  const int sm = (int)coarse_inverse_smem(p);
+#define INV_ATTR(NW) \
+  CK(cudaFuncSetAttribute(p->band_smem ? (const void*)k_coarse_inverse<NW, true> : (const void*)k_coarse_inverse<NW, false>, \
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, sm))
+  if (p->bw < 32) INV_ATTR(1);
+  else if (p->bw < 64) INV_ATTR(2);
+  else if (p->bw < 128) INV_ATTR(4);
+  else INV_ATTR(8);
+#undef INV_ATTR
+  return MPN_OK;
+}
+
+// The setup after the input copies: coefficients and weights of every level,
+// Jacobi diagonals, lambda_max estimates, the coarsest factorisation and
+// inverse.  Reads only the problem's own buffers.
+static int setup_body(mpn_problem* p, cudaStream_t st) {
   int B = p->B, F = p->F, V = p->V;
-  p->setup_ok = false;
-  p->zd_valid = false;
   Level& l0 = p->lv[0];
-  if (F > 0) CK(cudaMemcpyAsync(l0.fields, fields, sizeof(float) * (size_t)F * B * l0.g.N, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(p->scalars, scalars, sizeof(float) * (size_t)V * B, cudaMemcpyDeviceToDevice, st));
   ++p->nlaunch, k_rep4<<<(V * B + MPN_TPB - 1) / MPN_TPB, MPN_TPB, 0, st>>>(V * B, p->scalars, p->scal4);
   {
     Coef cf = make_coef(p, l0.fields);
@@ -646,23 +697,52 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
   // Jacobi diagonals and lambda_max(Dinv S) per level: the levels are
   // independent, so each runs its power iteration on a stream of its own
   // while the coarsest system is factorised on st.
-  if (!p->ev_fork) {
-    CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
-    for (int k = 0; k < MAXL; ++k) {
-      CK(cudaStreamCreateWithFlags(&p->aux[k], cudaStreamNonBlocking));
-      CK(cudaEventCreateWithFlags(&p->ev_join[k], cudaEventDisableTiming));
-    }
-  }
   CK(cudaEventRecord(p->ev_fork, st));
-  for (int k = 0; k < p->L; ++k) {
+  // the coarsest level first: its factorisation and inverse are the longest
+  // dependent chain of the setup, so st starts on it while the host is still
+  // launching the power iterations
+  {
+    Level& l = p->lv[p->L - 1];
+    Coef cf = make_coef(p, l.fields);
+    ++p->nlaunch, k_diag_inv<<<dim3(nblk(l.g.N), B), MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.dinv);
+    CKL();
+  }
+  // coarsest: banded assembly, Cholesky, explicit inverse
+  Level& lc = p->lv[p->L - 1];
+  Coef cfc = make_coef(p, lc.fields);
+  CK(cudaMemsetAsync(p->ferr, 0, sizeof(int) * B, st));
+  ++p->nlaunch, k_coarse_assemble<<<dim3(nblk(p->M), B), MPN_TPB, 0, st>>>(lc.g, cfc, lc.rho, p->bw, p->Kband);
+  if (p->band_smem) {
+    ++p->nlaunch, k_coarse_factor<true><<<B, 512, coarse_factor_smem(p), st>>>(p->M, p->bw, p->Kband, p->ferr);
+  } else {
+    ++p->nlaunch, k_coarse_factor<false><<<B, 512, sizeof(float) * p->bw, st>>>(p->M, p->bw, p->Kband, p->ferr);
+  }
+  // one warp per column of the inverse; the CTA stages the band, the
+  // reciprocal diagonal and one forward-solution vector per warp
+  {
+    const int nwarps = coarse_inverse_warps(p);
+    dim3 gi((p->M + nwarps - 1) / nwarps, B);
+    const size_t sm = coarse_inverse_smem(p);
+#define INV_LAUNCH2(NW, SM) \
+  ++p->nlaunch, k_coarse_inverse<NW, SM><<<gi, 32 * nwarps, sm, st>>>(p->M, p->bw, p->Kband, p->Kinv)
+#define INV_LAUNCH(NW) do { if (p->band_smem) INV_LAUNCH2(NW, true); else INV_LAUNCH2(NW, false); } while (0)
+    if (p->bw < 32) INV_LAUNCH(1);
+    else if (p->bw < 64) INV_LAUNCH(2);
+    else if (p->bw < 128) INV_LAUNCH(4);
+    else INV_LAUNCH(8);
+#undef INV_LAUNCH2
+#undef INV_LAUNCH
+  }
+
+  CKL();
+  for (int k = 0; k + 1 < p->L; ++k) {
     Level& l = p->lv[k];
     Coef cf = make_coef(p, l.fields);
     dim3 gr(nblk(l.g.N), B);
-    cudaStream_t sk = k == p->L - 1 ? st : p->aux[k];
-    if (sk != st) CK(cudaStreamWaitEvent(sk, p->ev_fork, 0));
+    cudaStream_t sk = p->aux[k];
+    CK(cudaStreamWaitEvent(sk, p->ev_fork, 0));
     ++p->nlaunch, k_diag_inv<<<gr, MPN_TPB, 0, sk>>>(l.g, cf, l.rho, l.dinv);
     CKL();
-    if (k == p->L - 1) break;
     // power method for lambda_max(Dinv S)
     ++p->nlaunch, k_fill_hash<<<gr, MPN_TPB, 0, sk>>>(l.g.N, l.t);
     double* pw = slot(p, S_PW0 + k);
@@ -675,41 +755,43 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
     CKL();
     CK(cudaEventRecord(p->ev_join[k], sk));
   }
-  // coarsest: banded assembly, Cholesky, explicit inverse
-  Level& lc = p->lv[p->L - 1];
-  Coef cfc = make_coef(p, lc.fields);
-  CK(cudaMemsetAsync(p->ferr, 0, sizeof(int) * B, st));
-  ++p->nlaunch, k_coarse_assemble<<<dim3(nblk(p->M), B), MPN_TPB, 0, st>>>(lc.g, cfc, lc.rho, p->bw, p->Kband);
-  if (p->band_smem) {
-    size_t smem = sizeof(float) * ((size_t)p->M * (p->bw + 1) + p->bw);
-    CK(cudaFuncSetAttribute(k_coarse_factor<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ++p->nlaunch, k_coarse_factor<true><<<B, 512, smem, st>>>(p->M, p->bw, p->Kband, p->ferr);
-  } else {
-    ++p->nlaunch, k_coarse_factor<false><<<B, 512, sizeof(float) * p->bw, st>>>(p->M, p->bw, p->Kband, p->ferr);
-  }
-  // one warp per column of the inverse; the CTA stages the band, the
-  // reciprocal diagonal and one forward-solution vector per warp
-  {
-    const size_t fixed = (p->band_smem ? (size_t)p->M * (p->bw + 1) : 0) + p->M;
-    int nwarps = (int)std::min<size_t>(32, (INV_SMEM_FLOATS - fixed) / p->M);
-    dim3 gi((p->M + nwarps - 1) / nwarps, B);
-    size_t sm = sizeof(float) * (fixed + (size_t)nwarps * p->M);
-#define INV_LAUNCH2(NW, SM)                                                                                  \
-  do {                                                                                                       \
-    CK(cudaFuncSetAttribute(k_coarse_inverse<NW, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
-    ++p->nlaunch, k_coarse_inverse<NW, SM><<<gi, 32 * nwarps, sm, st>>>(p->M, p->bw, p->Kband, p->Kinv);      \
-  } while (0)
-#define INV_LAUNCH(NW) do { if (p->band_smem) INV_LAUNCH2(NW, true); else INV_LAUNCH2(NW, false); } while (0)
-    if (p->bw < 32) INV_LAUNCH(1);
-    else if (p->bw < 64) INV_LAUNCH(2);
-    else if (p->bw < 128) INV_LAUNCH(4);
-    else INV_LAUNCH(8);
-#undef INV_LAUNCH2
-#undef INV_LAUNCH
-  }
-
   CKL();
   for (int k = 0; k + 1 < p->L; ++k) CK(cudaStreamWaitEvent(st, p->ev_join[k], 0));
+  return MPN_OK;
+}
+
+// Setup for new coefficients: copies them in on st, then replays the
+// captured setup graph on the internal stream, ordered after st and before
+// st's next work.
+static int setup(mpn_problem* p, const float* fields, const float* scalars, cudaStream_t st) {
+  int B = p->B, F = p->F, V = p->V;
+  p->setup_ok = false;
+  p->zd_valid = false;
+  Level& l0 = p->lv[0];
+  if (F > 0) CK(cudaMemcpyAsync(l0.fields, fields, sizeof(float) * (size_t)F * B * l0.g.N, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(p->scalars, scalars, sizeof(float) * (size_t)V * B, cudaMemcpyDeviceToDevice, st));
+  TRY(ensure_streams(p));
+  if (!p->setup_exec) {
+    TRY(coarse_attrs(p));
+    long long nl0 = p->nlaunch;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
+    int s = setup_body(p, p->gstream);
+    cudaError_t ec = cudaStreamEndCapture(p->gstream, &graph);
+    if (s != MPN_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+    CK(ec);
+    cudaError_t ei = cudaGraphInstantiate(&p->setup_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ei);
+    p->setup_kernels = p->nlaunch - nl0;
+    p->nlaunch = nl0;
+  }
+  CK(cudaEventRecord(p->ev_user, st));
+  CK(cudaStreamWaitEvent(p->gstream, p->ev_user, 0));
+  CK(cudaGraphLaunch(p->setup_exec, p->gstream));
+  p->nlaunch += p->setup_kernels;
+  CK(cudaEventRecord(p->ev_setup, p->gstream));
+  CK(cudaStreamWaitEvent(st, p->ev_setup, 0));
   p->setup_ok = true;
   return MPN_OK;
 }
@@ -921,10 +1003,7 @@ static int sweep_body(mpn_problem* p, const double* g_adj, int iters, int P, boo
 // profiling state).  Ordered after the caller's stream; returns once the
 // sweep's scalars are on the host.
 static int run_sweep(mpn_problem* p, const double* g_adj, int iters, int P, bool from_zero, cudaStream_t st) {
-  if (!p->gstream) {
-    CK(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&p->ev_user, cudaEventDisableTiming));
-  }
+  TRY(ensure_streams(p));
   int adj = g_adj ? 1 : 0;
   mpn_problem::SweepGraph* g = nullptr;
   for (auto& x : p->graphs)
