@@ -267,6 +267,30 @@ def test_forward_is_deterministic():
     assert np.array_equal(z1, z2)
 
 
+def test_one_problem_solves_new_coefficients_each_call():
+    """The setup after the input copies is captured once and replayed: a
+    problem object given other coefficients, right-hand sides and boundary
+    data (another seed; then the first data again) must solve each set, in
+    both directions, to the oracle's tolerance."""
+    wa = _round(wl.reaction_diffusion_2d(batch=2, n=(8, 16, 16), seed_base=2000))
+    wb = _round(wl.reaction_diffusion_2d(batch=2, n=(8, 16, 16), seed_base=7000))
+    assert not np.allclose(wa.fields, wb.fields)
+    s = _solver(wa)
+    V, N = asm.n_vars(wa.ndim), wa.npoints
+    rng = np.random.default_rng(9)
+    g = rng.normal(size=(wa.batch, V, N)).astype(np.float32)
+    for w in (wa, wb, wa):
+        args = (_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega))
+        z = s.forward(*args)
+        _, _, _, _, dz = s.adjoint(*args, z, _dev(g), reuse_setup=True, want_dz=True)
+        z, dz = z.cpu().numpy(), dz.cpu().numpy()
+        for b in range(w.batch):
+            A, d, kind, owner, zr, lam, el = _oracle_instance(w, b)
+            assert _rel(z[b].ravel(), zr) <= FWD_TOL, (b, _rel(z[b].ravel(), zr))
+            dzr, _ = og.adjoint_elim(el, g[b].astype(np.float64).ravel())
+            assert _rel(dz[b].ravel(), dzr) <= FWD_TOL, (b, _rel(dz[b].ravel(), dzr))
+
+
 def test_gradients_match_finite_differences_burgers():
     """Linearized Burgers, L = mean((u - target)^2): dL/dc, dL/df and dL/du0
     from the adjoint kernels against central differences of the FP64 oracle
