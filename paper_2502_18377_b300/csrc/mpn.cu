@@ -61,7 +61,6 @@ struct mpn_problem {
   Level lv[MAXL];
   int M, bw;           // coarsest system size and band width
   float *Kband = nullptr, *Kinv = nullptr;
-  float* Zl = nullptr;     // L^-1 of the coarsest factor (row-parallel inverse only)
   int* ferr = nullptr;
   int* kerr = nullptr;     // device word a kernel sets when a bounded wait gives up (sticky)
   float *scalars = nullptr, *rhs = nullptr, *omega = nullptr;
@@ -266,14 +265,6 @@ extern "C" int mpn_levels(const mpn_problem* p, int* nl, int* shapes) {
 // the same with c_xx and c_yy one field
 #define FS_MASK_RDI (FS_MASK_RD | FS_SHARE46)
 static size_t fs_smem(int tt, int ny) { return sizeof(float) * (size_t)(fs_rows_x(tt) + fs_rows_y(tt)) * ny; }
-// The coarsest inverse as L^-1 by columns in parallel, then (L^-1)^T L^-1,
-// when the band and the substitution windows fit in shared memory; else one
-// warp per column of K^-1 (k_coarse_inverse).
-static size_t coarse_linv_smem(const mpn_problem* p) {
-  const size_t W = (size_t)p->bw + 1;
-  return sizeof(float) * ((size_t)p->M * W + p->M + 2 * W * LINV_TPB);
-}
-static bool coarse_rowinv(const mpn_problem* p) { return coarse_linv_smem(p) <= 200 * 1024; }
 // Opt the fused step kernels into the shared memory of the largest tile.
 static int fs_set_smem() {
   int bytes = (int)fs_smem(8, FS_MAX_NY);
@@ -490,7 +481,6 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   size_t N0 = (size_t)p->lv[0].g.N * B;
   AL(p->Kband, (size_t)B * p->M * (p->bw + 1));
   AL(p->Kinv, (size_t)B * p->M * p->M);
-  if (coarse_rowinv(p)) AL(p->Zl, (size_t)B * p->M * p->M);
   AL(p->ferr, B);
   AL(p->kerr, 1);
   AL(p->scalars, (size_t)V * B);
@@ -668,10 +658,6 @@ static size_t coarse_inverse_smem(const mpn_problem* p) {
 static int coarse_attrs(mpn_problem* p) {
   if (p->band_smem)
     CK(cudaFuncSetAttribute(k_coarse_factor<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_factor_smem(p)));
-  if (coarse_rowinv(p)) {
-    CK(cudaFuncSetAttribute(k_coarse_linv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_linv_smem(p)));
-    return MPN_OK;
-  }
   const int sm = (int)coarse_inverse_smem(p);
 #define INV_ATTR(NW) \
   CK(cudaFuncSetAttribute(p->band_smem ? (const void*)k_coarse_inverse<NW, true> : (const void*)k_coarse_inverse<NW, false>, \
@@ -731,14 +717,9 @@ static int setup_body(mpn_problem* p, cudaStream_t st) {
   } else {
     ++p->nlaunch, k_coarse_factor<false><<<B, 512, sizeof(float) * p->bw, st>>>(p->M, p->bw, p->Kband, p->ferr);
   }
-  if (coarse_rowinv(p)) {
-    ++p->nlaunch, k_coarse_linv<<<dim3((p->M + LINV_TPB - 1) / LINV_TPB, B), LINV_TPB, coarse_linv_smem(p), st>>>(
-        p->M, p->bw, p->Kband, p->Zl);
-    const int nt = (p->M + SYRK_T - 1) / SYRK_T;
-    ++p->nlaunch, k_coarse_syrk<<<dim3(nt * (nt + 1) / 2, B), 256, 0, st>>>(p->M, p->Zl, p->Kinv);
-  } else {
-    // one warp per column of the inverse; the CTA stages the band, the
-    // reciprocal diagonal and one forward-solution vector per warp
+  // one warp per column of the inverse; the CTA stages the band, the
+  // reciprocal diagonal and one forward-solution vector per warp
+  {
     const int nwarps = coarse_inverse_warps(p);
     dim3 gi((p->M + nwarps - 1) / nwarps, B);
     const size_t sm = coarse_inverse_smem(p);

@@ -419,105 +419,6 @@ __global__ void k_coarse_factor(int M, int bw, float* __restrict__ Kb, int* __re
   }
 }
 
-// Explicit inverse K^-1 = L^-T L^-1 = Z^T Z in two kernels, for bands that
-// fit in shared memory next to the substitution windows.
-//
-// k_coarse_linv: Z = L^-1 (lower triangular), one thread per column c:
-// z_ic = (delta_ic - sum_{o=1..bw} L_{i,i-o} z_{i-o,c}) / L_ii.  The columns
-// are independent, so the CTA's threads step through the rows together
-// (every L row read is a broadcast) and never wait on each other.  A column's
-// last W = bw + 1 values sit in a shared-memory window, each value stored
-// twice (slots s and s + W) so that the W - 1 values a row reads are
-// contiguous; values of rows above the column (and above row 0) are zero.
-#define LINV_TPB 128
-__global__ void __launch_bounds__(LINV_TPB) k_coarse_linv(int M, int bw, const float* __restrict__ Lb,
-                                                          float* __restrict__ Z) {
-  extern __shared__ float sl[];
-  const int b = blockIdx.y;
-  const int W = bw + 1;
-  float* L = sl;                                   // M x W band of the factor
-  float* rd = sl + (size_t)M * W;                  // 1 / L_ii
-  float* win = rd + M;                             // 2W x LINV_TPB windows
-  const float* src = Lb + (size_t)b * M * W;
-  for (int t = threadIdx.x; t < M * W; t += blockDim.x) L[t] = src[t];
-  for (int t = threadIdx.x; t < 2 * W * LINV_TPB; t += blockDim.x) win[t] = 0.f;
-  __syncthreads();
-  for (int t = threadIdx.x; t < M; t += blockDim.x) rd[t] = 1.f / L[(size_t)t * W];
-  __syncthreads();
-  const int c0 = blockIdx.x * LINV_TPB, c = c0 + threadIdx.x;
-  float* zb = Z + (size_t)b * M * M;
-  if (c < M)
-    for (int i = 0; i < c0; ++i) zb[(size_t)i * M + c] = 0.f;
-  float* w = win + threadIdx.x;
-  int slot = c0 % W;                               // window slot of row i
-  for (int i = c0; i < M; ++i) {
-    const float* Li = L + (size_t)i * W;
-    const float* wr = w + (size_t)(slot + W) * LINV_TPB;   // wr[-o * LINV_TPB] holds z_{i-o}
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    int o = 1;
-    for (; o + 3 <= bw; o += 4) {
-      s0 += Li[o] * wr[-o * LINV_TPB];
-      s1 += Li[o + 1] * wr[-(o + 1) * LINV_TPB];
-      s2 += Li[o + 2] * wr[-(o + 2) * LINV_TPB];
-      s3 += Li[o + 3] * wr[-(o + 3) * LINV_TPB];
-    }
-    for (; o <= bw; ++o) s0 += Li[o] * wr[-o * LINV_TPB];
-    const float z = ((i == c ? 1.f : 0.f) - ((s0 + s1) + (s2 + s3))) * rd[i];
-    w[(size_t)slot * LINV_TPB] = z;
-    w[(size_t)(slot + W) * LINV_TPB] = z;
-    if (c < M) zb[(size_t)i * M + c] = z;
-    slot = slot + 1 == W ? 0 : slot + 1;
-  }
-}
-
-// k_coarse_syrk: K^-1 = Z^T Z, (K^-1)_ab = sum_{i >= max(a, b)} z_ia z_ib.
-// One CTA per 64 x 64 tile of the upper triangle (ta <= tb, linear index
-// over the triangle) and instance, writing the tile and its mirror; Z rows
-// staged 32 at a time, each thread accumulating a 4 x 4 block.
-#define SYRK_T 64
-__global__ void __launch_bounds__(256) k_coarse_syrk(int M, const float* __restrict__ Z, float* __restrict__ Kinv) {
-  __shared__ float za[32][SYRK_T], zbs[32][SYRK_T];
-  const int b = blockIdx.y;
-  int k = blockIdx.x, ta = 0;
-  const int nt = (M + SYRK_T - 1) / SYRK_T;
-  while (k >= nt - ta) { k -= nt - ta; ++ta; }
-  const int tb = ta + k;
-  const int a0 = ta * SYRK_T, b0 = tb * SYRK_T;
-  const float* zb = Z + (size_t)b * M * M;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[4][4] = {};
-  for (int i0 = b0; i0 < M; i0 += 32) {
-    for (int t = threadIdx.x; t < 32 * SYRK_T; t += blockDim.x) {
-      const int r = t / SYRK_T, q = t % SYRK_T, i = i0 + r;
-      za[r][q] = (i < M && a0 + q < M) ? zb[(size_t)i * M + a0 + q] : 0.f;
-      zbs[r][q] = (i < M && b0 + q < M) ? zb[(size_t)i * M + b0 + q] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int r = 0; r < 32; ++r) {
-      float av[4], bv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) { av[u] = za[r][tx * 4 + u]; bv[u] = zbs[r][ty * 4 + u]; }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
-    }
-    __syncthreads();
-  }
-  float* X = Kinv + (size_t)b * M * M;
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int a = a0 + tx * 4 + u, bb = b0 + ty * 4 + v;
-      if (a < M && bb < M) {
-        X[(size_t)a * M + bb] = acc[u][v];
-        X[(size_t)bb * M + a] = acc[u][v];
-      }
-    }
-}
-
 // Explicit inverse from the banded factor (bw < 32 NW): one warp per column c
 // solves L L^T x = e_c for the rows i >= c and writes them to column and row c
 // of the symmetric Kinv.  The CTA stages the band and the reciprocal diagonal
