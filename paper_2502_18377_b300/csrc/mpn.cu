@@ -721,7 +721,7 @@ static int setup_body(mpn_problem* p, cudaStream_t st) {
   // reciprocal diagonal and one forward-solution vector per warp
   {
     const int nwarps = coarse_inverse_warps(p);
-    dim3 gi((p->M + nwarps - 1) / nwarps, B);
+    dim3 gi(((p->M + nwarps - 1) / nwarps) * B);
     const size_t sm = coarse_inverse_smem(p);
 #define INV_LAUNCH2(NW, SM) \
   ++p->nlaunch, k_coarse_inverse<NW, SM><<<gi, 32 * nwarps, sm, st>>>(p->M, p->bw, p->Kband, p->Kinv)

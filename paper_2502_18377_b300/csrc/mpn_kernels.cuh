@@ -426,10 +426,15 @@ __global__ void k_coarse_factor(int M, int bw, float* __restrict__ Kb, int* __re
 // band row (or column) is split across the lanes and the dot product reduced
 // by shuffles; the last 32 NW values of the substitution live in NW registers
 // per lane and shift by one lane per step.
+// Grid: (column blocks x instances) in one dimension, column block major, so
+// the CTAs with the longest columns (small c: 2 (M - c) substitution steps)
+// start first and the short ones fill in behind them.
 template <int NW, bool SMEM>
 __global__ void k_coarse_inverse(int M, int bw, const float* __restrict__ Lb, float* __restrict__ Kinv) {
   extern __shared__ float sL[];
-  const int b = blockIdx.y;
+  const int ncb = (M + (int)(blockDim.x >> 5) - 1) / (int)(blockDim.x >> 5);
+  const int B = gridDim.x / ncb;
+  const int b = blockIdx.x % B, cb = blockIdx.x / B;
   const int W = bw + 1;
   const float* src = Lb + (size_t)b * M * W;
   float* rd = SMEM ? sL + (size_t)M * W : sL;
@@ -442,10 +447,8 @@ __global__ void k_coarse_inverse(int M, int bw, const float* __restrict__ Lb, fl
   const float* L = SMEM ? sL : src;        // band rows: shared memory, or global (L2)
   for (int t = threadIdx.x; t < M; t += blockDim.x) rd[t] = 1.f / L[(size_t)t * W];
   __syncthreads();
-  // column of this warp: long (small c) and short (large c) columns alternate
-  const int idx = blockIdx.x * (blockDim.x >> 5) + wid;
-  if (idx >= M) return;
-  const int c = (idx & 1) ? M - 1 - (idx >> 1) : (idx >> 1);
+  const int c = cb * (blockDim.x >> 5) + wid;   // column of this warp
+  if (c >= M) return;
   float* X = Kinv + (size_t)b * M * M;
   float w[NW];
   // forward: y_i = (delta_ic - sum_{j<i} L_ij y_j) / L_ii; w[k] on lane l holds
