@@ -656,8 +656,10 @@ static size_t coarse_inverse_smem(const mpn_problem* p) {
 // Opts the coarsest-level kernels of this problem into their shared memory
 // (host calls, kept out of the captured setup).
 static int coarse_attrs(mpn_problem* p) {
-  if (p->band_smem)
+  if (p->band_smem) {
     CK(cudaFuncSetAttribute(k_coarse_factor<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_factor_smem(p)));
+    CK(cudaFuncSetAttribute(k_coarse_factor1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_factor_smem(p)));
+  }
   const int sm = (int)coarse_inverse_smem(p);
 #define INV_ATTR(NW) \
   CK(cudaFuncSetAttribute(p->band_smem ? (const void*)k_coarse_inverse<NW, true> : (const void*)k_coarse_inverse<NW, false>, \
@@ -712,10 +714,14 @@ static int setup_body(mpn_problem* p, cudaStream_t st) {
   Coef cfc = make_coef(p, lc.fields);
   CK(cudaMemsetAsync(p->ferr, 0, sizeof(int) * B, st));
   ++p->nlaunch, k_coarse_assemble<<<dim3(nblk(p->M), B), MPN_TPB, 0, st>>>(lc.g, cfc, lc.rho, p->bw, p->Kband);
+  // bands up to FACT1_MAXBW: one barrier per column step (k_coarse_factor1)
+  const bool f1 = p->bw <= FACT1_MAXBW;
   if (p->band_smem) {
-    ++p->nlaunch, k_coarse_factor<true><<<B, 512, coarse_factor_smem(p), st>>>(p->M, p->bw, p->Kband, p->ferr);
+    if (f1) ++p->nlaunch, k_coarse_factor1<true><<<B, 512, coarse_factor_smem(p), st>>>(p->M, p->bw, p->Kband, p->ferr);
+    else ++p->nlaunch, k_coarse_factor<true><<<B, 512, coarse_factor_smem(p), st>>>(p->M, p->bw, p->Kband, p->ferr);
   } else {
-    ++p->nlaunch, k_coarse_factor<false><<<B, 512, sizeof(float) * p->bw, st>>>(p->M, p->bw, p->Kband, p->ferr);
+    if (f1) ++p->nlaunch, k_coarse_factor1<false><<<B, 512, 0, st>>>(p->M, p->bw, p->Kband, p->ferr);
+    else ++p->nlaunch, k_coarse_factor<false><<<B, 512, sizeof(float) * p->bw, st>>>(p->M, p->bw, p->Kband, p->ferr);
   }
   // one warp per column of the inverse; the CTA stages the band, the
   // reciprocal diagonal and one forward-solution vector per warp

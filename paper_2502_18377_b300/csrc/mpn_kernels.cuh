@@ -419,6 +419,75 @@ __global__ void k_coarse_factor(int M, int bw, float* __restrict__ Kb, int* __re
   }
 }
 
+// The same factorisation for bands of at most FACT1_MAXBW, one barrier per
+// column step.  Step k: every thread reads the pivot and the column-k entries
+// it needs (unscaled) and scales them itself; the triangular update of the
+// trailing block, bw (bw + 1) / 2 elements, is spread evenly over the block
+// (at most FACT1_EPT elements per thread, decoded once); the new pivot and
+// the scaled column entry a thread owns are written back at step k + 1, after
+// the barrier, when nobody reads them any more.
+#define FACT1_EPT 4
+#define FACT1_MAXBW 63
+template <bool SMEM>
+__global__ void __launch_bounds__(512) k_coarse_factor1(int M, int bw, float* __restrict__ Kb, int* __restrict__ err) {
+  extern __shared__ float shm[];
+  const int b = blockIdx.x;
+  float* K = Kb + (size_t)b * M * (bw + 1);
+  const int W = bw + 1;
+  float* sb = SMEM ? shm : K;
+  if (SMEM)
+    for (int t = threadIdx.x; t < M * W; t += blockDim.x) sb[t] = K[t];
+  // this thread's elements (i2, jj), jj <= i2 < bw, of the triangular update
+  int ei[FACT1_EPT], ej[FACT1_EPT];
+  const int ntri = bw * (bw + 1) / 2;
+#pragma unroll
+  for (int q = 0; q < FACT1_EPT; ++q) {
+    const int e = threadIdx.x + q * blockDim.x;
+    ei[q] = -1; ej[q] = 0;
+    if (e < ntri) {
+      int i2 = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+      while ((i2 + 1) * (i2 + 2) / 2 <= e) ++i2;
+      while (i2 * (i2 + 1) / 2 > e) --i2;
+      ei[q] = i2; ej[q] = e - i2 * (i2 + 1) / 2;
+    }
+  }
+  __syncthreads();
+  float own = 0.f, piv_prev = 0.f;
+  int own_at = -1;                       // sb index of the owned column entry (previous step)
+  bool bad = false;
+  for (int k = 0; k < M; ++k) {
+    // write-backs of step k - 1 (its readers have passed the barrier)
+    if (k > 0 && threadIdx.x == 0) sb[(size_t)(k - 1) * W] = piv_prev;
+    if (own_at >= 0) sb[own_at] = own;
+    float a = sb[(size_t)k * W];
+    if (!(a > 0.f)) { a = 1.f; bad = true; }
+    const float ipiv = rsqrtf(a);
+    piv_prev = a * ipiv;
+    const int nr = min(bw, M - k - 1);
+    const float* colk = sb + (size_t)(k + 1) * W + 1;   // colk[ii * (W + 1)] = K(k+1+ii, k), unscaled
+    own_at = -1;
+    if ((int)threadIdx.x < nr) {
+      own_at = (k + 1 + threadIdx.x) * W + threadIdx.x + 1;
+      own = sb[own_at] * ipiv;
+    }
+#pragma unroll
+    for (int q = 0; q < FACT1_EPT; ++q) {
+      const int i2 = ei[q], jj = ej[q];
+      if (i2 >= 0 && i2 < nr) {
+        const float li = colk[(size_t)i2 * (W + 1)] * ipiv, lj = colk[(size_t)jj * (W + 1)] * ipiv;
+        sb[(size_t)(k + 1 + i2) * W + (i2 - jj)] -= li * lj;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sb[(size_t)(M - 1) * W] = piv_prev;
+  if (own_at >= 0) sb[own_at] = own;
+  if (bad && threadIdx.x == 0) err[b] = 1;
+  __syncthreads();
+  if (SMEM)
+    for (int t = threadIdx.x; t < M * W; t += blockDim.x) K[t] = sb[t];
+}
+
 // Explicit inverse from the banded factor (bw < 32 NW): one warp per column c
 // solves L L^T x = e_c for the rows i >= c and writes them to column and row c
 // of the symmetric Kinv.  The CTA stages the band and the reciprocal diagonal
