@@ -115,7 +115,7 @@ struct mpn_problem {
   cudaEvent_t ev_fork = nullptr, ev_join[MAXL] = {};
 };
 
-enum { S_RZ = 0, S_PQ, S_RN, S_DU, S_UN, S_PW, S_GN, S_GR0, S_PW0 = S_GR0 + 8, NSLOT = S_PW0 + MAXL };
+enum { S_RZ = 0, S_PQ, S_RN, S_DU, S_UN, S_PW, S_GN, S_GR0, S_PW0 = S_GR0 + 8, S_PW1 = S_PW0 + MAXL, NSLOT = S_PW1 + MAXL };
 
 static inline double* slot(mpn_problem* p, int k) { return p->part + (size_t)k * p->B * MPN_PMAX; }
 
@@ -750,14 +750,17 @@ static int setup_body(mpn_problem* p, cudaStream_t st) {
     ++p->nlaunch, k_diag_inv<<<gr, MPN_TPB, 0, sk>>>(l.g, cf, l.rho, l.dinv);
     CKL();
     // power method for lambda_max(Dinv S)
-    ++p->nlaunch, k_fill_hash<<<gr, MPN_TPB, 0, sk>>>(l.g.N, l.t);
-    double* pw = slot(p, S_PW0 + k);
-    for (int it = 0; it < 12; ++it) {
+    // x_{k+1} = Dinv S x_k / ||x_k||: the norms are read from the partial
+    // sums of the previous step (two slots, alternating), so no separate
+    // normalisation pass
+    double* pw[2] = {slot(p, S_PW0 + k), slot(p, S_PW1 + k)};
+    ++p->nlaunch, k_fill_hash<<<gr, MPN_TPB, 0, sk>>>(l.g.N, l.t, pw[0]);
+    const int nit = 12;
+    for (int it = 0; it < nit; ++it) {
       TRY(apply_S(p, k, l.t, l.d, nullptr, sk));
-      ++p->nlaunch, k_power_w<<<gr, MPN_TPB, 0, sk>>>(l.g.N, l.dinv, l.d, l.e, pw);
-      if (it < 11) ++p->nlaunch, k_power_norm<<<gr, MPN_TPB, 0, sk>>>(l.g.N, l.e, l.t, pw, gr.x);
+      ++p->nlaunch, k_power_w<<<gr, MPN_TPB, 0, sk>>>(l.g.N, l.dinv, l.d, pw[it & 1], gr.x, l.t, pw[(it + 1) & 1]);
     }
-    ++p->nlaunch, k_scale_dinv<<<gr, MPN_TPB, 0, sk>>>(l.g.N, l.dinv, pw, gr.x, 1.1f, p->lam + k * B);
+    ++p->nlaunch, k_scale_dinv<<<gr, MPN_TPB, 0, sk>>>(l.g.N, l.dinv, pw[nit & 1], gr.x, 1.1f, p->lam + k * B);
     CKL();
     CK(cudaEventRecord(p->ev_join[k], sk));
   }

@@ -584,38 +584,40 @@ __global__ void k_coarse_solve(int M, const float* __restrict__ Kinv, const floa
 }
 
 // ------------------------------------------------------------ power method
-__global__ void k_fill_hash(int N, float* __restrict__ x) {
+// x_0 of the power method (deterministic positive pseudo-random values), with
+// partials of ||x_0||^2.
+__global__ void k_fill_hash(int N, float* __restrict__ x, double* __restrict__ part) {
   size_t off = (size_t)blockIdx.y * N;
+  double acc = 0;
   GRID_LOOP(p, N) {
     uint32_t h = (uint32_t)(p * 2654435761u) ^ (uint32_t)(blockIdx.y * 40503u + 12345u);
     h ^= h >> 15; h *= 2246822519u; h ^= h >> 13;
-    x[off + p] = (float)(h & 0xffff) / 65536.f + 0.25f;
-  }
-}
-
-// w = dinv * q, partial ||w||^2
-__global__ void k_power_w(int N, const float* __restrict__ dinv, const float* __restrict__ q,
-                          float* __restrict__ w, double* __restrict__ part) {
-  int b = blockIdx.y;
-  size_t off = (size_t)b * N;
-  double acc = 0;
-  GRID_LOOP(p, N) {
-    float v = dinv[off + p] * q[off + p];
-    w[off + p] = v;
+    const float v = (float)(h & 0xffff) / 65536.f + 0.25f;
+    x[off + p] = v;
     acc += (double)v * v;
   }
   double s = block_sum(acc);
-  if (threadIdx.x == 0) part[b * MPN_PMAX + blockIdx.x] = s;
+  if (threadIdx.x == 0) part[blockIdx.y * MPN_PMAX + blockIdx.x] = s;
 }
 
-// x = w / ||w||
-__global__ void k_power_norm(int N, const float* __restrict__ w, float* __restrict__ x,
-                             const double* __restrict__ part, int P) {
+// One power step after q = S x_k: x_{k+1} = Dinv q / ||x_k|| (= Dinv S applied
+// to the unit vector x_k / ||x_k||, so ||x_{k+1}|| estimates lambda_max), with
+// partials of ||x_{k+1}||^2 into part_out (a slot other than part_in).
+__global__ void k_power_w(int N, const float* __restrict__ dinv, const float* __restrict__ q,
+                          const double* __restrict__ part_in, int P, float* __restrict__ x,
+                          double* __restrict__ part_out) {
   int b = blockIdx.y;
-  double nn = sqrt(sum_partials(part, b, P));
-  float inv = nn > 0 ? (float)(1.0 / nn) : 0.f;
   size_t off = (size_t)b * N;
-  GRID_LOOP(p, N) x[off + p] = w[off + p] * inv;
+  const double nn = sqrt(sum_partials(part_in, b, P));
+  const float inv = nn > 0 ? (float)(1.0 / nn) : 0.f;
+  double acc = 0;
+  GRID_LOOP(p, N) {
+    float v = dinv[off + p] * q[off + p] * inv;
+    x[off + p] = v;
+    acc += (double)v * v;
+  }
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) part_out[b * MPN_PMAX + blockIdx.x] = s;
 }
 
 // dinv *= 1 / (safety * lambda),  lambda = ||w|| of the last power step.
