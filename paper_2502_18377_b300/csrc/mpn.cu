@@ -281,6 +281,12 @@ static int fs_set_smem() {
   return e == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
 }
 
+// Compile-time coefficient layout of the FP64 kernels: FS_MASK_RDI (c_xx and
+// c_yy one field), FS_MASK_RD, or 0 (layout read at run time).
+static int fp64_layout(const mpn_problem* p) {
+  if (p->field_mask != FS_MASK_RD) return 0;
+  return p->desc.field_of[4] == p->desc.field_of[6] ? FS_MASK_RDI : FS_MASK_RD;
+}
 // Instantiation of the fused coarse end for this problem's dimension and
 // coefficient layout.
 static const void* tail_fn(const mpn_problem* p) {
@@ -968,7 +974,10 @@ static int residual64(mpn_problem* p, const double* u, const double* g_adj, doub
     CKL();
     return MPN_OK;
   }
-  if (p->D == 3 && p->field_mask == FS_MASK_RD) {
+  if (p->D == 3 && fp64_layout(p) == FS_MASK_RDI) {
+    ++p->nlaunch, k_res64_y<3, FS_MASK_RDI><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    ++p->nlaunch, k_res64_q<3, FS_MASK_RDI><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
+  } else if (p->D == 3 && fp64_layout(p) == FS_MASK_RD) {
     ++p->nlaunch, k_res64_y<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
     ++p->nlaunch, k_res64_q<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
   } else if (p->D == 3) {
@@ -1118,7 +1127,9 @@ static int forward_impl(mpn_problem* p, const float* fields, const float* scalar
   int status = refine_solve(p, nullptr, u0 == nullptr, stats, st);
   if (status != MPN_OK && status != MPN_ERR_NOT_CONVERGED) return status;
   Coef cf = make_coef(p, l.fields);
-  if (p->D == 3 && p->field_mask == FS_MASK_RD)
+  if (p->D == 3 && fp64_layout(p) == FS_MASK_RDI)
+    ++p->nlaunch, k_recover<3, FS_MASK_RDI><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
+  else if (p->D == 3 && fp64_layout(p) == FS_MASK_RD)
     ++p->nlaunch, k_recover<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
   else if (p->D == 3)
     ++p->nlaunch, k_recover<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
@@ -1163,7 +1174,8 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
   Coef cf = make_coef(p, l.fields);
   // reduced right-hand side g_u - M_{u zeta} M_{zeta zeta}^{-1} g_zeta (FP64)
   if (p->D == 3) {
-    if (p->field_mask == FS_MASK_RD) ++p->nlaunch, k_adj_kappa<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
+    if (fp64_layout(p) == FS_MASK_RDI) ++p->nlaunch, k_adj_kappa<3, FS_MASK_RDI><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
+    else if (fp64_layout(p) == FS_MASK_RD) ++p->nlaunch, k_adj_kappa<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
     else ++p->nlaunch, k_adj_kappa<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
     ++p->nlaunch, k_adj_rhs<3><<<gr, MPN_TPB, 0, st>>>(l.g, g_z, p->kap, p->g64);
   } else {
@@ -1178,7 +1190,8 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
 #define GRAD_LAUNCH(DD, MK)                                                                              \
   ++p->nlaunch, k_gradients<DD, MK><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->rhs, p->uf64, p->u64, g_z, dfields, \
                                                            drhs, domega, dz, gp)
-  if (p->D == 3 && p->field_mask == FS_MASK_RD) GRAD_LAUNCH(3, FS_MASK_RD);
+  if (p->D == 3 && fp64_layout(p) == FS_MASK_RDI) GRAD_LAUNCH(3, FS_MASK_RDI);
+  else if (p->D == 3 && fp64_layout(p) == FS_MASK_RD) GRAD_LAUNCH(3, FS_MASK_RD);
   else if (p->D == 3) GRAD_LAUNCH(3, RES_ANY);
   else GRAD_LAUNCH(2, RES_ANY);
 #undef GRAD_LAUNCH

@@ -78,7 +78,9 @@ __device__ __forceinline__ void dforms1(int cls, float xm2, float xm1, float x0,
 #endif
 // with a compile-time layout: c_yy reads the field of c_xx (isotropic
 // diffusion), so the shared loads are issued once
+#ifndef FS_SHARE46
 #define FS_SHARE46 0x100
+#endif
 template <int MASK>
 struct CoefU4 {
   const float* base[7];

@@ -13,6 +13,11 @@
 // formed before the product (fewer FP64 operations: this pass is bound by the
 // FP64 pipe).
 #define RES_ANY 0x80
+// with a compile-time layout: c_yy reads the field of c_xx (isotropic
+// diffusion), so the shared loads and conversions are issued once
+#ifndef FS_SHARE46
+#define FS_SHARE46 0x100
+#endif
 template <int MASK>
 struct Coef64 {
   const Coef& cf;
@@ -23,7 +28,10 @@ struct Coef64 {
     for (int v = 0; v < 7; ++v) sv[v] = scal(v) ? (double)__ldg(c.ptr[v] + (size_t)b_ * c.bstride[v]) : 0.0;
   }
   __device__ __forceinline__ static constexpr bool scal(int v) { return MASK != RES_ANY && !((MASK >> v) & 1); }
-  __device__ __forceinline__ double at(int v, int p) const { return scal(v) ? sv[v] : (double)coefv(cf, v, b, p, 0); }
+  __device__ __forceinline__ double at(int v, int p) const {
+    if ((MASK & FS_SHARE46) && v == 6) v = 4;
+    return scal(v) ? sv[v] : (double)coefv(cf, v, b, p, 0);
+  }
 };
 
 
