@@ -290,6 +290,7 @@ static int fp64_layout(const mpn_problem* p) {
 // Instantiation of the fused coarse end for this problem's dimension and
 // coefficient layout.
 static const void* tail_fn(const mpn_problem* p) {
+  if (p->D == 3 && fp64_layout(p) == FS_MASK_RDI) return (const void*)k_vtail<3, FS_MASK_RDI>;
   if (p->D == 3) return p->field_mask == FS_MASK_RD ? (const void*)k_vtail<3, FS_MASK_RD> : (const void*)k_vtail<3, FS_ANY>;
   return (const void*)k_vtail<2, FS_ANY>;
 }

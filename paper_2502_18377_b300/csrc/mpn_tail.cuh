@@ -23,6 +23,9 @@ namespace cg = cooperative_groups;
 #ifndef FS_ANY
 #define FS_ANY 0x80
 #endif
+#ifndef FS_SHARE46
+#define FS_SHARE46 0x100
+#endif
 #define TAIL_MAXL 16
 // first fused level: at most TAIL_MAX_PPT points per thread and CTA (the
 // reaction-diffusion benchmark, 16 x 32 x 64 x 64: fused from 32 x 8 x 8,
@@ -125,11 +128,14 @@ struct TailView {
   }
   // coefficient v at CTA-local point j
   __device__ __forceinline__ bool is_field(int v) const { return MASK == FS_ANY ? fo[v] >= 0 : ((MASK >> v) & 1); }
+  // (FS_SHARE46: c_yy reads the field of c_xx, so the two share their loads)
   __device__ __forceinline__ float c(int v, int j) const {
+    if ((MASK & FS_SHARE46) && v == 6) v = 4;
     return is_field(v) ? tail_sm[L.o_f + fo[v] * L.cap + j] : scal[v];
   }
   // coefficient v at (time plane tp, in-plane index rem), any CTA
   __device__ __forceinline__ float cr(int v, int tp, int rem) const {
+    if ((MASK & FS_SHARE46) && v == 6) v = 4;
     return is_field(v) ? ld(L.o_f + fo[v] * L.cap, tp, rem) : scal[v];
   }
 };
