@@ -813,7 +813,9 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
 }
 
 // One V-cycle at level k: e_k ~ S_k^{-1} r_k (result in l.e).
-static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
+// started: the restriction into this level already started its smoother
+// (d = e = inv_th D^-1 r in the iterate buffer the pre-smoothing begins in).
+static int vcycle(mpn_problem* p, int k, cudaStream_t st, bool started = false) {
   Level& l = p->lv[k];
   int B = p->B;
   dim3 gr(nblk(l.g.N), B);
@@ -839,10 +841,12 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   memset(&a, 0, sizeof(a));
   a.r = l.r; a.d = l.d;
   // pre-smoothing from e = 0: d = Dinv r / th, e = d
-  if (vec4_len(l.g.N))
-    ++p->nlaunch, k_cheb_init<true><<<dim3(vgrid(l.g.N), B), MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, cur, l.d);
-  else
-    ++p->nlaunch, k_cheb_init<false><<<dim3(vgrid(l.g.N), B), MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, cur, l.d);
+  if (!started) {
+    if (vec4_len(l.g.N))
+      ++p->nlaunch, k_cheb_init<true><<<dim3(vgrid(l.g.N), B), MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, cur, l.d);
+    else
+      ++p->nlaunch, k_cheb_init<false><<<dim3(vgrid(l.g.N), B), MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, cur, l.d);
+  }
   for (int s = 1; s < m; ++s) {
     a.c1 = p->cheb_c1[s]; a.c2 = p->cheb_c2[s];
     a.x = cur; a.e = other(cur);
@@ -858,12 +862,17 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st) {
   a.out = l.t;
   stencil(p, k, a, SM_RES, st);
   Level& lc = p->lv[k + 1];
-  if (!l.cz[0] && l.cz[1] && l.cz[2] && l.g.per[1] && l.g.per[2] && l.g.n[2] % 8 == 0)
-    ++p->nlaunch, k_restrict_vec4<<<dim3(sblk(lc.g.N / 4), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.t, lc.r);
+  const bool vec4r = !l.cz[0] && l.cz[1] && l.cz[2] && l.g.per[1] && l.g.per[2] && l.g.n[2] % 8 == 0;
+  // the float4 restriction also starts the coarse level's smoother, unless
+  // that level is the fused coarse end or the coarsest solve
+  const bool start_c = vec4r && k + 1 != p->tail_k0 && k + 1 != p->L - 1;
+  if (vec4r)
+    ++p->nlaunch, k_restrict_vec4<<<dim3(sblk(lc.g.N / 4), B), MPN_TPB, 0, st>>>(
+        l.g, lc.g, l.t, lc.r, start_c ? lc.dinv : nullptr, p->cheb_inv_th, lc.fs_tt ? lc.e2 : lc.e, lc.d);
   else
     ++p->nlaunch, k_restrict_vec<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], l.t, lc.r);
   CKL();
-  TRY(vcycle(p, k + 1, st));
+  TRY(vcycle(p, k + 1, st, start_c));
   if (!l.cz[0] && l.cz[1] && l.cz[2] && l.g.per[1] && l.g.per[2] && l.g.n[2] % 4 == 0)
     ++p->nlaunch, k_prolong_add4<<<dim3(sblk(l.g.N / 4), B), MPN_TPB, 0, st>>>(l.g, lc.g, lc.e, cur);
   else

@@ -296,7 +296,11 @@ __global__ void k_prolong_add4(Grid gf, Grid gc, const float* __restrict__ ec, f
 
 // r_c = P^T r_f for the same case with n_y % 8 == 0: one thread owns 4
 // coarse points along y, i.e. fine y 2j-1 .. 2j+7 of three fine x rows.
-__global__ void k_restrict_vec4(Grid gf, Grid gc, const float* __restrict__ fine, float* __restrict__ coarse) {
+// With dinv_c set it also starts the coarse level's smoother (k_cheb_init's
+// work): d_c = e_c = inv_th D_c^-1 r_c.
+__global__ void k_restrict_vec4(Grid gf, Grid gc, const float* __restrict__ fine, float* __restrict__ coarse,
+                                const float* __restrict__ dinv_c, float inv_th, float* __restrict__ e_c,
+                                float* __restrict__ d_c) {
   const int b = blockIdx.y;
   const float* Fi = fine + (size_t)b * gf.N;
   float* Co = coarse + (size_t)b * gc.N;
@@ -309,6 +313,8 @@ __global__ void k_restrict_vec4(Grid gf, Grid gc, const float* __restrict__ fine
     const int row = fdivmod(q, G, invG, gq);
     const int t = fdivmod(row, n1c, inv1, X);
     const int fy = 8 * gq;                        // fine y of the group's first coarse point
+    const size_t jc = (size_t)b * gc.N + (size_t)q * 4;
+    const float4 di = dinv_c ? ld4(dinv_c + jc) : f4(0.f);
     float4 acc = f4(0.f);
 #pragma unroll
     for (int r = -1; r <= 1; ++r) {
@@ -323,6 +329,11 @@ __global__ void k_restrict_vec4(Grid gf, Grid gc, const float* __restrict__ fine
       acc = acc + w * o;
     }
     *reinterpret_cast<float4*>(Co + (size_t)q * 4) = acc;
+    if (dinv_c) {
+      const float4 v = inv_th * (di * acc);
+      *reinterpret_cast<float4*>(e_c + jc) = v;
+      *reinterpret_cast<float4*>(d_c + jc) = v;
+    }
   }
 }
 
