@@ -893,9 +893,10 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st, bool started = false) 
 }
 
 // z = V(r) at the finest level with partial <r, z> in slot S_RZ.
-static int precond(mpn_problem* p, cudaStream_t st) {
+// started: the kernel that wrote lv[0].r also started the smoother.
+static int precond(mpn_problem* p, cudaStream_t st, bool started = false) {
   Level& l = p->lv[0];
-  TRY(vcycle(p, 0, st));
+  TRY(vcycle(p, 0, st, started));
   dim3 gv(vgrid(l.g.N), p->B);
   if (vec4_len(l.g.N)) ++p->nlaunch, k_final_z<true><<<gv, MPN_TPB, 0, st>>>(l.g.N, l.e, l.r, p->z, slot(p, S_RZ));
   else ++p->nlaunch, k_final_z<false><<<gv, MPN_TPB, 0, st>>>(l.g.N, l.e, l.r, p->z, slot(p, S_RZ));
@@ -904,27 +905,31 @@ static int precond(mpn_problem* p, cudaStream_t st) {
 }
 
 // Inner FP32 PCG on S x = r (r = lv[0].r), fixed iteration count, x = p->x.
-static int pcg(mpn_problem* p, int iters, cudaStream_t st) {
+// started: the kernel that wrote r also started the first V-cycle's smoother;
+// the residual updates start the following ones.
+static int pcg(mpn_problem* p, int iters, cudaStream_t st, bool started) {
   Level& l = p->lv[0];
+  float* cur0 = l.fs_tt ? l.e2 : l.e;       // the iterate buffer the V-cycle's pre-smoothing begins in
   const int N = l.g.N;
   dim3 gv(vgrid(N), p->B);
   const int P = gv.x;
   const bool v4 = vec4_len(N);
   double* rz_old = p->dscal + p->B;
-  TRY(precond(p, st));
+  TRY(precond(p, st, started));
   if (v4) ++p->nlaunch, k_pcg_init<true><<<gv, MPN_TPB, 0, st>>>(N, p->z, p->x, p->pv);
   else ++p->nlaunch, k_pcg_init<false><<<gv, MPN_TPB, 0, st>>>(N, p->z, p->x, p->pv);
   for (int it = 0; it < iters; ++it) {
     TRY(apply_S(p, 0, p->pv, p->q, slot(p, S_PQ), st));
+    const float* dst = it < iters - 1 ? l.dinv : nullptr;   // a V-cycle follows
     if (v4)
       ++p->nlaunch, k_pcg_xr<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, P, p->pv, p->q,
-                                                            p->x, l.r, rz_old);
+                                                            p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, l.d);
     else
       ++p->nlaunch, k_pcg_xr<false><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, P, p->pv, p->q,
-                                                             p->x, l.r, rz_old);
+                                                             p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, l.d);
     CKL();
     if (it == iters - 1) break;
-    TRY(precond(p, st));
+    TRY(precond(p, st, true));
     if (v4) ++p->nlaunch, k_pcg_p<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), P, rz_old, p->z, p->pv);
     else ++p->nlaunch, k_pcg_p<false><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), P, rz_old, p->z, p->pv);
     CKL();
@@ -1011,10 +1016,13 @@ static int sweep_body(mpn_problem* p, const double* g_adj, int iters, int P, boo
   double* outv = p->dscal + 2 * B;  // [slots][B]
   // from a zero iterate the residual needs no operator apply on u
   TRY(residual64(p, from_zero ? nullptr : p->u64, g_adj, p->r64, slot(p, S_RN), st));
-  ++p->nlaunch, k_to32<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN), P, l.r, scale);
+  // CG's first V-cycle runs on this r: its smoother starts here
+  const bool cg = p->desc.krylov != MPN_KRYLOV_FGMRES;
+  ++p->nlaunch, k_to32<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN), P, l.r, scale, cg ? l.dinv : nullptr,
+                                                p->cheb_inv_th, l.fs_tt ? l.e2 : l.e, l.d);
   CKL();
   if (p->desc.krylov == MPN_KRYLOV_FGMRES) TRY(fgmres(p, iters, st));
-  else TRY(pcg(p, iters, st));
+  else TRY(pcg(p, iters, st, true));
   ++p->nlaunch, k_update64<<<gr, MPN_TPB, 0, st>>>(N, p->x, scale, p->u64, slot(p, S_DU), slot(p, S_UN));
   // correction and solution sizes measured on every unknown of z
   ++p->nlaunch, k_znorm<<<gr, MPN_TPB, 0, st>>>(l.g, p->u64, p->x, scale, slot(p, S_DU), slot(p, S_UN));

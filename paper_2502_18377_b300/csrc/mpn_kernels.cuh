@@ -676,24 +676,39 @@ __global__ void k_pcg_init(int N, const float* __restrict__ z, float* __restrict
 }
 // The vector loads of a thread's first group are issued before the block
 // sums the partial dot products, so their latency overlaps the reduction.
+// With dinv set it also starts the smoother of the V-cycle that follows on
+// the new r: d = e = inv_th D^-1 r.
 template <bool V4>
 __global__ void k_pcg_xr(int N, const double* __restrict__ part_rz, const double* __restrict__ part_pq, int P,
                          int Prz, const float* __restrict__ pv, const float* __restrict__ q, float* __restrict__ x,
-                         float* __restrict__ r, double* __restrict__ rz_old) {
+                         float* __restrict__ r, double* __restrict__ rz_old, const float* __restrict__ dinv,
+                         float inv_th, float* __restrict__ e, float* __restrict__ d) {
   const int b = blockIdx.y;
   const size_t off = (size_t)b * N;
   const int n = V4 ? N >> 2 : N;
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  float4 xv, pp, rv, qq;
-  if (i0 < n) { xv = vld<V4>(x + off, i0); pp = vld<V4>(pv + off, i0); rv = vld<V4>(r + off, i0); qq = vld<V4>(q + off, i0); }
+  float4 xv, pp, rv, qq, dv = f4(0.f);
+  if (i0 < n) {
+    xv = vld<V4>(x + off, i0); pp = vld<V4>(pv + off, i0); rv = vld<V4>(r + off, i0); qq = vld<V4>(q + off, i0);
+    if (dinv) dv = vld<V4>(dinv + off, i0);
+  }
   const double rz = sum_partials(part_rz, b, Prz);
   const double pq = sum_partials(part_pq, b, P);
   const float alpha = (pq > 0 && rz > 0) ? (float)(rz / pq) : 0.f;
   if (blockIdx.x == 0 && threadIdx.x == 0) rz_old[b] = rz;
   for (int i = i0; i < n; i += stride) {
-    if (i != i0) { xv = vld<V4>(x + off, i); pp = vld<V4>(pv + off, i); rv = vld<V4>(r + off, i); qq = vld<V4>(q + off, i); }
+    if (i != i0) {
+      xv = vld<V4>(x + off, i); pp = vld<V4>(pv + off, i); rv = vld<V4>(r + off, i); qq = vld<V4>(q + off, i);
+      if (dinv) dv = vld<V4>(dinv + off, i);
+    }
+    const float4 rn = rv - alpha * qq;
     vst<V4>(x + off, i, xv + alpha * pp);
-    vst<V4>(r + off, i, rv - alpha * qq);
+    vst<V4>(r + off, i, rn);
+    if (dinv) {
+      const float4 v = inv_th * (dv * rn);
+      vst<V4>(e + off, i, v);
+      vst<V4>(d + off, i, v);
+    }
   }
 }
 template <bool V4>
@@ -871,14 +886,25 @@ __global__ void k_copy_norm64(int N, const double* __restrict__ g, double* __res
   if (threadIdx.x == 0) part[b * MPN_PMAX + blockIdx.x] = s;
 }
 
+// With dinv set it also starts the finest level's smoother on r32 (the
+// V-cycle that follows): d = e = inv_th D^-1 r32.
 __global__ void k_to32(int N, const double* __restrict__ r64, const double* __restrict__ part, int P,
-                       float* __restrict__ r32, double* __restrict__ scale) {
+                       float* __restrict__ r32, double* __restrict__ scale, const float* __restrict__ dinv,
+                       float inv_th, float* __restrict__ e, float* __restrict__ d) {
   int b = blockIdx.y;
   double nn = sqrt(sum_partials(part, b, P));
   if (blockIdx.x == 0 && threadIdx.x == 0) scale[b] = nn;
   double inv = nn > 0 ? 1.0 / nn : 0.0;
   size_t off = (size_t)b * N;
-  GRID_LOOP(p, N) r32[off + p] = (float)(r64[off + p] * inv);
+  GRID_LOOP(p, N) {
+    const float r = (float)(r64[off + p] * inv);
+    r32[off + p] = r;
+    if (dinv) {
+      const float v = inv_th * (dinv[off + p] * r);
+      e[off + p] = v;
+      d[off + p] = v;
+    }
+  }
 }
 
 // u += scale * x; partials ||scale x||^2 and ||u||^2
