@@ -271,7 +271,7 @@ static int fs_set_smem() {
   cudaError_t e = cudaSuccess;
 #define FS_ATTR(M, T, P1, P2, MK) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<M, T, P1, P2, MK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-#define FS_ATTR_M(T, P1, P2, MK) FS_ATTR(SM_POST0, T, P1, P2, MK); FS_ATTR(SM_CHEB, T, P1, P2, MK); FS_ATTR(SM_RES, T, P1, P2, MK); FS_ATTR(SM_APPLY, T, P1, P2, MK)
+#define FS_ATTR_M(T, P1, P2, MK) FS_ATTR(SM_POST0, T, P1, P2, MK); FS_ATTR(SM_CHEB, T, P1, P2, MK); FS_ATTR(SM_RES, T, P1, P2, MK); FS_ATTR(SM_APPLY, T, P1, P2, MK); FS_ATTR(SM_CHEB_DOT, T, P1, P2, MK)
 #define FS_ATTR_P(T) FS_ATTR_M(T, true, true, FS_ANY); FS_ATTR_M(T, true, false, FS_ANY); FS_ATTR_M(T, false, true, FS_ANY); FS_ATTR_M(T, false, false, FS_ANY); FS_ATTR_M(T, true, true, FS_MASK_RD); FS_ATTR_M(T, true, true, FS_MASK_RDI)
   FS_ATTR_P(8);
   FS_ATTR_P(4);
@@ -574,6 +574,7 @@ static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st
   switch (mode) {                                                                                    \
     case SM_POST0: ++p->nlaunch, k_step3<SM_POST0, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break; \
     case SM_CHEB: ++p->nlaunch, k_step3<SM_CHEB, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;   \
+    case SM_CHEB_DOT: ++p->nlaunch, k_step3<SM_CHEB_DOT, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break; \
     case SM_RES: ++p->nlaunch, k_step3<SM_RES, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;     \
     default: ++p->nlaunch, k_step3<SM_APPLY, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;     \
   }
@@ -815,7 +816,9 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
 // One V-cycle at level k: e_k ~ S_k^{-1} r_k (result in l.e).
 // started: the restriction into this level already started its smoother
 // (d = e = inv_th D^-1 r in the iterate buffer the pre-smoothing begins in).
-static int vcycle(mpn_problem* p, int k, cudaStream_t st, bool started = false) {
+// zdot (fused level 0 only): its last smoothing step writes the partials of
+// <e, r> of the V-cycle's result there.
+static int vcycle(mpn_problem* p, int k, cudaStream_t st, bool started = false, double* zdot = nullptr) {
   Level& l = p->lv[k];
   int B = p->B;
   dim3 gr(nblk(l.g.N), B);
@@ -885,7 +888,9 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st, bool started = false) 
   for (int s = 1; s < m; ++s) {
     a.c1 = p->cheb_c1[s]; a.c2 = p->cheb_c2[s];
     a.x = cur; a.e = other(cur);
-    stencil(p, k, a, SM_CHEB, st);
+    const bool dot = zdot && s == m - 1;
+    a.part = dot ? zdot : nullptr;
+    stencil(p, k, a, dot ? SM_CHEB_DOT : SM_CHEB, st);
     cur = other(cur);
   }
   CKL();
@@ -894,14 +899,24 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st, bool started = false) 
 
 // z = V(r) at the finest level with partial <r, z> in slot S_RZ.
 // started: the kernel that wrote lv[0].r also started the smoother.
-static int precond(mpn_problem* p, cudaStream_t st, bool started = false) {
+// zin_e: z is the V-cycle's result lv[0].e itself, the partials of <r, z>
+// written by its last smoothing step (see z_in_e()); else z is copied out.
+static int precond(mpn_problem* p, cudaStream_t st, bool started = false, bool zin_e = false) {
   Level& l = p->lv[0];
-  TRY(vcycle(p, 0, st, started));
+  TRY(vcycle(p, 0, st, started, zin_e ? slot(p, S_RZ) : nullptr));
+  if (zin_e) return MPN_OK;
   dim3 gv(vgrid(l.g.N), p->B);
   if (vec4_len(l.g.N)) ++p->nlaunch, k_final_z<true><<<gv, MPN_TPB, 0, st>>>(l.g.N, l.e, l.r, p->z, slot(p, S_RZ));
   else ++p->nlaunch, k_final_z<false><<<gv, MPN_TPB, 0, st>>>(l.g.N, l.e, l.r, p->z, slot(p, S_RZ));
   CKL();
   return MPN_OK;
+}
+
+// PCG may take z from the finest level's iterate buffer (the V-cycle ends in
+// lv[0].e, which nothing overwrites before z is consumed) when that level runs
+// the fused step's smoothing through the V-cycle's end.
+static bool z_in_e(const mpn_problem* p) {
+  return p->lv[0].fs_tt && p->tail_k0 != 0 && p->L > 1 && p->desc.cheb_degree >= 2;
 }
 
 // Inner FP32 PCG on S x = r (r = lv[0].r), fixed iteration count, x = p->x.
@@ -913,25 +928,28 @@ static int pcg(mpn_problem* p, int iters, cudaStream_t st, bool started) {
   const int N = l.g.N;
   dim3 gv(vgrid(N), p->B);
   const int P = gv.x;
+  const bool ze = z_in_e(p);
+  float* zv = ze ? l.e : p->z;
+  const int Prz = ze ? l.papply : P;         // partials of <r, z>
   const bool v4 = vec4_len(N);
   double* rz_old = p->dscal + p->B;
-  TRY(precond(p, st, started));
-  if (v4) ++p->nlaunch, k_pcg_init<true><<<gv, MPN_TPB, 0, st>>>(N, p->z, p->x, p->pv);
-  else ++p->nlaunch, k_pcg_init<false><<<gv, MPN_TPB, 0, st>>>(N, p->z, p->x, p->pv);
+  TRY(precond(p, st, started, ze));
+  if (v4) ++p->nlaunch, k_pcg_init<true><<<gv, MPN_TPB, 0, st>>>(N, zv, p->x, p->pv);
+  else ++p->nlaunch, k_pcg_init<false><<<gv, MPN_TPB, 0, st>>>(N, zv, p->x, p->pv);
   for (int it = 0; it < iters; ++it) {
     TRY(apply_S(p, 0, p->pv, p->q, slot(p, S_PQ), st));
     const float* dst = it < iters - 1 ? l.dinv : nullptr;   // a V-cycle follows
     if (v4)
-      ++p->nlaunch, k_pcg_xr<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, P, p->pv, p->q,
+      ++p->nlaunch, k_pcg_xr<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, Prz, p->pv, p->q,
                                                             p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, l.d);
     else
-      ++p->nlaunch, k_pcg_xr<false><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, P, p->pv, p->q,
+      ++p->nlaunch, k_pcg_xr<false><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, Prz, p->pv, p->q,
                                                              p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, l.d);
     CKL();
     if (it == iters - 1) break;
-    TRY(precond(p, st, true));
-    if (v4) ++p->nlaunch, k_pcg_p<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), P, rz_old, p->z, p->pv);
-    else ++p->nlaunch, k_pcg_p<false><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), P, rz_old, p->z, p->pv);
+    TRY(precond(p, st, true, ze));
+    if (v4) ++p->nlaunch, k_pcg_p<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), Prz, rz_old, zv, p->pv);
+    else ++p->nlaunch, k_pcg_p<false><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), Prz, rz_old, zv, p->pv);
     CKL();
   }
   return MPN_OK;

@@ -256,8 +256,8 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
     const size_t j = off + p;
     float4 ur = make_float4(0.f, 0.f, 0.f, 0.f), udi = ur, ud = ur;
     if (MODE != SM_APPLY) ur = ld4(a.r + j);
-    if (MODE == SM_POST0 || MODE == SM_CHEB) udi = ld4(a.dinv + j);
-    if (MODE == SM_CHEB) ud = ld4(a.d + j);
+    if (MODE == SM_POST0 || MODE == SM_CHEB || MODE == SM_CHEB_DOT) udi = ld4(a.dinv + j);
+    if (MODE == SM_CHEB || MODE == SM_CHEB_DOT) ud = ld4(a.d + j);
     const float* yr = ys + ((ot + 1) * RYW + ox + 1) * n2;
     const float4 yc = lds4(yr + y0);
     const int pxm = (PER1 && x == 0) ? p + (n1 - 1) * n2 : p - n2;
@@ -368,12 +368,14 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
     } else {
       const float4 res = ur + qv;
       float4 dn = a.c2 * (udi * res);
-      if (MODE == SM_CHEB) dn = dn + a.c1 * ud;
+      if (MODE == SM_CHEB || MODE == SM_CHEB_DOT) dn = dn + a.c1 * ud;
+      const float4 en = xj + dn;
       *reinterpret_cast<float4*>(a.d + j) = dn;
-      *reinterpret_cast<float4*>(a.e + j) = xj + dn;
+      *reinterpret_cast<float4*>(a.e + j) = en;
+      if (MODE == SM_CHEB_DOT) acc += en.x * ur.x + en.y * ur.y + en.z * ur.z + en.w * ur.w;   // <e', r>
     }
   }
-  if (MODE == SM_APPLY && a.part) {
+  if ((MODE == SM_APPLY || MODE == SM_CHEB_DOT) && a.part) {
     double s = block_sum((double)acc);
     if (threadIdx.x == 0) a.part[b * MPN_PMAX + blockIdx.x] = s;
   }

@@ -15,7 +15,8 @@
 #pragma once
 #include "mpn_device.cuh"
 
-enum { SM_POST0 = 0, SM_CHEB = 1, SM_RES = 2, SM_APPLY = 3 };
+enum { SM_POST0 = 0, SM_CHEB = 1, SM_RES = 2, SM_APPLY = 3,
+       SM_CHEB_DOT = 4 };   // fused step only: a Chebyshev step that also sums <e', r>
 
 struct StepArgs {
   const float* x;     // operand of S (pass 1 and the theta 1_B term)
@@ -25,7 +26,7 @@ struct StepArgs {
   float* e;           // iterate (modes 0, 1: updated in place; it is x)
   float* d;           // direction (modes 0, 1)
   float* out;         // mode 2: r - S x;  mode 3: S x
-  double* part;       // mode 3: partials of <x, S x> (nullable)
+  double* part;       // mode 3: partials of <x, S x>; mode 4: of <e', r> (nullable)
   int* err;           // set when a bounded wait gives up (fused step; nullable)
   float c1, c2;
 };
