@@ -74,6 +74,7 @@ struct mpn_problem {
   double *fgpart = nullptr, *fgH = nullptr, *fgc = nullptr, *fgs = nullptr, *fgg = nullptr, *fgy = nullptr, *fgh = nullptr;
   int* field_of_dev = nullptr;
   float *x = nullptr, *pv = nullptr, *q = nullptr, *z = nullptr;
+  float* pv2 = nullptr;    // second PCG direction buffer (fused direction update)
   double *u64 = nullptr, *r64 = nullptr, *y64 = nullptr, *g64 = nullptr;
   double* rho64 = nullptr;  // finest-level point weights in FP64 (refinement residual)
   double *kap = nullptr;
@@ -271,7 +272,7 @@ static int fs_set_smem() {
   cudaError_t e = cudaSuccess;
 #define FS_ATTR(M, T, P1, P2, MK) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<M, T, P1, P2, MK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-#define FS_ATTR_M(T, P1, P2, MK) FS_ATTR(SM_POST0, T, P1, P2, MK); FS_ATTR(SM_CHEB, T, P1, P2, MK); FS_ATTR(SM_RES, T, P1, P2, MK); FS_ATTR(SM_APPLY, T, P1, P2, MK); FS_ATTR(SM_CHEB_DOT, T, P1, P2, MK)
+#define FS_ATTR_M(T, P1, P2, MK) FS_ATTR(SM_POST0, T, P1, P2, MK); FS_ATTR(SM_CHEB, T, P1, P2, MK); FS_ATTR(SM_RES, T, P1, P2, MK); FS_ATTR(SM_APPLY, T, P1, P2, MK); FS_ATTR(SM_CHEB_DOT, T, P1, P2, MK); FS_ATTR(SM_APPLYP, T, P1, P2, MK)
 #define FS_ATTR_P(T) FS_ATTR_M(T, true, true, FS_ANY); FS_ATTR_M(T, true, false, FS_ANY); FS_ATTR_M(T, false, true, FS_ANY); FS_ATTR_M(T, false, false, FS_ANY); FS_ATTR_M(T, true, true, FS_MASK_RD); FS_ATTR_M(T, true, true, FS_MASK_RDI)
   FS_ATTR_P(8);
   FS_ATTR_P(4);
@@ -495,6 +496,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   AL(p->rhs, N0); AL(p->omega, N0);
   AL(p->field_of_dev, 8);
   AL(p->x, N0); AL(p->pv, N0); AL(p->q, N0); AL(p->z, N0);
+  if (p->lv[0].fs_tt) AL(p->pv2, N0);
   AL(p->u64, N0); AL(p->r64, N0); AL(p->y64, N0); AL(p->g64, N0); AL(p->rho64, N0);
   AL(p->uf64, N0); AL(p->kap, N0 * V);
   AL(p->part, (size_t)NSLOT * B * MPN_PMAX);
@@ -575,6 +577,7 @@ static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st
     case SM_POST0: ++p->nlaunch, k_step3<SM_POST0, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break; \
     case SM_CHEB: ++p->nlaunch, k_step3<SM_CHEB, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;   \
     case SM_CHEB_DOT: ++p->nlaunch, k_step3<SM_CHEB_DOT, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break; \
+    case SM_APPLYP: ++p->nlaunch, k_step3<SM_APPLYP, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break; \
     case SM_RES: ++p->nlaunch, k_step3<SM_RES, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;     \
     default: ++p->nlaunch, k_step3<SM_APPLY, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;     \
   }
@@ -934,6 +937,37 @@ static int pcg(mpn_problem* p, int iters, cudaStream_t st, bool started) {
   const bool v4 = vec4_len(N);
   double* rz_old = p->dscal + p->B;
   TRY(precond(p, st, started, ze));
+  if (l.fs_tt) {
+    // the direction update rides on the operator apply (mode SM_APPLYP):
+    // p = z, then p = z + beta p, written to the other direction buffer
+    CK(cudaMemsetAsync(p->x, 0, sizeof(float) * (size_t)N * p->B, st));
+    float* pb[2] = {p->pv, p->pv2};
+    int c = 0;
+    for (int it = 0; it < iters; ++it) {
+      StepArgs a;
+      memset(&a, 0, sizeof(a));
+      a.x = zv; a.out = p->q; a.part = slot(p, S_PQ);
+      if (it == 0) {
+        a.e = pb[c];
+      } else {
+        a.d = pb[c]; a.e = pb[c ^ 1];
+        a.rz = slot(p, S_RZ); a.nrz = Prz; a.rz_old = rz_old;
+        c ^= 1;
+      }
+      stencil(p, 0, a, SM_APPLYP, st);
+      const float* dst = it < iters - 1 ? l.dinv : nullptr;   // a V-cycle follows
+      if (v4)
+        ++p->nlaunch, k_pcg_xr<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, Prz, pb[c], p->q,
+                                                              p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, l.d);
+      else
+        ++p->nlaunch, k_pcg_xr<false><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, Prz, pb[c], p->q,
+                                                               p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, l.d);
+      CKL();
+      if (it == iters - 1) break;
+      TRY(precond(p, st, true, ze));
+    }
+    return MPN_OK;
+  }
   if (v4) ++p->nlaunch, k_pcg_init<true><<<gv, MPN_TPB, 0, st>>>(N, zv, p->x, p->pv);
   else ++p->nlaunch, k_pcg_init<false><<<gv, MPN_TPB, 0, st>>>(N, zv, p->x, p->pv);
   for (int it = 0; it < iters; ++it) {

@@ -165,9 +165,38 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
       bulk_g2s(xs + r * n2, X + (size_t)t * pl + (size_t)x * n2, (unsigned)(len * n2 * sizeof(float)), &bar);
     });
   }
+  // PCG's direction update (mode 5): beta from the partial sums, read while
+  // the operand copies are in flight
+  float beta = 0.f;
+  if (MODE == SM_APPLYP && a.d) {
+    const double rz = sum_partials(a.rz, b, a.nrz), ro = a.rz_old[b];
+    beta = (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f;
+  }
   __syncthreads();
   if (!mbar_wait(&bar, 0, FS_WAIT_LIMIT) && a.err) atomicExch(a.err, 1);
   __syncthreads();
+  if (MODE == SM_APPLYP) {
+    // the operand p = x + beta d on the tile and its halo (x staged above),
+    // and p on the tile rows to e, a buffer other than d (neighbouring tiles
+    // read d as their halo)
+    for (int i = threadIdx.x; i < fs_rows_x(TT) * G; i += FS_TPB) {
+      int gq;
+      const int row = fdivmod(i, G, invG, gq);
+      const int rt = row / RXW, rx = row % RXW;
+      const int t = t0 - 2 + rt;
+      int x = x0 - 2 + rx;
+      if (t < 0 || t >= n0) continue;
+      if (PER1) { if (x < 0) x += n1; else if (x >= n1) x -= n1; }
+      else if (x < 0 || x >= n1) continue;
+      const size_t q = off + (size_t)t * pl + (size_t)x * n2 + 4 * gq;
+      float* sp = xs + row * n2 + 4 * gq;
+      float4 v = lds4(sp);
+      if (a.d) v = v + beta * ld4(a.d + q);
+      *reinterpret_cast<float4*>(sp) = v;
+      if (rt >= 2 && rt < TT + 2 && rx >= 2 && rx < FS_TX + 2) *reinterpret_cast<float4*>(a.e + q) = v;
+    }
+    __syncthreads();
+  }
 
   // each thread keeps one float4 group gi of the rows and strides over rows
   const int rstride = FS_TPB / G;
@@ -255,7 +284,7 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
     // overlaps it
     const size_t j = off + p;
     float4 ur = make_float4(0.f, 0.f, 0.f, 0.f), udi = ur, ud = ur;
-    if (MODE != SM_APPLY) ur = ld4(a.r + j);
+    if (MODE != SM_APPLY && MODE != SM_APPLYP) ur = ld4(a.r + j);
     if (MODE == SM_POST0 || MODE == SM_CHEB || MODE == SM_CHEB_DOT) udi = ld4(a.dinv + j);
     if (MODE == SM_CHEB || MODE == SM_CHEB_DOT) ud = ld4(a.d + j);
     const float* yr = ys + ((ot + 1) * RYW + ox + 1) * n2;
@@ -360,7 +389,7 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
       if (y0 + 3 == n2 - 1) qv.w -= g.theta * xj.w;
     }
     // qv = -(S x) on the group
-    if (MODE == SM_APPLY) {
+    if (MODE == SM_APPLY || MODE == SM_APPLYP) {
       *reinterpret_cast<float4*>(a.out + j) = make_float4(-qv.x, -qv.y, -qv.z, -qv.w);
       acc -= qv.x * xj.x + qv.y * xj.y + qv.z * xj.z + qv.w * xj.w;
     } else if (MODE == SM_RES) {
@@ -375,7 +404,7 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
       if (MODE == SM_CHEB_DOT) acc += en.x * ur.x + en.y * ur.y + en.z * ur.z + en.w * ur.w;   // <e', r>
     }
   }
-  if ((MODE == SM_APPLY || MODE == SM_CHEB_DOT) && a.part) {
+  if ((MODE == SM_APPLY || MODE == SM_APPLYP || MODE == SM_CHEB_DOT) && a.part) {
     double s = block_sum((double)acc);
     if (threadIdx.x == 0) a.part[b * MPN_PMAX + blockIdx.x] = s;
   }

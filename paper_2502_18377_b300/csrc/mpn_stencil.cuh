@@ -16,7 +16,8 @@
 #include "mpn_device.cuh"
 
 enum { SM_POST0 = 0, SM_CHEB = 1, SM_RES = 2, SM_APPLY = 3,
-       SM_CHEB_DOT = 4 };   // fused step only: a Chebyshev step that also sums <e', r>
+       SM_CHEB_DOT = 4,     // fused step only: a Chebyshev step that also sums <e', r>
+       SM_APPLYP = 5 };     // fused step only: apply to p = x + beta d, p also written to e
 
 struct StepArgs {
   const float* x;     // operand of S (pass 1 and the theta 1_B term)
@@ -29,6 +30,10 @@ struct StepArgs {
   double* part;       // mode 3: partials of <x, S x>; mode 4: of <e', r> (nullable)
   int* err;           // set when a bounded wait gives up (fused step; nullable)
   float c1, c2;
+  // mode 5: beta = sum(rz partials, nrz of them) / rz_old[b] (0 when d is null)
+  const double* rz;
+  const double* rz_old;
+  int nrz;
 };
 
 // p -> (t, x, y) without integer division.
