@@ -552,9 +552,11 @@ static void prof_mark(mpn_problem* p, cudaStream_t st) {
 static void prof_flush(mpn_problem* p, int e0, int e1) {
   if (!p->prof_on) return;
   const Level& l = p->lv[0];
-  // algorithmic bytes of one smoothing step on the finest grid: read e, d, r,
-  // dinv, rho and the F coefficient fields once, write e and d (FP32)
-  double bytes = 4.0 * (7 + p->F) * (double)l.g.N * p->B;
+  // algorithmic bytes of the bracketed smoothing step on the finest grid
+  // (FP32): read e, r, dinv, rho and the F coefficient fields once, and either
+  // the previous iterate (fused step, no direction array) or the direction d,
+  // write e (and d)
+  double bytes = 4.0 * (l.fs_tt ? 6 + p->F : 7 + p->F) * (double)l.g.N * p->B;
   for (int k = e0; k + 1 < e1; k += 2) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, p->prof_ev[k], p->prof_ev[k + 1]) == cudaSuccess) {
@@ -843,24 +845,30 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st, bool started = false, 
   // ends in e.
   float* cur = l.fs_tt ? l.e2 : l.e;
   auto other = [&](float* e) { return !l.fs_tt ? e : (e == l.e ? l.e2 : l.e); };
+  // A fused level keeps no direction array: its Chebyshev steps read the
+  // previous iterate (the other buffer, null after a start from zero).
+  float* ddir = l.fs_tt ? nullptr : l.d;
+  auto prev = [&](float* e, bool zero) -> float* { return !l.fs_tt ? l.d : (zero ? nullptr : other(e)); };
   StepArgs a;
   memset(&a, 0, sizeof(a));
-  a.r = l.r; a.d = l.d;
+  a.r = l.r;
   // pre-smoothing from e = 0: d = Dinv r / th, e = d
   if (!started) {
     if (vec4_len(l.g.N))
-      ++p->nlaunch, k_cheb_init<true><<<dim3(vgrid(l.g.N), B), MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, cur, l.d);
+      ++p->nlaunch, k_cheb_init<true><<<dim3(vgrid(l.g.N), B), MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, cur, ddir);
     else
-      ++p->nlaunch, k_cheb_init<false><<<dim3(vgrid(l.g.N), B), MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, cur, l.d);
+      ++p->nlaunch, k_cheb_init<false><<<dim3(vgrid(l.g.N), B), MPN_TPB, 0, st>>>(l.g.N, l.r, l.dinv, p->cheb_inv_th, cur, ddir);
   }
+  // profiling brackets one smoothing step per V-cycle (each event is a graph
+  // node of its own, so bracketing every step would slow the sweep): the
+  // second, the first that reads a previous iterate
+  const int prof_s = m >= 3 ? 2 : 1;
   for (int s = 1; s < m; ++s) {
     a.c1 = p->cheb_c1[s]; a.c2 = p->cheb_c2[s];
-    a.x = cur; a.e = other(cur);
-    // profiling brackets one smoothing step per V-cycle (each event is a
-    // graph node of its own, so bracketing every step would slow the sweep)
-    if (prof && s == 1) prof_mark(p, st);
+    a.x = cur; a.e = other(cur); a.d = prev(cur, s == 1);
+    if (prof && s == prof_s) prof_mark(p, st);
     stencil(p, k, a, SM_CHEB, st);
-    if (prof && s == 1) prof_mark(p, st);
+    if (prof && s == prof_s) prof_mark(p, st);
     cur = other(cur);
   }
   // residual, restricted to the coarse level
@@ -874,7 +882,8 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st, bool started = false, 
   const bool start_c = vec4r && k + 1 != p->tail_k0 && k + 1 != p->L - 1;
   if (vec4r)
     ++p->nlaunch, k_restrict_vec4<<<dim3(sblk(lc.g.N / 4), B), MPN_TPB, 0, st>>>(
-        l.g, lc.g, l.t, lc.r, start_c ? lc.dinv : nullptr, p->cheb_inv_th, lc.fs_tt ? lc.e2 : lc.e, lc.d);
+        l.g, lc.g, l.t, lc.r, start_c ? lc.dinv : nullptr, p->cheb_inv_th, lc.fs_tt ? lc.e2 : lc.e,
+        lc.fs_tt ? nullptr : lc.d);
   else
     ++p->nlaunch, k_restrict_vec<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], l.t, lc.r);
   CKL();
@@ -885,12 +894,12 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st, bool started = false, 
     ++p->nlaunch, k_prolong_add<<<gr, MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], lc.e, nullptr, cur);
   // post-smoothing
   a.c1 = 0.f; a.c2 = p->cheb_inv_th;
-  a.x = cur; a.e = other(cur);
+  a.x = cur; a.e = other(cur); a.d = ddir;
   stencil(p, k, a, SM_POST0, st);
   cur = other(cur);
   for (int s = 1; s < m; ++s) {
     a.c1 = p->cheb_c1[s]; a.c2 = p->cheb_c2[s];
-    a.x = cur; a.e = other(cur);
+    a.x = cur; a.e = other(cur); a.d = prev(cur, false);
     const bool dot = zdot && s == m - 1;
     a.part = dot ? zdot : nullptr;
     stencil(p, k, a, dot ? SM_CHEB_DOT : SM_CHEB, st);
@@ -928,6 +937,7 @@ static bool z_in_e(const mpn_problem* p) {
 static int pcg(mpn_problem* p, int iters, cudaStream_t st, bool started) {
   Level& l = p->lv[0];
   float* cur0 = l.fs_tt ? l.e2 : l.e;       // the iterate buffer the V-cycle's pre-smoothing begins in
+  float* ddir0 = l.fs_tt ? nullptr : l.d;   // its direction array (none on a fused level)
   const int N = l.g.N;
   dim3 gv(vgrid(N), p->B);
   const int P = gv.x;
@@ -958,10 +968,10 @@ static int pcg(mpn_problem* p, int iters, cudaStream_t st, bool started) {
       const float* dst = it < iters - 1 ? l.dinv : nullptr;   // a V-cycle follows
       if (v4)
         ++p->nlaunch, k_pcg_xr<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, Prz, pb[c], p->q,
-                                                              p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, l.d);
+                                                              p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, ddir0);
       else
         ++p->nlaunch, k_pcg_xr<false><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, Prz, pb[c], p->q,
-                                                               p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, l.d);
+                                                               p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, ddir0);
       CKL();
       if (it == iters - 1) break;
       TRY(precond(p, st, true, ze));
@@ -975,10 +985,10 @@ static int pcg(mpn_problem* p, int iters, cudaStream_t st, bool started) {
     const float* dst = it < iters - 1 ? l.dinv : nullptr;   // a V-cycle follows
     if (v4)
       ++p->nlaunch, k_pcg_xr<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, Prz, p->pv, p->q,
-                                                            p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, l.d);
+                                                            p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, ddir0);
     else
       ++p->nlaunch, k_pcg_xr<false><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, Prz, p->pv, p->q,
-                                                             p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, l.d);
+                                                             p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, ddir0);
     CKL();
     if (it == iters - 1) break;
     TRY(precond(p, st, true, ze));
@@ -1071,7 +1081,7 @@ static int sweep_body(mpn_problem* p, const double* g_adj, int iters, int P, boo
   // CG's first V-cycle runs on this r: its smoother starts here
   const bool cg = p->desc.krylov != MPN_KRYLOV_FGMRES;
   ++p->nlaunch, k_to32<<<gr, MPN_TPB, 0, st>>>(N, p->r64, slot(p, S_RN), P, l.r, scale, cg ? l.dinv : nullptr,
-                                                p->cheb_inv_th, l.fs_tt ? l.e2 : l.e, l.d);
+                                                p->cheb_inv_th, l.fs_tt ? l.e2 : l.e, l.fs_tt ? nullptr : l.d);
   CKL();
   if (p->desc.krylov == MPN_KRYLOV_FGMRES) TRY(fgmres(p, iters, st));
   else TRY(pcg(p, iters, st, true));

@@ -15,7 +15,10 @@
 // >= 3, such a row is always inside the halo of 1.
 //
 // The operand is read with a halo, so the Chebyshev modes must not update it
-// in place: a.x is read, a.e written (the caller alternates two buffers).
+// in place: a.x is read, a.e written (the caller alternates two buffers).  The
+// Chebyshev direction is x minus the previous iterate, which a.d points to
+// (the other buffer, read at the point, then overwritten by the new iterate;
+// null on the first step from zero): no direction array is kept.
 #pragma once
 #include "mpn_device.cuh"
 #include "mpn_stencil.cuh"
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
     float4 ur = make_float4(0.f, 0.f, 0.f, 0.f), udi = ur, ud = ur;
     if (MODE != SM_APPLY && MODE != SM_APPLYP) ur = ld4(a.r + j);
     if (MODE == SM_POST0 || MODE == SM_CHEB || MODE == SM_CHEB_DOT) udi = ld4(a.dinv + j);
-    if (MODE == SM_CHEB || MODE == SM_CHEB_DOT) ud = ld4(a.d + j);
+    if ((MODE == SM_CHEB || MODE == SM_CHEB_DOT) && a.d) ud = ld4(a.d + j);   // previous iterate
     const float* yr = ys + ((ot + 1) * RYW + ox + 1) * n2;
     const float4 yc = lds4(yr + y0);
     const int pxm = (PER1 && x == 0) ? p + (n1 - 1) * n2 : p - n2;
@@ -397,9 +400,10 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
     } else {
       const float4 res = ur + qv;
       float4 dn = a.c2 * (udi * res);
-      if (MODE == SM_CHEB || MODE == SM_CHEB_DOT) dn = dn + a.c1 * ud;
+      // the direction is the difference of the last two iterates, so no
+      // direction array is read or written (a.d: previous iterate, null = 0)
+      if (MODE == SM_CHEB || MODE == SM_CHEB_DOT) dn = dn + a.c1 * (xj - ud);
       const float4 en = xj + dn;
-      *reinterpret_cast<float4*>(a.d + j) = dn;
       *reinterpret_cast<float4*>(a.e + j) = en;
       if (MODE == SM_CHEB_DOT) acc += en.x * ur.x + en.y * ur.y + en.z * ur.z + en.w * ur.w;   // <e', r>
     }

@@ -183,7 +183,8 @@ __device__ __forceinline__ void vst(float* a, int i, float4 v) {
 // The smoother iterates e <- e + d with
 //   d_0 = Dinv r_0 / th,  d_k = c1_k d_{k-1} + c2_k Dinv r_k,
 // r_k = r - S e_k, Dinv already scaled by 1 / lambda_max(Dinv S).
-// First smoothing step from e = 0 (look-ahead form): d = Dinv r / th, e = d.
+// First smoothing step from e = 0 (look-ahead form): d = Dinv r / th, e = d
+// (d null on levels that keep no direction array).
 template <bool V4>
 __global__ void k_cheb_init(int N, const float* __restrict__ r, const float* __restrict__ dinv, float inv_th,
                             float* __restrict__ e, float* __restrict__ d) {
@@ -192,7 +193,7 @@ __global__ void k_cheb_init(int N, const float* __restrict__ r, const float* __r
   GRID_LOOP(i, n) {
     float4 v = inv_th * (vld<V4>(dinv + off, i) * vld<V4>(r + off, i));
     vst<V4>(e + off, i, v);
-    vst<V4>(d + off, i, v);
+    if (d) vst<V4>(d + off, i, v);
   }
 }
 
@@ -332,7 +333,7 @@ __global__ void k_restrict_vec4(Grid gf, Grid gc, const float* __restrict__ fine
     if (dinv_c) {
       const float4 v = inv_th * (di * acc);
       *reinterpret_cast<float4*>(e_c + jc) = v;
-      *reinterpret_cast<float4*>(d_c + jc) = v;
+      if (d_c) *reinterpret_cast<float4*>(d_c + jc) = v;
     }
   }
 }
@@ -707,7 +708,7 @@ __global__ void k_pcg_xr(int N, const double* __restrict__ part_rz, const double
     if (dinv) {
       const float4 v = inv_th * (dv * rn);
       vst<V4>(e + off, i, v);
-      vst<V4>(d + off, i, v);
+      if (d) vst<V4>(d + off, i, v);
     }
   }
 }
@@ -902,7 +903,7 @@ __global__ void k_to32(int N, const double* __restrict__ r64, const double* __re
     if (dinv) {
       const float v = inv_th * (dinv[off + p] * r);
       e[off + p] = v;
-      d[off + p] = v;
+      if (d) d[off + p] = v;
     }
   }
 }

@@ -24,8 +24,8 @@ struct StepArgs {
   const float* y;     // pass-1 output
   const float* r;     // right-hand side at this level
   const float* dinv;  // Chebyshev-scaled inverse diagonal
-  float* e;           // iterate (modes 0, 1: updated in place; it is x)
-  float* d;           // direction (modes 0, 1)
+  float* e;           // iterate (modes 0, 1: updated in place; it is x; fused step: the new iterate)
+  float* d;           // direction (modes 0, 1); fused step, modes 1, 4: the previous iterate (null = 0)
   float* out;         // mode 2: r - S x;  mode 3: S x
   double* part;       // mode 3: partials of <x, S x>; mode 4: of <e', r> (nullable)
   int* err;           // set when a bounded wait gives up (fused step; nullable)
