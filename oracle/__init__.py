@@ -10,10 +10,11 @@ parameter gradients from the saddle-point system of Eq. 11 and the gradient
 formulas that follow it.
 
 Modules
-  assemble   rows of A and d (Eqs. 3-8), boundary set, row counts
-  solve      least-squares solve via Eq. 10 (and via Eq. 9 as a cross-check)
-  grad       adjoint solve (Eq. 11) and dL/dc, dL/db, dL/domega
-  cg64       FP64 conjugate gradient on the normal equations (Eq. 9) over the
-             assembled CSR matrix, in plain C with OpenMP, for grids too large
-             for the direct factorisation
+  assemble      rows of A and d (Eqs. 3-8), boundary set, row counts
+  solve         least-squares solve via Eq. 10 (and via Eq. 9 as a cross-check)
+  grad          adjoint solve (Eq. 11) and dL/dc, dL/db, dL/domega
+  manufactured  data whose least-squares solution is known exactly at any grid
+                size (consistent equation and boundary data for any u; adjoint
+                sources on u with their exact solution), for full-size checks
+  conv          the warm-start network's 3x3x3 convolution, written plainly
 """

@@ -132,6 +132,25 @@ def box_filter(x, periodic):
     return y
 
 
+def low_mode_field(rng, geom, modes=4):
+    """Sum of `modes` products of a random quadratic in t and a random
+    lowest-wavenumber cosine (wavenumbers 0..2 per spatial dimension, over the
+    grid's extent) with N(0, 1) amplitudes: a smooth grid function (N,) used
+    as a manufactured solution."""
+    n = tuple(geom["n"])
+    coords = [np.arange(k) / (k - 1 if (d == 0 or not geom["periodic"][d]) else k)
+              for d, k in enumerate(n)]
+    mesh = np.meshgrid(*coords, indexing="ij")
+    acc = np.zeros(mesh[0].shape)
+    for _ in range(modes):
+        a = rng.normal(size=3)
+        ks = rng.integers(0, 3, size=len(n) - 1)
+        phase = rng.uniform(0.0, 2.0 * math.pi)
+        arg = phase + sum(2.0 * math.pi * k * m for k, m in zip(ks, mesh[1:]))
+        acc += rng.normal() * (a[0] + a[1] * mesh[0] + a[2] * mesh[0] ** 2) * np.cos(arg)
+    return acc.ravel()
+
+
 def advection_diffusion_1d(batch=4, n=(32, 32), seed_base=1000, stencil=3,
                            final_time_rows=False):
     """u_t + a u_x - nu u_xx = f on t in [0,1], x in [0,1] (Dirichlet in x).

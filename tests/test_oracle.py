@@ -390,3 +390,73 @@ def test_elimination_route_matches_kkt_route_3d():
     z2, lam2, _ = osv.solve_lsq_elim(A, d, 7)
     assert np.linalg.norm(z1 - z2) <= 1e-9 * np.linalg.norm(z1)
     assert osv.normal_residual(A, d, z2) < 1e-12
+
+
+# ------------------------------------------- data with a known LS solution
+@pytest.mark.parametrize("n,per,final", [((6, 7), (False, False), False), ((6, 8), (False, True), True),
+                                         ((5, 6, 8), (False, True, False), False),
+                                         ((5, 6, 8), (False, False, False), True),
+                                         ((5, 8, 8), (False, True, True), False),
+                                         ((4, 3, 5), (False, False, True), False)])
+def test_manufactured_data_is_consistent_for_any_u(n, per, final):
+    """oracle.manufactured: for a white-noise u (no smoothness at all) and
+    random coefficient fields, the assembled system (Eqs. 3-8) with the
+    manufactured b and omega has zero residual at z_e, and the saddle-point
+    solve (Eq. 10) returns z_e with a zero dual.  A wrong weight, sign or
+    step power in any difference form, or a missing edge case, leaves a
+    residual of order one."""
+    w = wl.random_problem(51, n, per, final_time_rows=final)
+    rng = np.random.default_rng(52)
+    N = int(np.prod(n))
+    c = w.full_coeff()[:, 0]
+    u = rng.normal(size=N)
+    from oracle import manufactured as mf
+    z, b, om = mf.consistent_data(w.geom, c, u)
+    assert np.array_equal(z[0], u)
+    A, d, kind, owner = asm.assemble(w.geom, c, b, om)
+    assert np.linalg.norm(A @ z.ravel() - d) <= 1e-13 * np.linalg.norm(d)
+    zs, lam, kkt = osv.solve_lsq(A, d)
+    assert np.linalg.norm(zs - z.ravel()) <= 1e-10 * np.linalg.norm(z)
+    assert np.abs(lam).max() <= 1e-9 * np.abs(d).max()
+    # the backward system (Eq. 11) with g = A^T A z' returns z' for any z'
+    zp = rng.normal(size=A.shape[1])
+    dz, dlam = og.adjoint(kkt, A.T @ (A @ zp))
+    assert np.linalg.norm(dz - zp) <= 1e-9 * np.linalg.norm(zp)
+    assert np.linalg.norm(dlam + A @ zp) <= 1e-9 * np.linalg.norm(A @ zp)
+
+
+def test_manufactured_data_matches_polynomial_derivatives():
+    """On a separable quadratic in every non-periodic dimension the difference
+    forms are exact, so the manufactured derivative unknowns equal the
+    analytic derivatives (pins the 1/s, 1/s^2 scaling and the variable order)."""
+    from oracle import manufactured as mf
+    g = _geom((5, 6, 7), (False, False, False), lengths=(1.0, 2.0, 0.5))
+    t, x, y = (np.arange(k) * s for k, s in zip(g["n"], g["step"]))
+    T, X, Y = np.meshgrid(t, x, y, indexing="ij")
+    u = (1 + 2 * T - 3 * T * T) * (0.5 - X + 0.25 * X * X) * (2 + Y + 4 * Y * Y)
+    z = mf.consistent_z(g, u.ravel())
+    pt, px, py = (1 + 2 * T - 3 * T * T), (0.5 - X + 0.25 * X * X), (2 + Y + 4 * Y * Y)
+    ref = [u, (2 - 6 * T) * px * py, -6 * px * py, pt * (-1 + 0.5 * X) * py, pt * 0.5 * py,
+           pt * px * (1 + 8 * Y), pt * px * 8]
+    for v in range(7):
+        np.testing.assert_allclose(z[v], ref[v].ravel(), rtol=1e-11, atol=1e-11)
+
+
+@pytest.mark.parametrize("n,per,final", [((6, 8), (False, True), False), ((5, 6, 8), (False, True, True), False),
+                                         ((5, 6, 7), (False, False, False), True)])
+def test_eliminated_pair_solves_the_adjoint_system(n, per, final):
+    """oracle.manufactured.eliminated_pair: g vanishes on every derivative
+    unknown, and the backward saddle-point system (Eq. 11) with this g returns
+    z_e (the oracle's KKT route, which never forms the point blocks)."""
+    from oracle import manufactured as mf
+    w = wl.random_problem(61, n, per, final_time_rows=final)
+    c = w.full_coeff()[:, 0]
+    A, d, kind, owner = asm.assemble(w.geom, c, w.rhs[0], w.omega[0])
+    V, N = asm.n_vars(len(n)), int(np.prod(n))
+    u = wl.low_mode_field(np.random.default_rng(62), w.geom)
+    z, g, resid = mf.eliminated_pair(A, V, u)
+    assert resid < 1e-12
+    assert np.array_equal(z[:N], u) and not np.any(g[N:])
+    kkt = osv.KKT(A)
+    dz, dlam = og.adjoint(kkt, g)
+    assert np.linalg.norm(dz - z) <= 1e-9 * np.linalg.norm(z)
