@@ -81,10 +81,12 @@ typedef struct mpn_desc {
   int fused_coarse;       /* 1: the coarse levels whose data fit in one thread-block cluster's shared
                              memory per instance run as one kernel per V-cycle; 0: one kernel per
                              operator pass at every level (same arithmetic) */
-  int fused_step;         /* 1: on levels with float4 rows (D = 3, n_y % 4 == 0, 8 <= n_y <= 128,
-                             n_x % 4 == 0, n_t % 4 == 0) both operator passes of a smoothing step,
-                             residual or apply run as one kernel through shared memory; 0: two kernels
-                             (same arithmetic) */
+  int fused_step;         /* 1: on levels with float4 rows (D = 3, n_y % 4 == 0, n_y >= 8,
+                             n_x % 4 == 0) both operator passes of a smoothing step, residual or apply
+                             run as one kernel through shared memory, on tiles of whole y rows where
+                             n_y <= 128 (n_t % 4 == 0) and of 64-point y segments where n_y > 128
+                             (n_y % 64 == 0, n_t % 8 == 0); 2: the same with y segments wherever
+                             they apply (n_y >= 128); 0: two kernels (same arithmetic) */
   int krylov;             /* inner FP32 solver of each refinement sweep: MPN_KRYLOV_CG (conjugate
                              gradients) or MPN_KRYLOV_FGMRES (flexible GMRES(m), m = the sweep's
                              iteration count, with the same V-cycle as right preconditioner, the
@@ -144,7 +146,8 @@ int mpn_forward(mpn_problem* p, const float* fields, const float* scalars,
  * [B][V][N], solves A^T A d_z = g_z and writes dl/dfields [F][B][N],
  * dl/dscalars [V][B] (entries of field-backed v are written as 0),
  * dl/drhs [B][N] and dl/domega [B][N] (zero off the boundary set).
- * dz (nullable) receives d_z.  The duals lambda* and d_lambda are formed in
+ * dz (nullable) receives d_z [B][V][N] and dz64 (nullable) the same in FP64
+ * (double), as the refinement holds it.  The duals lambda* and d_lambda are formed in
  * FP64 from the FP64 forward solution the problem keeps.
  * flags bit 0 (MPN_REUSE_SETUP): the data are those of the last mpn_forward
  * on this problem, so its multigrid setup and FP64 solution are reused;
@@ -154,7 +157,7 @@ int mpn_forward(mpn_problem* p, const float* fields, const float* scalars,
 int mpn_adjoint(mpn_problem* p, const float* fields, const float* scalars,
                 const float* rhs, const float* omega, const float* z,
                 const float* g_z, float* dfields, float* dscalars, float* drhs,
-                float* domega, float* dz, int flags, mpn_stats* stats, void* stream);
+                float* domega, float* dz, double* dz64, int flags, mpn_stats* stats, void* stream);
 
 /* dl/dz of l = mean over (b, i) of (u - target)^2, written into g_z [B][V][N]
  * (zero on the derivative unknowns): the loss used by the benchmarks. */
@@ -168,10 +171,13 @@ int mpn_apply_reduced(mpn_problem* p, const float* fields, const float* scalars,
                       const float* u, float* q, void* stream);
 
 /* Live timing of the finest-level Chebyshev smoothing step (the solver's
- * dominant kernel work): CUDA events around each of its launches on the
+ * dominant kernel work): CUDA events around one such step per V-cycle on the
  * solve stream.  Reads the totals accumulated since the last reset (time in
- * ms, launches, algorithmic bytes = 4 (7 + F) N B per launch: e, d, r, Dinv,
- * rho and the F fields read once, e and d written) and the number of kernels
+ * ms, launches, algorithmic bytes per launch = 4 (6 + F) N B where the level
+ * runs the fused step: the iterate, the previous iterate, r, Dinv, rho and
+ * the F fields read once, the new iterate written; 4 (7 + F) N B on the
+ * two-pass kernels: e, d, r, Dinv, rho and the fields read, e and d written)
+ * and the number of kernels
  * this problem launched; then, if enable >= 0, switches timing on (1) or off
  * (0) and resets the totals.  Outputs are host pointers (nullable). */
 int mpn_profile(mpn_problem* p, int enable, double* ms_total, long long* launches, double* bytes,
@@ -188,10 +194,12 @@ int mpn_profile(mpn_problem* p, int enable, double* ms_total, long long* launche
  *   desc     host; grid, batch, coefficient layout (solver fields unused)
  *   fields   device [F][B][N], scalars device [V][B], u device [B][N]
  *   q        device [B][N] output, q = S u
- * B * N above MPN_NOALLOC_MAX_POINTS returns MPN_ERR_UNSUPPORTED.  The first
- * call on a device resolves the array's device address for that device
- * (with that device current); make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race.
+ * B * N above MPN_NOALLOC_MAX_POINTS, or B above 65535, returns
+ * MPN_ERR_UNSUPPORTED.  Every call looks up the array's device address on
+ * the current device (a host-side query that allocates nothing); the first
+ * call on a device also loads the library's device code there, so make it
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU race.
  * Asynchronous on `stream`. */
 #define MPN_NOALLOC_MAX_POINTS 4194304
 int mpn_apply_reduced_noalloc(const mpn_desc* desc, const float* fields, const float* scalars,

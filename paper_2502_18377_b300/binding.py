@@ -56,7 +56,7 @@ EXPORTS = {
     "mpn_levels": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "mpn_fused_level": (ctypes.c_int, [_P]),
     "mpn_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(MpnStats), _P]),
-    "mpn_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int,
+    "mpn_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int,
                                    ctypes.POINTER(MpnStats), _P]),
     "mpn_mse_grad": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "mpn_apply_reduced": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -153,8 +153,29 @@ def make_desc(geom: dict, batch: int, field_of, nfields: int) -> MpnDesc:
     return d
 
 
+def _check_numel(name, t, n):
+    """float32 with exactly n elements (the C ABI reads and writes n floats)."""
+    if t.dtype != torch.float32:
+        raise ValueError(f"{name} must be float32, got {t.dtype}")
+    if t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
+
+
 def apply_reduced_noalloc(desc: MpnDesc, fields, scalars, u, q):
-    """q = S u through the allocation-free entry point (q preallocated)."""
+    """q = S u through the allocation-free entry point (q preallocated).
+
+    The descriptor is built apart from the tensors, so their sizes are checked
+    against it here: a short q or u would otherwise be read or written out of
+    bounds by the kernels."""
+    N = 1
+    for k in range(desc.ndim):
+        N *= desc.n[k]
+    B, V = desc.batch, 1 + 2 * desc.ndim
+    _check_numel("u", u, B * N)
+    _check_numel("q", q, B * N)
+    _check_numel("scalars", scalars, V * B)
+    if desc.nfields:
+        _check_numel("fields", fields, desc.nfields * B * N)
     lib = load()
     s = lib.mpn_apply_reduced_noalloc(ctypes.byref(desc), _ptr(fields) if desc.nfields else None, _ptr(scalars),
                                       _ptr(u), _ptr(q), _stream())
@@ -188,7 +209,7 @@ class Solver:
         d.tol, d.max_refine, d.inner_iters = tol, max_refine, inner_iters
         d.cheb_degree, d.coarse_min, d.max_coarse = cheb_degree, coarse_min, max_coarse
         d.fused_coarse = int(bool(fused_coarse))
-        d.fused_step = int(bool(fused_step))
+        d.fused_step = int(fused_step)
         d.krylov = KRYLOV[krylov]
         d.coarsen_time = int(bool(coarsen_time))
         d.direct = int(bool(direct))
@@ -246,8 +267,9 @@ class Solver:
             raise MpnError(s, "mpn_forward")
         return z
 
-    def adjoint(self, fields, scalars, rhs, omega, z, g_z, reuse_setup=False, want_dz=False):
-        """Returns (dfields, dscalars, drhs, domega[, dz])."""
+    def adjoint(self, fields, scalars, rhs, omega, z, g_z, reuse_setup=False, want_dz=False, dz64=None):
+        """Returns (dfields, dscalars, drhs, domega[, dz]); dz64 (float64
+        [B][V][N]), if given, receives d_z as the FP64 refinement holds it."""
         self._inputs(fields, scalars, rhs, omega)
         _check_f32("g_z", g_z, (self.B, self.V, self.N))
         dev = rhs.device
@@ -256,10 +278,12 @@ class Solver:
         drhs = torch.empty((self.B, self.N), device=dev, dtype=torch.float32)
         dom = torch.empty((self.B, self.N), device=dev, dtype=torch.float32)
         dz = torch.empty((self.B, self.V, self.N), device=dev, dtype=torch.float32) if want_dz else None
+        if dz64 is not None and (dz64.dtype != torch.float64 or tuple(dz64.shape) != (self.B, self.V, self.N)):
+            raise ValueError("dz64 must be float64 [B][V][N]")
         st = MpnStats()
         s = self.lib.mpn_adjoint(self._h, _ptr(fields) if self.F else None, _ptr(scalars), _ptr(rhs),
                                  _ptr(omega), _ptr(z), _ptr(g_z), _ptr(dfields), _ptr(dscal), _ptr(drhs),
-                                 _ptr(dom), _ptr(dz), MPN_REUSE_SETUP if reuse_setup else 0,
+                                 _ptr(dom), _ptr(dz), _ptr(dz64), MPN_REUSE_SETUP if reuse_setup else 0,
                                  ctypes.byref(st), _stream())
         self.last_stats = st.as_dict()
         if s != 0:
@@ -284,6 +308,10 @@ class Solver:
         return ms.value, n.value, by.value, k.value
 
     def apply_reduced(self, fields, scalars, u):
+        _check_f32("scalars", scalars, (self.V, self.B))
+        if self.F > 0:
+            _check_f32("fields", fields, (self.F, self.B, self.N))
+        _check_numel("u", u, self.B * self.N)
         q = torch.empty_like(u)
         s = self.lib.mpn_apply_reduced(self._h, _ptr(fields) if self.F else None, _ptr(scalars), _ptr(u),
                                        _ptr(q), _stream())

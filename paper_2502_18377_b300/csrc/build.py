@@ -10,12 +10,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 PKG = os.path.dirname(HERE)
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libmpn.so")
-SOURCES = [os.path.join(HERE, "mpn.cu"), os.path.join(HERE, "mpn_noalloc.cu"), os.path.join(HERE, "mpn_conv.cu")]
-DEPS = SOURCES + [os.path.join(HERE, f) for f in os.listdir(HERE) if f.endswith(".cuh")] + \
+SOURCES = [os.path.join(HERE, f) for f in ("mpn.cu", "mpn_step_row.cu", "mpn_step_y.cu", "mpn_noalloc.cu",
+                                          "mpn_conv.cu")]
+DEPS = SOURCES + [os.path.join(HERE, f) for f in os.listdir(HERE) if f.endswith((".cuh", ".h"))] + \
     [os.path.join(ROOT, "include", "mpn.h")]
+OBJ_DIR = os.path.join(PKG, "_build")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]
+              "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
 
 def nvcc():
@@ -33,16 +35,35 @@ def up_to_date():
 
 
 def build(force=False, verbose=False):
+    """Compiles every translation unit to an object in parallel, then links
+    the shared library."""
     if not force and up_to_date():
         return LIB
-    cmd = [nvcc()] + NVCC_FLAGS + ["-I", os.path.join(ROOT, "include"), "-o", LIB] + SOURCES
+    from concurrent.futures import ThreadPoolExecutor
+    os.makedirs(OBJ_DIR, exist_ok=True)
+    inc = ["-I", os.path.join(ROOT, "include")]
+
+    def compile_one(src):
+        obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
+        cmd = [nvcc()] + NVCC_FLAGS + inc + ["-c", src, "-o", obj]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        return obj, r
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        results = list(ex.map(compile_one, SOURCES))
+    for obj, r in results:
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
+        if verbose and r.stderr:
+            print(r.stderr)
+    cmd = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", LIB] + [o for o, _ in results]
     if verbose:
-        print(" ".join(cmd))
+        print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
-    if verbose and r.stderr:
-        print(r.stderr)
+        raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
     return LIB
 
 

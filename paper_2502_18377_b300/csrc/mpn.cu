@@ -25,6 +25,7 @@
 #include "mpn_stencil.cuh"
 #include "mpn_tail.cuh"
 #include "mpn_fused.cuh"
+#include "mpn_step.h"
 
 #define MAXL 16
 
@@ -47,7 +48,9 @@ struct Level {
   int vec4 = 0;        // float4 stencil kernels apply (D = 3, n_y % 4 == 0)
   int papply = 0;      // partial sums per instance written by an operator apply
   int cz[3];           // dims halved from this level to the next
-  int fs_tt = 0;       // > 0: operator steps as one fused kernel with TT-plane tiles (k_step3)
+  int fs_tt = 0;       // > 0: operator steps as one fused kernel with TT-plane tiles
+  int fs_ty = 0;       // fused tiles of fs_ty y points (k_step3y), or of whole y rows when 0 (k_step3)
+  int fs_layout = SL_ANY;  // compile-time coefficient layout of the fused kernels
   float* e2 = nullptr; // second iterate buffer of the fused smoother (the operand is read with a halo)
   float* fields = nullptr;  // [F][B][N]
   float *rho = nullptr, *dinv = nullptr;
@@ -256,35 +259,23 @@ extern "C" int mpn_levels(const mpn_problem* p, int* nl, int* shapes) {
   return MPN_OK;
 }
 
+// rows of at most this many points stay whole in a fused tile; wider rows
+// (a multiple of 64, >= 128) are split into 64-point y segments
 #define FS_MAX_NY 128
 // largest whole-problem system of the direct path (unknowns per instance)
 #define MPN_DIRECT_MAX 4096
 // shared memory of the coarsest-inverse kernel (floats)
 #define INV_SMEM_FLOATS (224 * 1024 / 4)
-// c_0, c_xx and c_yy fields, every other coefficient a per-instance scalar
-#define FS_MASK_RD ((1 << 0) | (1 << 4) | (1 << 6))
-// the same with c_xx and c_yy one field
-#define FS_MASK_RDI (FS_MASK_RD | FS_SHARE46)
-static size_t fs_smem(int tt, int ny) { return sizeof(float) * (size_t)(fs_rows_x(tt) + fs_rows_y(tt)) * ny; }
-// Opt the fused step kernels into the shared memory of the largest tile.
+// Opt the fused step kernels into the shared memory of their largest tile.
 static int fs_set_smem() {
-  int bytes = (int)fs_smem(8, FS_MAX_NY);
-  cudaError_t e = cudaSuccess;
-#define FS_ATTR(M, T, P1, P2, MK) \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step3<M, T, P1, P2, MK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-#define FS_ATTR_M(T, P1, P2, MK) FS_ATTR(SM_POST0, T, P1, P2, MK); FS_ATTR(SM_CHEB, T, P1, P2, MK); FS_ATTR(SM_RES, T, P1, P2, MK); FS_ATTR(SM_APPLY, T, P1, P2, MK); FS_ATTR(SM_CHEB_DOT, T, P1, P2, MK); FS_ATTR(SM_APPLYP, T, P1, P2, MK)
-#define FS_ATTR_P(T) FS_ATTR_M(T, true, true, FS_ANY); FS_ATTR_M(T, true, false, FS_ANY); FS_ATTR_M(T, false, true, FS_ANY); FS_ATTR_M(T, false, false, FS_ANY); FS_ATTR_M(T, true, true, FS_MASK_RD); FS_ATTR_M(T, true, true, FS_MASK_RDI)
-  FS_ATTR_P(8);
-  FS_ATTR_P(4);
-#undef FS_ATTR_P
-#undef FS_ATTR_M
-#undef FS_ATTR
-  return e == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
+  return (step_row_attrs() == 0 && step_y_attrs() == 0) ? MPN_OK : MPN_ERR_CUDA;
 }
 
-// Compile-time coefficient layout of the FP64 kernels: FS_MASK_RDI (c_xx and
-// c_yy one field), FS_MASK_RD, or 0 (layout read at run time).
+// Compile-time coefficient layout of the FP64 kernels and the fused coarse
+// end: FS_MASK_RDI (c_xx and c_yy one field), FS_MASK_RD, FS_MASK_TR, or 0
+// (layout read at run time).
 static int fp64_layout(const mpn_problem* p) {
+  if (p->field_mask == FS_MASK_TR) return FS_MASK_TR;
   if (p->field_mask != FS_MASK_RD) return 0;
   return p->desc.field_of[4] == p->desc.field_of[6] ? FS_MASK_RDI : FS_MASK_RD;
 }
@@ -292,6 +283,7 @@ static int fp64_layout(const mpn_problem* p) {
 // coefficient layout.
 static const void* tail_fn(const mpn_problem* p) {
   if (p->D == 3 && fp64_layout(p) == FS_MASK_RDI) return (const void*)k_vtail<3, FS_MASK_RDI>;
+  if (p->D == 3 && fp64_layout(p) == FS_MASK_TR) return (const void*)k_vtail<3, FS_MASK_TR>;
   if (p->D == 3) return p->field_mask == FS_MASK_RD ? (const void*)k_vtail<3, FS_MASK_RD> : (const void*)k_vtail<3, FS_ANY>;
   return (const void*)k_vtail<2, FS_ANY>;
 }
@@ -408,6 +400,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   if (d.inner_iters < 1 || d.max_refine < 1 || d.cheb_degree < 1 || d.cheb_degree > 30) return MPN_ERR_INVALID_ARG;
   if (d.coarse_min < 3 || !(d.tol > 0)) return MPN_ERR_INVALID_ARG;
   if (d.krylov != MPN_KRYLOV_CG && d.krylov != MPN_KRYLOV_FGMRES) return MPN_ERR_INVALID_ARG;
+  if (d.fused_step < 0 || d.fused_step > 2) return MPN_ERR_INVALID_ARG;
   int V = 1 + 2 * d.ndim;
   for (int k = 0; k < d.ndim; ++k) {
     if (d.n[k] < 3 || !(d.step[k] > 0)) return MPN_ERR_INVALID_ARG;
@@ -455,11 +448,26 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
     Level& l = p->lv[k];
     l.vec4 = (p->D == 3 && l.g.n[2] % 4 == 0 && l.g.n[2] >= 8) ? 1 : 0;
     l.papply = l.vec4 ? sblk(l.g.N / 4) : sblk(l.g.N);
-    // fused operator step: whole y rows of at most FS_MAX_NY points in shared
-    // memory, tiles that divide the t and x extents
-    if (d.fused_step && l.vec4 && l.g.n[2] <= FS_MAX_NY && l.g.n[1] % FS_TX == 0) {
-      l.fs_tt = l.g.n[0] % 8 == 0 ? 8 : (l.g.n[0] % 4 == 0 ? 4 : 0);
-      if (l.fs_tt) l.papply = (l.g.n[0] / l.fs_tt) * (l.g.n[1] / FS_TX);
+    // fused operator step: tiles that divide the t and x extents, with whole
+    // y rows of at most FS_MAX_NY points, or 64-point y segments of wider rows
+    // (or of rows >= 128 with fused_step = 2)
+    if (d.fused_step && l.vec4 && l.g.n[1] % FS_TX == 0) {
+      const int n0 = l.g.n[0], n2 = l.g.n[2];
+      const bool per1 = l.g.per[1], per2 = l.g.per[2];
+      const bool rd = p->field_mask == FS_MASK_RD;
+      l.fs_layout = !(per1 && per2) ? SL_ANY
+                    : rd ? (d.field_of[4] == d.field_of[6] ? SL_RDI : SL_RD)
+                    : p->field_mask == FS_MASK_TR ? SL_TR : SL_ANY;
+      const int tt = n0 % 8 == 0 ? 8 : (n0 % 4 == 0 ? 4 : 0);
+      const bool split_ok = n2 % 64 == 0 && n2 >= 128 && step_y_has(8, 64, per1, per2, l.fs_layout) && n0 % 8 == 0;
+      const bool whole_ok = tt && n2 <= FS_MAX_NY && step_row_has(tt, per1, per2, l.fs_layout);
+      if (split_ok && (d.fused_step == 2 || !whole_ok)) { l.fs_tt = 8; l.fs_ty = 64; }
+      else if (whole_ok) { l.fs_tt = tt; l.fs_ty = 0; }
+      if (l.fs_tt) {
+        l.papply = step_ctas(StepTile{l.fs_tt, l.fs_ty}, l.g);
+        if (l.papply > MPN_PMAX) l.fs_tt = l.fs_ty = 0;   // too many partial sums per instance
+      }
+      if (!l.fs_tt) l.papply = sblk(l.g.N / 4);
     }
   }
   Level& lc = p->lv[p->L - 1];
@@ -572,29 +580,10 @@ static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st
   if (!a.dinv) a.dinv = l.dinv;
   if (!a.err) a.err = p->kerr;
   if (l.fs_tt) {
-    dim3 gs((l.g.n[0] / l.fs_tt) * (l.g.n[1] / FS_TX), p->B);
-    size_t sm = fs_smem(l.fs_tt, l.g.n[2]);
-#define FS_LAUNCH(T, P1, P2, MK)                                                                     \
-  switch (mode) {                                                                                    \
-    case SM_POST0: ++p->nlaunch, k_step3<SM_POST0, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break; \
-    case SM_CHEB: ++p->nlaunch, k_step3<SM_CHEB, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;   \
-    case SM_CHEB_DOT: ++p->nlaunch, k_step3<SM_CHEB_DOT, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break; \
-    case SM_APPLYP: ++p->nlaunch, k_step3<SM_APPLYP, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break; \
-    case SM_RES: ++p->nlaunch, k_step3<SM_RES, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;     \
-    default: ++p->nlaunch, k_step3<SM_APPLY, T, P1, P2, MK><<<gs, FS_TPB, sm, st>>>(l.g, cf, l.rho, a); break;     \
-  }
-#define FS_LAUNCH_T(P1, P2, MK) if (l.fs_tt == 8) { FS_LAUNCH(8, P1, P2, MK) } else { FS_LAUNCH(4, P1, P2, MK) }
-    // compile-time coefficient layout for the common case of a reaction term
-    // and an isotropic diffusion field with scalar first-order and time terms
-    if (l.g.per[1] && l.g.per[2] && p->field_mask == FS_MASK_RD && p->desc.field_of[4] == p->desc.field_of[6]) {
-      FS_LAUNCH_T(true, true, FS_MASK_RDI)
-    } else if (l.g.per[1] && l.g.per[2] && p->field_mask == FS_MASK_RD) { FS_LAUNCH_T(true, true, FS_MASK_RD) }
-    else if (l.g.per[1] && l.g.per[2]) { FS_LAUNCH_T(true, true, FS_ANY) }
-    else if (l.g.per[1]) { FS_LAUNCH_T(true, false, FS_ANY) }
-    else if (l.g.per[2]) { FS_LAUNCH_T(false, true, FS_ANY) }
-    else { FS_LAUNCH_T(false, false, FS_ANY) }
-#undef FS_LAUNCH_T
-#undef FS_LAUNCH
+    const size_t sm = step_smem(StepTile{l.fs_tt, l.fs_ty}, l.g.n[2]);
+    ++p->nlaunch;
+    if (l.fs_ty) step_y_launch(mode, l.fs_tt, l.fs_ty, l.g.per[1], l.g.per[2], l.fs_layout, p->B, sm, st, l.g, cf, l.rho, a);
+    else step_row_launch(mode, l.fs_tt, l.g.per[1], l.g.per[2], l.fs_layout, p->B, sm, st, l.g, cf, l.rho, a);
     return;
   }
   if (l.vec4) {
@@ -1057,6 +1046,9 @@ static int residual64(mpn_problem* p, const double* u, const double* g_adj, doub
   } else if (p->D == 3 && fp64_layout(p) == FS_MASK_RD) {
     ++p->nlaunch, k_res64_y<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
     ++p->nlaunch, k_res64_q<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
+  } else if (p->D == 3 && fp64_layout(p) == FS_MASK_TR) {
+    ++p->nlaunch, k_res64_y<3, FS_MASK_TR><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    ++p->nlaunch, k_res64_q<3, FS_MASK_TR><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
   } else if (p->D == 3) {
     ++p->nlaunch, k_res64_y<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
     ++p->nlaunch, k_res64_q<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
@@ -1211,6 +1203,8 @@ static int forward_impl(mpn_problem* p, const float* fields, const float* scalar
     ++p->nlaunch, k_recover<3, FS_MASK_RDI><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
   else if (p->D == 3 && fp64_layout(p) == FS_MASK_RD)
     ++p->nlaunch, k_recover<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
+  else if (p->D == 3 && fp64_layout(p) == FS_MASK_TR)
+    ++p->nlaunch, k_recover<3, FS_MASK_TR><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
   else if (p->D == 3)
     ++p->nlaunch, k_recover<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
   else
@@ -1234,7 +1228,8 @@ extern "C" int mpn_forward(mpn_problem* p, const float* fields, const float* sca
 
 extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* scalars, const float* rhs,
                            const float* omega, const float* z, const float* g_z, float* dfields, float* dscalars,
-                           float* drhs, float* domega, float* dz, int flags, mpn_stats* stats, void* stream) {
+                           float* drhs, float* domega, float* dz, double* dz64, int flags, mpn_stats* stats,
+                           void* stream) {
   if (!p) return MPN_ERR_INVALID_ARG;
   TRY(check_ptrs(scalars, rhs));
   TRY(check_ptrs(omega, g_z));
@@ -1256,6 +1251,7 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
   if (p->D == 3) {
     if (fp64_layout(p) == FS_MASK_RDI) ++p->nlaunch, k_adj_kappa<3, FS_MASK_RDI><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
     else if (fp64_layout(p) == FS_MASK_RD) ++p->nlaunch, k_adj_kappa<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
+    else if (fp64_layout(p) == FS_MASK_TR) ++p->nlaunch, k_adj_kappa<3, FS_MASK_TR><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
     else ++p->nlaunch, k_adj_kappa<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, g_z, p->kap);
     ++p->nlaunch, k_adj_rhs<3><<<gr, MPN_TPB, 0, st>>>(l.g, g_z, p->kap, p->g64);
   } else {
@@ -1269,9 +1265,10 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
   double* gp = slot(p, S_GR0);
 #define GRAD_LAUNCH(DD, MK)                                                                              \
   ++p->nlaunch, k_gradients<DD, MK><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->rhs, p->uf64, p->u64, g_z, dfields, \
-                                                           drhs, domega, dz, gp)
+                                                           drhs, domega, dz, dz64, gp)
   if (p->D == 3 && fp64_layout(p) == FS_MASK_RDI) GRAD_LAUNCH(3, FS_MASK_RDI);
   else if (p->D == 3 && fp64_layout(p) == FS_MASK_RD) GRAD_LAUNCH(3, FS_MASK_RD);
+  else if (p->D == 3 && fp64_layout(p) == FS_MASK_TR) GRAD_LAUNCH(3, FS_MASK_TR);
   else if (p->D == 3) GRAD_LAUNCH(3, RES_ANY);
   else GRAD_LAUNCH(2, RES_ANY);
 #undef GRAD_LAUNCH

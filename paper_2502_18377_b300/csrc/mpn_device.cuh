@@ -24,7 +24,19 @@
 #include <stdint.h>
 
 #define MPN_TPB 256
+#define GRID_LOOP(p, N) for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (N); p += gridDim.x * blockDim.x)
 #define MPN_PMAX 4096  // partial sums per instance (max CTAs per instance)
+
+// Coefficient layouts fixed at compile time (bit v: c_v is a field, else a
+// per-instance scalar).  FS_ANY: the layout is read at run time.
+#define FS_ANY 0x80
+// c_yy reads the field of c_xx (isotropic diffusion)
+#define FS_SHARE46 0x100
+// reaction-diffusion: c_0, c_xx, c_yy fields
+#define FS_MASK_RD ((1 << 0) | (1 << 4) | (1 << 6))
+#define FS_MASK_RDI (FS_MASK_RD | FS_SHARE46)
+// transport: the velocity fields c_x, c_y
+#define FS_MASK_TR ((1 << 3) | (1 << 5))
 
 struct Grid {
   int D;          // 2 or 3

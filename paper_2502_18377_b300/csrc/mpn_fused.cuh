@@ -21,7 +21,7 @@
 // null on the first step from zero): no direction array is kept.
 #pragma once
 #include "mpn_device.cuh"
-#include "mpn_stencil.cuh"
+#include "mpn_stepargs.cuh"
 
 #define FS_TX 4
 #define FS_TPB 256
@@ -75,15 +75,8 @@ __device__ __forceinline__ void dforms1(int cls, float xm2, float xm1, float x0,
 // Coefficient access.  MASK = FS_ANY: fields at stride 1 and per-instance
 // scalars (stored four times) at stride 0, one load either way.  Otherwise
 // bit v of MASK says that c_v is a field (the problem's layout is fixed at
-// compile time): scalars are loaded once into registers and fields per group.
-#ifndef FS_ANY
-#define FS_ANY 0x80
-#endif
-// with a compile-time layout: c_yy reads the field of c_xx (isotropic
-// diffusion), so the shared loads are issued once
-#ifndef FS_SHARE46
-#define FS_SHARE46 0x100
-#endif
+// compile time): scalars are loaded once into registers and fields per group;
+// with FS_SHARE46, c_yy reads the field of c_xx, so their loads are issued once.
 template <int MASK>
 struct CoefU4 {
   const float* base[7];
@@ -289,7 +282,9 @@ __global__ void __launch_bounds__(FS_TPB) k_step3(Grid g, Coef cf, const float* 
     float4 ur = make_float4(0.f, 0.f, 0.f, 0.f), udi = ur, ud = ur;
     if (MODE != SM_APPLY && MODE != SM_APPLYP) ur = ld4(a.r + j);
     if (MODE == SM_POST0 || MODE == SM_CHEB || MODE == SM_CHEB_DOT) udi = ld4(a.dinv + j);
-    if ((MODE == SM_CHEB || MODE == SM_CHEB_DOT) && a.d) ud = ld4(a.d + j);   // previous iterate
+    // previous iterate: the buffer this step overwrites at the same point, so a
+    // coherent load (not the read-only path)
+    if ((MODE == SM_CHEB || MODE == SM_CHEB_DOT) && a.d) ud = __ldcg(reinterpret_cast<const float4*>(a.d + j));
     const float* yr = ys + ((ot + 1) * RYW + ox + 1) * n2;
     const float4 yc = lds4(yr + y0);
     const int pxm = (PER1 && x == 0) ? p + (n1 - 1) * n2 : p - n2;

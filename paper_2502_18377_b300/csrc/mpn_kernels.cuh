@@ -5,19 +5,15 @@
 #pragma once
 #include "mpn_device.cuh"
 
-#define GRID_LOOP(p, N) for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < (N); p += gridDim.x * blockDim.x)
 
 // FP64 coefficient access.  MASK = RES_ANY: every c_v read and converted per
 // use.  Otherwise bit v of MASK says c_v is a field; the per-instance scalars
 // are converted once per thread and the difference forms they multiply are
 // formed before the product (fewer FP64 operations: this pass is bound by the
 // FP64 pipe).
-#define RES_ANY 0x80
-// with a compile-time layout: c_yy reads the field of c_xx (isotropic
-// diffusion), so the shared loads and conversions are issued once
-#ifndef FS_SHARE46
-#define FS_SHARE46 0x100
-#endif
+// With FS_SHARE46, c_yy reads the field of c_xx, so the shared loads and
+// conversions are issued once.
+#define RES_ANY FS_ANY
 template <int MASK>
 struct Coef64 {
   const Coef& cf;
@@ -1032,7 +1028,7 @@ template <int D, int MASK>
 __global__ void k_gradients(Grid g, Coef cf, const double* __restrict__ rho64, const float* __restrict__ rhs,
                             const double* __restrict__ uf, const double* __restrict__ du, const float* __restrict__ gz,
                             float* __restrict__ dfields, float* __restrict__ drhs, float* __restrict__ domega,
-                            float* __restrict__ dz_out, double* __restrict__ part) {
+                            float* __restrict__ dz_out, double* __restrict__ dz64_out, double* __restrict__ part) {
   int b = blockIdx.y;
   const Coef64<MASK> C(cf, b);
   constexpr int V = 1 + 2 * D;
@@ -1063,6 +1059,10 @@ __global__ void k_gradients(Grid g, Coef cf, const double* __restrict__ rho64, c
     if (dz_out) {
 #pragma unroll
       for (int v = 0; v < V; ++v) dz_out[((size_t)b * V + v) * g.N + p] = (float)dv[v];
+    }
+    if (dz64_out) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) dz64_out[((size_t)b * V + v) * g.N + p] = dv[v];
     }
   }
 #pragma unroll

@@ -16,7 +16,6 @@
 // B*N entries before reading them, so nothing needs clearing, but calls that
 // overlap on the GPU (e.g. on two streams) race on it.
 #include <cuda_runtime.h>
-#include <mutex>
 #include <cstdio>
 #include <cstring>
 
@@ -27,23 +26,14 @@ static __device__ __align__(256) float g_noalloc_y[MPN_NOALLOC_MAX_POINTS];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-float* g_scratch[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device, resolved once
-// per device (the host-side name of a __device__ array is not a device
-// address).
+// Device address of the scratch array on the current device.  The host-side
+// name of a __device__ array is not a device address, so every call asks the
+// runtime for it (a host-side lookup that allocates nothing; resolving it per
+// call also stays correct after the device's context is re-created).
 int scratch_ptr(float** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MPN_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_y) != cudaSuccess || !p) return MPN_ERR_CUDA;
-    g_scratch[dev] = static_cast<float*>(p);
-  }
-  *out = g_scratch[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_y) != cudaSuccess || !p) return MPN_ERR_CUDA;
+  *out = static_cast<float*>(p);
   return MPN_OK;
 }
 
@@ -92,6 +82,7 @@ extern "C" int mpn_apply_reduced_noalloc(const mpn_desc* desc, const float* fiel
     if (d.field_of[v] < -1 || d.field_of[v] >= d.nfields) return MPN_ERR_INVALID_ARG;
   if (d.nfields > 0 && !fields) return MPN_ERR_INVALID_ARG;
   if (N * d.batch > (long long)MPN_NOALLOC_MAX_POINTS) return MPN_ERR_UNSUPPORTED;  // scratch too small
+  if (d.batch > 65535) return MPN_ERR_UNSUPPORTED;   // one grid row of CTAs per instance
 
   float* y = nullptr;
   int s = scratch_ptr(&y);
@@ -126,6 +117,7 @@ extern "C" int mpn_apply_reduced_noalloc(const mpn_desc* desc, const float* fiel
   }
 
   cudaStream_t st = (cudaStream_t)stream;
+  (void)cudaGetLastError();   // an earlier call's error is not this call's
   int nb = (int)((N + MPN_TPB - 1) / MPN_TPB);
   if (nb > 1024) nb = 1024;
   dim3 gr(nb, d.batch);

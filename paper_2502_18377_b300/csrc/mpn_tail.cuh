@@ -20,12 +20,6 @@
 namespace cg = cooperative_groups;
 
 #define TAIL_TPB 512
-#ifndef FS_ANY
-#define FS_ANY 0x80
-#endif
-#ifndef FS_SHARE46
-#define FS_SHARE46 0x100
-#endif
 #define TAIL_MAXL 16
 // first fused level: at most TAIL_MAX_PPT points per thread and CTA (the
 // reaction-diffusion benchmark, 16 x 32 x 64 x 64: fused from 32 x 8 x 8,

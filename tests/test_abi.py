@@ -48,3 +48,23 @@ def test_error_strings_without_gpu():
     d.periodic[0] = 0
     d.krylov = 7
     assert lib.mpn_create(ctypes.byref(d), ctypes.byref(h)) == 1      # unknown inner solver: invalid
+
+
+def test_binding_rejects_missized_tensors_without_launching():
+    """The allocation-free apply takes its sizes from a descriptor built apart
+    from the tensors: a short output, a short operand or a non-float32 tensor
+    is refused on the host, before anything reaches the library (CPU tensors:
+    nothing here can launch)."""
+    import pytest
+    import torch
+    from paper_2502_18377_b300 import binding
+    geom = dict(n=(8, 16, 16), step=(1 / 7, 1 / 16, 1 / 16), periodic=(False, True, True))
+    desc = binding.make_desc(geom, 2, [1, -1, -1, -1, 0, -1, 0], 2)
+    N = 8 * 16 * 16
+    ok = dict(fields=torch.zeros(2, 2, N), scalars=torch.zeros(7, 2), u=torch.zeros(2, N), q=torch.zeros(2, N))
+    for name, bad in (("q", torch.zeros(2, N - 1)), ("u", torch.zeros(N)), ("fields", torch.zeros(1, 2, N)),
+                      ("scalars", torch.zeros(7, 1)), ("u", torch.zeros(2, N, dtype=torch.float64))):
+        args = dict(ok)
+        args[name] = bad
+        with pytest.raises(ValueError, match=name):
+            binding.apply_reduced_noalloc(desc, args["fields"], args["scalars"], args["u"], args["q"])

@@ -1,17 +1,38 @@
-"""Full-size checks in the benchmark's launch configuration.
+"""Full-size checks, in the launch configuration the benchmark times (solver
+defaults), element by element against the oracle.
 
 * Linearized Burgers at its full size (B = 32, 128 x 256): the oracle solves
   sampled instances exactly; forward z and the gradients must match (1e-6 /
   1e-5 relative L2).
-* Reaction-diffusion at the benchmark size (B = 16, 32 x 64 x 64): a direct
-  solve per instance is out of the oracle's reach, so the check is a property
-  that holds at any size: the oracle assembles A and d of sampled instances
-  and evaluates the FP64 normal-equation residual ||A^T (d - A z)|| / ||A^T d||
-  of the solver's FP64 output (Eq. 9), and the dual lambda = d - A z must be
-  orthogonal to the columns of A in the same sense (it is the same quantity).
-  Bound: the refinement stops at a predicted relative error of 1e-7 in z; with
-  ||A^T A|| ||z|| / ||A^T d|| of order 1e2..1e3 for these instances, the
-  residual of a 1e-6-accurate z is below 1e-6 — the test requires 1e-7.
+* Reaction-diffusion at the benchmark size (B = 16, 32 x 64 x 64), the larger
+  reaction-diffusion workload (B = 8, 64 x 128 x 128) and transport (B = 4,
+  32 x 256 x 256): a factorisation per instance is out of the oracle's reach,
+  so the data are manufactured such that the exact least-squares solution is
+  known at any size (oracle.manufactured), with the workload's own coefficient
+  fields:
+    - forward: b and omega of every instance made consistent with a rough
+      (box-filtered white-noise) u, so z* = z_e (Eqs. 3-9); every instance's z
+      is compared with z_e (relative L2 <= 1e-6 on the whole z and the u block);
+    - adjoint: a source on u only (the form a loss on u gives, as the
+      benchmark's MSE loss does), g = A^T A z_e with z_e's derivative unknowns
+      eliminated point by point, so d_z = z_e (Eq. 11); sampled instances carry
+      it, the others a zero source (d_z = 0 exactly).
+  The solver receives float32 data.  Rounding b and omega moves the forward's
+  exact solution by far less than 1e-6 (the whole z is compared).  Rounding g
+  moves the adjoint's exact u by a few 1e-8 for a low-mode u_e (3e-8 measured
+  by the oracle at 16 x 32 x 32; 1e-5 for a rough u_e, and 2e-3 in the whole
+  z for a source on every unknown), but the derivative blocks, which are
+  second differences of u over s^2 at these fine grids, carry that rounding
+  at up to 5e-6 (measured on the transport workload, unchanged when the
+  solver's tolerance is tightened from 1e-7 to 1e-11: the solver has the exact
+  solution of the rounded source).  So the u block is compared with u_e, and
+  the derivative blocks with the oracle's point-local elimination applied to
+  the solver's FP64 u, which is what they are for the exact solution of any
+  u-only source.  Sources on the derivative unknowns are compared at the small
+  sizes of the parity tests, where the oracle solves the rounded source
+  itself.
+* The workload's own data at the benchmark size: the FP64 normal-equation
+  residual of sampled instances (a property that holds at any size).
 """
 import numpy as np
 import pytest
@@ -19,10 +40,12 @@ import torch
 
 from oracle import assemble as asm
 from oracle import grad as og
+from oracle import manufactured as mf
 from oracle import solve as osv
 from paper_2502_18377_b300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
+TOL = 1e-6
 
 
 def _round(w):
@@ -37,6 +60,10 @@ def _dev(a):
 
 def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _r32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
 def test_burgers_full_size_sampled_instances():
@@ -54,7 +81,7 @@ def test_burgers_full_size_sampled_instances():
     for b in (0, 17, 31):
         A, d, kind, owner = asm.assemble(w.geom, w.full_coeff()[:, b], w.rhs[b], w.omega[b])
         zr, lam, el = osv.solve_lsq_elim(A, d, V)
-        assert _rel(zc[b].ravel(), zr) <= 1e-6, (b, _rel(zc[b].ravel(), zr))
+        assert _rel(zc[b].ravel(), zr) <= TOL, (b, _rel(zc[b].ravel(), zr))
         dz, dlam = og.adjoint_elim(el, gzc[b].ravel())
         dc, db, dw = og.gradients(w.geom, A, d, kind, owner, zr, lam, dz, dlam)
         assert _rel(dfields[0, b], dc[3]) <= 1e-5
@@ -62,7 +89,80 @@ def test_burgers_full_size_sampled_instances():
         assert _rel(dom[b], dw) <= 1e-5
 
 
+FULL = [("reaction_diffusion_2d_B16_32x64x64", 2, (0, 7, 15)),
+        ("reaction_diffusion_2d_B8_64x128x128", 4, (0, 5)),
+        ("transport_2d_B4_32x256x256", 5, (0, 3))]
+
+
+@pytest.mark.parametrize("name,cfg,sampled", FULL, ids=[f[0] for f in FULL])
+def test_manufactured_forward_full_size(name, cfg, sampled):
+    from paper_2502_18377_b300.binding import Solver
+    w = _round(wl.CONFIGS[cfg]())
+    B, V, N = w.batch, asm.n_vars(w.ndim), w.npoints
+    coeff = w.full_coeff()
+    rng = np.random.default_rng(7000 + cfg)
+    ze = np.empty((B, V, N))
+    rhs = np.empty((B, N))
+    om = np.empty((B, N))
+    for b in range(B):
+        u = wl.box_filter(rng.normal(size=w.geom["n"]), w.geom["periodic"]).ravel()
+        zb, rb, ob = mf.consistent_data(w.geom, coeff[:, b], u)
+        ze[b], rhs[b], om[b] = zb, rb, ob
+    s = Solver(w.geom, w.batch, w.field_of, w.fields.shape[0])
+    z64 = torch.empty((B, V, N), device="cuda", dtype=torch.float64)
+    z = s.forward(_dev(w.fields), _dev(w.scalars), _dev(rhs), _dev(om), z64=z64)
+    z, z64 = z.cpu().numpy(), z64.cpu().numpy()
+    for b in range(B):
+        assert _rel(z[b].ravel(), ze[b].ravel()) <= TOL, (name, b, _rel(z[b].ravel(), ze[b].ravel()), s.last_stats)
+        assert _rel(z[b, 0], ze[b, 0]) <= TOL, (name, b, _rel(z[b, 0], ze[b, 0]))
+        assert _rel(z64[b].ravel(), ze[b].ravel()) <= TOL
+
+
+@pytest.mark.parametrize("name,cfg,sampled", FULL, ids=[f[0] for f in FULL])
+def test_manufactured_adjoint_full_size(name, cfg, sampled):
+    """Adjoint solve (Eq. 11) with a source on u only.  The u block of d_z
+    must match u_e; the derivative blocks must be the oracle's point-local
+    elimination of the solver's own FP64 d_u (the derivative unknowns of the
+    exact solution are that map of its u for any such source, and the map
+    amplifies the float32 rounding of g into these blocks; see the module
+    docstring)."""
+    from paper_2502_18377_b300.binding import Solver
+    w = _round(wl.CONFIGS[cfg]())
+    B, V, N = w.batch, asm.n_vars(w.ndim), w.npoints
+    coeff = w.full_coeff()
+    rng = np.random.default_rng(8000 + cfg)
+    g = np.zeros((B, V, N))
+    ue, mats = {}, {}
+    for b in sampled:
+        A, d, kind, owner = asm.assemble(w.geom, coeff[:, b], w.rhs[b], w.omega[b])
+        u = wl.low_mode_field(rng, w.geom)
+        zb, gb, resid = mf.eliminated_pair(A, V, u)
+        assert resid < 1e-10, resid
+        ue[b], mats[b] = u, A
+        g[b] = gb.reshape(V, N)
+    s = Solver(w.geom, w.batch, w.field_of, w.fields.shape[0])
+    args = (_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega))
+    z = s.forward(*args)
+    dz64 = torch.empty((B, V, N), device="cuda", dtype=torch.float64)
+    dz = s.adjoint(*args, z, _dev(g), reuse_setup=True, want_dz=True, dz64=dz64)[4].cpu().numpy()
+    dz64 = dz64.cpu().numpy()
+    stats = dict(s.last_stats)
+    for b in range(B):
+        if b not in ue:
+            assert not np.any(dz[b]) and not np.any(dz64[b]), (name, b)
+            continue
+        assert _rel(dz64[b, 0], ue[b]) <= TOL, (name, b, _rel(dz64[b, 0], ue[b]), stats)
+        assert _rel(dz[b, 0], ue[b]) <= TOL
+        wmap = mf.eliminate_w(mats[b], V, dz64[b, 0])
+        assert _rel(dz64[b, 1:].ravel(), wmap.ravel()) <= 1e-9, (name, b, _rel(dz64[b, 1:].ravel(), wmap.ravel()))
+        assert _rel(dz[b].ravel(), dz64[b].ravel()) <= 1e-7
+
+
 def test_reaction_diffusion_bench_size_residual():
+    """The workload's own (inconsistent) data at the benchmark size: the
+    oracle assembles A and d of sampled instances and evaluates the FP64
+    normal-equation residual ||A^T (d - A z)|| / ||A^T d|| of the solver's FP64
+    output (Eq. 9); the FP32 output is that solution rounded."""
     from paper_2502_18377_b300.binding import Solver
     w = _round(wl.reaction_diffusion_2d())          # B = 16, 32 x 64 x 64
     s = Solver(w.geom, w.batch, w.field_of, w.fields.shape[0])
@@ -78,5 +178,4 @@ def test_reaction_diffusion_bench_size_residual():
         A, d, kind, owner = asm.assemble(w.geom, w.full_coeff()[:, b], w.rhs[b], w.omega[b])
         res = osv.normal_residual(A, d, z64c[b].ravel())
         assert res <= 1e-7, (b, res, stats)
-        # the FP32 output is the FP64 one rounded
         assert _rel(zc[b].ravel(), z64c[b].ravel()) <= 1e-7

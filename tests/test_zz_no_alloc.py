@@ -62,3 +62,18 @@ def test_noalloc_rejects_oversize():
     with pytest.raises(MpnError) as e:
         apply_reduced_noalloc(desc, tiny, tiny, tiny, tiny)
     assert e.value.status == 2
+
+
+def test_noalloc_rejects_batches_beyond_the_grid_limit():
+    """One row of CTAs per instance: more than 65535 instances is refused
+    with UNSUPPORTED before any launch, even when B * N fits the scratch."""
+    from paper_2502_18377_b300.binding import MpnError, apply_reduced_noalloc, make_desc
+    geom = dict(n=(3, 3), step=(0.5, 0.5), periodic=(False, False))
+    B = 70000
+    desc = make_desc(geom, B, [-1] * 5, 0)
+    u = torch.zeros((B, 9), device="cuda")
+    q = torch.zeros((B, 9), device="cuda")
+    scal = torch.zeros((5, B), device="cuda")
+    with pytest.raises(MpnError) as e:
+        apply_reduced_noalloc(desc, None, scal, u, q)
+    assert e.value.status == 2
