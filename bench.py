@@ -3,11 +3,14 @@ FP64-oracle accuracy (relative L2 1e-6), with the roofline of the dominant
 kernel, end-to-end throughput through the C ABI with host buffers, clocks,
 and the CPU oracle as baseline.
 
-Workload (one step): the 2D+time reaction-diffusion family
-u_t = d (u_xx + u_yy) + r u + f, batch 16 per GPU, grid 32 x 64 x 64, periodic
-in x and y, seeded smooth fields; forward solve, MSE loss gradient against a
-seeded target, adjoint solve, parameter gradients.  Inputs are resident in
-HBM when the timed region starts.
+Workload of the headline line (one step): the 2D+time transport family
+u_t + v1 u_x + v2 u_y - 1e-3 (u_xx + u_yy) = sin(4 y), batch 4 per GPU, grid
+32 x 256 x 256 on [0, 2 pi)^2, periodic, a seeded divergence-free velocity
+field with a k^-3 spectrum; forward solve, MSE loss gradient against a
+seeded target, adjoint solve, parameter gradients.  The 2D+time
+reaction-diffusion family at B = 8, 64 x 128 x 128 and at B = 16,
+32 x 64 x 64 is measured the same way and reported under "other_workloads".
+Inputs are resident in HBM when the timed region starts.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -28,14 +31,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "grid-points/s, fwd+adjoint solve to 1e-6 rel. L2 vs FP64; % of HBM roofline"
 UNIT = "grid-points/s"
-WORKLOAD = "reaction_diffusion_2d"
-BATCH, GRID = 16, (32, 64, 64)
 L2_BYTES = 126 * 2 ** 20
 
+# name -> (generator in workloads, batch per GPU, grid, seed base)
+WORKLOADS = {
+    "transport_2d": ("transport_2d", 4, (32, 256, 256), 5000),
+    "reaction_diffusion_2d_64x128x128": ("reaction_diffusion_2d", 8, (64, 128, 128), 4000),
+    "reaction_diffusion_2d": ("reaction_diffusion_2d", 16, (32, 64, 64), 2000),
+}
+HEADLINE = "transport_2d"
+WORKLOAD = HEADLINE
+BATCH, GRID = WORKLOADS[HEADLINE][1], WORKLOADS[HEADLINE][2]
 
-# DRAM bytes of one finest-level smoothing step (k_step3<CHEB>) from one ncu
-# capture of this workload; None once that kernel changes.
-PAIR_TRAFFIC_BYTES = 59.0e6
+# DRAM bytes of one finest-level smoothing step of the headline workload from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); None until
+# captured for the current kernel.
+STEP_TRAFFIC_BYTES = None
 
 
 def _peaks():
@@ -98,11 +109,12 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def make_inputs(rank, batch=BATCH, grid=GRID):
+def make_inputs(rank, batch=None, grid=None, name=HEADLINE):
     """This rank's batch: the workload with seeds of its own (instances are
     independent, so ranks share nothing)."""
     from paper_2502_18377_b300 import workloads as wl
-    w = wl.reaction_diffusion_2d(batch=batch, n=grid, seed_base=2000 + 100_000 * rank)
+    gen, b0, g0, seed = WORKLOADS[name]
+    w = getattr(wl, gen)(batch=batch or b0, n=grid or g0, seed_base=seed + 100_000 * rank)
     f32 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float32))
     return w, f32(w.fields), f32(w.scalars), f32(w.rhs), f32(w.omega), f32(w.target)
 
@@ -124,14 +136,14 @@ def job_throughput(world, batch, npoints, ms):
     return world * batch * npoints / (ms / 1e3)
 
 
-def cpu_oracle_step(seed, n):
+def cpu_oracle_step(seed, n, name=HEADLINE):
     """Oracle forward + adjoint for one instance of the workload family at grid
     n (float32-rounded inputs); returns (seconds, points)."""
     from oracle import assemble as asm
     from oracle import grad as og
     from oracle import solve as osv
     from paper_2502_18377_b300 import workloads as wl
-    w = wl.reaction_diffusion_2d(batch=1, n=n, seed_base=seed)
+    w = getattr(wl, WORKLOADS[name][0])(batch=1, n=n, seed_base=seed)
     r = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
     ww = wl.Workload(w.name, w.geom, w.field_of, r(w.scalars), r(w.fields), r(w.rhs), r(w.omega), r(w.target))
     t0 = time.perf_counter()
@@ -151,41 +163,40 @@ def run_reference(args):
         return
     n = (16, 16, 16)
     for k in range(args.warmup):
-        cpu_oracle_step(2000 + k, n)
+        cpu_oracle_step(5000 + k, n)
     tot, pts = 0.0, 0
     for k in range(args.steps):
-        dt, N = cpu_oracle_step(2000 + args.warmup + k, n)
+        dt, N = cpu_oracle_step(5000 + args.warmup + k, n)
         tot += dt
         pts += N
     v = pts / tot
-    sample = f"one instance per step of {WORKLOAD} at {n[0]}x{n[1]}x{n[2]} (1/32 of a 16x32x64x64 batch's points); oracle = sparse assembly + block-elimination LU of the normal equations + FP64 refinement, forward + adjoint + gradients"
+    sample = (f"one instance per step of {HEADLINE} at {n[0]}x{n[1]}x{n[2]} (the workload's generator at a grid "
+              f"the oracle factorises in about a second); oracle = sparse assembly + block-elimination LU of the "
+              f"normal equations + FP64 refinement, forward + adjoint + gradients, one thread")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "batch": BATCH, "grid": list(GRID),
+            "data": "synthetic", "config": {"workload": HEADLINE, "batch": BATCH, "grid": list(GRID),
                                             "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args):
+def measure(name, args, dev, world, rank, steps, warmup, flush, e2e=False):
+    """Times `steps` forward + MSE-gradient + adjoint steps of one workload
+    (after `warmup` untimed ones) with CUDA events, L2 flushed between steps
+    outside the events; returns a dict of the figures."""
     import torch
     import torch.distributed as dist
     from paper_2502_18377_b300.binding import Solver
 
-    rank, world, local = _env_rank()
-    if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    w, fields, scal, rhs, om, tgt = make_inputs(rank)
+    w, fields, scal, rhs, om, tgt = make_inputs(rank, name=name)
     s = Solver(w.geom, w.batch, w.field_of, fields.shape[0], krylov=args.krylov)
     D = lambda a: torch.from_numpy(a).to(dev)
     F_, S_, R_, O_, T_ = D(fields), D(scal), D(rhs), D(om), D(tgt)
     V, N, B = s.V, s.N, s.B
     z = torch.empty((B, V, N), device=dev)
-    flush = torch.empty(2 * L2_BYTES // 4, device=dev)
 
     def step(fields_t, scal_t, rhs_t, om_t, tgt_t):
         s.forward(fields_t, scal_t, rhs_t, om_t, z=z)
@@ -194,18 +205,16 @@ def run_ours(args):
         out = s.adjoint(fields_t, scal_t, rhs_t, om_t, z, gz, reuse_setup=True)
         return out, st_f, s.last_stats
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step(F_, S_, R_, O_, T_)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clocks = Clocks(local)
-    clocks.start()
     s.profile(1)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     stats = []
     torch.cuda.synchronize()
-    for k in range(args.steps):
+    for k in range(steps):
         flush.fill_(float(k))          # L2 flush between timed steps (outside the step events)
         ev[k][0].record()
         out, sf, sa = step(F_, S_, R_, O_, T_)
@@ -213,13 +222,15 @@ def run_ours(args):
         stats.append((sf, sa))
     torch.cuda.synchronize()
     prof_ms, prof_n, prof_bytes, kernels = s.profile(0)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(step_ms) / len(step_ms)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     ms = job_time_ms(ms, world, dev)
-    clk = clocks.stop()
-
+    res = {"name": name, "B": B, "N": N, "V": V, "grid": list(w.geom["n"]), "ms": ms,
+           "value": job_throughput(world, B, N, ms), "prof_ms": prof_ms, "prof_n": prof_n,
+           "prof_bytes": prof_bytes, "kernels": kernels, "stats": stats[-1], "levels": s.levels(),
+           "fused_level": s.fused_level(), "e2e": None}
+    if not e2e:
+        return res
     # end to end: host buffers through the public API (pinned H2D, D2H of the gradients)
-    e2e = None
     pin = lambda a: torch.from_numpy(a).pin_memory()
     hF, hS, hR, hO, hT = pin(fields), pin(scal), pin(rhs), pin(om), pin(tgt)
     h_out = [torch.empty((s.F, B, N)).pin_memory(), torch.empty((V, B)).pin_memory(),
@@ -236,57 +247,95 @@ def run_ours(args):
             dst.copy_(src, non_blocking=True)
         torch.cuda.current_stream().synchronize()
 
-    if not args.no_e2e:
+    e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2e_ms = []
+    for k in range(max(1, min(steps, 5))):
+        flush.fill_(float(k))
+        e0.record()
         e2e_step()
+        e1.record()
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e2e_ms = []
-        for k in range(max(1, min(args.steps, 5))):
-            flush.fill_(float(k))
-            e0.record()
-            e2e_step()
-            e1.record()
-            torch.cuda.synchronize()
-            e2e_ms.append(e0.elapsed_time(e1))
-        e2e = {"value": job_throughput(world, B, N, job_time_ms(statistics.mean(e2e_ms), world, dev)), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        e2e_ms.append(e0.elapsed_time(e1))
+    res["e2e"] = {"value": job_throughput(world, B, N, job_time_ms(statistics.mean(e2e_ms), world, dev)),
+                  "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    return res
 
+
+def _achieved(res):
+    n = res["prof_n"]
+    return (res["prof_bytes"] / n) / (res["prof_ms"] / n / 1e3) / 1e9 if n else None
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    flush = torch.empty(2 * L2_BYTES // 4, device=dev)
+    clocks = Clocks(local)
+    clocks.start()
+    head = measure(HEADLINE, args, dev, world, rank, args.steps, args.warmup, flush, e2e=not args.no_e2e)
+    clk = clocks.stop()
+    others = []
+    if not args.headline_only:
+        for name in WORKLOADS:
+            if name != HEADLINE:
+                others.append(measure(name, args, dev, world, rank, max(3, args.steps // 2), args.warmup, flush))
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
     peaks, src = _peaks()
     hbm = float(peaks["hbm_gbs"])
-    achieved = (prof_bytes / prof_n) / (prof_ms / prof_n / 1e3) / 1e9 if prof_n else None
-    value = job_throughput(world, B, N, ms)
+    achieved = _achieved(head)
     cpu = None
     if not args.no_cpu_baseline:
         n_s = (16, 32, 32)
-        dt, pts = cpu_oracle_step(2000, n_s)
+        dt, pts = cpu_oracle_step(5000, n_s)
         cpu = {"value": pts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one instance of {WORKLOAD} at {n_s[0]}x{n_s[1]}x{n_s[2]} (1/8 of the points of one instance; the oracle's cost grows faster than linearly, so this overstates its throughput at full size), forward + adjoint + gradients, {dt:.1f} s"}
-    sf, sa = stats[-1]
+               "sample": f"one instance of {HEADLINE} at {n_s[0]}x{n_s[1]}x{n_s[2]} (the workload's generator at a "
+                         f"grid the oracle factorises in seconds; its cost grows faster than linearly in the points, "
+                         f"so this overstates its throughput at full size), forward + adjoint + gradients, one "
+                         f"thread, {dt:.1f} s"}
+    sf, sa = head["stats"]
+    B, N, V = head["B"], head["N"], head["V"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64-refinement", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch_per_gpu": B, "grid": list(GRID), "periodic": [0, 1, 1],
-                   "krylov": args.krylov,
-                   "unknowns_per_instance": V * N, "tol": 1e-7, "parallelism": f"replicas{world}",
-                   "l2": "flushed between timed steps (256 MB write outside the step events)"},
-        "roofline": {"bound": "hbm", "kernel": "finest-level Chebyshev smoothing step (k_step3: L and L^T passes fused through shared memory)",
+        "config": {"workload": HEADLINE, "batch_per_gpu": B, "grid": head["grid"], "periodic": [0, 1, 1],
+                   "krylov": args.krylov, "unknowns_per_instance": V * N, "tol": 1e-7,
+                   "parallelism": f"replicas{world}",
+                   "l2": "flushed between timed steps (256 MB write outside the step events); "
+                         "one level's working set exceeds L2 as well"},
+        "roofline": {"bound": "hbm", "kernel": "finest-level Chebyshev smoothing step (L and L^T passes fused "
+                                               "through shared memory on 64-point y segments)",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": PAIR_TRAFFIC_BYTES,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the finest-level smoothing step kernel, one capture, bytes per step (profiles/finest_smoothing_step_reaction_diffusion_2d_B16_32x64x64.md)",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": STEP_TRAFFIC_BYTES,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the finest-level "
+                                       "smoothing step, one capture, bytes per launch",
                      "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.4 TB/s",
-                     "launches": prof_n, "avg_launch_us": 1e3 * prof_ms / prof_n if prof_n else None},
+                     "launches": head["prof_n"],
+                     "avg_launch_us": 1e3 * head["prof_ms"] / head["prof_n"] if head["prof_n"] else None},
         "clocks": clk,
-        "e2e": e2e,
-        "gpu_launches": kernels,
-        "gpu_launches_per_step": kernels / args.steps,
-        "solver": {"forward": sf, "adjoint": sa},
+        "e2e": head["e2e"],
+        "gpu_launches": head["kernels"],
+        "gpu_launches_per_step": head["kernels"] / args.steps,
+        "solver": {"forward": sf, "adjoint": sa, "levels": head["levels"], "fused_coarse_level": head["fused_level"]},
         "cpu_baseline": cpu,
+        "other_workloads": [
+            {"workload": o["name"], "batch_per_gpu": o["B"], "grid": o["grid"], "value": o["value"], "unit": UNIT,
+             "ms_per_step": o["ms"], "steps": max(3, args.steps // 2),
+             "dominant_step_GBps": _achieved(o), "dominant_step_frac": (_achieved(o) / hbm) if _achieved(o) else None,
+             "gpu_launches_per_step": o["kernels"] / max(3, args.steps // 2),
+             "solver": {"forward": o["stats"][0], "adjoint": o["stats"][1]}} for o in others],
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -301,6 +350,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--headline-only", action="store_true", help="skip the other workloads")
     ap.add_argument("--krylov", default="cg", choices=["cg", "fgmres"],
                     help="inner FP32 solver of each refinement sweep (flexible GMRES is the solver of Section 3.1)")
     args = ap.parse_args()

@@ -33,7 +33,7 @@ def _worker(rank, world, port, q, fail_rank):
         w, fields, scal, rhs, om, tgt = bench.make_inputs(rank, batch=2, grid=(4, 8, 8))
         ms = bench.job_time_ms(10.0 + 3.0 * rank, world)
         value = bench.job_throughput(world, 2, w.npoints, ms)
-        q.put((rank, float(np.abs(rhs).sum()), float(np.abs(fields).sum()), ms, value, w.npoints))
+        q.put((rank, float(np.abs(tgt).sum()), float(np.abs(fields).sum()), ms, value, w.npoints))
         dist.barrier()
     finally:
         dist.destroy_process_group()
@@ -63,9 +63,9 @@ def test_two_ranks_shard_batches_and_take_the_slowest_rank():
     codes, out = _run(2)
     assert codes == [0, 0], codes
     assert len(out) == 2
-    (r0, rhs0, f0, ms0, v0, n), (r1, rhs1, f1, ms1, v1, _) = out
+    (r0, tgt0, f0, ms0, v0, n), (r1, tgt1, f1, ms1, v1, _) = out
     # each rank has its own batch
-    assert rhs0 != rhs1 and f0 != f1
+    assert tgt0 != tgt1 and f0 != f1
     # the job's step time is the slowest rank's, on every rank
     assert ms0 == ms1 == 13.0
     # throughput counts both ranks' points
