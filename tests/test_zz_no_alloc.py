@@ -58,9 +58,13 @@ def test_noalloc_rejects_oversize():
     geom["n"] = n_big
     geom["step"] = (1.0, 1.0, 1.0)
     desc = make_desc(geom, 1, w.field_of, 2)
-    tiny = torch.zeros(4, device="cuda")
+    N = int(np.prod(n_big))
+    u = torch.zeros(N, device="cuda")
+    q = torch.zeros(N, device="cuda")
+    fields = torch.zeros((2, 1, N), device="cuda")
+    scal = torch.zeros((7, 1), device="cuda")
     with pytest.raises(MpnError) as e:
-        apply_reduced_noalloc(desc, tiny, tiny, tiny, tiny)
+        apply_reduced_noalloc(desc, fields, scal, u, q)
     assert e.value.status == 2
 
 
