@@ -38,6 +38,10 @@
  * refinement sweep reads a few per-instance scalars back to the host, so a
  * solve call returns after its work is complete.
  *
+ * Diagnostics: with the environment variable MPN_TRACE set, every refinement
+ * sweep prints its inner iterations, correction size, residual and predicted
+ * error to stderr.
+ *
  * Errors: every call returns an mpn_status.  Nothing aborts or hangs: PCG
  * and refinement counts are capped; a non-finite value or a growing residual
  * is reported, and stats are filled in either way.

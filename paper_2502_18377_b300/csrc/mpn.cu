@@ -1138,12 +1138,13 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
   if (!zero_start) TRY(residual64(p, nullptr, g_adj, p->r64, slot(p, S_GN), st));
   std::vector<double> gnorm(B, 0.0);
   int iters = p->desc.direct ? 1 : p->desc.inner_iters, total_iters = 0;
+  const bool trace = getenv("MPN_TRACE") != nullptr;
   for (int sweep = 0; sweep < p->desc.max_refine; ++sweep) {
     TRY(run_sweep(p, g_adj, iters, P, zero_start && sweep == 0, st));
     total_iters += iters;
     const double* h = p->hbuf;
     if (*(const int*)(h + 5 * B)) { status = MPN_ERR_CUDA; break; }   // a kernel's bounded wait gave up
-    double maxpred = 0, maxupd = 0, maxres = 0, maxrate = 0;
+    double maxpred = 0, maxupd = 0, maxres = 0, maxrate = 0, maxq = 0;
     bool bad = false, grew = false;
     for (int b = 0; b < B; ++b) {
       double rn = sqrt(h[0 * B + b]), du = sqrt(h[1 * B + b]), un = sqrt(h[2 * B + b]);
@@ -1156,6 +1157,7 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
       // and the remaining error is the geometric tail of the next
       // corrections: upd (q + q^2 + ...) = upd q / (1 - q)
       const double q1 = upd / std::max(prev_upd[b], 1e-300);
+      if (sweep >= 1) maxq = std::max(maxq, q1);
       const double q = sweep >= 1 ? std::max(q1, prev_q[b]) : q1;
       if (sweep >= 1) prev_q[b] = q1;
       double pred = sweep < 2 ? upd : (q < 1.0 ? upd * q / (1.0 - q) : HUGE_VAL);
@@ -1174,8 +1176,13 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
     if (bad) { status = MPN_ERR_NONFINITE; break; }
     if (grew) { status = MPN_ERR_DIVERGED; break; }
     if ((sweep >= 2 && maxpred <= p->desc.tol) || (sweep >= 1 && maxupd <= p->desc.tol * 0.1)) { status = MPN_OK; break; }
+    const int done_iters = iters;
     // a sweep that gained less than a digit: lengthen the inner solve
     if (!p->desc.direct && sweep >= 1 && maxrate > 0.1 && iters < 8 * p->desc.inner_iters) iters *= 2;
+    if (trace)
+      fprintf(stderr, "[mpn] %s sweep %d: %d inner iterations, update %.3e, residual %.3e, predicted error %.3e, "
+                      "gain %.3e -> next %d\n", g_adj ? "adjoint" : "forward", sweep, done_iters, maxupd, maxres,
+              maxpred, maxq, iters);
   }
   if (stats) *stats = sres;
   return status;
