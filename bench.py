@@ -33,12 +33,8 @@ METRIC = "grid-points/s, fwd+adjoint solve to 1e-6 rel. L2 vs FP64; % of HBM roo
 UNIT = "grid-points/s"
 L2_BYTES = 126 * 2 ** 20
 
-# name -> (generator in workloads, batch per GPU, grid, seed base)
-WORKLOADS = {
-    "transport_2d": ("transport_2d", 4, (32, 256, 256), 5000),
-    "reaction_diffusion_2d_64x128x128": ("reaction_diffusion_2d", 8, (64, 128, 128), 4000),
-    "reaction_diffusion_2d": ("reaction_diffusion_2d", 16, (32, 64, 64), 2000),
-}
+from paper_2502_18377_b300.settings import BENCH_WORKLOADS as WORKLOADS  # noqa: E402
+
 HEADLINE = "transport_2d"
 WORKLOAD = HEADLINE
 BATCH, GRID = WORKLOADS[HEADLINE][1], WORKLOADS[HEADLINE][2]
@@ -112,9 +108,8 @@ class Clocks:
 def make_inputs(rank, batch=None, grid=None, name=HEADLINE):
     """This rank's batch: the workload with seeds of its own (instances are
     independent, so ranks share nothing)."""
-    from paper_2502_18377_b300 import workloads as wl
-    gen, b0, g0, seed = WORKLOADS[name]
-    w = getattr(wl, gen)(batch=batch or b0, n=grid or g0, seed_base=seed + 100_000 * rank)
+    from paper_2502_18377_b300 import settings
+    w = settings.make(name, batch=batch, grid=grid, seed_offset=100_000 * rank)
     f32 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float32))
     return w, f32(w.fields), f32(w.scalars), f32(w.rhs), f32(w.omega), f32(w.target)
 
@@ -143,7 +138,7 @@ def cpu_oracle_step(seed, n, name=HEADLINE):
     from oracle import grad as og
     from oracle import solve as osv
     from paper_2502_18377_b300 import workloads as wl
-    w = getattr(wl, WORKLOADS[name][0])(batch=1, n=n, seed_base=seed)
+    w = WORKLOADS[name][0](batch=1, n=n, seed_base=seed)
     r = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
     ww = wl.Workload(w.name, w.geom, w.field_of, r(w.scalars), r(w.fields), r(w.rhs), r(w.omega), r(w.target))
     t0 = time.perf_counter()
@@ -192,7 +187,7 @@ def measure(name, args, dev, world, rank, steps, warmup, flush, e2e=False):
     from paper_2502_18377_b300.binding import Solver
 
     w, fields, scal, rhs, om, tgt = make_inputs(rank, name=name)
-    s = Solver(w.geom, w.batch, w.field_of, fields.shape[0], krylov=args.krylov)
+    s = Solver(w.geom, w.batch, w.field_of, fields.shape[0], krylov=args.krylov, **WORKLOADS[name][4])
     D = lambda a: torch.from_numpy(a).to(dev)
     F_, S_, R_, O_, T_ = D(fields), D(scal), D(rhs), D(om), D(tgt)
     V, N, B = s.V, s.N, s.B
@@ -311,7 +306,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64-refinement", "data": "synthetic",
         "config": {"workload": HEADLINE, "batch_per_gpu": B, "grid": head["grid"], "periodic": [0, 1, 1],
-                   "krylov": args.krylov, "unknowns_per_instance": V * N, "tol": 1e-7,
+                   "krylov": args.krylov, "solver_settings": WORKLOADS[HEADLINE][4],
+                   "unknowns_per_instance": V * N, "tol": 1e-7,
                    "parallelism": f"replicas{world}",
                    "l2": "flushed between timed steps (256 MB write outside the step events); "
                          "one level's working set exceeds L2 as well"},
@@ -332,7 +328,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "other_workloads": [
             {"workload": o["name"], "batch_per_gpu": o["B"], "grid": o["grid"], "value": o["value"], "unit": UNIT,
-             "ms_per_step": o["ms"], "steps": max(3, args.steps // 2),
+             "ms_per_step": o["ms"], "steps": max(3, args.steps // 2), "solver_settings": WORKLOADS[o["name"]][4],
              "dominant_step_GBps": _achieved(o), "dominant_step_frac": (_achieved(o) / hbm) if _achieved(o) else None,
              "gpu_launches_per_step": o["kernels"] / max(3, args.steps // 2),
              "solver": {"forward": o["stats"][0], "adjoint": o["stats"][1]}} for o in others],

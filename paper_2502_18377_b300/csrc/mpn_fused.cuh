@@ -53,6 +53,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 #define FS_WAIT_LIMIT (1 << 22)
 
 __device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+// Asks L2 for the line holding p (no register, no wait).
+__device__ __forceinline__ void pf_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // Shared-memory floats of the tile for a y extent n2.
 __host__ __device__ constexpr int fs_rows_x(int TT) { return (TT + 4) * (FS_TX + 4); }
@@ -94,6 +96,13 @@ struct CoefU4 {
     if (MASK == FS_ANY) return ld4(base[v] + p * ps[v]);
     if ((MASK & FS_SHARE46) && v == 6) v = 4;
     return ((MASK >> v) & 1) ? ld4(base[v] + p) : f4(sv[v]);
+  }
+  // L2 prefetch of the fields at point p (compile-time layouts only)
+  __device__ __forceinline__ void prefetch(int p) const {
+    if (MASK == FS_ANY) return;
+#pragma unroll
+    for (int v = 0; v < 7; ++v)
+      if (((MASK >> v) & 1) && !((MASK & FS_SHARE46) && v == 6)) pf_l2(base[v] + p);
   }
   __device__ __forceinline__ float at(int v, int p) const {
     if (MASK == FS_ANY) return __ldg(base[v] + p * ps[v]);

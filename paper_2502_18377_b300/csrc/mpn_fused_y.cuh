@@ -50,8 +50,12 @@ __global__ void __launch_bounds__(FS_TPB) k_step3y(Grid g, Coef cf, const float*
   const float i2t = g.is2[0], i2x = g.is2[1], i2y = g.is2[2];
 
   // 1. operand rows t0-2 .. t0+TT+1 x x0-2 .. x0+FS_TX+1, y0t-4 .. y0t+TY+3;
-  //    warp 0 issues the copies, lane l the rows l, l + 32, ...
+  //    warp 0 issues the copies, lane l the rows l, l + 32, ...  The barrier
+  //    is initialised first, so no thread waits for the copies to be issued:
+  //    meanwhile every thread asks L2 for the global data its passes read.
   __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
   if (threadIdx.x < 32) {
     // visits the segments (global point of the row's first copied y, shared
     // column, length) of shared row `row`; none when the row lies outside a
@@ -85,22 +89,43 @@ __global__ void __launch_bounds__(FS_TPB) k_step3y(Grid g, Coef cf, const float*
     for (int row = threadIdx.x; row < fs_rows_x(TT); row += 32)
       segments(row, [&](int, int, int len) { bytes += (unsigned)len * 4u; });
     bytes = __reduce_add_sync(0xffffffffu, bytes);
-    if (threadIdx.x == 0) {
-      mbar_init(&bar, 1);
-      mbar_expect_tx(&bar, bytes);
-    }
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, bytes);
     __syncwarp();
     for (int row = threadIdx.x; row < fs_rows_x(TT); row += 32)
       segments(row, [&](int src, int dst, int len) { bulk_g2s(xs + dst, X + src, (unsigned)len * 4u, &bar); });
+  }
+  {
+    // L2 prefetch of the thread's own groups: rho and the coefficient fields
+    // of its pass-1 rows, the update operands and fields of its pass-2 rows
+    int gq;
+    const int r0 = fdivmod((int)threadIdx.x, G, invG, gq);
+    constexpr int rs = FS_TPB / G;
+    if (r0 < rs) {
+      const int gy = y0t + 4 * gq;
+      for (int row = r0; row < fs_rows_y(TT); row += rs) {
+        const int t = t0 - 1 + row / RYW;
+        int x = x0 - 1 + row % RYW;
+        if (t < 0 || t >= n0) continue;
+        if (PER1) { if (x < 0) x += n1; else if (x >= n1) x -= n1; }
+        else if (x < 0 || x >= n1) continue;
+        const int q = t * pl + x * n2 + gy;
+        pf_l2(rho + off + q);
+        C.prefetch(q);
+      }
+      for (int row = r0; row < TT * FS_TX; row += rs) {
+        const size_t j = off + (size_t)(t0 + row / FS_TX) * pl + (size_t)(x0 + row % FS_TX) * n2 + gy;
+        if (MODE != SM_APPLY && MODE != SM_APPLYP) pf_l2(a.r + j);
+        if (MODE == SM_POST0 || MODE == SM_CHEB || MODE == SM_CHEB_DOT) pf_l2(a.dinv + j);
+        if ((MODE == SM_CHEB || MODE == SM_CHEB_DOT) && a.d) pf_l2(a.d + j);
+      }
+    }
   }
   float beta = 0.f;
   if (MODE == SM_APPLYP && a.d) {
     const double rz = sum_partials(a.rz, b, a.nrz), ro = a.rz_old[b];
     beta = (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f;
   }
-  __syncthreads();
   if (!mbar_wait(&bar, 0, FS_WAIT_LIMIT) && a.err) atomicExch(a.err, 1);
-  __syncthreads();
   if (MODE == SM_APPLYP) {
     // p = x + beta d on the staged operand (tile and halo), p on the tile to e
     constexpr int GW = W / 4;

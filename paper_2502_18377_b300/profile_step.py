@@ -17,32 +17,28 @@ import json
 import numpy as np
 import torch
 
-from . import workloads as wl
+from . import settings
 from .binding import Solver
-
-WORKLOADS = {
-    "transport_2d": (wl.transport_2d, 4, (32, 256, 256)),
-    "reaction_diffusion_2d_64x128x128": (wl.reaction_diffusion_2d, 8, (64, 128, 128)),
-    "reaction_diffusion_2d": (wl.reaction_diffusion_2d, 16, (32, 64, 64)),
-}
-
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="transport_2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="transport_2d", choices=sorted(settings.BENCH_WORKLOADS))
     ap.add_argument("--batch", type=int)
     ap.add_argument("--grid", type=int, nargs=3)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--fused-step", type=int, default=1)
-    ap.add_argument("--inner-iters", type=int, default=5)
-    ap.add_argument("--cheb-degree", type=int, default=5)
+    ap.add_argument("--inner-iters", type=int, help="default: the workload's benchmark setting")
+    ap.add_argument("--cheb-degree", type=int, help="default: the workload's benchmark setting")
     a = ap.parse_args()
-    gen, b0, g0 = WORKLOADS[a.workload]
-    w = gen(batch=a.batch or b0, n=tuple(a.grid) if a.grid else g0)
+    w = settings.make(a.workload, batch=a.batch, grid=a.grid)
+    kw = settings.solver_kwargs(a.workload)
+    if a.inner_iters:
+        kw["inner_iters"] = a.inner_iters
+    if a.cheb_degree:
+        kw["cheb_degree"] = a.cheb_degree
     dev = lambda x: torch.tensor(np.asarray(x, dtype=np.float32), device="cuda").contiguous()
-    s = Solver(w.geom, w.batch, w.field_of, w.fields.shape[0], fused_step=a.fused_step,
-               inner_iters=a.inner_iters, cheb_degree=a.cheb_degree)
+    s = Solver(w.geom, w.batch, w.field_of, w.fields.shape[0], fused_step=a.fused_step, **kw)
     args = (dev(w.fields), dev(w.scalars), dev(w.rhs), dev(w.omega))
     tgt = dev(w.target)
     z = torch.empty((w.batch, s.V, w.npoints), device="cuda")
@@ -56,6 +52,7 @@ def main():
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
+    s.profile(1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(a.steps):
@@ -63,9 +60,12 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(a.steps, 1)
+    pm, pn, pb, kernels = s.profile(0)
+    dom = {"us": 1e3 * pm / pn, "GBps": pb / pn / (pm / pn / 1e3) / 1e9} if pn else None
     print(json.dumps({"workload": a.workload, "batch": w.batch, "grid": list(w.geom["n"]), "ms_per_step": ms,
-                      "points_per_s": w.batch * w.npoints / ms * 1e3, "levels": s.levels(),
-                      "forward": fwd, "adjoint": adj}))
+                      "points_per_s": w.batch * w.npoints / ms * 1e3, "levels": s.levels(), "solver_settings": kw,
+                      "forward": fwd, "adjoint": adj,
+                      "dominant_step": dom, "kernels_per_step": kernels / max(a.steps, 1)}))
 
 
 if __name__ == "__main__":

@@ -1,5 +1,6 @@
-"""Full-size checks, in the launch configuration the benchmark times (solver
-defaults), element by element against the oracle.
+"""Full-size checks, in the launch configuration the benchmark times (the
+workloads and solver settings of paper_2502_18377_b300.settings), element by
+element against the oracle.
 
 * Linearized Burgers at its full size (B = 32, 128 x 256): the oracle solves
   sampled instances exactly; forward z and the gradients must match (1e-6 /
@@ -89,15 +90,26 @@ def test_burgers_full_size_sampled_instances():
         assert _rel(dom[b], dw) <= 1e-5
 
 
-FULL = [("reaction_diffusion_2d_B16_32x64x64", 2, (0, 7, 15)),
-        ("reaction_diffusion_2d_B8_64x128x128", 4, (0, 5)),
-        ("transport_2d_B4_32x256x256", 5, (0, 3))]
+FULL = [("reaction_diffusion_2d", 2, (0, 7, 15)),
+        ("reaction_diffusion_2d_64x128x128", 4, (0, 5)),
+        ("transport_2d", 5, (0, 3))]
+
+
+def _bench_solver(name, w):
+    """The solver as the benchmark creates it for workload `name`."""
+    from paper_2502_18377_b300 import settings
+    from paper_2502_18377_b300.binding import Solver
+    return Solver(w.geom, w.batch, w.field_of, w.fields.shape[0], **settings.solver_kwargs(name))
+
+
+def _bench_workload(name):
+    from paper_2502_18377_b300 import settings
+    return _round(settings.make(name))
 
 
 @pytest.mark.parametrize("name,cfg,sampled", FULL, ids=[f[0] for f in FULL])
 def test_manufactured_forward_full_size(name, cfg, sampled):
-    from paper_2502_18377_b300.binding import Solver
-    w = _round(wl.CONFIGS[cfg]())
+    w = _bench_workload(name)
     B, V, N = w.batch, asm.n_vars(w.ndim), w.npoints
     coeff = w.full_coeff()
     rng = np.random.default_rng(7000 + cfg)
@@ -108,7 +120,7 @@ def test_manufactured_forward_full_size(name, cfg, sampled):
         u = wl.box_filter(rng.normal(size=w.geom["n"]), w.geom["periodic"]).ravel()
         zb, rb, ob = mf.consistent_data(w.geom, coeff[:, b], u)
         ze[b], rhs[b], om[b] = zb, rb, ob
-    s = Solver(w.geom, w.batch, w.field_of, w.fields.shape[0])
+    s = _bench_solver(name, w)
     z64 = torch.empty((B, V, N), device="cuda", dtype=torch.float64)
     z = s.forward(_dev(w.fields), _dev(w.scalars), _dev(rhs), _dev(om), z64=z64)
     z, z64 = z.cpu().numpy(), z64.cpu().numpy()
@@ -126,8 +138,7 @@ def test_manufactured_adjoint_full_size(name, cfg, sampled):
     exact solution are that map of its u for any such source, and the map
     amplifies the float32 rounding of g into these blocks; see the module
     docstring)."""
-    from paper_2502_18377_b300.binding import Solver
-    w = _round(wl.CONFIGS[cfg]())
+    w = _bench_workload(name)
     B, V, N = w.batch, asm.n_vars(w.ndim), w.npoints
     coeff = w.full_coeff()
     rng = np.random.default_rng(8000 + cfg)
@@ -140,7 +151,7 @@ def test_manufactured_adjoint_full_size(name, cfg, sampled):
         assert resid < 1e-10, resid
         ue[b], mats[b] = u, A
         g[b] = gb.reshape(V, N)
-    s = Solver(w.geom, w.batch, w.field_of, w.fields.shape[0])
+    s = _bench_solver(name, w)
     args = (_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega))
     z = s.forward(*args)
     dz64 = torch.empty((B, V, N), device="cuda", dtype=torch.float64)
