@@ -83,6 +83,8 @@ struct mpn_problem {
   double *kap = nullptr;
   double *uf64 = nullptr;  // FP64 u of the last forward (the adjoint's lambda*)
   double *part = nullptr;  // partial-sum slots [NSLOT][B][PMAX]
+  int* pcnt = nullptr;     // [2][B] CTA counters of the fused steps that finish <r, z> and <p, S p>
+  double* ptot = nullptr;  // [2][B] their finished sums
   double *dscal = nullptr; // device scalars: scale[B], rz_old[B], out[8][B]
   float* lam = nullptr;    // lambda_max per level and instance [L][B]
   double* hbuf = nullptr;  // pinned host buffer
@@ -262,6 +264,11 @@ extern "C" int mpn_levels(const mpn_problem* p, int* nl, int* shapes) {
 // rows of at most this many points stay whole in a fused tile; wider rows
 // (a multiple of 64, >= 128) are split into 64-point y segments
 #define FS_MAX_NY 128
+// CTAs of one fused step below which a level's tiles are made thinner in time
+// (148 SMs x 4 resident CTAs)
+#ifndef FS_MIN_CTAS
+#define FS_MIN_CTAS 592
+#endif
 // largest whole-problem system of the direct path (unknowns per instance)
 #define MPN_DIRECT_MAX 4096
 // shared memory of the coarsest-inverse kernel (floats)
@@ -458,7 +465,10 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
       l.fs_layout = !(per1 && per2) ? SL_ANY
                     : rd ? (d.field_of[4] == d.field_of[6] ? SL_RDI : SL_RD)
                     : p->field_mask == FS_MASK_TR ? SL_TR : SL_ANY;
-      const int tt = n0 % 8 == 0 ? 8 : (n0 % 4 == 0 ? 4 : 0);
+      int tt = n0 % 8 == 0 ? 8 : (n0 % 4 == 0 ? 4 : 0);
+      // whole-row levels with rows of >= 64 points that 8-plane tiles would
+      // leave short of one wave of CTAs on the device take 4-plane tiles
+      if (tt == 8 && n2 >= 64 && (n0 / 8) * (l.g.n[1] / FS_TX) * p->B < FS_MIN_CTAS) tt = 4;
       const bool split_ok = n2 % 64 == 0 && n2 >= 128 && step_y_has(8, 64, per1, per2, l.fs_layout) && n0 % 8 == 0;
       const bool whole_ok = tt && n2 <= FS_MAX_NY && step_row_has(tt, per1, per2, l.fs_layout);
       if (split_ok && (d.fused_step == 2 || !whole_ok)) { l.fs_tt = 8; l.fs_ty = 64; }
@@ -508,6 +518,8 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   AL(p->u64, N0); AL(p->r64, N0); AL(p->y64, N0); AL(p->g64, N0); AL(p->rho64, N0);
   AL(p->uf64, N0); AL(p->kap, N0 * V);
   AL(p->part, (size_t)NSLOT * B * MPN_PMAX);
+  AL(p->pcnt, (size_t)2 * B);
+  AL(p->ptot, (size_t)2 * B);
   AL(p->dscal, (size_t)16 * B);
   AL(p->lam, (size_t)MAXL * B);
   if (d.krylov == MPN_KRYLOV_FGMRES) {
@@ -525,6 +537,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   for (int v = 0; v < 8; ++v) fo[v] = v < V ? d.field_of[v] : -1;
   if (cudaMemcpy(p->field_of_dev, fo, sizeof(fo), cudaMemcpyHostToDevice) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
   if (cudaMemset(p->kerr, 0, sizeof(int)) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
+  if (cudaMemset(p->pcnt, 0, sizeof(int) * 2 * B) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
   if (cudaMallocHost((void**)&p->hbuf, sizeof(double) * 16 * B) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
 
   // Chebyshev coefficients on [lo, 1] for Dinv scaled by 1 / lambda_max
@@ -891,6 +904,9 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st, bool started = false, 
     a.x = cur; a.e = other(cur); a.d = prev(cur, false);
     const bool dot = zdot && s == m - 1;
     a.part = dot ? zdot : nullptr;
+    // the step's last CTA per instance also finishes <e', r> (PCG's <r, z>)
+    a.cnt = dot ? p->pcnt : nullptr;
+    a.tot = dot ? p->ptot : nullptr;
     stencil(p, k, a, dot ? SM_CHEB_DOT : SM_CHEB, st);
     cur = other(cur);
   }
@@ -946,21 +962,25 @@ static int pcg(mpn_problem* p, int iters, cudaStream_t st, bool started) {
       StepArgs a;
       memset(&a, 0, sizeof(a));
       a.x = zv; a.out = p->q; a.part = slot(p, S_PQ);
+      a.cnt = p->pcnt + p->B; a.tot = p->ptot + p->B;   // <p, S p> finished by the step's last CTAs
       if (it == 0) {
         a.e = pb[c];
       } else {
         a.d = pb[c]; a.e = pb[c ^ 1];
         a.rz = slot(p, S_RZ); a.nrz = Prz; a.rz_old = rz_old;
+        a.rz_tot = ze ? p->ptot : nullptr;
         c ^= 1;
       }
       stencil(p, 0, a, SM_APPLYP, st);
       const float* dst = it < iters - 1 ? l.dinv : nullptr;   // a V-cycle follows
       if (v4)
         ++p->nlaunch, k_pcg_xr<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, Prz, pb[c], p->q,
-                                                              p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, ddir0);
+                                                              p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, ddir0,
+                                                              ze ? p->ptot : nullptr, p->ptot + p->B);
       else
         ++p->nlaunch, k_pcg_xr<false><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, Prz, pb[c], p->q,
-                                                               p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, ddir0);
+                                                               p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, ddir0,
+                                                               ze ? p->ptot : nullptr, p->ptot + p->B);
       CKL();
       if (it == iters - 1) break;
       TRY(precond(p, st, true, ze));
@@ -974,10 +994,12 @@ static int pcg(mpn_problem* p, int iters, cudaStream_t st, bool started) {
     const float* dst = it < iters - 1 ? l.dinv : nullptr;   // a V-cycle follows
     if (v4)
       ++p->nlaunch, k_pcg_xr<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, Prz, p->pv, p->q,
-                                                            p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, ddir0);
+                                                            p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, ddir0,
+                                                            nullptr, nullptr);
     else
       ++p->nlaunch, k_pcg_xr<false><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, Prz, p->pv, p->q,
-                                                             p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, ddir0);
+                                                             p->x, l.r, rz_old, dst, p->cheb_inv_th, cur0, ddir0,
+                                                             nullptr, nullptr);
     CKL();
     if (it == iters - 1) break;
     TRY(precond(p, st, true, ze));

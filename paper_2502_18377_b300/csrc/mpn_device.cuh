@@ -325,6 +325,38 @@ __device__ __forceinline__ double block_sum(double v) {
   return r;
 }
 
+// Writes this CTA's partial sum s (valid in thread 0) for instance b; with a
+// counter, the last of the instance's nblk CTAs to finish (a fence, then one
+// atomic increment per CTA) sums all partials in a fixed order into tot[b]
+// and resets the counter, so consumers read one number instead of every CTA
+// of theirs summing the partials again.  Deterministic: the order of the
+// final sum does not depend on which CTA is last.  All threads must call it.
+__device__ __forceinline__ void partial_finish(double s, double* __restrict__ part, int* cnt, double* tot, int b,
+                                               int blk, int nblk) {
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    part[b * MPN_PMAX + blk] = s;
+    int l = 0;
+    if (cnt) {
+      __threadfence();
+      l = atomicAdd(cnt + b, 1) == nblk - 1;
+    }
+    last = l;
+  }
+  __syncthreads();
+  if (last && threadIdx.x < 32) {
+    __threadfence();
+    double v = 0;
+    for (int k = threadIdx.x; k < nblk; k += 32) v += __ldcg(part + b * MPN_PMAX + k);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) {
+      tot[b] = v;
+      cnt[b] = 0;
+    }
+  }
+}
+
 // Sum of the P partials of instance b (consumer-side second stage); every
 // thread of the block receives the same value.
 __device__ __forceinline__ double sum_partials(const double* __restrict__ part, int b, int P) {

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(FS_TPB) k_step3y(Grid g, Coef cf, const float*
   }
   float beta = 0.f;
   if (MODE == SM_APPLYP && a.d) {
-    const double rz = sum_partials(a.rz, b, a.nrz), ro = a.rz_old[b];
+    const double rz = a.rz_tot ? a.rz_tot[b] : sum_partials(a.rz, b, a.nrz), ro = a.rz_old[b];
     beta = (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f;
   }
   if (!mbar_wait(&bar, 0, FS_WAIT_LIMIT) && a.err) atomicExch(a.err, 1);
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(FS_TPB) k_step3y(Grid g, Coef cf, const float*
     }
   }
   if ((MODE == SM_APPLY || MODE == SM_APPLYP || MODE == SM_CHEB_DOT) && a.part) {
-    double s = block_sum((double)acc);
-    if (threadIdx.x == 0) a.part[b * MPN_PMAX + blockIdx.x] = s;
+    const double s = block_sum((double)acc);
+    partial_finish(s, a.part, a.cnt, a.tot, b, blockIdx.x, gridDim.x);
   }
 }

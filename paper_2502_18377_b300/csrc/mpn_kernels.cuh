@@ -679,7 +679,8 @@ template <bool V4>
 __global__ void k_pcg_xr(int N, const double* __restrict__ part_rz, const double* __restrict__ part_pq, int P,
                          int Prz, const float* __restrict__ pv, const float* __restrict__ q, float* __restrict__ x,
                          float* __restrict__ r, double* __restrict__ rz_old, const float* __restrict__ dinv,
-                         float inv_th, float* __restrict__ e, float* __restrict__ d) {
+                         float inv_th, float* __restrict__ e, float* __restrict__ d,
+                         const double* __restrict__ tot_rz, const double* __restrict__ tot_pq) {
   const int b = blockIdx.y;
   const size_t off = (size_t)b * N;
   const int n = V4 ? N >> 2 : N;
@@ -689,8 +690,9 @@ __global__ void k_pcg_xr(int N, const double* __restrict__ part_rz, const double
     xv = vld<V4>(x + off, i0); pp = vld<V4>(pv + off, i0); rv = vld<V4>(r + off, i0); qq = vld<V4>(q + off, i0);
     if (dinv) dv = vld<V4>(dinv + off, i0);
   }
-  const double rz = sum_partials(part_rz, b, Prz);
-  const double pq = sum_partials(part_pq, b, P);
+  // the finished sums where the producing kernels wrote them, else the partials
+  const double rz = tot_rz ? tot_rz[b] : sum_partials(part_rz, b, Prz);
+  const double pq = tot_pq ? tot_pq[b] : sum_partials(part_pq, b, P);
   const float alpha = (pq > 0 && rz > 0) ? (float)(rz / pq) : 0.f;
   if (blockIdx.x == 0 && threadIdx.x == 0) rz_old[b] = rz;
   for (int i = i0; i < n; i += stride) {
