@@ -264,6 +264,11 @@ extern "C" int mpn_levels(const mpn_problem* p, int* nl, int* shapes) {
 // rows of at most this many points stay whole in a fused tile; wider rows
 // (a multiple of 64, >= 128) are split into 64-point y segments
 #define FS_MAX_NY 128
+// Lower end of the Chebyshev smoothing interval, as a fraction of the
+// estimated lambda_max of D^-1 S
+#ifndef MPN_CHEB_LO
+#define MPN_CHEB_LO 0.1
+#endif
 // CTAs of one fused step below which a level's tiles are made thinner in time
 // (148 SMs x 4 resident CTAs)
 #ifndef FS_MIN_CTAS
@@ -541,7 +546,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   if (cudaMallocHost((void**)&p->hbuf, sizeof(double) * 16 * B) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
 
   // Chebyshev coefficients on [lo, 1] for Dinv scaled by 1 / lambda_max
-  const double lo = 0.1, th = (1.0 + lo) / 2, de = (1.0 - lo) / 2, sg = th / de;
+  const double lo = MPN_CHEB_LO, th = (1.0 + lo) / 2, de = (1.0 - lo) / 2, sg = th / de;
   p->cheb_inv_th = (float)(1.0 / th);
   double r0 = 1.0 / sg;
   for (int k = 1; k < d.cheb_degree && k < 32; ++k) {
