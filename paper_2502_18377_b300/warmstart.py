@@ -29,6 +29,27 @@ def _chk(s, where):
         raise MpnError(s, where)
 
 
+def allreduce_mean(tensors, group=None):
+    """Averages `tensors` in place over the ranks of the process group, in one
+    all-reduce of a flat buffer (sum, then division by the world size): with
+    an equal batch shard per rank, the mean of the per-rank gradients of the
+    per-rank mean loss is the gradient of the full-batch mean loss.  NCCL for
+    GPU tensors, gloo for CPU tensors; a no-op without a multi-rank group.
+    Raises if a rank has left (the collective fails or times out), so a
+    failed rank is reported, never waited on forever."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:
+        return
+    flat = torch.cat([t.reshape(-1) for t in tensors])
+    dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
+    flat /= dist.get_world_size(group)
+    off = 0
+    for t in tensors:
+        n = t.numel()
+        t.copy_(flat[off:off + n].view_as(t))
+        off += n
+
+
 class WarmStartNet:
     def __init__(self, geom: dict, batch: int, nfields: int, seed: int = 0, lr: float = 1e-3,
                  device="cuda"):
@@ -149,9 +170,13 @@ class WarmStartNet:
                 g = ws["dx"]
         return ws["loss"].sum() / (self.B * self.N)
 
-    def train_step(self, fields, rhs, u_target):
+    def train_step(self, fields, rhs, u_target, group=None):
+        """One Adam step on this rank's batch; under a multi-rank process
+        group the weight and bias gradients are first averaged over the ranks
+        (data parallelism: every rank holds the same parameters)."""
         loss = self.gradients(fields, rhs, u_target)
         ws = self._ws
+        allreduce_mean(ws["dw"] + ws["db"], group)
         self.step += 1
         st = _stream()
         params = self.w + self.b

@@ -79,3 +79,78 @@ def test_a_failing_rank_is_reported_not_hung():
     codes, out = _run(2, fail_rank=1)
     assert codes[1] != 0
     assert all(c is not None for c in codes), codes
+
+
+def _grad_worker(rank, world, port, q, leave_after):
+    """Linear least squares on a shard of a fixed batch: the all-reduced mean
+    of the per-rank gradients must equal the full-batch gradient.  With
+    leave_after >= 0, rank 1 leaves after that many steps and rank 0 must
+    see its next collective fail, not hang."""
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import datetime
+    import torch
+    import torch.distributed as dist
+    from paper_2502_18377_b300.warmstart import allreduce_mean
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    g = torch.Generator().manual_seed(3)
+    X = torch.randn(8, 3, generator=g, dtype=torch.float64)
+    y = torch.randn(8, generator=g, dtype=torch.float64)
+    w = torch.randn(3, generator=g, dtype=torch.float64)
+    b = torch.zeros(1, dtype=torch.float64)
+    shard = slice(4 * rank, 4 * rank + 4)
+    try:
+        for step in range(3):
+            if leave_after >= 0 and rank == 1 and step == leave_after:
+                return                                  # leaves between steps
+            Xr, yr = X[shard], y[shard]
+            res = Xr @ w + b - yr
+            gw = 2.0 / Xr.shape[0] * Xr.T @ res          # gradient of this rank's mean loss
+            gb = (2.0 / Xr.shape[0] * res.sum()).reshape(1)
+            allreduce_mean([gw, gb])
+            full = X @ w + b - y
+            ok = bool(torch.allclose(gw, 2.0 / 8 * X.T @ full, rtol=1e-12, atol=1e-12) and
+                      torch.allclose(gb, (2.0 / 8 * full.sum()).reshape(1), rtol=1e-12, atol=1e-12))
+            q.put((rank, step, ok, ""))
+            w = w - 0.1 * gw
+            b = b - 0.1 * gb
+    except Exception as e:                              # the collective failed: report it
+        q.put((rank, -1, False, type(e).__name__))
+    finally:
+        try:
+            dist.destroy_process_group()
+        except Exception:
+            pass
+
+
+def _run_grad(world, leave_after):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_grad_worker, args=(r, world, port, q, leave_after)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    for p in procs:
+        if p.is_alive():
+            p.terminate()
+            p.join(timeout=10)
+    out = []
+    while not q.empty():
+        out.append(q.get())
+    return [p.exitcode for p in procs], sorted(out)
+
+
+def test_gradient_allreduce_equals_full_batch_gradient():
+    codes, out = _run_grad(2, -1)
+    assert codes == [0, 0], codes
+    assert len(out) == 6 and all(ok for _, _, ok, _ in out), out
+
+
+def test_rank_leaving_between_steps_is_reported():
+    codes, out = _run_grad(2, 1)
+    assert codes == [0, 0], codes
+    steps0 = [s for r, s, ok, _ in out if r == 0]
+    assert 0 in steps0                                  # the first step ran on both ranks
+    assert any(r == 0 and s == -1 and err for r, s, ok, err in out), out   # rank 0 saw the failure
