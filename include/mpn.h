@@ -155,13 +155,28 @@ int mpn_forward(mpn_problem* p, const float* fields, const float* scalars,
  * FP64 from the FP64 forward solution the problem keeps.
  * flags bit 0 (MPN_REUSE_SETUP): the data are those of the last mpn_forward
  * on this problem, so its multigrid setup and FP64 solution are reused;
- * without it (or if no forward was done) the forward solve is recomputed
- * first.  z (the caller's FP32 forward output) may be null; it is not read. */
+ * without it, if no forward was done, or if fields, scalars, rhs or omega are
+ * not the buffers that last forward read, the forward solve is recomputed
+ * first.  (A caller that may have changed the contents of the same buffers,
+ * or run another forward in between, compares mpn_generation before and
+ * after.)  z (the caller's FP32 forward output) may be null; it is not read. */
 #define MPN_REUSE_SETUP 1
 int mpn_adjoint(mpn_problem* p, const float* fields, const float* scalars,
                 const float* rhs, const float* omega, const float* z,
                 const float* g_z, float* dfields, float* dscalars, float* drhs,
                 float* domega, float* dz, double* dz64, int flags, mpn_stats* stats, void* stream);
+
+/* Number of forward solves completed on this problem (the adjoint's own
+ * recomputations included); -1 for a null problem.  Host-side query. */
+long long mpn_generation(const mpn_problem* p);
+
+/* Host-side fault injection for tests of the error path: the next solve on
+ * this problem sets, by a memset on its stream before the first refinement
+ * sweep, the device error word that a kernel's bounded wait sets when it
+ * gives up, so that solve returns MPN_ERR_CUDA the way a real give-up would.
+ * No kernel waits, traps or faults; the problem stays usable (every solve
+ * starts with the word cleared). */
+int mpn_inject_wait_failure(mpn_problem* p);
 
 /* dl/dz of l = mean over (b, i) of (u - target)^2, written into g_z [B][V][N]
  * (zero on the derivative unknowns): the loss used by the benchmarks. */

@@ -5,7 +5,10 @@ fields and per-instance scalars, right-hand side b, Dirichlet values omega).
 Backward (Eq. 11 and the gradients after it): one adjoint solve with the same
 operator gives dl/dfields, dl/dscalars, dl/db and dl/domega.  With
 ``recompute=True`` the forward solution is not kept for the backward pass;
-the adjoint call recomputes it (less memory, one more solve).
+the adjoint call recomputes it (less memory, one more solve).  Without it,
+the backward pass reuses the problem's kept forward state only if no other
+forward ran on the same solver in between (its generation counter is
+unchanged); otherwise it recomputes, so interleaved solves never mix states.
 """
 from __future__ import annotations
 
@@ -24,6 +27,7 @@ class NeuRLPSolve(torch.autograd.Function):
         z = solver.forward(fields_c, scalars_c, rhs_c, omega_c)
         ctx.solver = solver
         ctx.recompute = recompute
+        ctx.gen = solver.generation()
         if recompute:
             ctx.save_for_backward(fields_c, scalars_c, rhs_c, omega_c)
         else:
@@ -35,8 +39,9 @@ class NeuRLPSolve(torch.autograd.Function):
         saved = ctx.saved_tensors
         fields, scalars, rhs, omega = saved[:4]
         z = None if ctx.recompute else saved[4]
+        reuse = not ctx.recompute and ctx.solver.generation() == ctx.gen
         dfields, dscal, drhs, dom = ctx.solver.adjoint(fields, scalars, rhs, omega, z, g_z.contiguous(),
-                                                       reuse_setup=not ctx.recompute)
+                                                       reuse_setup=reuse)
         return dfields, dscal, drhs, dom, None, None
 
 

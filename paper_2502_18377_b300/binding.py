@@ -58,6 +58,8 @@ EXPORTS = {
     "mpn_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(MpnStats), _P]),
     "mpn_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int,
                                    ctypes.POINTER(MpnStats), _P]),
+    "mpn_generation": (ctypes.c_longlong, [_P]),
+    "mpn_inject_wait_failure": (ctypes.c_int, [_P]),
     "mpn_mse_grad": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "mpn_apply_reduced": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "mpn_profile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -236,6 +238,17 @@ class Solver:
     @property
     def workspace_bytes(self):
         return int(self.lib.mpn_workspace_bytes(self._h))
+
+    def generation(self):
+        """Forward solves completed on this problem so far."""
+        return int(self.lib.mpn_generation(self._h))
+
+    def inject_wait_failure(self):
+        """Test hook: the next solve reports a kernel's bounded wait giving up
+        (MPN_ERR_CUDA) through the device error word, without any fault."""
+        s = self.lib.mpn_inject_wait_failure(self._h)
+        if s != 0:
+            raise MpnError(s, "mpn_inject_wait_failure")
 
     def fused_level(self):
         """First level of the fused coarse end of the V-cycle, or -1."""

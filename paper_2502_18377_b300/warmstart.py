@@ -202,3 +202,37 @@ class WarmStartNet:
         self.step, self.lr = sd["step"], sd["lr"]
         self.in_scale = sd["in_scale"].to(self.dev)
         self.out_scale = sd["out_scale"]
+
+
+class WarmStartTrainer:
+    """Epochs over a fixed list of training batches (fields, rhs, u) in a
+    seeded order: one permutation per epoch from a CPU generator.  Its
+    checkpoint holds the network's parameters, Adam moments and step, the
+    generator's state and the data cursor (epoch, permutation, position), so
+    a run resumed from it repeats the uninterrupted run bit for bit (the
+    layer kernels and their reductions are deterministic)."""
+
+    def __init__(self, net: WarmStartNet, batches, seed: int = 0, group=None):
+        self.net, self.batches, self.group = net, batches, group
+        self.gen = torch.Generator().manual_seed(seed)
+        self.epoch, self.pos = 0, 0
+        self.perm = torch.randperm(len(batches), generator=self.gen)
+
+    def step(self):
+        """One Adam step on the next batch; returns its loss (device scalar)."""
+        if self.pos == len(self.perm):
+            self.epoch += 1
+            self.pos = 0
+            self.perm = torch.randperm(len(self.batches), generator=self.gen)
+        f, r, u = self.batches[int(self.perm[self.pos])]
+        self.pos += 1
+        return self.net.train_step(f, r, u, self.group)
+
+    def state_dict(self):
+        return dict(net=self.net.state_dict(), gen=self.gen.get_state(), epoch=self.epoch, pos=self.pos,
+                    perm=self.perm.clone())
+
+    def load_state_dict(self, sd):
+        self.net.load_state_dict(sd["net"])
+        self.gen.set_state(sd["gen"])
+        self.epoch, self.pos, self.perm = sd["epoch"], sd["pos"], sd["perm"].clone()

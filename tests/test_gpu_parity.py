@@ -443,3 +443,21 @@ def test_ysplit_operator_three_segments():
             el = _oracle_instance(w, b)[6]
             ref = el.S @ u[b].astype(np.float64)
             assert _rel(q[b], ref) <= 2e-5, (per, b, _rel(q[b], ref))
+
+
+def test_device_error_word_reaches_the_host():
+    """The error word a kernel's bounded wait sets when it gives up is read
+    back with each sweep's scalars and turned into MPN_ERR_CUDA.  Injected on
+    the host (no kernel waits or faults); the next solve starts with the word
+    clear and meets the oracle."""
+    from paper_2502_18377_b300.binding import MpnError
+    w = _round(wl.reaction_diffusion_2d(batch=2, n=(8, 16, 16)))
+    s = _solver(w)
+    args = [_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega)]
+    s.inject_wait_failure()
+    with pytest.raises(MpnError) as e:
+        s.forward(*args)
+    assert e.value.status == 6 and "bounded wait" in str(e.value), e.value
+    z = s.forward(*args).cpu().numpy()
+    zr = _oracle_instance(w, 0)[4]
+    assert _rel(z[0].ravel(), zr) <= FWD_TOL

@@ -157,3 +157,42 @@ def test_trained_network_gains():
     print("warm-start gain:", dict(err0=err0, cold=cold, warm=warm))
     assert warm["pcg_iters"] <= cold["pcg_iters"], (warm, cold)
     assert float((z_warm - z_cold).norm() / z_cold.norm()) <= 2e-6
+
+
+def test_trainer_checkpoint_resume_is_bitwise():
+    """Train 5 steps, checkpoint (parameters, Adam moments, step, scales,
+    generator state, data cursor), resume in a fresh trainer for 6 more
+    steps: every parameter and moment equals that of an uninterrupted
+    11-step run bit for bit (the cursor crosses an epoch boundary)."""
+    import io
+    from paper_2502_18377_b300.warmstart import WarmStartNet, WarmStartTrainer
+    dev = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")
+    batches = []
+    for k in range(4):
+        w = _small_family(2, 30000 + 10 * k)
+        batches.append((dev(w.fields), dev(w.rhs), dev(w.target)))
+
+    def make():
+        net = WarmStartNet(w.geom, 2, 2, seed=5, lr=2e-3)
+        net.fit_scales(*batches[0])
+        return WarmStartTrainer(net, batches, seed=11)
+
+    full = make()
+    for _ in range(11):
+        full.step()
+    first = make()
+    for _ in range(5):
+        first.step()
+    buf = io.BytesIO()
+    torch.save(first.state_dict(), buf)
+    buf.seek(0)
+    resumed = make()
+    resumed.load_state_dict(torch.load(buf))
+    for _ in range(6):
+        resumed.step()
+    torch.cuda.synchronize()
+    assert resumed.epoch == full.epoch == 2 and resumed.pos == full.pos
+    a, b = full.net, resumed.net
+    for x, y in zip(a.w + a.b + a.m + a.v + a.wb, b.w + b.b + b.m + b.v + b.wb):
+        assert torch.equal(x, y)
+    assert a.step == b.step == 11
