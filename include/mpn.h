@@ -245,7 +245,7 @@ typedef struct mpn_conv_desc {
 #define MPN_CONV_RELU 1   /* y = max(., 0) */
 #define MPN_CONV_F32 2    /* FP32 output (else BF16) */
 #define MPN_CONV_BIAS 4   /* add bias */
-#define MPN_WGRAD_CHUNK 2048
+#define MPN_WGRAD_CHUNK 65536   /* points per partial sum of the weight gradient */
 #define MPN_MSE_BLOCKS 64
 
 /* y = act(conv(x, W) + b): BF16 tensor-core (mma.sync m16n8k16) implicit GEMM, FP32 accumulation. */
@@ -257,8 +257,9 @@ int mpn_conv3d_backward_data(const mpn_conv_desc* d, const void* g_out, const vo
                              float* g_in, void* stream);
 /* Bytes of FP32 scratch mpn_conv3d_backward_weights needs. */
 size_t mpn_conv3d_wgrad_scratch_bytes(const mpn_conv_desc* d);
-/* dW [27][cout][cin] = sum_p g_out[p][co] x[nbr(p, tap)][ci], db [cout] = sum_p g_out[p][co]
- * (FP32 accumulation, deterministic two-stage reduction). */
+/* dW [27][cout][cin] = sum_p g_out[p][co] x[nbr(p, tap)][ci], db [cout] = sum_p g_out[p][co]:
+ * per tap a GEMM over the points on the tensor cores (mma.sync m16n8k16 bf16, FP32 accumulation)
+ * for every chunk of MPN_WGRAD_CHUNK points, then the chunks summed in a fixed order (deterministic). */
 int mpn_conv3d_backward_weights(const mpn_conv_desc* d, const void* g_out, const void* x, float* scratch,
                                 float* dw, float* db, void* stream);
 /* out (BF16) = g * (y > 0) elementwise (y BF16, nullable: no mask), n elements. */
@@ -266,7 +267,8 @@ int mpn_relu_mask(long long n, const float* g, const void* y, void* out, void* s
 /* Adam on FP32 master weights w with moments m, v (step >= 1); w_bf16 (nullable) gets the BF16 copy. */
 int mpn_adam_step(long long n, float* w, const float* g, float* m, float* v, float lr, float beta1, float beta2,
                   float eps, int step, void* w_bf16, void* stream);
-/* x0 [B][N][16] BF16 = (fields[0..F), rhs) * scale[c], channels zero-padded. */
+/* x0 [B][N][16] BF16 = (fields[0..F), rhs, running sum over time planes 0..t of rhs at the same
+ * (x, y)) * scale[c], channels zero-padded; F <= 14. */
 int mpn_pack_inputs(const mpn_conv_desc* d, int nfields, const float* fields, const float* rhs, const float* scale,
                     void* x0, void* stream);
 /* MSE of channel 0 of y [B][N][16] (FP32) against target [B][N]: g (same shape as y) and

@@ -1170,6 +1170,11 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
   p->inject_wait = 0;
   // ||rhs|| for the relative residual: the first residual when starting from 0
   if (!zero_start) TRY(residual64(p, nullptr, g_adj, p->r64, slot(p, S_GN), st));
+  // first sweep whose predicted error can end the refinement: from a zero
+  // start the first update is the whole solution, so the contraction is
+  // measured from the second ratio on (third sweep); from a warm start the
+  // first update is already a correction (second sweep)
+  const int first = zero_start ? 2 : 1;
   std::vector<double> gnorm(B, 0.0);
   int iters = p->desc.direct ? 1 : p->desc.inner_iters, total_iters = 0;
   const bool trace = getenv("MPN_TRACE") != nullptr;
@@ -1198,7 +1203,7 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
       if (sweep >= 1) maxq = std::max(maxq, q1);
       const double q = sweep >= 1 ? std::max(q1, prev_q[b]) : q1;
       if (sweep >= 1) prev_q[b] = q1;
-      double pred = sweep < 2 ? upd : (q < 1.0 ? upd * q / (1.0 - q) : HUGE_VAL);
+      double pred = sweep < first ? upd : (q < 1.0 ? upd * q / (1.0 - q) : HUGE_VAL);
       if (sweep >= 2 && upd > 10.0 * prev_upd[b] && upd > 1e-3) grew = true;
       if (sweep >= 2) maxrate = std::max(maxrate, upd / std::max(prev_upd[b], 1e-300));
       prev_upd[b] = upd;
@@ -1213,7 +1218,7 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
     sres.rel_residual = maxres;
     if (bad) { status = MPN_ERR_NONFINITE; break; }
     if (grew) { status = MPN_ERR_DIVERGED; break; }
-    if ((sweep >= 2 && maxpred <= p->desc.tol) || (sweep >= 1 && maxupd <= p->desc.tol * 0.1)) { status = MPN_OK; break; }
+    if ((sweep >= first && maxpred <= p->desc.tol) || (sweep >= 1 && maxupd <= p->desc.tol * 0.1)) { status = MPN_OK; break; }
     const int done_iters = iters;
     // a sweep that gained less than a digit: lengthen the inner solve
     if (!p->desc.direct && sweep >= 1 && maxrate > 0.1 && iters < 8 * p->desc.inner_iters) iters *= 2;

@@ -8,7 +8,8 @@
 //
 //   mpn_conv3d_forward        y = act(conv(x, W) + b)      tensor cores (mma.sync m16n8k16 bf16)
 //   mpn_conv3d_backward_data  dx = conv^T(dy, W)            same kernel on flipped, transposed W
-//   mpn_conv3d_backward_weights dW, db from dy and x       FP32 CUDA-core reduction, two stages
+//   mpn_conv3d_backward_weights dW, db from dy and x       tensor cores per tap and chunk of points,
+//                                                           then a fixed-order sum over the chunks
 //   mpn_relu_mask             g = dx * (y > 0) -> BF16
 //   mpn_adam_step             FP32 masters + BF16 copy
 //   mpn_pack_inputs / mpn_mse_u  data plumbing of the net
@@ -149,43 +150,144 @@ __global__ void k_flip_transpose(int CI, int CO, const __nv_bfloat16* __restrict
   wt[((size_t)(26 - tap) * CI + ci) * CO + co] = w[i];
 }
 
-// Weight gradient, stage 1: per (chunk of points, tap) partial sums
-// dW[tap][co][ci] = sum_p g[p][co] x[nbr(p, tap)][ci]   (FP32 accumulation)
-// and, for the centre tap, db[co] = sum_p g[p][co].
+// Weight gradient on the tensor cores, stage 1: for one tap (blockIdx.y) and
+// one chunk of points (blockIdx.x),
+//   dW_tap[co][ci] = sum_p g[p][co] x[nbr(p, tap)][ci],
+// a GEMM with M = co, N = ci and K running over the points: sub-tiles of 64
+// points are staged in shared memory as bf16 pairs packed along the point
+// axis (G as [co][pair], the tap's gathered X as [ci][pair]), so every
+// m16n8k16 fragment register is one 32-bit shared load; each of the 4 warps
+// takes 16 points of a sub-tile.  The warps' accumulators are added in a
+// fixed order; the centre tap's CTAs also sum g for db.  Deterministic.
 template <int CI, int CO>
-__global__ void __launch_bounds__(256) k_wgrad_part(CGrid g, int B, int chunk, const __nv_bfloat16* __restrict__ gr,
-                                                    const __nv_bfloat16* __restrict__ x, float* __restrict__ part,
-                                                    float* __restrict__ bpart) {
-  constexpr int CPT = CI * CO / 256 > 0 ? CI * CO / 256 : 1;   // (co, ci) pairs per thread
-  constexpr int TPC = CI / CPT;                                  // threads per co
+__global__ void __launch_bounds__(128) k_wgrad_mma(CGrid g, long long total, int chunk,
+                                                   const __nv_bfloat16* __restrict__ gr,
+                                                   const __nv_bfloat16* __restrict__ x, float* __restrict__ part,
+                                                   float* __restrict__ bpart) {
+  constexpr int PT = 64, PP = PT / 2 + 4;     // points per sub-tile; pair stride (padded)
+  constexpr int MT = CO / 16, NT = CI / 8;
+  __shared__ uint32_t gs[CO * PP];            // G^T, packed point pairs
+  __shared__ uint32_t xs[CI * PP];            // X_tap^T, packed point pairs
+  __shared__ float red[CO * CI];
+  __shared__ float bred[32 * CO];
   const int tap = blockIdx.y;
   const int dt = tap / 9 - 1, dx = (tap / 3) % 3 - 1, dy = tap % 3 - 1;
-  const int t = threadIdx.x;
-  const int co = t / TPC, ci0 = (t % TPC) * CPT;
-  const bool active = co < CO;
-  float acc[CPT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  // staging role: point pair j (0..31), channel quarter q (0..3)
+  const int j = threadIdx.x >> 2, q = threadIdx.x & 3;
+  const long long p0 = (long long)blockIdx.x * chunk;
+  const long long p1 = p0 + chunk < total ? p0 + chunk : total;
+  float acc[MT][NT][4];
 #pragma unroll
-  for (int k = 0; k < CPT; ++k) acc[k] = 0.f;
-  float bacc = 0.f;
-  long long total = (long long)B * g.N;
-  long long p0 = (long long)blockIdx.x * chunk, p1 = p0 + chunk < total ? p0 + chunk : total;
-  for (long long pp = p0; pp < p1; ++pp) {
-    int b = (int)(pp / g.N), p = (int)(pp - (long long)b * g.N);
-    int pos[3]; cdecode(g, p, pos);
-    int q = cnbr(g, pos, dt, dx, dy);
-    if (!active) continue;
-    float gv = __bfloat162float(gr[((size_t)b * g.N + p) * CO + co]);
-    bacc += gv;
-    if (q < 0) continue;
-    const __nv_bfloat16* xr = x + ((size_t)b * g.N + q) * CI + ci0;
+  for (int m = 0; m < MT; ++m)
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) acc[k] += gv * __bfloat162float(xr[k]);
+    for (int n = 0; n < NT; ++n)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[m][n][k] = 0.f;
+  float bacc[CO / 4];
+#pragma unroll
+  for (int k = 0; k < CO / 4; ++k) bacc[k] = 0.f;
+  for (long long base = p0; base < p1; base += PT) {
+    // stage the pair (2j, 2j+1): channels [q C/4, (q+1) C/4) of g and of x at the neighbour
+    uint32_t ga[CO / 8], gb[CO / 8], xa[CI / 8], xb[CI / 8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long pp = base + 2 * j + h;
+      uint32_t* gw = h ? gb : ga;
+      uint32_t* xw = h ? xb : xa;
+      int nb = -1;
+      size_t row = 0;
+      if (pp < p1) {
+        const int b = (int)(pp / g.N), p = (int)(pp - (long long)b * g.N);
+        int pos[3]; cdecode(g, p, pos);
+        const int qn = cnbr(g, pos, dt, dx, dy);
+        row = (size_t)b * g.N;
+        nb = qn;
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(gr + (row + p) * CO + q * (CO / 4));
+#pragma unroll
+        for (int k = 0; k < CO / 8; ++k) gw[k] = src[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < CO / 8; ++k) gw[k] = 0u;
+      }
+      if (nb >= 0) {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(x + (row + nb) * CI + q * (CI / 4));
+#pragma unroll
+        for (int k = 0; k < CI / 8; ++k) xw[k] = src[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < CI / 8; ++k) xw[k] = 0u;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < CO / 8; ++k) {
+      const int c = q * (CO / 4) + 2 * k;
+      gs[c * PP + j] = __byte_perm(ga[k], gb[k], 0x5410);
+      gs[(c + 1) * PP + j] = __byte_perm(ga[k], gb[k], 0x7632);
+      if (tap == 13) {
+        const __nv_bfloat162 a2 = *reinterpret_cast<const __nv_bfloat162*>(&ga[k]);
+        const __nv_bfloat162 b2 = *reinterpret_cast<const __nv_bfloat162*>(&gb[k]);
+        bacc[2 * k] += __bfloat162float(a2.x) + __bfloat162float(b2.x);
+        bacc[2 * k + 1] += __bfloat162float(a2.y) + __bfloat162float(b2.y);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < CI / 8; ++k) {
+      const int c = q * (CI / 4) + 2 * k;
+      xs[c * PP + j] = __byte_perm(xa[k], xb[k], 0x5410);
+      xs[(c + 1) * PP + j] = __byte_perm(xa[k], xb[k], 0x7632);
+    }
+    __syncthreads();
+    const int k0 = warp * 8;                  // this warp's first pair (16 points)
+    uint32_t a[MT][4], bf[NT][2];
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      a[m][0] = gs[(m * 16 + gid) * PP + k0 + tig];
+      a[m][1] = gs[(m * 16 + gid + 8) * PP + k0 + tig];
+      a[m][2] = gs[(m * 16 + gid) * PP + k0 + tig + 4];
+      a[m][3] = gs[(m * 16 + gid + 8) * PP + k0 + tig + 4];
+    }
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+      bf[n][0] = xs[(n * 8 + gid) * PP + k0 + tig];
+      bf[n][1] = xs[(n * 8 + gid) * PP + k0 + tig + 4];
+    }
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+      for (int n = 0; n < NT; ++n) mma_bf16(acc[m][n], a[m], bf[n]);
+    __syncthreads();
   }
-  if (active) {
-    float* o = part + (((size_t)blockIdx.x * 27 + tap) * CO + co) * CI + ci0;
+  // the four warps' sums, added in warp order
+  for (int i = threadIdx.x; i < CO * CI; i += blockDim.x) red[i] = 0.f;
+  __syncthreads();
+  for (int w = 0; w < 4; ++w) {
+    if (warp == w) {
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) o[k] = acc[k];
-    if (tap == 13 && ci0 == 0) bpart[(size_t)blockIdx.x * CO + co] = bacc;
+      for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+          const int co = m * 16 + gid, ci = n * 8 + 2 * tig;
+          red[co * CI + ci] += acc[m][n][0];
+          red[co * CI + ci + 1] += acc[m][n][1];
+          red[(co + 8) * CI + ci] += acc[m][n][2];
+          red[(co + 8) * CI + ci + 1] += acc[m][n][3];
+        }
+    }
+    __syncthreads();
+  }
+  float* o = part + ((size_t)blockIdx.x * 27 + tap) * CO * CI;
+  for (int i = threadIdx.x; i < CO * CI; i += blockDim.x) o[i] = red[i];
+  if (tap == 13) {
+#pragma unroll
+    for (int k = 0; k < CO / 4; ++k) bred[j * CO + q * (CO / 4) + k] = bacc[k];
+    __syncthreads();
+    for (int c = threadIdx.x; c < CO; c += blockDim.x) {
+      float sacc = 0.f;
+      for (int jj = 0; jj < 32; ++jj) sacc += bred[jj * CO + c];
+      bpart[(size_t)blockIdx.x * CO + c] = sacc;
+    }
   }
 }
 
@@ -232,6 +334,24 @@ __global__ void k_pack(int N, int F, const float* __restrict__ fields, const flo
       if (c < F) v = fields[((size_t)c * B + b) * N + p] * scale[c];
       else if (c == F) v = rhs[(size_t)b * N + p] * scale[c];
       o[c] = __float2bfloat16_rn(v);
+    }
+  }
+}
+
+// Channel F + 1: the running sum over time planes of rhs at the same (x, y)
+// (planes 0..t), times scale[F + 1]: the solution of a PDE that is first order
+// in time depends on the right-hand side of every earlier plane, which the
+// 3x3x3 stencils of a few layers cannot reach.  One thread per (b, x, y).
+__global__ void k_pack_tsum(int nt, int plane, int F, const float* __restrict__ rhs, const float* __restrict__ scale,
+                            __nv_bfloat16* __restrict__ x0, int B) {
+  const int b = blockIdx.y;
+  const float sc = scale[F + 1];
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < plane; c += gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int t = 0; t < nt; ++t) {
+      const size_t p = (size_t)b * nt * plane + (size_t)t * plane + c;
+      acc += rhs[p];
+      x0[p * 16 + F + 1] = __float2bfloat16_rn(acc * sc);
     }
   }
 }
@@ -360,11 +480,12 @@ extern "C" int mpn_conv3d_backward_weights(const mpn_conv_desc* d, const void* g
   float* part = scratch;
   float* bpart = scratch + (size_t)nchunk * nw;
   dim3 gr(nchunk, 27);
+  const long long tot = (long long)d->batch * g.N;
   const __nv_bfloat16* go = (const __nv_bfloat16*)g_out;
   const __nv_bfloat16* xx = (const __nv_bfloat16*)x;
-  if (d->cin == 16 && d->cout == 32) k_wgrad_part<16, 32><<<gr, 256, 0, st>>>(g, d->batch, MPN_WGRAD_CHUNK, go, xx, part, bpart);
-  else if (d->cin == 32 && d->cout == 32) k_wgrad_part<32, 32><<<gr, 256, 0, st>>>(g, d->batch, MPN_WGRAD_CHUNK, go, xx, part, bpart);
-  else if (d->cin == 32 && d->cout == 16) k_wgrad_part<32, 16><<<gr, 256, 0, st>>>(g, d->batch, MPN_WGRAD_CHUNK, go, xx, part, bpart);
+  if (d->cin == 16 && d->cout == 32) k_wgrad_mma<16, 32><<<gr, 128, 0, st>>>(g, tot, MPN_WGRAD_CHUNK, go, xx, part, bpart);
+  else if (d->cin == 32 && d->cout == 32) k_wgrad_mma<32, 32><<<gr, 128, 0, st>>>(g, tot, MPN_WGRAD_CHUNK, go, xx, part, bpart);
+  else if (d->cin == 32 && d->cout == 16) k_wgrad_mma<32, 16><<<gr, 128, 0, st>>>(g, tot, MPN_WGRAD_CHUNK, go, xx, part, bpart);
   else return MPN_ERR_UNSUPPORTED;
   k_wgrad_reduce<<<(nw + 255) / 256, 256, 0, st>>>(nchunk, nw, part, dw);
   k_wgrad_reduce<<<(d->cout + 255) / 256, 256, 0, st>>>(nchunk, d->cout, bpart, db);
@@ -389,10 +510,13 @@ extern "C" int mpn_adam_step(long long n, float* w, const float* g, float* m, fl
 
 extern "C" int mpn_pack_inputs(const mpn_conv_desc* d, int nfields, const float* fields, const float* rhs,
                                const float* scale, void* x0, void* stream) {
-  if (!d || nfields < 0 || nfields > 15 || !rhs || !scale || !x0 || (nfields > 0 && !fields)) return MPN_ERR_INVALID_ARG;
+  if (!d || nfields < 0 || nfields > 14 || !rhs || !scale || !x0 || (nfields > 0 && !fields)) return MPN_ERR_INVALID_ARG;
   int N = d->n[0] * d->n[1] * d->n[2];
   dim3 gr((N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024, d->batch);
   k_pack<<<gr, 256, 0, (cudaStream_t)stream>>>(N, nfields, fields, rhs, scale, (__nv_bfloat16*)x0, d->batch);
+  const int plane = d->n[1] * d->n[2];
+  dim3 gp((plane + 255) / 256 < 1024 ? (plane + 255) / 256 : 1024, d->batch);
+  k_pack_tsum<<<gp, 256, 0, (cudaStream_t)stream>>>(d->n[0], plane, nfields, rhs, scale, (__nv_bfloat16*)x0, d->batch);
   return cudaGetLastError() == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
 }
 

@@ -8,8 +8,10 @@ C ABI layer by layer.  The prediction is handed to the solver as u0; the
 solver still iterates to the same tolerance, so the network can only change
 how many iterations that takes, never the answer.
 
-Layers (padded channels): (F+1 -> 16) -> 32 ReLU -> 32 ReLU -> 32 ReLU -> 16
-(channel 0 is u / out_scale).  Activations are channels-last BF16 [B][N][C].
+Layers (padded channels): (F+2 -> 16) -> 32 ReLU -> 32 ReLU -> 32 ReLU -> 16
+(channel 0 is u / out_scale).  Inputs: the coefficient fields, the right-hand
+side and its running sum over the time planes (the solution depends on the
+forcing of every earlier plane, beyond the layers' 9-plane reach).  Activations are channels-last BF16 [B][N][C].
 """
 from __future__ import annotations
 
@@ -56,8 +58,8 @@ class WarmStartNet:
         n = tuple(geom["n"])
         if len(n) != 3:
             raise ValueError("the warm-start network works on (t, x, y) grids")
-        if nfields + 1 > 16:
-            raise ValueError("at most 15 coefficient fields")
+        if nfields + 2 > 16:
+            raise ValueError("at most 14 coefficient fields")
         self.lib = load()
         self.geom, self.B, self.F, self.N = geom, batch, nfields, int(np.prod(n))
         self.dev = torch.device(device)
@@ -72,7 +74,7 @@ class WarmStartNet:
             self.desc.append(d)
         rng = np.random.default_rng(seed)
         self.w, self.wb, self.b, self.m, self.v = [], [], [], [], []
-        real_in = [nfields + 1, 32, 32, 32]
+        real_in = [nfields + 2, 32, 32, 32]
         real_out = [32, 32, 32, 1]
         for (ci, co), ri, ro in zip(LAYERS, real_in, real_out):
             w = np.zeros((27, co, ci), dtype=np.float32)
@@ -97,6 +99,9 @@ class WarmStartNet:
         for f in range(self.F):
             sc[f] = 1.0 / max(float(fields[f].float().pow(2).mean().sqrt()), 1e-12)
         sc[self.F] = 1.0 / max(float(rhs.float().pow(2).mean().sqrt()), 1e-12)
+        nt = int(self.geom["n"][0])
+        tsum = rhs.float().reshape(rhs.shape[0], nt, -1).cumsum(1)
+        sc[self.F + 1] = 1.0 / max(float(tsum.pow(2).mean().sqrt()), 1e-12)
         self.in_scale = torch.tensor(sc, device=self.dev)
         self.out_scale = max(float(u.float().pow(2).mean().sqrt()), 1e-12)
 

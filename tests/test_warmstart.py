@@ -196,3 +196,28 @@ def test_trainer_checkpoint_resume_is_bitwise():
     for x, y in zip(a.w + a.b + a.m + a.v + a.wb, b.w + b.b + b.m + b.v + b.wb):
         assert torch.equal(x, y)
     assert a.step == b.step == 11
+
+
+def test_packed_inputs():
+    """Input channels of the network: the fields and the right-hand side
+    scaled, and the running sum over time planes of the right-hand side
+    (plain numpy cumulative sum), BF16-rounded; zero padding above."""
+    from paper_2502_18377_b300.binding import _ptr, _stream, load
+    lib = load()
+    w = _small_family(2, 9100)
+    n, B, F = w.geom["n"], 2, 2
+    d = _desc(n, w.geom["periodic"], B, 16, 32)
+    scale = np.array([0.5, 2.0, 3.0, 0.25] + [1.0] * 12, dtype=np.float32)
+    fields = torch.tensor(np.asarray(w.fields, dtype=np.float32), device="cuda")
+    rhs = torch.tensor(np.asarray(w.rhs, dtype=np.float32), device="cuda")
+    x0 = torch.empty((B, w.npoints, 16), device="cuda", dtype=torch.bfloat16)
+    sc = torch.tensor(scale, device="cuda")
+    assert lib.mpn_pack_inputs(ctypes.byref(d), F, _ptr(fields), _ptr(rhs), _ptr(sc), _ptr(x0), _stream()) == 0
+    got = x0.float().cpu().numpy().astype(np.float64)
+    f32 = np.asarray(w.fields, dtype=np.float32).astype(np.float64)
+    r32 = np.asarray(w.rhs, dtype=np.float32).astype(np.float64)
+    tsum = np.cumsum(r32.reshape(B, n[0], -1), axis=1).reshape(B, -1)
+    refs = [f32[0] * 0.5, f32[1] * 2.0, r32 * 3.0, tsum * 0.25]
+    for c, ref in enumerate(refs):
+        assert _rel(got[:, :, c], ref) <= 8e-3, (c, _rel(got[:, :, c], ref))
+    assert not np.any(got[:, :, 4:])
