@@ -190,3 +190,38 @@ def test_reaction_diffusion_bench_size_residual():
         res = osv.normal_residual(A, d, z64c[b].ravel())
         assert res <= 1e-7, (b, res, stats)
         assert _rel(zc[b].ravel(), z64c[b].ravel()) <= 1e-7
+
+
+def test_benchmark_instance_against_the_exact_oracle_solution():
+    """Instance 0 of the reaction-diffusion benchmark workload (B = 16,
+    32 x 64 x 64), its own data: the oracle's exact FP64 solution (block
+    elimination + sparse LU, written once by tests/golden/make_fullsize_golden.py)
+    at 1024 sampled entries of z and of d_z (the MSE-loss adjoint), the norm
+    of every variable block, and sampled gradients.  Relative errors: sampled
+    z and d_z and block norms <= 1e-6, gradients <= 1e-5."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "fullsize_reaction_diffusion_b0.json")
+    ref = json.load(open(path))
+    w = _bench_workload("reaction_diffusion_2d")
+    s = _bench_solver("reaction_diffusion_2d", w)
+    B, V, N = w.batch, 7, w.npoints
+    args = (_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega))
+    z64 = torch.empty((B, V, N), device="cuda", dtype=torch.float64)
+    z = s.forward(*args, z64=z64)
+    gz = s.mse_grad(z, _dev(w.target))
+    dz64 = torch.empty((B, V, N), device="cuda", dtype=torch.float64)
+    dfields, dscal, drhs, dom, dz = s.adjoint(*args, z, gz, reuse_setup=True, want_dz=True, dz64=dz64)
+    z0, dz0 = z64[0].cpu().numpy().ravel(), dz64[0].cpu().numpy().ravel()
+    iz = np.array(ref["z_index"])
+    assert _rel(z0[iz], np.array(ref["z"])) <= TOL, _rel(z0[iz], np.array(ref["z"]))
+    assert _rel(dz0[iz], np.array(ref["dz"])) <= TOL, _rel(dz0[iz], np.array(ref["dz"]))
+    for v in range(V):
+        for got, want in ((z0, ref["z_block_norms"][v]), (dz0, ref["dz_block_norms"][v])):
+            nv = np.linalg.norm(got[v * N:(v + 1) * N])
+            assert abs(nv - want) <= TOL * want, (v, nv, want)
+    ip = np.array(ref["point_index"])
+    df, dr = dfields.cpu().numpy(), drhs.cpu().numpy()
+    for f in range(len(ref["dfields"])):
+        assert _rel(df[f, 0, ip], np.array(ref["dfields"][f])) <= 1e-5, f
+    assert _rel(dr[0, ip], np.array(ref["drhs"])) <= 1e-5
