@@ -42,7 +42,7 @@ BATCH, GRID = WORKLOADS[HEADLINE][1], WORKLOADS[HEADLINE][2]
 # DRAM bytes of one finest-level smoothing step of the headline workload from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); None until
 # captured for the current kernel.
-STEP_TRAFFIC_BYTES = None
+STEP_TRAFFIC_BYTES = 226.3e6
 
 
 def _peaks():
@@ -282,6 +282,48 @@ def measure(name, args, dev, world, rank, steps, warmup, flush, e2e=False):
     return res
 
 
+def plain_fp32_comparison(name, dev, rank, flush, iters=(25, 50, 100), reps=3):
+    """Forward solves of the workload: the mixed-precision solve (FP32
+    multigrid-CG inside FP64 refinement, to its tolerance) against plain FP32
+    multigrid-preconditioned CG (one sweep of k iterations from zero, no FP64
+    refinement), same V-cycle and settings; error of each against the mixed
+    solution (relative L2 of the whole z, max over instances), mean time of
+    `reps` solves (CUDA events, L2 flushed before each)."""
+    import torch
+    from paper_2502_18377_b300.binding import Solver
+    w, fields, scal, rhs, om, _ = make_inputs(rank, name=name)
+    kw = WORKLOADS[name][4]
+    D = lambda a: torch.from_numpy(a).to(dev)
+    args = (D(fields), D(scal), D(rhs), D(om))
+
+    def timed(s):
+        s.forward(*args, allow_not_converged=True)
+        tms = []
+        for k in range(reps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            z = s.forward(*args, allow_not_converged=True)
+            e1.record()
+            torch.cuda.synchronize()
+            tms.append(e0.elapsed_time(e1))
+        return z, statistics.mean(tms), dict(s.last_stats)
+
+    mixed = Solver(w.geom, w.batch, w.field_of, fields.shape[0], **kw)
+    z_ref, ms_ref, st = timed(mixed)
+    B = z_ref.shape[0]
+    out = {"mixed": {"ms_forward": ms_ref, "sweeps": st["sweeps"], "pcg_iters": st["pcg_iters"],
+                     "pred_error": st["pred_error"]}, "plain_fp32": []}
+    del mixed
+    for k in iters:
+        s = Solver(w.geom, w.batch, w.field_of, fields.shape[0], max_refine=1, **dict(kw, inner_iters=k))
+        z, ms, _ = timed(s)
+        err = float(((z - z_ref).reshape(B, -1).norm(dim=1) / z_ref.reshape(B, -1).norm(dim=1)).max())
+        out["plain_fp32"].append({"pcg_iters": k, "ms_forward": ms, "rel_error_vs_mixed": err})
+        del s
+    return out
+
+
 def _achieved(res):
     n = res["prof_n"]
     return (res["prof_bytes"] / n) / (res["prof_ms"] / n / 1e3) / 1e9 if n else None
@@ -301,6 +343,7 @@ def run_ours(args):
     clocks.start()
     head = measure(HEADLINE, args, dev, world, rank, args.steps, args.warmup, flush, e2e=not args.no_e2e)
     clk = clocks.stop()
+    plain = None if args.headline_only else plain_fp32_comparison(HEADLINE, dev, rank, flush)
     others = []
     if not args.headline_only:
         for name in WORKLOADS:
@@ -334,7 +377,7 @@ def run_ours(args):
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": STEP_TRAFFIC_BYTES,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the finest-level "
-                                       "smoothing step, one capture, bytes per launch",
+                                       "smoothing step of this workload, one cold capture, bytes per launch",
                      "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.4 TB/s",
                      "launches": head["prof_n"],
                      "avg_launch_us": 1e3 * head["prof_ms"] / head["prof_n"] if head["prof_n"] else None},
@@ -344,6 +387,7 @@ def run_ours(args):
         "gpu_launches_per_step": head["kernels"] / args.steps,
         "solver": {"forward": sf, "adjoint": sa, "levels": head["levels"], "fused_coarse_level": head["fused_level"]},
         "cpu_baseline": cpu,
+        "plain_fp32_mgcg_vs_mixed": plain,
         "other_workloads": [
             {"workload": o["name"], "batch_per_gpu": o["B"], "grid": o["grid"], "value": o["value"], "unit": UNIT,
              "ms_per_step": o["ms"], "steps": max(3, args.steps // 2), "solver_settings": WORKLOADS[o["name"]][4],
