@@ -311,8 +311,14 @@ static void plan_tail(mpn_problem* p) {
   p->tail_k0 = -1;
   if (!p->desc.fused_coarse || p->L < 2) return;
   const int n0 = p->lv[0].g.n[0];
+  // cluster size: 4 CTAs per instance, more (up to TAIL_MAX_CLUSTER) while
+  // the batch gives fewer than TAIL_TARGET_CTAS CTAs in all; smaller sizes
+  // are tried when a larger one finds no plan
+  int cs_want = 4;
+  while (cs_want < TAIL_MAX_CLUSTER && p->B * cs_want < TAIL_TARGET_CTAS) cs_want *= 2;
+  for (int cs_try = cs_want; cs_try >= 1; cs_try /= 2) {
   int cs = 1;
-  while (cs * 2 <= std::min(TAIL_MAX_CLUSTER, n0)) cs *= 2;
+  while (cs * 2 <= std::min(cs_try, n0)) cs *= 2;
   const int P = (n0 + cs - 1) / cs;
   const size_t budget = 200 * 1024;
   for (int k0 = 0; k0 + 1 < p->L; ++k0) {
@@ -364,9 +370,10 @@ static void plan_tail(mpn_problem* p) {
     ta.rin = p->lv[k0].r;
     ta.eout = p->lv[k0].e;
     const void* fn = tail_fn(p);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        (cs > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
       (void)cudaGetLastError();
-      return;
+      break;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, p->B);
@@ -379,10 +386,11 @@ static void plan_tail(mpn_problem* p) {
     int ncl = 0;
     if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) != cudaSuccess || ncl < 1) {
       (void)cudaGetLastError();
-      return;
+      break;
     }
     p->tail_k0 = k0; p->tail_cs = cs; p->tail_smem = smem;
     return;
+  }
   }
 }
 

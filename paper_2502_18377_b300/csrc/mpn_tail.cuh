@@ -28,8 +28,13 @@ namespace cg = cooperative_groups;
 #ifndef TAIL_MAX_PPT
 #define TAIL_MAX_PPT 2
 #endif
+// clusters larger than 4 CTAs per instance only while the batch gives fewer
+// CTAs than this in all (small batches leave most SMs idle otherwise)
+#ifndef TAIL_TARGET_CTAS
+#define TAIL_TARGET_CTAS 64
+#endif
 #ifndef TAIL_MAX_CLUSTER
-#define TAIL_MAX_CLUSTER 4
+#define TAIL_MAX_CLUSTER 16
 #endif
 
 struct TailLevel {
