@@ -103,6 +103,15 @@ typedef struct mpn_desc {
                              system is factorised (banded Cholesky, explicit inverse) once per forward
                              solve and every refinement sweep applies the inverse (at most 4096 grid
                              points per instance); 0 (default): multigrid-preconditioned Krylov */
+  int variable_steps;     /* 1: every interval of every axis has a step of its own, per instance
+                             (Section 2, "discretization"; learnable), given by mpn_set_steps before
+                             the first solve; step[] is then unused.  The derivative rows take the
+                             three-point forms of the quadratic through their points (central inside
+                             and on periodic axes with sbar = (h_{i-1} + h_i) / 2, one-sided at the
+                             ends of open axes with sbar = the adjacent interval); the Taylor rows
+                             use the interval to the neighbour.  Runs the general two-pass kernels
+                             on every level (no fused step, no fused coarse end).  0 (default):
+                             uniform steps step[] */
 } mpn_desc;
 
 enum { MPN_KRYLOV_CG = 0, MPN_KRYLOV_FGMRES = 1 };
@@ -119,7 +128,8 @@ typedef struct mpn_stats {
 typedef struct mpn_problem mpn_problem;
 
 /* Fills *desc with defaults (tol 1e-7, max_refine 12, inner_iters 5,
- * cheb_degree 5, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 1, krylov CG, coarsen_time 0, direct 0). */
+ * cheb_degree 5, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 1, krylov CG, coarsen_time 0, direct 0,
+ * variable_steps 0). */
 int mpn_default_desc(mpn_desc* desc);
 
 /* Validates the descriptor, builds the grid hierarchy (spatial halving, time
@@ -165,6 +175,30 @@ int mpn_adjoint(mpn_problem* p, const float* fields, const float* scalars,
                 const float* rhs, const float* omega, const float* z,
                 const float* g_z, float* dfields, float* dscalars, float* drhs,
                 float* domega, float* dz, double* dz64, int flags, mpn_stats* stats, void* stream);
+
+/* Per-interval steps of a variable_steps problem (Section 2, "discretization"):
+ * steps (device, float) holds, axis by axis (time first), [B][m_d] with
+ * m_d = n_d - 1 intervals on an open axis (h_k = x_{k+1} - x_k) and n_d on a
+ * periodic one (the last closes the period); sum over d of B m_d floats.  The
+ * problem copies them (the caller may reuse the buffer on return) and the
+ * next solve builds its hierarchy from them: a coarsened periodic axis sums
+ * pairs of intervals, a coarsened open axis places its points at the fine
+ * fractional indices and interpolates their coordinates.  Synchronises
+ * `stream`.  Errors: INVALID_ARG (null, not a variable_steps problem, a step
+ * that is not a positive finite number; the problem keeps no steps then). */
+int mpn_set_steps(mpn_problem* p, const float* steps, void* stream);
+
+/* dl/dsteps for a variable_steps problem, in the layout of mpn_set_steps,
+ * from the FP64 forward solution z64 and the FP64 adjoint solution dz64
+ * ([B][V][N] double each, as mpn_forward and mpn_adjoint write them for the
+ * steps last set): the gradient formula after Eq. 11 through the entries of A
+ * that depend on the steps.  With lambda = d - A z and d_lambda = -A d_z,
+ *   dl/dh_k = -sum over the derivative and Taylor rows r of d(f_r g_r)/dh_k,
+ *   f = A z, g = A d_z  (z, d_z held fixed),
+ * computed exactly (forward-mode derivatives of each row's entries), one CTA
+ * per (instance, axis, interval) summing in a fixed order.  Asynchronous on
+ * `stream`.  Errors: INVALID_ARG. */
+int mpn_step_grads(mpn_problem* p, const double* z64, const double* dz64, float* dsteps, void* stream);
 
 /* Number of forward solves completed on this problem (the adjoint's own
  * recomputations included); -1 for a null problem.  Host-side query. */

@@ -29,7 +29,7 @@ class MpnDesc(ctypes.Structure):
                 ("cheb_degree", ctypes.c_int), ("coarse_min", ctypes.c_int),
                 ("max_coarse", ctypes.c_int), ("fused_coarse", ctypes.c_int),
                 ("fused_step", ctypes.c_int), ("krylov", ctypes.c_int), ("coarsen_time", ctypes.c_int),
-                ("direct", ctypes.c_int)]
+                ("direct", ctypes.c_int), ("variable_steps", ctypes.c_int)]
 
 KRYLOV = {"cg": 0, "fgmres": 1}
 
@@ -59,6 +59,8 @@ EXPORTS = {
     "mpn_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int,
                                    ctypes.POINTER(MpnStats), _P]),
     "mpn_generation": (ctypes.c_longlong, [_P]),
+    "mpn_set_steps": (ctypes.c_int, [_P, _P, _P]),
+    "mpn_step_grads": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "mpn_inject_wait_failure": (ctypes.c_int, [_P]),
     "mpn_mse_grad": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "mpn_apply_reduced": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -191,7 +193,7 @@ class Solver:
 
     def __init__(self, geom: dict, batch: int, field_of, nfields: int, tol=1e-7, max_refine=12,
                  inner_iters=5, cheb_degree=5, coarse_min=4, max_coarse=2048, fused_coarse=True,
-                 fused_step=True, krylov="cg", coarsen_time=False, direct=False):
+                 fused_step=True, krylov="cg", coarsen_time=False, direct=False, variable_steps=False):
         lib = load()
         d = MpnDesc()
         lib.mpn_default_desc(ctypes.byref(d))
@@ -215,6 +217,7 @@ class Solver:
         d.krylov = KRYLOV[krylov]
         d.coarsen_time = int(bool(coarsen_time))
         d.direct = int(bool(direct))
+        d.variable_steps = int(bool(variable_steps))
         h = ctypes.c_void_p()
         s = lib.mpn_create(ctypes.byref(d), ctypes.byref(h))
         if s != 0:
@@ -228,6 +231,9 @@ class Solver:
             self.N *= k
         self.field_of = list(field_of)
         self.last_stats = None
+        self.variable_steps = bool(variable_steps)
+        # intervals per axis: n - 1 on an open axis, n on a periodic one
+        self.step_counts = [n[k] if d.periodic[k] else n[k] - 1 for k in range(D)]
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -303,6 +309,37 @@ class Solver:
             raise MpnError(s, "mpn_adjoint")
         out = (dfields[: self.F], dscal, drhs, dom)
         return out + (dz,) if want_dz else out
+
+    def set_steps(self, steps):
+        """Per-interval steps of a variable_steps problem: one float32 tensor
+        [B, m_d] per axis (time first; m_d = n_d - 1, or n_d on a periodic
+        axis).  The library copies them; the next solves use them."""
+        if not self.variable_steps:
+            raise ValueError("set_steps needs a variable_steps problem")
+        if len(steps) != self.D:
+            raise ValueError(f"expected {self.D} step tensors")
+        for k, (t, m) in enumerate(zip(steps, self.step_counts)):
+            _check_f32(f"steps[{k}]", t, (self.B, m))
+        flat = torch.cat([t.reshape(-1) for t in steps]).contiguous()
+        s = self.lib.mpn_set_steps(self._h, _ptr(flat), _stream())
+        if s != 0:
+            raise MpnError(s, "mpn_set_steps")
+
+    def step_grads(self, z64, dz64):
+        """dl/dsteps (one float32 tensor [B, m_d] per axis) from the FP64
+        forward solution and the FP64 adjoint solution ([B][V][N] each)."""
+        for name, t in (("z64", z64), ("dz64", dz64)):
+            if t.dtype != torch.float64 or tuple(t.shape) != (self.B, self.V, self.N):
+                raise ValueError(f"{name} must be float64 [B][V][N]")
+        out = torch.empty(self.B * sum(self.step_counts), device=z64.device, dtype=torch.float32)
+        s = self.lib.mpn_step_grads(self._h, _ptr(z64), _ptr(dz64), _ptr(out), _stream())
+        if s != 0:
+            raise MpnError(s, "mpn_step_grads")
+        parts, off = [], 0
+        for m in self.step_counts:
+            parts.append(out[off: off + self.B * m].view(self.B, m))
+            off += self.B * m
+        return parts
 
     def mse_grad(self, z, target, g_z=None):
         if g_z is None:

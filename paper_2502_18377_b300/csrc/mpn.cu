@@ -26,6 +26,7 @@
 #include "mpn_tail.cuh"
 #include "mpn_fused.cuh"
 #include "mpn_step.h"
+#include "mpn_steps.cuh"
 
 #define MAXL 16
 
@@ -89,6 +90,15 @@ struct mpn_problem {
   double *dscal = nullptr; // device scalars: scale[B], rz_old[B], out[8][B]
   float* lam = nullptr;    // lambda_max per level and instance [L][B]
   double* hbuf = nullptr;  // pinned host buffer
+  // per-interval steps (variable_steps): intervals [L][B][3][stn] (level 0
+  // from mpn_set_steps, the others built by the setup), step records
+  // [L][B][3][stn][ST_REC] in FP64 and FP32, the step check word
+  int stn = 0;
+  double* hlev = nullptr;
+  double* st64 = nullptr;
+  float* st32 = nullptr;
+  int* sterr = nullptr;
+  bool steps_set = false;
   size_t bytes = 0;
   bool setup_ok = false;
   bool zd_valid = false;   // uf64 holds the FP64 u of the last forward
@@ -216,6 +226,7 @@ extern "C" int mpn_default_desc(mpn_desc* d) {
   d->krylov = MPN_KRYLOV_CG;
   d->coarsen_time = 0;
   d->direct = 0;
+  d->variable_steps = 0;
   return MPN_OK;
 }
 
@@ -309,7 +320,7 @@ static const void* tail_fn(const mpn_problem* p) {
 // or the cluster cannot be resident on this device.
 static void plan_tail(mpn_problem* p) {
   p->tail_k0 = -1;
-  if (!p->desc.fused_coarse || p->L < 2) return;
+  if (!p->desc.fused_coarse || p->L < 2 || p->desc.variable_steps) return;
   const int n0 = p->lv[0].g.n[0];
   // cluster size: 4 CTAs per instance, more (up to TAIL_MAX_CLUSTER) while
   // the batch gives fewer than TAIL_TARGET_CTAS CTAs in all; smaller sizes
@@ -424,9 +435,10 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   if (d.coarse_min < 3 || !(d.tol > 0)) return MPN_ERR_INVALID_ARG;
   if (d.krylov != MPN_KRYLOV_CG && d.krylov != MPN_KRYLOV_FGMRES) return MPN_ERR_INVALID_ARG;
   if (d.fused_step < 0 || d.fused_step > 2) return MPN_ERR_INVALID_ARG;
+  if (d.variable_steps != 0 && d.variable_steps != 1) return MPN_ERR_INVALID_ARG;
   int V = 1 + 2 * d.ndim;
   for (int k = 0; k < d.ndim; ++k) {
-    if (d.n[k] < 3 || !(d.step[k] > 0)) return MPN_ERR_INVALID_ARG;
+    if (d.n[k] < 3 || !(d.variable_steps || d.step[k] > 0)) return MPN_ERR_INVALID_ARG;
   }
   if (d.ndim == 2 && d.n[2] != 1 && d.n[2] != 0) return MPN_ERR_INVALID_ARG;
   for (int v = 0; v < V; ++v)
@@ -443,7 +455,9 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
 
   // hierarchy: halve spatial dims (t kept unless coarsen_time) while the half is >= coarse_min
   int n[3] = {p->desc.n[0], p->desc.n[1], p->desc.n[2]};
-  double s[3] = {d.step[0], d.step[1], p->D == 3 ? d.step[2] : 1.0};
+  // (per-interval steps: the uniform steps of the levels are unused)
+  double s[3] = {d.variable_steps ? 1.0 : d.step[0], d.variable_steps ? 1.0 : d.step[1],
+                 p->D == 3 && !d.variable_steps ? d.step[2] : 1.0};
   int per[3] = {0, d.periodic[1], p->D == 3 ? d.periodic[2] : 0};
   float theta = 1.f;
   p->L = 0;
@@ -469,7 +483,8 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   }
   for (int k = 0; k < p->L; ++k) {
     Level& l = p->lv[k];
-    l.vec4 = (p->D == 3 && l.g.n[2] % 4 == 0 && l.g.n[2] >= 8) ? 1 : 0;
+    // per-interval steps: the general (scalar) kernels only
+    l.vec4 = (p->D == 3 && l.g.n[2] % 4 == 0 && l.g.n[2] >= 8 && !d.variable_steps) ? 1 : 0;
     l.papply = l.vec4 ? sblk(l.g.N / 4) : sblk(l.g.N);
     // fused operator step: tiles that divide the t and x extents, with whole
     // y rows of at most FS_MAX_NY points, or 64-point y segments of wider rows
@@ -538,6 +553,20 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   AL(p->ptot, (size_t)2 * B);
   AL(p->dscal, (size_t)16 * B);
   AL(p->lam, (size_t)MAXL * B);
+  if (d.variable_steps) {
+    p->stn = std::max(p->desc.n[0], std::max(p->desc.n[1], p->desc.n[2]));
+    const size_t per_level = (size_t)B * 3 * p->stn;
+    AL(p->hlev, per_level * p->L);
+    AL(p->st64, per_level * p->L * ST_REC);
+    AL(p->st32, per_level * p->L * ST_REC);
+    AL(p->sterr, 1);
+    for (int k = 0; k < p->L; ++k) {
+      Grid& g = p->lv[k].g;
+      g.st64 = p->st64 + per_level * k * ST_REC;
+      g.st32 = p->st32 + per_level * k * ST_REC;
+      g.stn = p->stn;
+    }
+  }
   if (d.krylov == MPN_KRYLOV_FGMRES) {
     p->mk = std::min(FG_MMAX, 8 * d.inner_iters);
     const int mk = p->mk;
@@ -709,6 +738,22 @@ static int coarse_attrs(mpn_problem* p) {
 static int setup_body(mpn_problem* p, cudaStream_t st) {
   int B = p->B, F = p->F, V = p->V;
   Level& l0 = p->lv[0];
+  if (p->desc.variable_steps) {
+    // intervals of every level, then the step records of every level
+    const size_t per_level = (size_t)B * 3 * p->stn;
+    const int nrec = (int)per_level;
+    for (int k = 0; k < p->L; ++k) {
+      if (k > 0) {
+        const Level& lf = p->lv[k - 1];
+        ++p->nlaunch, k_level_steps<<<(B * p->D + 63) / 64, 64, 0, st>>>(
+            lf.g, p->lv[k].g, lf.cz[0], lf.cz[1], lf.cz[2], p->hlev + per_level * (k - 1), p->hlev + per_level * k, B);
+      }
+      ++p->nlaunch, k_step_table<<<(nrec + 127) / 128, 128, 0, st>>>(
+          p->lv[k].g, p->hlev + per_level * k, p->st64 + per_level * k * ST_REC, p->st32 + per_level * k * ST_REC, B,
+          p->sterr);
+    }
+    CKL();
+  }
   ++p->nlaunch, k_rep4<<<(V * B + MPN_TPB - 1) / MPN_TPB, MPN_TPB, 0, st>>>(V * B, p->scalars, p->scal4);
   {
     Coef cf = make_coef(p, l0.fields);
@@ -1279,7 +1324,7 @@ static int forward_impl(mpn_problem* p, const float* fields, const float* scalar
 extern "C" int mpn_forward(mpn_problem* p, const float* fields, const float* scalars, const float* rhs,
                            const float* omega, const float* u0, float* z, double* z64, mpn_stats* stats,
                            void* stream) {
-  if (!p) return MPN_ERR_INVALID_ARG;
+  if (!p || (p->desc.variable_steps && !p->steps_set)) return MPN_ERR_INVALID_ARG;
   TRY(check_ptrs(scalars, rhs));
   if (!omega || (!z && !z64)) return MPN_ERR_INVALID_ARG;
   if (p->F > 0 && !fields) return MPN_ERR_INVALID_ARG;
@@ -1290,7 +1335,7 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
                            const float* omega, const float* z, const float* g_z, float* dfields, float* dscalars,
                            float* drhs, float* domega, float* dz, double* dz64, int flags, mpn_stats* stats,
                            void* stream) {
-  if (!p) return MPN_ERR_INVALID_ARG;
+  if (!p || (p->desc.variable_steps && !p->steps_set)) return MPN_ERR_INVALID_ARG;
   TRY(check_ptrs(scalars, rhs));
   TRY(check_ptrs(omega, g_z));
   TRY(check_ptrs(dscalars, drhs));
@@ -1341,6 +1386,33 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
   return status;
 }
 
+extern "C" int mpn_set_steps(mpn_problem* p, const float* steps, void* stream) {
+  if (!p || !steps || !p->desc.variable_steps) return MPN_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the kept setup and forward state belong to the old steps
+  p->steps_set = false;
+  p->setup_ok = false;
+  p->zd_valid = false;
+  const int nrec = p->B * 3 * p->stn;
+  CK(cudaMemsetAsync(p->sterr, 0, sizeof(int), st));
+  ++p->nlaunch, k_steps_in<<<(nrec + 127) / 128, 128, 0, st>>>(p->lv[0].g, steps, p->hlev, p->B, p->sterr);
+  CKL();
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, p->sterr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (bad) return MPN_ERR_INVALID_ARG;
+  p->steps_set = true;
+  return MPN_OK;
+}
+
+extern "C" int mpn_step_grads(mpn_problem* p, const double* z64, const double* dz64, float* dsteps, void* stream) {
+  if (!p || !z64 || !dz64 || !dsteps || !p->desc.variable_steps || !p->steps_set) return MPN_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  ++p->nlaunch, k_step_grads<<<dim3(p->stn, p->D, p->B), MPN_TPB, 0, st>>>(p->lv[0].g, p->hlev, z64, dz64, dsteps, p->B);
+  CKL();
+  return MPN_OK;
+}
+
 extern "C" long long mpn_generation(const mpn_problem* p) { return p ? p->gen : -1; }
 
 extern "C" int mpn_inject_wait_failure(mpn_problem* p) {
@@ -1361,6 +1433,7 @@ extern "C" int mpn_apply_reduced(mpn_problem* p, const float* fields, const floa
                                  void* stream) {
   if (!p || !scalars || !u || !q) return MPN_ERR_INVALID_ARG;
   if (p->F > 0 && !fields) return MPN_ERR_INVALID_ARG;
+  if (p->desc.variable_steps && !p->steps_set) return MPN_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   TRY(setup(p, fields, scalars, st));
   TRY(apply_S(p, 0, u, q, nullptr, st));

@@ -49,7 +49,33 @@ struct Grid {
   float is1[3], is2[3];    // 1/s, 1/s^2
   double ds1[3], ds2[3];   // 1/s, 1/s^2 in FP64
   float inv_pl, inv_n2;    // 1 / (n[1] n[2]), 1 / n[2] (index decoding)
+  // Per-interval steps (null: the uniform steps above).  One record of
+  // ST_REC values per (instance, dimension, position), FP64 and FP32 copies:
+  // record (b, d, i) at ((b * 3 + d) * stn + i) * ST_REC.
+  const double* st64;
+  const float* st32;
+  int stn;
 };
+
+// Step record of one grid position along one dimension (per-interval steps).
+// In the scaled unknowns w = (sbar u', sbar^2 u'') of the position, with
+// sbar the scale of its derivative rows:
+//   [ST_W1 + k], [ST_W2 + k]  weights of u at offset ST_BASE + k (k < 3) in
+//                            sbar u' and sbar^2 u'' (the difference forms)
+//   [ST_IS1], [ST_IS2]       1 / sbar, 1 / sbar^2
+//   [ST_W .. ST_W + 2]       W = (w11, w12, w22), the quadratic form of the
+//                            position's derivative and Taylor rows in delta
+//   [ST_WI .. ST_WI + 2]     W^{-1}
+//   [ST_BASE]                first offset of the forms: -1 inside or periodic,
+//                            0 at the first point, -2 at the last
+#define ST_REC 16
+#define ST_W1 0
+#define ST_W2 3
+#define ST_IS1 6
+#define ST_IS2 7
+#define ST_W 8
+#define ST_WI 11
+#define ST_BASE 14
 
 // Host: the reciprocals decode_fast() reads.
 inline void grid_set_inverses(Grid& g) {
@@ -111,7 +137,10 @@ __device__ __forceinline__ void decode_fast(const Grid& g, int p, int pos[3]) {
   pos[1] = fdivmod(rem, g.n[2], g.inv_n2, i2);
   pos[2] = i2;
 }
+// Per-interval steps count as edges everywhere: only the general forms read
+// the step records.
 __device__ __forceinline__ bool any_edge(const Grid& g, const int pos[3]) {
+  if (g.st64) return true;
   bool e = pos[0] < 3 || pos[0] > g.n[0] - 4;
   for (int d = 1; d < 3; ++d)
     if (d < g.D && !g.per[d]) e |= pos[d] < 3 || pos[d] > g.n[d] - 4;
@@ -191,14 +220,63 @@ template <class T> __device__ __forceinline__ T is2_of(const Grid& g, int d);
 template <> __device__ __forceinline__ float is2_of<float>(const Grid& g, int d) { return g.is2[d]; }
 template <> __device__ __forceinline__ double is2_of<double>(const Grid& g, int d) { return g.ds2[d]; }
 
+// ------------------------------------------ uniform or per-interval steps
+// The record of position i along d of instance b (per-interval steps only).
+template <class T> __device__ __forceinline__ const T* st_rec(const Grid& g, int b, int d, int i);
+template <> __device__ __forceinline__ const double* st_rec<double>(const Grid& g, int b, int d, int i) {
+  return g.st64 + ((size_t)(b * 3 + d) * g.stn + i) * ST_REC;
+}
+template <> __device__ __forceinline__ const float* st_rec<float>(const Grid& g, int b, int d, int i) {
+  return g.st32 + ((size_t)(b * 3 + d) * g.stn + i) * ST_REC;
+}
+
+// Weight of u_{i+o} in the scaled difference form of order `order` at
+// position i along d (Eq. 5): sbar^order u^(order) = sum_o w(o) u_{i+o}.
+template <class T>
+__device__ __forceinline__ T swt(const Grid& g, int b, int d, int i, int order, int o) {
+  if (!g.st64) return (T)dweight(order, i, g.n[d], g.per[d], o);
+  const T* r = st_rec<T>(g, b, d, i);
+  const int k = o - (int)r[ST_BASE];
+  return (k >= 0 && k < 3) ? r[(order == 1 ? ST_W1 : ST_W2) + k] : (T)0;
+}
+// 1 / sbar and 1 / sbar^2 at position i along d.
+template <class T>
+__device__ __forceinline__ T sis1(const Grid& g, int b, int d, int i) {
+  return g.st64 ? st_rec<T>(g, b, d, i)[ST_IS1] : is1_of<T>(g, d);
+}
+template <class T>
+__device__ __forceinline__ T sis2(const Grid& g, int b, int d, int i) {
+  return g.st64 ? st_rec<T>(g, b, d, i)[ST_IS2] : is2_of<T>(g, d);
+}
+// y = W^{-1} x at position i along d.
+template <class T>
+__device__ __forceinline__ void swinv(const Grid& g, int b, int d, int i, T x1, T x2, T& y1, T& y2) {
+  if (!g.st64) { winv<T>(edge_class(g, d, i), x1, x2, y1, y2); return; }
+  const T* r = st_rec<T>(g, b, d, i);
+  y1 = r[ST_WI] * x1 + r[ST_WI + 1] * x2;
+  y2 = r[ST_WI + 1] * x1 + r[ST_WI + 2] * x2;
+}
+// W at position i along d.
+__device__ __forceinline__ void swmat(const Grid& g, int b, int d, int i, double& w11, double& w12, double& w22) {
+  if (!g.st64) { wmat(edge_class(g, d, i), w11, w12, w22); return; }
+  const double* r = st_rec<double>(g, b, d, i);
+  w11 = r[ST_W]; w12 = r[ST_W + 1]; w22 = r[ST_W + 2];
+}
+
 // Point weight rho_i = 1 / (1 + sum_d beta_d^T W_d^{-1} beta_d).
 template <class T, int DD = 0>
 __device__ __forceinline__ T rho_point(const Grid& g, const Coef& cf, int b, int p, const int pos[3]) {
   T gam = 0;
 #pragma unroll
   for (int d = 0; d < (DD ? DD : g.D); ++d) {
-    T b1 = (T)coefv(cf, 1 + 2 * d, b, p, g.N) * is1_of<T>(g, d);
-    T b2 = (T)coefv(cf, 2 + 2 * d, b, p, g.N) * is2_of<T>(g, d);
+    T b1 = (T)coefv(cf, 1 + 2 * d, b, p, g.N) * sis1<T>(g, b, d, pos[d]);
+    T b2 = (T)coefv(cf, 2 + 2 * d, b, p, g.N) * sis2<T>(g, b, d, pos[d]);
+    if (g.st64) {
+      T q1, q2;
+      swinv<T>(g, b, d, pos[d], b1, b2, q1, q2);
+      gam += b1 * q1 + b2 * q2;
+      continue;
+    }
     int cls = edge_class(g, d, pos[d]);
     if (cls == 0) gam += b1 * b1 * (T)(1.0 / 3.0) + b2 * b2 * (T)(2.0 / 3.0);
     else {
@@ -225,15 +303,15 @@ __device__ __forceinline__ T Lrow(const Grid& g, const Coef& cf, int b, int p, c
     T a1 = 0, a2 = 0;
 #pragma unroll
     for (int o = -2; o <= 2; ++o) {
-      float w1 = dweight(1, pos[d], g.n[d], g.per[d], o);
-      float w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
-      if (w1 == 0.f && w2 == 0.f) continue;
+      T w1 = swt<T>(g, b, d, pos[d], 1, o);
+      T w2 = swt<T>(g, b, d, pos[d], 2, o);
+      if (w1 == (T)0 && w2 == (T)0) continue;
       T xv;
       if (o == 0) xv = xc;
       else { int q = nbr(g, p, pos, d, o); xv = x[q]; if (x2) xv += x2[q]; }
-      a1 += (T)w1 * xv; a2 += (T)w2 * xv;
+      a1 += w1 * xv; a2 += w2 * xv;
     }
-    acc += c1 * a1 * is1_of<T>(g, d) + c2 * a2 * is2_of<T>(g, d);
+    acc += c1 * a1 * sis1<T>(g, b, d, pos[d]) + c2 * a2 * sis2<T>(g, b, d, pos[d]);
   }
   return acc;
 }
@@ -250,13 +328,13 @@ __device__ __forceinline__ T LTgather(const Grid& g, const Coef& cf, int b, int 
       int ip = pos[d] - o;
       if (g.per[d]) ip = wrap1(ip, g.n[d]);
       else if (ip < 0 || ip >= g.n[d]) continue;
-      float w1 = dweight(1, ip, g.n[d], g.per[d], o);
-      float w2 = dweight(2, ip, g.n[d], g.per[d], o);
-      if (w1 == 0.f && w2 == 0.f) continue;
+      T w1 = swt<T>(g, b, d, ip, 1, o);
+      T w2 = swt<T>(g, b, d, ip, 2, o);
+      if (w1 == (T)0 && w2 == (T)0) continue;
       int q = p + (ip - pos[d]) * g.stride[d];
       T c1 = (T)coefv(cf, 1 + 2 * d, b, q, g.N);
       T c2 = (T)coefv(cf, 2 + 2 * d, b, q, g.N);
-      acc += y[q] * (c1 * (T)w1 * is1_of<T>(g, d) + c2 * (T)w2 * is2_of<T>(g, d));
+      acc += y[q] * (c1 * w1 * sis1<T>(g, b, d, ip) + c2 * w2 * sis2<T>(g, b, d, ip));
     }
   }
   return acc;

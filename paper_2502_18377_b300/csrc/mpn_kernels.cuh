@@ -90,8 +90,8 @@ __global__ void k_diag_inv(Grid g, Coef cf, const float* __restrict__ rho, float
     // own row: L_jj
     float Ljj = coefv(cf, 0, b, p, g.N);
     for (int d = 0; d < g.D; ++d)
-      Ljj += coefv(cf, 1 + 2 * d, b, p, g.N) * dweight(1, pos[d], g.n[d], g.per[d], 0) * g.is1[d] +
-             coefv(cf, 2 + 2 * d, b, p, g.N) * dweight(2, pos[d], g.n[d], g.per[d], 0) * g.is2[d];
+      Ljj += coefv(cf, 1 + 2 * d, b, p, g.N) * swt<float>(g, b, d, pos[d], 1, 0) * sis1<float>(g, b, d, pos[d]) +
+             coefv(cf, 2 + 2 * d, b, p, g.N) * swt<float>(g, b, d, pos[d], 2, 0) * sis2<float>(g, b, d, pos[d]);
     float acc = rh[p] * Ljj * Ljj;
     for (int d = 0; d < g.D; ++d)
       for (int o = -2; o <= 2; ++o) {
@@ -99,10 +99,11 @@ __global__ void k_diag_inv(Grid g, Coef cf, const float* __restrict__ rho, float
         int ip = pos[d] - o;
         if (g.per[d]) ip = wrap1(ip, g.n[d]);
         else if (ip < 0 || ip >= g.n[d]) continue;
-        float w1 = dweight(1, ip, g.n[d], g.per[d], o), w2 = dweight(2, ip, g.n[d], g.per[d], o);
+        float w1 = swt<float>(g, b, d, ip, 1, o), w2 = swt<float>(g, b, d, ip, 2, o);
         if (w1 == 0.f && w2 == 0.f) continue;
         int q = p + (ip - pos[d]) * g.stride[d];
-        float Lij = coefv(cf, 1 + 2 * d, b, q, g.N) * w1 * g.is1[d] + coefv(cf, 2 + 2 * d, b, q, g.N) * w2 * g.is2[d];
+        float Lij = coefv(cf, 1 + 2 * d, b, q, g.N) * w1 * sis1<float>(g, b, d, ip) +
+                    coefv(cf, 2 + 2 * d, b, q, g.N) * w2 * sis2<float>(g, b, d, ip);
         acc += rh[q] * Lij * Lij;
       }
     if (is_boundary(g, pos)) acc += g.theta;
@@ -355,35 +356,35 @@ __global__ void k_coarse_assemble(Grid g, Coef cf, const float* __restrict__ rho
           i = j;
           Lij = coefv(cf, 0, b, i, g.N);
           for (int d = 0; d < g.D; ++d)
-            Lij += (double)coefv(cf, 1 + 2 * d, b, i, g.N) * dweight(1, pi[d], g.n[d], g.per[d], 0) * g.ds1[d] +
-                   (double)coefv(cf, 2 + 2 * d, b, i, g.N) * dweight(2, pi[d], g.n[d], g.per[d], 0) * g.ds2[d];
+            Lij += (double)coefv(cf, 1 + 2 * d, b, i, g.N) * swt<double>(g, b, d, pi[d], 1, 0) * sis1<double>(g, b, d, pi[d]) +
+                   (double)coefv(cf, 2 + 2 * d, b, i, g.N) * swt<double>(g, b, d, pi[d], 2, 0) * sis2<double>(g, b, d, pi[d]);
         } else {
           if (o == 0) continue;
           int ip = pj[d0] - o;
           if (g.per[d0]) ip = wrap1(ip, g.n[d0]);
           else if (ip < 0 || ip >= g.n[d0]) continue;
-          float w1 = dweight(1, ip, g.n[d0], g.per[d0], o), w2 = dweight(2, ip, g.n[d0], g.per[d0], o);
-          if (w1 == 0.f && w2 == 0.f) continue;
+          double w1 = swt<double>(g, b, d0, ip, 1, o), w2 = swt<double>(g, b, d0, ip, 2, o);
+          if (w1 == 0.0 && w2 == 0.0) continue;
           i = j + (ip - pj[d0]) * g.stride[d0];
           pi[d0] = ip;
-          Lij = (double)coefv(cf, 1 + 2 * d0, b, i, g.N) * w1 * g.ds1[d0] +
-                (double)coefv(cf, 2 + 2 * d0, b, i, g.N) * w2 * g.ds2[d0];
+          Lij = (double)coefv(cf, 1 + 2 * d0, b, i, g.N) * w1 * sis1<double>(g, b, d0, ip) +
+                (double)coefv(cf, 2 + 2 * d0, b, i, g.N) * w2 * sis2<double>(g, b, d0, ip);
         }
         double f = Lij * (double)rh[i];
         // row i of L: center and off-center entries
         double Lii = coefv(cf, 0, b, i, g.N);
         for (int d = 0; d < g.D; ++d)
-          Lii += (double)coefv(cf, 1 + 2 * d, b, i, g.N) * dweight(1, pi[d], g.n[d], g.per[d], 0) * g.ds1[d] +
-                 (double)coefv(cf, 2 + 2 * d, b, i, g.N) * dweight(2, pi[d], g.n[d], g.per[d], 0) * g.ds2[d];
+          Lii += (double)coefv(cf, 1 + 2 * d, b, i, g.N) * swt<double>(g, b, d, pi[d], 1, 0) * sis1<double>(g, b, d, pi[d]) +
+                 (double)coefv(cf, 2 + 2 * d, b, i, g.N) * swt<double>(g, b, d, pi[d], 2, 0) * sis2<double>(g, b, d, pi[d]);
         if (i <= j && j - i <= bw) row[j - i] += (float)(f * Lii);
         for (int d = 0; d < g.D; ++d)
           for (int o2 = -2; o2 <= 2; ++o2) {
             if (o2 == 0) continue;
-            float w1 = dweight(1, pi[d], g.n[d], g.per[d], o2), w2 = dweight(2, pi[d], g.n[d], g.per[d], o2);
-            if (w1 == 0.f && w2 == 0.f) continue;
+            double w1 = swt<double>(g, b, d, pi[d], 1, o2), w2 = swt<double>(g, b, d, pi[d], 2, o2);
+            if (w1 == 0.0 && w2 == 0.0) continue;
             int k = nbr(g, i, pi, d, o2);
-            double Lik = (double)coefv(cf, 1 + 2 * d, b, i, g.N) * w1 * g.ds1[d] +
-                         (double)coefv(cf, 2 + 2 * d, b, i, g.N) * w2 * g.ds2[d];
+            double Lik = (double)coefv(cf, 1 + 2 * d, b, i, g.N) * w1 * sis1<double>(g, b, d, pi[d]) +
+                         (double)coefv(cf, 2 + 2 * d, b, i, g.N) * w2 * sis2<double>(g, b, d, pi[d]);
             if (k <= j && j - k <= bw) row[j - k] += (float)(f * Lik);
           }
       }
@@ -956,33 +957,34 @@ __device__ __forceinline__ double recover_point(const Grid& g, const Coef64<MASK
   size_t off = (size_t)b * g.N;
   double uc = u[off + p];
   double Est = C.at(0, p) * uc - bE;
-  double a[3][2], hw[3][2], qb[3][2];
+  double a[3][2], hw[3][2], qb[3][2], is[3][2];
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     double a1 = 0, a2 = 0;
-    if (g.per[d] || (pos[d] > 0 && pos[d] < g.n[d] - 1)) {
+    if (!g.st64 && (g.per[d] || (pos[d] > 0 && pos[d] < g.n[d] - 1))) {
       const double um = u[off + nbr(g, p, pos, d, -1)], up = u[off + nbr(g, p, pos, d, 1)];
       a1 = 0.5 * (up - um); a2 = up - 2.0 * uc + um;
     } else {
 #pragma unroll
       for (int o = -2; o <= 2; ++o) {
-        float w1 = dweight(1, pos[d], g.n[d], g.per[d], o), w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
-        if (w1 == 0.f && w2 == 0.f) continue;
+        double w1 = swt<double>(g, b, d, pos[d], 1, o), w2 = swt<double>(g, b, d, pos[d], 2, o);
+        if (w1 == 0.0 && w2 == 0.0) continue;
         double xv = o == 0 ? uc : u[off + nbr(g, p, pos, d, o)];
-        a1 += (double)w1 * xv; a2 += (double)w2 * xv;
+        a1 += w1 * xv; a2 += w2 * xv;
       }
     }
-    int cls = edge_class(g, d, pos[d]);
-    double b1 = C.at(1 + 2 * d, p) * g.ds1[d];
-    double b2 = C.at(2 + 2 * d, p) * g.ds2[d];
+    const double i1 = sis1<double>(g, b, d, pos[d]), i2 = sis2<double>(g, b, d, pos[d]);
+    is[d][0] = i1; is[d][1] = i2;
+    double b1 = C.at(1 + 2 * d, p) * i1;
+    double b2 = C.at(2 + 2 * d, p) * i2;
     a[d][0] = a1; a[d][1] = a2;
     Est += b1 * a1 + b2 * a2;
-    winv<double>(cls, b1, b2, qb[d][0], qb[d][1]);    // W^{-1} beta
+    swinv<double>(g, b, d, pos[d], b1, b2, qb[d][0], qb[d][1]);    // W^{-1} beta
     hw[d][0] = hw[d][1] = 0;
     if (gz) {
-      double g1 = (double)gz[((size_t)b * V + 1 + 2 * d) * g.N + p] * g.ds1[d];
-      double g2 = (double)gz[((size_t)b * V + 2 + 2 * d) * g.N + p] * g.ds2[d];
-      winv<double>(cls, g1, g2, hw[d][0], hw[d][1]);  // W^{-1} h_g
+      double g1 = (double)gz[((size_t)b * V + 1 + 2 * d) * g.N + p] * i1;
+      double g2 = (double)gz[((size_t)b * V + 2 + 2 * d) * g.N + p] * i2;
+      swinv<double>(g, b, d, pos[d], g1, g2, hw[d][0], hw[d][1]);  // W^{-1} h_g
       Est += b1 * hw[d][0] + b2 * hw[d][1];
     }
   }
@@ -990,8 +992,8 @@ __device__ __forceinline__ double recover_point(const Grid& g, const Coef64<MASK
   zo[0] = uc;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    zo[1 + 2 * d] = (a[d][0] + hw[d][0] - rE * qb[d][0]) * g.ds1[d];
-    zo[2 + 2 * d] = (a[d][1] + hw[d][1] - rE * qb[d][1]) * g.ds2[d];
+    zo[1 + 2 * d] = (a[d][0] + hw[d][0] - rE * qb[d][0]) * is[d][0];
+    zo[2 + 2 * d] = (a[d][1] + hw[d][1] - rE * qb[d][1]) * is[d][1];
   }
   return rE;
 }
@@ -1087,14 +1089,14 @@ __global__ void k_adj_kappa(Grid g, Coef cf, const float* __restrict__ gz, doubl
     double hw[3][2], be[3][2], bwh = 0, gam = 0;
     #pragma unroll
     for (int d = 0; d < D; ++d) {
-      int cls = edge_class(g, d, pos[d]);
-      double b1 = C.at(1 + 2 * d, p) * g.ds1[d];
-      double b2 = C.at(2 + 2 * d, p) * g.ds2[d];
+      const double i1 = sis1<double>(g, b, d, pos[d]), i2 = sis2<double>(g, b, d, pos[d]);
+      double b1 = C.at(1 + 2 * d, p) * i1;
+      double b2 = C.at(2 + 2 * d, p) * i2;
       be[d][0] = b1; be[d][1] = b2;
-      double h1 = (double)gz[((size_t)b * V + 1 + 2 * d) * g.N + p] * g.ds1[d];
-      double h2 = (double)gz[((size_t)b * V + 2 + 2 * d) * g.N + p] * g.ds2[d];
-      winv<double>(cls, h1, h2, hw[d][0], hw[d][1]);
-      double q1, q2; winv<double>(cls, b1, b2, q1, q2);
+      double h1 = (double)gz[((size_t)b * V + 1 + 2 * d) * g.N + p] * i1;
+      double h2 = (double)gz[((size_t)b * V + 2 + 2 * d) * g.N + p] * i2;
+      swinv<double>(g, b, d, pos[d], h1, h2, hw[d][0], hw[d][1]);
+      double q1, q2; swinv<double>(g, b, d, pos[d], b1, b2, q1, q2);
       bwh += b1 * hw[d][0] + b2 * hw[d][1];
       gam += b1 * q1 + b2 * q2;
     }
@@ -1102,11 +1104,10 @@ __global__ void k_adj_kappa(Grid g, Coef cf, const float* __restrict__ gz, doubl
     double bpsi = 0;
     #pragma unroll
     for (int d = 0; d < D; ++d) {
-      int cls = edge_class(g, d, pos[d]);
-      double q1, q2; winv<double>(cls, be[d][0], be[d][1], q1, q2);
+      double q1, q2; swinv<double>(g, b, d, pos[d], be[d][0], be[d][1], q1, q2);
       double ps1 = hw[d][0] - q1 * fac, ps2 = hw[d][1] - q2 * fac;
       bpsi += be[d][0] * ps1 + be[d][1] * ps2;
-      double w11, w12, w22; wmat(cls, w11, w12, w22);
+      double w11, w12, w22; swmat(g, b, d, pos[d], w11, w12, w22);
       kap[((size_t)(1 + 2 * d) * gridDim.y + b) * g.N + p] = -(w11 * ps1 + w12 * ps2);
       kap[((size_t)(2 + 2 * d) * gridDim.y + b) * g.N + p] = -(w12 * ps1 + w22 * ps2);
     }
@@ -1129,8 +1130,8 @@ __global__ void k_adj_rhs(Grid g, const float* __restrict__ gz, const double* __
         int ip = pos[d] - o;
         if (g.per[d]) ip = wrap1(ip, g.n[d]);
         else if (ip < 0 || ip >= g.n[d]) continue;
-        float w1 = dweight(1, ip, g.n[d], g.per[d], o), w2 = dweight(2, ip, g.n[d], g.per[d], o);
-        if (w1 == 0.f && w2 == 0.f) continue;
+        double w1 = swt<double>(g, b, d, ip, 1, o), w2 = swt<double>(g, b, d, ip, 2, o);
+        if (w1 == 0.0 && w2 == 0.0) continue;
         int q = p + (ip - pos[d]) * g.stride[d];
         acc += w1 * kap[((size_t)(1 + 2 * d) * B + b) * g.N + q] + w2 * kap[((size_t)(2 + 2 * d) * B + b) * g.N + q];
       }
@@ -1186,14 +1187,15 @@ __global__ void k_znorm(Grid g, const double* __restrict__ u, const float* __res
         x1 = 0.5f * (xp - xm); x2 = xp - 2.f * xc + xm;
       } else {
         for (int o = -2; o <= 2; ++o) {
-          float w1 = dweight(1, pos[d], g.n[d], g.per[d], o), w2 = dweight(2, pos[d], g.n[d], g.per[d], o);
+          float w1 = swt<float>(g, b, d, pos[d], 1, o), w2 = swt<float>(g, b, d, pos[d], 2, o);
           if (w1 == 0.f && w2 == 0.f) continue;
           int q = o == 0 ? p : nbr(g, p, pos, d, o);
           float uv = (float)ub[q], xv = sc * xb[q];
           u1 += w1 * uv; u2 += w2 * uv; x1 += w1 * xv; x2 += w2 * xv;
         }
       }
-      u1 *= g.is1[d]; u2 *= g.is2[d]; x1 *= g.is1[d]; x2 *= g.is2[d];
+      const float i1 = sis1<float>(g, b, d, pos[d]), i2 = sis2<float>(g, b, d, pos[d]);
+      u1 *= i1; u2 *= i2; x1 *= i1; x2 *= i2;
       a2 += u1 * u1 + u2 * u2; a1 += x1 * x1 + x2 * x2;
     }
   }

@@ -35,6 +35,7 @@ __device__ __forceinline__ int nb1(const Grid& g, int p, const int pos[3], int d
 
 template <int D>
 __device__ __forceinline__ bool edge_any(const Grid& g, const int pos[3]) {
+  if (g.st64) return true;   // per-interval steps: the general forms everywhere
   bool e = pos[0] < 3 || pos[0] > g.n[0] - 4;
 #pragma unroll
   for (int d = 1; d < D; ++d) e |= !g.per[d] && (pos[d] < 3 || pos[d] > g.n[d] - 4);
