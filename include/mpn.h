@@ -112,6 +112,13 @@ typedef struct mpn_desc {
                              use the interval to the neighbour.  Runs the general two-pass kernels
                              on every level (no fused step, no fused coarse end).  0 (default):
                              uniform steps step[] */
+  double bc_alpha[3];     /* boundary rows on both faces of spatial axis d (d = 1, 2; entry 0 unused): */
+  double bc_beta[3];      /* alpha_d u + beta_d du/dx_d = omega (Section 2: Dirichlet, Neumann or
+                             mixed conditions).  Dirichlet (1, 0) is the default; any other pair on an
+                             open axis makes the problem run the general two-pass kernels on every
+                             level.  A point on several faces has the row of the first face in the
+                             order t = 0, t = t_f, then the spatial axes in order (time faces are
+                             Dirichlet).  alpha and beta must be finite and not both zero. */
 } mpn_desc;
 
 enum { MPN_KRYLOV_CG = 0, MPN_KRYLOV_FGMRES = 1 };
@@ -129,7 +136,7 @@ typedef struct mpn_problem mpn_problem;
 
 /* Fills *desc with defaults (tol 1e-7, max_refine 12, inner_iters 5,
  * cheb_degree 5, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 1, krylov CG, coarsen_time 0, direct 0,
- * variable_steps 0). */
+ * variable_steps 0, Dirichlet boundary rows: bc_alpha 1, bc_beta 0). */
 int mpn_default_desc(mpn_desc* desc);
 
 /* Validates the descriptor, builds the grid hierarchy (spatial halving, time

@@ -29,7 +29,8 @@ class MpnDesc(ctypes.Structure):
                 ("cheb_degree", ctypes.c_int), ("coarse_min", ctypes.c_int),
                 ("max_coarse", ctypes.c_int), ("fused_coarse", ctypes.c_int),
                 ("fused_step", ctypes.c_int), ("krylov", ctypes.c_int), ("coarsen_time", ctypes.c_int),
-                ("direct", ctypes.c_int), ("variable_steps", ctypes.c_int)]
+                ("direct", ctypes.c_int), ("variable_steps", ctypes.c_int),
+                ("bc_alpha", ctypes.c_double * 3), ("bc_beta", ctypes.c_double * 3)]
 
 KRYLOV = {"cg": 0, "fgmres": 1}
 
@@ -218,6 +219,12 @@ class Solver:
         d.coarsen_time = int(bool(coarsen_time))
         d.direct = int(bool(direct))
         d.variable_steps = int(bool(variable_steps))
+        # boundary rows alpha u + beta du/dx_d = omega per spatial axis
+        # (geom["bc"] = {d: (alpha, beta)}; Dirichlet where absent)
+        for k, (a, b) in dict(geom.get("bc", {})).items():
+            if not 1 <= int(k) < D:
+                raise ValueError(f"boundary kind for axis {k}: only spatial axes 1..{D - 1}")
+            d.bc_alpha[int(k)], d.bc_beta[int(k)] = float(a), float(b)
         h = ctypes.c_void_p()
         s = lib.mpn_create(ctypes.byref(d), ctypes.byref(h))
         if s != 0:

@@ -56,6 +56,7 @@ struct Level {
   float* fields = nullptr;  // [F][B][N]
   float *rho = nullptr, *dinv = nullptr;
   float *r = nullptr, *e = nullptr, *d = nullptr, *y = nullptr, *t = nullptr;
+  float *r12 = nullptr, *r22 = nullptr, *y2 = nullptr;   // Neumann / mixed rows (see Grid)
 };
 
 struct mpn_problem {
@@ -99,6 +100,10 @@ struct mpn_problem {
   float* st32 = nullptr;
   int* sterr = nullptr;
   bool steps_set = false;
+  // Neumann / mixed boundary rows: per-level R12, R22 and second pass-1
+  // output (FP32 [L][B][N] each) and their finest-level FP64 copies
+  bool mixed = false;
+  double *r12d = nullptr, *r22d = nullptr, *y2d = nullptr;
   size_t bytes = 0;
   bool setup_ok = false;
   bool zd_valid = false;   // uf64 holds the FP64 u of the last forward
@@ -227,6 +232,7 @@ extern "C" int mpn_default_desc(mpn_desc* d) {
   d->coarsen_time = 0;
   d->direct = 0;
   d->variable_steps = 0;
+  for (int k = 0; k < 3; ++k) { d->bc_alpha[k] = 1.0; d->bc_beta[k] = 0.0; }
   return MPN_OK;
 }
 
@@ -320,7 +326,7 @@ static const void* tail_fn(const mpn_problem* p) {
 // or the cluster cannot be resident on this device.
 static void plan_tail(mpn_problem* p) {
   p->tail_k0 = -1;
-  if (!p->desc.fused_coarse || p->L < 2 || p->desc.variable_steps) return;
+  if (!p->desc.fused_coarse || p->L < 2 || p->desc.variable_steps || p->mixed) return;
   const int n0 = p->lv[0].g.n[0];
   // cluster size: 4 CTAs per instance, more (up to TAIL_MAX_CLUSTER) while
   // the batch gives fewer than TAIL_TARGET_CTAS CTAs in all; smaller sizes
@@ -436,6 +442,13 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   if (d.krylov != MPN_KRYLOV_CG && d.krylov != MPN_KRYLOV_FGMRES) return MPN_ERR_INVALID_ARG;
   if (d.fused_step < 0 || d.fused_step > 2) return MPN_ERR_INVALID_ARG;
   if (d.variable_steps != 0 && d.variable_steps != 1) return MPN_ERR_INVALID_ARG;
+  bool mixed = false;
+  for (int k = 1; k < d.ndim; ++k) {
+    if (d.periodic[k]) continue;
+    const double a = d.bc_alpha[k], bt = d.bc_beta[k];
+    if (!std::isfinite(a) || !std::isfinite(bt) || (a == 0.0 && bt == 0.0)) return MPN_ERR_INVALID_ARG;
+    mixed = mixed || a != 1.0 || bt != 0.0;
+  }
   int V = 1 + 2 * d.ndim;
   for (int k = 0; k < d.ndim; ++k) {
     if (d.n[k] < 3 || !(d.variable_steps || d.step[k] > 0)) return MPN_ERR_INVALID_ARG;
@@ -449,6 +462,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
 
   mpn_problem* p = new mpn_problem();
   p->desc = d;
+  p->mixed = mixed;
   p->D = d.ndim; p->V = V; p->F = d.nfields; p->B = d.batch;
   for (int v = 0; v < V; ++v) if (d.field_of[v] >= 0) p->field_mask |= 1 << v;
   if (p->D == 2) p->desc.n[2] = 1;
@@ -483,8 +497,8 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   }
   for (int k = 0; k < p->L; ++k) {
     Level& l = p->lv[k];
-    // per-interval steps: the general (scalar) kernels only
-    l.vec4 = (p->D == 3 && l.g.n[2] % 4 == 0 && l.g.n[2] >= 8 && !d.variable_steps) ? 1 : 0;
+    // per-interval steps, Neumann / mixed rows: the general (scalar) kernels only
+    l.vec4 = (p->D == 3 && l.g.n[2] % 4 == 0 && l.g.n[2] >= 8 && !d.variable_steps && !mixed) ? 1 : 0;
     l.papply = l.vec4 ? sblk(l.g.N / 4) : sblk(l.g.N);
     // fused operator step: tiles that divide the t and x extents, with whole
     // y rows of at most FS_MAX_NY points, or 64-point y segments of wider rows
@@ -565,6 +579,24 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
       g.st64 = p->st64 + per_level * k * ST_REC;
       g.st32 = p->st32 + per_level * k * ST_REC;
       g.stn = p->stn;
+    }
+  }
+  if (mixed) {
+    AL(p->r12d, N0); AL(p->r22d, N0); AL(p->y2d, N0);
+    for (int k = 0; k < p->L; ++k) {
+      Level& l = p->lv[k];
+      const size_t N = (size_t)l.g.N * B;
+      AL(l.r12, N); AL(l.r22, N); AL(l.y2, N);
+      Grid& g = l.g;
+      g.mixed = 1;
+      for (int e = 0; e < 3; ++e) {
+        const bool on = e >= 1 && e < p->D && !d.periodic[e] && (d.bc_alpha[e] != 1.0 || d.bc_beta[e] != 0.0);
+        g.bcm[e] = on ? 1 : 0;
+        g.bca[e] = on ? (float)d.bc_alpha[e] : 1.f;
+        g.bcb[e] = on ? (float)d.bc_beta[e] : 0.f;
+      }
+      g.r12 = l.r12; g.r22 = l.r22; g.y2 = l.y2;
+      if (k == 0) { g.r12d = p->r12d; g.r22d = p->r22d; g.y2d = p->y2d; }
     }
   }
   if (d.krylov == MPN_KRYLOV_FGMRES) {
@@ -759,6 +791,9 @@ static int setup_body(mpn_problem* p, cudaStream_t st) {
     Coef cf = make_coef(p, l0.fields);
     if (p->D == 3) ++p->nlaunch, k_rho_fine<3><<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, p->rho64);
     else ++p->nlaunch, k_rho_fine<2><<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, p->rho64);
+    if (p->mixed)
+      ++p->nlaunch, k_mixed_weights<<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, l0.r12, l0.r22, p->rho64,
+                                                                          p->r12d, p->r22d);
     CKL();
   }
   for (int k = 1; k < p->L; ++k) {
@@ -770,6 +805,11 @@ static int setup_body(mpn_problem* p, cudaStream_t st) {
       ++p->nlaunch, k_restrict_field<<<gf, MPN_TPB, 0, st>>>(lf.g, lc.g, lf.cz[0], lf.cz[1], lf.cz[2], lf.fields, lc.fields, 1.f);
     ++p->nlaunch, k_restrict_field<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(lf.g, lc.g, lf.cz[0], lf.cz[1], lf.cz[2], lf.rho,
                                                                lc.rho, (float)(1 << nd));
+    if (p->mixed) {
+      Coef cfc = make_coef(p, lc.fields);
+      ++p->nlaunch, k_mixed_weights<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(lc.g, cfc, lc.rho, lc.r12, lc.r22, nullptr,
+                                                                          nullptr, nullptr);
+    }
     CKL();
   }
   // Jacobi diagonals and lambda_max(Dinv S) per level: the levels are
@@ -1124,19 +1164,19 @@ static int residual64(mpn_problem* p, const double* u, const double* g_adj, doub
     return MPN_OK;
   }
   if (p->D == 3 && fp64_layout(p) == FS_MASK_RDI) {
-    ++p->nlaunch, k_res64_y<3, FS_MASK_RDI><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    ++p->nlaunch, k_res64_y<3, FS_MASK_RDI><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, om, p->y64);
     ++p->nlaunch, k_res64_q<3, FS_MASK_RDI><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
   } else if (p->D == 3 && fp64_layout(p) == FS_MASK_RD) {
-    ++p->nlaunch, k_res64_y<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    ++p->nlaunch, k_res64_y<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, om, p->y64);
     ++p->nlaunch, k_res64_q<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
   } else if (p->D == 3 && fp64_layout(p) == FS_MASK_TR) {
-    ++p->nlaunch, k_res64_y<3, FS_MASK_TR><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    ++p->nlaunch, k_res64_y<3, FS_MASK_TR><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, om, p->y64);
     ++p->nlaunch, k_res64_q<3, FS_MASK_TR><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
   } else if (p->D == 3) {
-    ++p->nlaunch, k_res64_y<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    ++p->nlaunch, k_res64_y<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, om, p->y64);
     ++p->nlaunch, k_res64_q<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
   } else {
-    ++p->nlaunch, k_res64_y<2, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, p->y64);
+    ++p->nlaunch, k_res64_y<2, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, u, src, om, p->y64);
     ++p->nlaunch, k_res64_q<2, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->y64, g_adj, om, u, out, part);
   }
   CKL();
@@ -1303,15 +1343,15 @@ static int forward_impl(mpn_problem* p, const float* fields, const float* scalar
   if (status != MPN_OK && status != MPN_ERR_NOT_CONVERGED) return status;
   Coef cf = make_coef(p, l.fields);
   if (p->D == 3 && fp64_layout(p) == FS_MASK_RDI)
-    ++p->nlaunch, k_recover<3, FS_MASK_RDI><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
+    ++p->nlaunch, k_recover<3, FS_MASK_RDI><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, p->omega, nullptr, z, z64);
   else if (p->D == 3 && fp64_layout(p) == FS_MASK_RD)
-    ++p->nlaunch, k_recover<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
+    ++p->nlaunch, k_recover<3, FS_MASK_RD><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, p->omega, nullptr, z, z64);
   else if (p->D == 3 && fp64_layout(p) == FS_MASK_TR)
-    ++p->nlaunch, k_recover<3, FS_MASK_TR><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
+    ++p->nlaunch, k_recover<3, FS_MASK_TR><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, p->omega, nullptr, z, z64);
   else if (p->D == 3)
-    ++p->nlaunch, k_recover<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
+    ++p->nlaunch, k_recover<3, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, p->omega, nullptr, z, z64);
   else
-    ++p->nlaunch, k_recover<2, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, nullptr, z, z64);
+    ++p->nlaunch, k_recover<2, RES_ANY><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->u64, p->rhs, p->omega, nullptr, z, z64);
   CKL();
   CK(cudaMemcpyAsync(p->uf64, p->u64, sizeof(double) * N0, cudaMemcpyDeviceToDevice, st));
   p->zd_valid = true;
@@ -1372,7 +1412,7 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
   if (status != MPN_OK && status != MPN_ERR_NOT_CONVERGED) return status;
   double* gp = slot(p, S_GR0);
 #define GRAD_LAUNCH(DD, MK)                                                                              \
-  ++p->nlaunch, k_gradients<DD, MK><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->rhs, p->uf64, p->u64, g_z, dfields, \
+  ++p->nlaunch, k_gradients<DD, MK><<<gr, MPN_TPB, 0, st>>>(l.g, cf, p->rho64, p->rhs, p->omega, p->uf64, p->u64, g_z, dfields, \
                                                            drhs, domega, dz, dz64, gp)
   if (p->D == 3 && fp64_layout(p) == FS_MASK_RDI) GRAD_LAUNCH(3, FS_MASK_RDI);
   else if (p->D == 3 && fp64_layout(p) == FS_MASK_RD) GRAD_LAUNCH(3, FS_MASK_RD);

@@ -55,6 +55,22 @@ struct Grid {
   const double* st64;
   const float* st32;
   int stn;
+  // Neumann / mixed boundary rows alpha u + beta du/dx_d = omega on both
+  // faces of spatial axis d where bcm[d] (the time faces and the other axes
+  // keep Dirichlet rows).  Their point weights (the 2x2 matrix R of the
+  // equation and boundary rows of a face point) live in per-level arrays:
+  // rho holds R11, r12 / r22 the rest (zero off those points), y2 receives
+  // the boundary-row part of the first operator pass; r12d / r22d / y2d are
+  // the FP64 copies of the finest level.
+  int mixed;
+  int bcm[3];
+  float bca[3], bcb[3];
+  const float* r12;
+  const float* r22;
+  float* y2;
+  const double* r12d;
+  const double* r22d;
+  double* y2d;
 };
 
 // Step record of one grid position along one dimension (per-interval steps).
@@ -137,10 +153,10 @@ __device__ __forceinline__ void decode_fast(const Grid& g, int p, int pos[3]) {
   pos[1] = fdivmod(rem, g.n[2], g.inv_n2, i2);
   pos[2] = i2;
 }
-// Per-interval steps count as edges everywhere: only the general forms read
-// the step records.
+// Per-interval steps and Neumann / mixed rows count as edges everywhere:
+// only the general forms read the step records and the boundary rows.
 __device__ __forceinline__ bool any_edge(const Grid& g, const int pos[3]) {
-  if (g.st64) return true;
+  if (g.st64 || g.mixed) return true;
   bool e = pos[0] < 3 || pos[0] > g.n[0] - 4;
   for (int d = 1; d < 3; ++d)
     if (d < g.D && !g.per[d]) e |= pos[d] < 3 || pos[d] > g.n[d] - 4;
@@ -186,6 +202,26 @@ __device__ __forceinline__ bool is_boundary(const Grid& g, const int pos[3]) {
   for (int d = 1; d < g.D; ++d)
     if (!g.per[d] && (pos[d] == 0 || pos[d] == g.n[d] - 1)) return true;
   return false;
+}
+
+// Axis of the boundary row of a point: -1 none, 0 a time face (Dirichlet),
+// d >= 1 a face of spatial axis d.  A point on several faces has the row of
+// the first in the order t = 0, t = t_f, then the spatial axes in order.
+__device__ __forceinline__ int bc_axis(const Grid& g, const int pos[3]) {
+  if (pos[0] == 0 || (g.final_rows && pos[0] == g.n[0] - 1)) return 0;
+  for (int d = 1; d < g.D; ++d)
+    if (!g.per[d] && (pos[d] == 0 || pos[d] == g.n[d] - 1)) return d;
+  return -1;
+}
+// The spatial axis of the point's Neumann / mixed row, or -1.
+__device__ __forceinline__ int mixed_axis(const Grid& g, const int pos[3]) {
+  if (!g.mixed) return -1;
+  const int e = bc_axis(g, pos);
+  return (e >= 1 && g.bcm[e]) ? e : -1;
+}
+// The point has a Dirichlet row (weight theta in the reduced operator).
+__device__ __forceinline__ bool dirichlet_point(const Grid& g, const int pos[3]) {
+  return is_boundary(g, pos) && mixed_axis(g, pos) < 0;
 }
 
 template <int D>
@@ -335,6 +371,43 @@ __device__ __forceinline__ T LTgather(const Grid& g, const Coef& cf, int b, int 
       T c1 = (T)coefv(cf, 1 + 2 * d, b, q, g.N);
       T c2 = (T)coefv(cf, 2 + 2 * d, b, q, g.N);
       acc += y[q] * (c1 * w1 * sis1<T>(g, b, d, ip) + c2 * w2 * sis2<T>(g, b, d, ip));
+    }
+  }
+  return acc;
+}
+
+// (B x)_i = alpha x_i + beta (du/dx_e)_i: the Neumann / mixed row of face
+// point p (axis e) with the first-derivative form of its position.
+template <class T>
+__device__ __forceinline__ T Brow(const Grid& g, int b, int p, const int pos[3], int e, const T* __restrict__ x) {
+  T a1 = 0;
+#pragma unroll
+  for (int o = -2; o <= 2; ++o) {
+    const T w = swt<T>(g, b, e, pos[e], 1, o);
+    if (w == (T)0) continue;
+    a1 += w * x[o == 0 ? p : nbr(g, p, pos, e, o)];
+  }
+  return (T)g.bca[e] * x[p] + (T)g.bcb[e] * sis1<T>(g, b, e, pos[e]) * a1;
+}
+
+// (B^T y2)_j: gather over the Neumann / mixed rows that touch point j.
+template <class T>
+__device__ __forceinline__ T BTgather(const Grid& g, int b, int p, const int pos[3], const T* __restrict__ y2) {
+  T acc = 0;
+  for (int e = 1; e < g.D; ++e) {
+    if (!g.bcm[e] || g.per[e]) continue;
+#pragma unroll
+    for (int o = -2; o <= 2; ++o) {
+      const int ip = pos[e] - o;
+      if (ip != 0 && ip != g.n[e] - 1) continue;   // rows sit on the faces of e
+      int pi[3] = {pos[0], pos[1], pos[2]};
+      pi[e] = ip;
+      if (bc_axis(g, pi) != e) continue;
+      const T w = swt<T>(g, b, e, ip, 1, o);
+      T c = (T)g.bcb[e] * sis1<T>(g, b, e, ip) * w;
+      if (o == 0) c += (T)g.bca[e];
+      if (c == (T)0) continue;
+      acc += c * y2[p + (ip - pos[e]) * g.stride[e]];
     }
   }
   return acc;

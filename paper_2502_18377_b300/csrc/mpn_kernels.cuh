@@ -44,6 +44,46 @@ __global__ void k_rho_fine(Grid g, Coef cf, float* __restrict__ rho, double* __r
   }
 }
 
+// Weights of the points with a Neumann / mixed row (axis e): with
+// beta = (c_{1+2d} / sbar_d, c_{2+2d} / sbar_d^2) per axis and
+// gamma = b_e / sbar_e on the first derivative along e, the 2x2 weight of the
+// point's (equation, boundary) rows is R = (I + K^T W^{-1} K)^{-1},
+// K = [beta, gamma]: rho <- R11, r12 <- R12, r22 <- R22, each times theta
+// (1 on the finest level, the level's boundary-row weight on coarser ones).
+// Other points: r12 = r22 = 0, rho untouched.
+__global__ void k_mixed_weights(Grid g, Coef cf, float* __restrict__ rho, float* __restrict__ r12,
+                                float* __restrict__ r22, double* __restrict__ rho64, double* __restrict__ r12d,
+                                double* __restrict__ r22d) {
+  int b = blockIdx.y;
+  const size_t off = (size_t)b * g.N;
+  GRID_LOOP(p, g.N) {
+    int pos[3]; decode_fast(g, p, pos);
+    const int e = mixed_axis(g, pos);
+    if (e < 1) {
+      r12[off + p] = 0.f; r22[off + p] = 0.f;
+      if (r12d) { r12d[off + p] = 0.0; r22d[off + p] = 0.0; }
+      continue;
+    }
+    double g11 = 0.0, be1 = 0.0, be2 = 0.0;
+    for (int d = 0; d < g.D; ++d) {
+      const double b1 = (double)coefv(cf, 1 + 2 * d, b, p, g.N) * sis1<double>(g, b, d, pos[d]);
+      const double b2 = (double)coefv(cf, 2 + 2 * d, b, p, g.N) * sis2<double>(g, b, d, pos[d]);
+      double q1, q2;
+      swinv<double>(g, b, d, pos[d], b1, b2, q1, q2);
+      g11 += b1 * q1 + b2 * q2;
+      if (d == e) { be1 = b1; be2 = b2; }
+    }
+    const double gm = g.bcb[e] * sis1<double>(g, b, e, pos[e]);
+    double qg1, qg2;
+    swinv<double>(g, b, e, pos[e], gm, 0.0, qg1, qg2);
+    const double g12 = be1 * qg1 + be2 * qg2, g22 = gm * qg1;
+    const double idet = (double)g.theta / ((1.0 + g11) * (1.0 + g22) - g12 * g12);
+    const double R11 = (1.0 + g22) * idet, R12 = -g12 * idet, R22 = (1.0 + g11) * idet;
+    rho[off + p] = (float)R11; r12[off + p] = (float)R12; r22[off + p] = (float)R22;
+    if (rho64) { rho64[off + p] = R11; r12d[off + p] = R12; r22d[off + p] = R22; }
+  }
+}
+
 // Full-weighting restriction of a point field (1/4, 1/2, 1/4 per coarsened
 // dimension; clamped at non-periodic edges), times `scale`.  fine/coarse are
 // [nb][Nf] / [nb][Nc] with the batch-like index in blockIdx.y.
@@ -88,11 +128,17 @@ __global__ void k_diag_inv(Grid g, Coef cf, const float* __restrict__ rho, float
   GRID_LOOP(p, g.N) {
     int pos[3]; decode_fast(g, p, pos);
     // own row: L_jj
+    const size_t off = (size_t)b * g.N;
     float Ljj = coefv(cf, 0, b, p, g.N);
     for (int d = 0; d < g.D; ++d)
       Ljj += coefv(cf, 1 + 2 * d, b, p, g.N) * swt<float>(g, b, d, pos[d], 1, 0) * sis1<float>(g, b, d, pos[d]) +
              coefv(cf, 2 + 2 * d, b, p, g.N) * swt<float>(g, b, d, pos[d], 2, 0) * sis2<float>(g, b, d, pos[d]);
     float acc = rh[p] * Ljj * Ljj;
+    const int ej = mixed_axis(g, pos);
+    if (ej >= 1) {   // own Neumann / mixed row
+      const float Bjj = g.bca[ej] + g.bcb[ej] * sis1<float>(g, b, ej, pos[ej]) * swt<float>(g, b, ej, pos[ej], 1, 0);
+      acc += 2.f * g.r12[off + p] * Ljj * Bjj + g.r22[off + p] * Bjj * Bjj;
+    }
     for (int d = 0; d < g.D; ++d)
       for (int o = -2; o <= 2; ++o) {
         if (o == 0) continue;
@@ -105,55 +151,17 @@ __global__ void k_diag_inv(Grid g, Coef cf, const float* __restrict__ rho, float
         float Lij = coefv(cf, 1 + 2 * d, b, q, g.N) * w1 * sis1<float>(g, b, d, ip) +
                     coefv(cf, 2 + 2 * d, b, q, g.N) * w2 * sis2<float>(g, b, d, ip);
         acc += rh[q] * Lij * Lij;
+        if (g.mixed) {   // the Neumann / mixed row of point q along d
+          int pq[3] = {pos[0], pos[1], pos[2]};
+          pq[d] = ip;
+          if (mixed_axis(g, pq) == d) {
+            const float Bij = g.bcb[d] * sis1<float>(g, b, d, ip) * w1;
+            acc += 2.f * g.r12[off + q] * Lij * Bij + g.r22[off + q] * Bij * Bij;
+          }
+        }
       }
-    if (is_boundary(g, pos)) acc += g.theta;
+    if (dirichlet_point(g, pos)) acc += g.theta;
     dinv[(size_t)b * g.N + p] = acc > 0 ? 1.f / acc : 0.f;
-  }
-}
-
-// ------------------------------------------------------ operator: two passes
-// y = rho (src - L (x + x2)); rho null => computed from the coefficients;
-// x null => L x = 0.
-template <class T>
-__global__ void k_Lpass(Grid g, Coef cf, const float* __restrict__ rho, const T* __restrict__ x,
-                        const T* __restrict__ x2, const float* __restrict__ src, T* __restrict__ y) {
-  int b = blockIdx.y;
-  size_t off = (size_t)b * g.N;
-  GRID_LOOP(p, g.N) {
-    int pos[3]; decode_fast(g, p, pos);
-    T Lx = x ? Lrow<T>(g, cf, b, p, pos, x + off, x2 ? x2 + off : nullptr) : (T)0;
-    T r = rho ? (T)rho[off + p] : rho_point<T>(g, cf, b, p, pos);
-    T s = src ? (T)src[off + p] : (T)0;
-    y[off + p] = r * (s - Lx);
-  }
-}
-
-// out = sgn * (base + L^T y + theta 1_B (omega - x)); base/omega/x nullable.
-// If dotv is non-null, writes per-block partials of <out, dotv>.
-template <class T>
-__global__ void k_LTpass(Grid g, Coef cf, const T* __restrict__ y, const float* __restrict__ base,
-                         const T* __restrict__ baseT, const float* __restrict__ omega, const T* __restrict__ x,
-                         T sgn, T* __restrict__ out, const T* __restrict__ dotv, double* __restrict__ part) {
-  int b = blockIdx.y;
-  size_t off = (size_t)b * g.N;
-  double acc = 0;
-  GRID_LOOP(p, g.N) {
-    int pos[3]; decode_fast(g, p, pos);
-    T v = LTgather<T>(g, cf, b, p, pos, y + off);
-    if (base) v += (T)base[off + p];
-    if (baseT) v += baseT[off + p];
-    if (is_boundary(g, pos)) {
-      T bc = omega ? (T)omega[off + p] : (T)0;
-      if (x) bc -= x[off + p];
-      v += (T)g.theta * bc;
-    }
-    v *= sgn;
-    out[off + p] = v;
-    if (dotv) acc += (double)v * (double)dotv[off + p];
-  }
-  if (dotv) {
-    double s = block_sum(acc);
-    if (threadIdx.x == 0) part[b * MPN_PMAX + blockIdx.x] = s;
   }
 }
 
@@ -345,8 +353,9 @@ __global__ void k_coarse_assemble(Grid g, Coef cf, const float* __restrict__ rho
     int pj[3]; decode_fast(g, j, pj);
     float* row = K + (size_t)j * (bw + 1);
     for (int k = 0; k <= bw; ++k) row[k] = 0.f;
-    if (is_boundary(g, pj)) row[0] += g.theta;
-    // rows i of L that touch j: i = j (center) and i = j - o e_d
+    if (dirichlet_point(g, pj)) row[0] += g.theta;
+    // rows i of L that touch j: i = j (center) and i = j - o e_d; a point with
+    // a Neumann / mixed row adds [L_ij, B_ij] R [L_ik, B_ik]^T
     for (int d0 = -1; d0 < g.D; ++d0) {
       for (int o = -2; o <= 2; ++o) {
         int i, pi[3] = {pj[0], pj[1], pj[2]};
@@ -371,6 +380,25 @@ __global__ void k_coarse_assemble(Grid g, Coef cf, const float* __restrict__ rho
                 (double)coefv(cf, 2 + 2 * d0, b, i, g.N) * w2 * sis2<double>(g, b, d0, ip);
         }
         double f = Lij * (double)rh[i];
+        const int ei = mixed_axis(g, pi);
+        if (ei >= 1) {
+          double Bij = 0.0;
+          if (d0 < 0) Bij = g.bca[ei] + g.bcb[ei] * sis1<double>(g, b, ei, pi[ei]) * swt<double>(g, b, ei, pi[ei], 1, 0);
+          else if (d0 == ei) Bij = g.bcb[ei] * sis1<double>(g, b, ei, pi[ei]) * swt<double>(g, b, ei, pi[ei], 1, o);
+          const size_t oi = (size_t)b * g.N + i;
+          const double r12 = g.r12[oi], r22 = g.r22[oi];
+          f += Bij * r12;
+          const double fB = Lij * r12 + Bij * r22;
+          // row i of B: alpha at i and the first-derivative form along ei
+          for (int o2 = -2; o2 <= 2; ++o2) {
+            const double w = swt<double>(g, b, ei, pi[ei], 1, o2);
+            double Bik = g.bcb[ei] * sis1<double>(g, b, ei, pi[ei]) * w;
+            if (o2 == 0) Bik += g.bca[ei];
+            if (Bik == 0.0) continue;
+            const int k = o2 == 0 ? i : nbr(g, i, pi, ei, o2);
+            if (k <= j && j - k <= bw) row[j - k] += (float)(fB * Bik);
+          }
+        }
         // row i of L: center and off-center entries
         double Lii = coefv(cf, 0, b, i, g.N);
         for (int d = 0; d < g.D; ++d)
@@ -949,10 +977,17 @@ __global__ void k_set_u(int N, const float* __restrict__ u0, double* __restrict_
 // the (small) equation-row residual.  The duals follow from it:
 // lambda_E = -rho E* (forward, bE = b) and d_lambda_E = -rho E* (adjoint).
 // Returns rho E*.
+// A point with a Neumann / mixed row B u + gamma^T w = omega (gamma = beta / s
+// on the first derivative along its axis e) has two point rows: with
+// E* = (E1*, E2*), E2* = B u - omE + gamma^T W^{-1} h_g, and R its 2x2 weight,
+//   w = a(u) + W^{-1} h_g - W^{-1} (beta (R E*)_1 + gamma (R E*)_2),
+// the duals of its equation and boundary rows are -(R E*)_1 and -(R E*)_2.
+// Returns (R E*)_1 and writes (R E*)_2 to *rE2 (E2* itself, the Dirichlet
+// residual u - omega, at other boundary points; 0 elsewhere).
 template <int D, int MASK>
 __device__ __forceinline__ double recover_point(const Grid& g, const Coef64<MASK>& C, int b, int p, const int pos[3],
-                                                const double* __restrict__ u, double rho, double bE,
-                                                const float* __restrict__ gz, double* zo) {
+                                                const double* __restrict__ u, double rho, double bE, double omE,
+                                                const float* __restrict__ gz, double* zo, double* rE2) {
   constexpr int V = 1 + 2 * D;
   size_t off = (size_t)b * g.N;
   double uc = u[off + p];
@@ -990,6 +1025,21 @@ __device__ __forceinline__ double recover_point(const Grid& g, const Coef64<MASK
   }
   double rE = rho * Est;
   zo[0] = uc;
+  const int e = mixed_axis(g, pos);
+  if (e >= 1) {
+    const double gm = g.bcb[e] * is[e][0];
+    const double E2 = Brow<double>(g, b, p, pos, e, u + off) - omE + gm * hw[e][0];
+    const double r12 = g.r12d[off + p], r22 = g.r22d[off + p];
+    rE = rho * Est + r12 * E2;
+    const double re2 = r12 * Est + r22 * E2;
+    double qg1, qg2;
+    swinv<double>(g, b, e, pos[e], gm, 0.0, qg1, qg2);   // W^{-1} gamma
+    hw[e][0] -= re2 * qg1;
+    hw[e][1] -= re2 * qg2;
+    *rE2 = re2;
+  } else {
+    *rE2 = is_boundary(g, pos) ? uc - omE : 0.0;
+  }
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     zo[1 + 2 * d] = (a[d][0] + hw[d][0] - rE * qb[d][0]) * is[d][0];
@@ -1001,16 +1051,17 @@ __device__ __forceinline__ double recover_point(const Grid& g, const Coef64<MASK
 // z (FP32 and/or FP64) from u.
 template <int D, int MASK>
 __global__ void k_recover(Grid g, Coef cf, const double* __restrict__ rho64, const double* __restrict__ u,
-                          const float* __restrict__ bE, const float* __restrict__ gz, float* __restrict__ zf,
-                          double* __restrict__ zd) {
+                          const float* __restrict__ bE, const float* __restrict__ omE, const float* __restrict__ gz,
+                          float* __restrict__ zf, double* __restrict__ zd) {
   int b = blockIdx.y;
   const Coef64<MASK> C(cf, b);
   constexpr int V = 1 + 2 * D;
   size_t off = (size_t)b * g.N;
   GRID_LOOP(p, g.N) {
     int pos[3]; decode_fast(g, p, pos);
-    double zo[7];
-    recover_point<D, MASK>(g, C, b, p, pos, u, rho64[off + p], bE ? (double)bE[off + p] : 0.0, gz, zo);
+    double zo[7], r2;
+    recover_point<D, MASK>(g, C, b, p, pos, u, rho64[off + p], bE ? (double)bE[off + p] : 0.0,
+                           omE ? (double)omE[off + p] : 0.0, gz, zo, &r2);
     size_t zb = (size_t)b * V * g.N;
     for (int v = 0; v < V; ++v) {
       if (zf) zf[zb + (size_t)v * g.N + p] = (float)zo[v];
@@ -1024,12 +1075,14 @@ __global__ void k_recover(Grid g, Coef cf, const double* __restrict__ rho64, con
 //   lambda_E = b - E z* = rho (b - L u)                       (closed form)
 //   dlambda_E = -E d_z = -rho (L d_u + beta^T W^{-1} S^{-1} g_zeta)
 //   dl/dc_v = dlambda_E z_v + lambda_E dz_v,  dl/db = -dlambda_E,
-//   dl/domega = d_u on boundary points.
+//   dl/domega = -d_lambda_B: d_u on Dirichlet points, (R E*)_2 of the adjoint
+//   on Neumann / mixed points.
 // z and d_z are recovered on the fly.  Field
 // gradients sum over the unknowns sharing a field; scalar gradients are
 // reduced per instance (partials in part[v]).
 template <int D, int MASK>
 __global__ void k_gradients(Grid g, Coef cf, const double* __restrict__ rho64, const float* __restrict__ rhs,
+                            const float* __restrict__ omega,
                             const double* __restrict__ uf, const double* __restrict__ du, const float* __restrict__ gz,
                             float* __restrict__ dfields, float* __restrict__ drhs, float* __restrict__ domega,
                             float* __restrict__ dz_out, double* __restrict__ dz64_out, double* __restrict__ part) {
@@ -1040,10 +1093,11 @@ __global__ void k_gradients(Grid g, Coef cf, const double* __restrict__ rho64, c
   size_t off = (size_t)b * g.N;
   GRID_LOOP(p, g.N) {
     int pos[3]; decode_fast(g, p, pos);
-    double zv[7], dv[7];
+    double zv[7], dv[7], r2, dr2;
     double r = rho64[off + p];
-    double lam = -recover_point<D, MASK>(g, C, b, p, pos, uf, r, (double)rhs[off + p], nullptr, zv);
-    double dlam = -recover_point<D, MASK>(g, C, b, p, pos, du, r, 0.0, gz, dv);
+    double lam = -recover_point<D, MASK>(g, C, b, p, pos, uf, r, (double)rhs[off + p], (double)omega[off + p],
+                                         nullptr, zv, &r2);
+    double dlam = -recover_point<D, MASK>(g, C, b, p, pos, du, r, 0.0, 0.0, gz, dv, &dr2);
     double cv[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -1059,7 +1113,7 @@ __global__ void k_gradients(Grid g, Coef cf, const double* __restrict__ rho64, c
       dfields[((size_t)f * cf.B + b) * g.N + p] = (float)s;
     }
     drhs[off + p] = (float)(-dlam);
-    domega[off + p] = is_boundary(g, pos) ? (float)dv[0] : 0.f;
+    domega[off + p] = is_boundary(g, pos) ? (float)dr2 : 0.f;
     if (dz_out) {
 #pragma unroll
       for (int v = 0; v < V; ++v) dz_out[((size_t)b * V + v) * g.N + p] = (float)dv[v];
@@ -1100,18 +1154,32 @@ __global__ void k_adj_kappa(Grid g, Coef cf, const float* __restrict__ gz, doubl
       bwh += b1 * hw[d][0] + b2 * hw[d][1];
       gam += b1 * q1 + b2 * q2;
     }
-    double fac = bwh / (1.0 + gam);
-    double bpsi = 0;
+    // (W + K K^T)^{-1} h = W^{-1} h - W^{-1} K (I + K^T W^{-1} K)^{-1} K^T W^{-1} h with
+    // K = [beta] (one row) or [beta, gamma] at a Neumann / mixed point
+    double fac = bwh / (1.0 + gam), fac2 = 0.0, gm = 0.0, qg1 = 0.0, qg2 = 0.0;
+    const int e = mixed_axis(g, pos);
+    if (e >= 1) {
+      gm = g.bcb[e] * sis1<double>(g, b, e, pos[e]);
+      swinv<double>(g, b, e, pos[e], gm, 0.0, qg1, qg2);
+      const double hwg = gm * hw[e][0];
+      const double g12 = be[e][0] * qg1 + be[e][1] * qg2, g22 = gm * qg1;
+      const double idet = 1.0 / ((1.0 + gam) * (1.0 + g22) - g12 * g12);
+      fac = ((1.0 + g22) * bwh - g12 * hwg) * idet;
+      fac2 = ((1.0 + gam) * hwg - g12 * bwh) * idet;
+    }
+    double bpsi = 0, gpsi = 0;
     #pragma unroll
     for (int d = 0; d < D; ++d) {
       double q1, q2; swinv<double>(g, b, d, pos[d], be[d][0], be[d][1], q1, q2);
       double ps1 = hw[d][0] - q1 * fac, ps2 = hw[d][1] - q2 * fac;
+      if (d == e) { ps1 -= qg1 * fac2; ps2 -= qg2 * fac2; gpsi = gm * ps1; }
       bpsi += be[d][0] * ps1 + be[d][1] * ps2;
       double w11, w12, w22; swmat(g, b, d, pos[d], w11, w12, w22);
       kap[((size_t)(1 + 2 * d) * gridDim.y + b) * g.N + p] = -(w11 * ps1 + w12 * ps2);
       kap[((size_t)(2 + 2 * d) * gridDim.y + b) * g.N + p] = -(w12 * ps1 + w22 * ps2);
     }
-    kap[(size_t)b * g.N + p] = C.at(0, p) * bpsi;
+    // the boundary row's u part is alpha at the point itself
+    kap[(size_t)b * g.N + p] = C.at(0, p) * bpsi + (e >= 1 ? g.bca[e] * gpsi : 0.0);
   }
 }
 
@@ -1209,10 +1277,12 @@ __global__ void k_znorm(Grid g, const double* __restrict__ u, const float* __res
 // throughput, not memory, bounds these):
 //   k_res64_y:  y = rho (b - L u)              (b, u nullable => 0)
 //   k_res64_q:  r = base + L^T y + theta 1_B (omega - u), partials of ||r||^2
-// Points away from non-periodic edges use the central weights directly.
+// Points away from non-periodic edges use the central weights directly.  A
+// point with a Neumann / mixed row takes (y, y2) = R (b - L u, omega - B u)
+// and its boundary row adds B^T y2 (omega nullable => 0).
 template <int D, int MASK>
 __global__ void k_res64_y(Grid g, Coef cf, const double* __restrict__ rho64, const double* __restrict__ u,
-                          const float* __restrict__ bsrc, double* __restrict__ y) {
+                          const float* __restrict__ bsrc, const float* __restrict__ omega, double* __restrict__ y) {
   int b = blockIdx.y;
   size_t off = (size_t)b * g.N;
   const Coef64<MASK> C(cf, b);
@@ -1233,6 +1303,14 @@ __global__ void k_res64_y(Grid g, Coef cf, const double* __restrict__ rho64, con
       }
     }
     double s = bsrc ? (double)bsrc[off + p] : 0.0;
+    const int e = mixed_axis(g, pos);
+    if (e >= 1) {
+      const double eB = (omega ? (double)omega[off + p] : 0.0) - (u ? Brow<double>(g, b, p, pos, e, u + off) : 0.0);
+      const double r12 = g.r12d[off + p];
+      y[off + p] = rho64[off + p] * (s - Lu) + r12 * eB;
+      g.y2d[off + p] = r12 * (s - Lu) + g.r22d[off + p] * eB;
+      continue;
+    }
     y[off + p] = rho64[off + p] * (s - Lu);
   }
 }
@@ -1264,9 +1342,11 @@ __global__ void k_res64_q(Grid g, Coef cf, const double* __restrict__ y, const d
       }
     } else {
       q = LTgather<double, D>(g, cf, b, p, pos, yb);
+      if (g.mixed) q += BTgather<double>(g, b, p, pos, g.y2d + off);
     }
     if (base) q += base[off + p];
-    if (is_boundary_t<D>(g, pos)) q += (double)g.theta * ((omega ? (double)omega[off + p] : 0.0) - (u ? u[off + p] : 0.0));
+    if (is_boundary_t<D>(g, pos) && mixed_axis(g, pos) < 0)
+      q += (double)g.theta * ((omega ? (double)omega[off + p] : 0.0) - (u ? u[off + p] : 0.0));
     out[off + p] = q;
     acc += q * q;
   }

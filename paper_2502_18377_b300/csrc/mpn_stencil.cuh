@@ -35,7 +35,7 @@ __device__ __forceinline__ int nb1(const Grid& g, int p, const int pos[3], int d
 
 template <int D>
 __device__ __forceinline__ bool edge_any(const Grid& g, const int pos[3]) {
-  if (g.st64) return true;   // per-interval steps: the general forms everywhere
+  if (g.st64 || g.mixed) return true;   // the general forms everywhere
   bool e = pos[0] < 3 || pos[0] > g.n[0] - 4;
 #pragma unroll
   for (int d = 1; d < D; ++d) e |= !g.per[d] && (pos[d] < 3 || pos[d] > g.n[d] - 4);
@@ -63,6 +63,14 @@ __global__ void __launch_bounds__(256) k_Ly(Grid g, Coef cf, const float* __rest
       }
     } else {
       Lx = Lrow<float, D>(g, cf, b, p, pos, xb, nullptr);
+      const int e = mixed_axis(g, pos);
+      if (e >= 1) {   // Neumann / mixed row: y = -R (L x, B x)
+        const float Bx = Brow<float>(g, b, p, pos, e, xb);
+        const float r12 = g.r12[off + p], r22 = g.r22[off + p];
+        y[off + p] = -(rho[off + p] * Lx + r12 * Bx);
+        g.y2[off + p] = -(r12 * Lx + r22 * Bx);
+        continue;
+      }
     }
     y[off + p] = -rho[off + p] * Lx;
   }
@@ -90,9 +98,10 @@ __global__ void __launch_bounds__(256) k_LTy(Grid g, Coef cf, StepArgs a) {
       }
     } else {
       q = LTgather<float, D>(g, cf, b, p, pos, yb);
+      if (g.mixed) q += BTgather<float>(g, b, p, pos, g.y2 + off);
     }
     float xj = a.x[off + p];
-    if (is_boundary_t<D>(g, pos)) q -= g.theta * xj;
+    if (is_boundary_t<D>(g, pos) && mixed_axis(g, pos) < 0) q -= g.theta * xj;
     // q = -(S x)_j
     const size_t j = off + p;
     if (MODE == SM_APPLY) {
