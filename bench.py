@@ -42,7 +42,7 @@ BATCH, GRID = WORKLOADS[HEADLINE][1], WORKLOADS[HEADLINE][2]
 # DRAM bytes of one finest-level smoothing step of the headline workload from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); None until
 # captured for the current kernel.
-STEP_TRAFFIC_BYTES = 226.3e6
+STEP_TRAFFIC_BYTES = None
 
 
 def _peaks():
@@ -373,7 +373,7 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MB write outside the step events); "
                          "one level's working set exceeds L2 as well"},
         "roofline": {"bound": "hbm", "kernel": "finest-level Chebyshev smoothing step (L and L^T passes fused "
-                                               "through shared memory on 64-point y segments)",
+                                               "through shared memory, 16 x 64 columns marching along t)",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": STEP_TRAFFIC_BYTES,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the finest-level "

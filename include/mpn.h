@@ -90,7 +90,14 @@ typedef struct mpn_desc {
                              run as one kernel through shared memory, on tiles of whole y rows where
                              n_y <= 128 (n_t % 4 == 0) and of 64-point y segments where n_y > 128
                              (n_y % 64 == 0, n_t % 8 == 0); 2: the same with y segments wherever
-                             they apply (n_y >= 128); 0: two kernels (same arithmetic) */
+                             they apply (n_y >= 128); 3 (default): as 1, and on levels with periodic
+                             x and y, n_x % 16 == 0, n_y % 64 == 0, n_t % 8 == 0, uniform steps and
+                             a coefficient layout whose fields are c_x and c_y (transport) or c_0
+                             and c_xx = c_yy (reaction-diffusion), whose 16 x 64 columns number at
+                             least half the SMs over the batch, every step but PCG's direction
+                             update marches along t through shared memory (one CTA per column and
+                             chunk of time planes); 4: the same on every such level whatever its
+                             size; 0: two kernels (same arithmetic) */
   int krylov;             /* inner FP32 solver of each refinement sweep: MPN_KRYLOV_CG (conjugate
                              gradients) or MPN_KRYLOV_FGMRES (flexible GMRES(m), m = the sweep's
                              iteration count, with the same V-cycle as right preconditioner, the
@@ -135,7 +142,7 @@ typedef struct mpn_stats {
 typedef struct mpn_problem mpn_problem;
 
 /* Fills *desc with defaults (tol 1e-7, max_refine 12, inner_iters 5,
- * cheb_degree 5, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 1, krylov CG, coarsen_time 0, direct 0,
+ * cheb_degree 5, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 3, krylov CG, coarsen_time 0, direct 0,
  * variable_steps 0, Dirichlet boundary rows: bc_alpha 1, bc_beta 0). */
 int mpn_default_desc(mpn_desc* desc);
 

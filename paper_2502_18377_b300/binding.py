@@ -194,7 +194,7 @@ class Solver:
 
     def __init__(self, geom: dict, batch: int, field_of, nfields: int, tol=1e-7, max_refine=12,
                  inner_iters=5, cheb_degree=5, coarse_min=4, max_coarse=2048, fused_coarse=True,
-                 fused_step=True, krylov="cg", coarsen_time=False, direct=False, variable_steps=False):
+                 fused_step=3, krylov="cg", coarsen_time=False, direct=False, variable_steps=False):
         lib = load()
         d = MpnDesc()
         lib.mpn_default_desc(ctypes.byref(d))

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 PKG = os.path.dirname(HERE)
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libmpn.so")
-SOURCES = [os.path.join(HERE, f) for f in ("mpn.cu", "mpn_step_row.cu", "mpn_step_y.cu", "mpn_noalloc.cu",
+SOURCES = [os.path.join(HERE, f) for f in ("mpn.cu", "mpn_step_row.cu", "mpn_step_y.cu", "mpn_step_march.cu", "mpn_noalloc.cu",
                                           "mpn_conv.cu")]
 DEPS = SOURCES + [os.path.join(HERE, f) for f in os.listdir(HERE) if f.endswith((".cuh", ".h"))] + \
     [os.path.join(ROOT, "include", "mpn.h")]

@@ -52,6 +52,8 @@ struct Level {
   int fs_tt = 0;       // > 0: operator steps as one fused kernel with TT-plane tiles
   int fs_ty = 0;       // fused tiles of fs_ty y points (k_step3y), or of whole y rows when 0 (k_step3)
   int fs_layout = SL_ANY;  // compile-time coefficient layout of the fused kernels
+  int ms_tc = 0;       // > 0: the t-marching fused step (k_march) with this many planes per CTA, for
+                       // every mode but the direction-update apply
   float* e2 = nullptr; // second iterate buffer of the fused smoother (the operand is read with a halo)
   float* fields = nullptr;  // [F][B][N]
   float *rho = nullptr, *dinv = nullptr;
@@ -227,7 +229,7 @@ extern "C" int mpn_default_desc(mpn_desc* d) {
   d->coarse_min = 4;
   d->max_coarse = 2048;
   d->fused_coarse = 1;
-  d->fused_step = 1;
+  d->fused_step = 3;
   d->krylov = MPN_KRYLOV_CG;
   d->coarsen_time = 0;
   d->direct = 0;
@@ -300,7 +302,7 @@ extern "C" int mpn_levels(const mpn_problem* p, int* nl, int* shapes) {
 #define INV_SMEM_FLOATS (224 * 1024 / 4)
 // Opt the fused step kernels into the shared memory of their largest tile.
 static int fs_set_smem() {
-  return (step_row_attrs() == 0 && step_y_attrs() == 0) ? MPN_OK : MPN_ERR_CUDA;
+  return (step_row_attrs() == 0 && step_y_attrs() == 0 && march_attrs() == 0) ? MPN_OK : MPN_ERR_CUDA;
 }
 
 // Compile-time coefficient layout of the FP64 kernels and the fused coarse
@@ -440,7 +442,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   if (d.inner_iters < 1 || d.max_refine < 1 || d.cheb_degree < 1 || d.cheb_degree > 30) return MPN_ERR_INVALID_ARG;
   if (d.coarse_min < 3 || !(d.tol > 0)) return MPN_ERR_INVALID_ARG;
   if (d.krylov != MPN_KRYLOV_CG && d.krylov != MPN_KRYLOV_FGMRES) return MPN_ERR_INVALID_ARG;
-  if (d.fused_step < 0 || d.fused_step > 2) return MPN_ERR_INVALID_ARG;
+  if (d.fused_step < 0 || d.fused_step > 4) return MPN_ERR_INVALID_ARG;
   if (d.variable_steps != 0 && d.variable_steps != 1) return MPN_ERR_INVALID_ARG;
   bool mixed = false;
   for (int k = 1; k < d.ndim; ++k) {
@@ -495,6 +497,8 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
       }
     theta *= (float)(1 << nd);
   }
+  int nsm = 148, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   for (int k = 0; k < p->L; ++k) {
     Level& l = p->lv[k];
     // per-interval steps, Neumann / mixed rows: the general (scalar) kernels only
@@ -523,6 +527,15 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
         if (l.papply > MPN_PMAX) l.fs_tt = l.fs_ty = 0;   // too many partial sums per instance
       }
       if (!l.fs_tt) l.papply = sblk(l.g.N / 4);
+      // t-marching columns where they apply: with fused_step = 3 on levels
+      // whose columns (x two chunks of time) fill the SMs, with 4 on all
+      if (l.fs_tt && d.fused_step >= 3 && march_has(l.g, per1, per2, l.fs_layout) &&
+          (d.fused_step == 4 || 2 * march_cols(l.g) * p->B >= nsm)) {
+        l.ms_tc = march_planes(l.g, p->B, nsm);
+        const int pm = march_cols(l.g) * (n0 / l.ms_tc);
+        if (pm <= MPN_PMAX) l.papply = pm;
+        else l.ms_tc = 0;
+      }
     }
   }
   Level& lc = p->lv[p->L - 1];
@@ -669,6 +682,11 @@ static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st
   a.y = l.y;
   if (!a.dinv) a.dinv = l.dinv;
   if (!a.err) a.err = p->kerr;
+  if (l.ms_tc && mode != SM_APPLYP) {
+    ++p->nlaunch;
+    march_launch(mode, l.fs_layout, p->B, l.ms_tc, st, l.g, cf, l.rho, a);
+    return;
+  }
   if (l.fs_tt) {
     const size_t sm = step_smem(StepTile{l.fs_tt, l.fs_ty}, l.g.n[2]);
     ++p->nlaunch;

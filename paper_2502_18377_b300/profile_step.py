@@ -3,7 +3,7 @@ profilers (ncu) and quick timings: no clock sampling, no L2 flush, nothing
 else on the GPU.
 
 python -m paper_2502_18377_b300.profile_step [--workload transport_2d]
-    [--batch B] [--grid T X Y] [--steps K] [--warmup W] [--fused-step 0|1|2]
+    [--batch B] [--grid T X Y] [--steps K] [--warmup W] [--fused-step 0|1|2|3|4]
     [--inner-iters N] [--cheb-degree M]
 
 The environment variable MPN_TRACE makes the library print every refinement
@@ -27,7 +27,7 @@ def main():
     ap.add_argument("--grid", type=int, nargs=3)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=1)
-    ap.add_argument("--fused-step", type=int, default=1)
+    ap.add_argument("--fused-step", type=int, default=3)
     ap.add_argument("--inner-iters", type=int, help="default: the workload's benchmark setting")
     ap.add_argument("--cheb-degree", type=int, help="default: the workload's benchmark setting")
     a = ap.parse_args()

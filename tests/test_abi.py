@@ -37,7 +37,7 @@ def test_error_strings_without_gpu():
     d = binding.MpnDesc()
     assert lib.mpn_default_desc(ctypes.byref(d)) == 0
     assert d.stencil == 3 and d.inner_iters >= 1
-    assert d.fused_coarse == 1 and d.fused_step == 1 and d.krylov == 0 and d.coarsen_time == 0 and d.direct == 0 and d.max_coarse == 2048   # last fields: layout agrees with the header
+    assert d.fused_coarse == 1 and d.fused_step == 3 and d.krylov == 0 and d.coarsen_time == 0 and d.direct == 0 and d.max_coarse == 2048   # last fields: layout agrees with the header
     assert lib.mpn_fused_level(None) == -1
     h = ctypes.c_void_p()
     d.stencil = 5
