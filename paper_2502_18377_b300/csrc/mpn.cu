@@ -54,6 +54,7 @@ struct Level {
   int fs_layout = SL_ANY;  // compile-time coefficient layout of the fused kernels
   int ms_tc = 0;       // > 0: the t-marching fused step (k_march) with this many planes per CTA, for
                        // every mode but the direction-update apply
+  int ms_mx = 16;      // x rows of its columns
   float* e2 = nullptr; // second iterate buffer of the fused smoother (the operand is read with a halo)
   float* fields = nullptr;  // [F][B][N]
   float *rho = nullptr, *dinv = nullptr;
@@ -528,13 +529,20 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
       }
       if (!l.fs_tt) l.papply = sblk(l.g.N / 4);
       // t-marching columns where they apply: with fused_step = 3 on levels
-      // whose columns (x two chunks of time) fill the SMs, with 4 on all
-      if (l.fs_tt && d.fused_step >= 3 && march_has(l.g, per1, per2, l.fs_layout) &&
-          (d.fused_step == 4 || 2 * march_cols(l.g) * p->B >= nsm)) {
-        l.ms_tc = march_planes(l.g, p->B, nsm);
-        const int pm = march_cols(l.g) * (n0 / l.ms_tc);
-        if (pm <= MPN_PMAX) l.papply = pm;
-        else l.ms_tc = 0;
+      // whose columns of 16 rows fill the SMs' resident CTAs over the batch,
+      // with 4 on all (16 rows where they divide n_x, else 8)
+      if (l.fs_tt && d.fused_step >= 3) {
+        for (int mx : {16, 8}) {
+          if (!march_has(l.g, per1, per2, l.fs_layout, mx)) continue;
+          // (8-row columns measured slower than the whole-row tiles on the
+          // levels they would serve: used with fused_step = 4 only)
+          if (d.fused_step == 3 && (mx != 16 || march_ctas_per_sm(mx) * march_cols(l.g, mx) * p->B < nsm)) continue;
+          const int tc = march_planes(l.g, p->B, nsm, mx);
+          const int pm = march_cols(l.g, mx) * (n0 / tc);
+          if (pm > MPN_PMAX) continue;
+          l.ms_tc = tc; l.ms_mx = mx; l.papply = pm;
+          break;
+        }
       }
     }
   }
@@ -684,7 +692,7 @@ static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st
   if (!a.err) a.err = p->kerr;
   if (l.ms_tc && mode != SM_APPLYP) {
     ++p->nlaunch;
-    march_launch(mode, l.fs_layout, p->B, l.ms_tc, st, l.g, cf, l.rho, a);
+    march_launch(mode, l.fs_layout, p->B, l.ms_mx, l.ms_tc, st, l.g, cf, l.rho, a);
     return;
   }
   if (l.fs_tt) {
@@ -1082,15 +1090,30 @@ static int pcg(mpn_problem* p, int iters, cudaStream_t st, bool started) {
       memset(&a, 0, sizeof(a));
       a.x = zv; a.out = p->q; a.part = slot(p, S_PQ);
       a.cnt = p->pcnt + p->B; a.tot = p->ptot + p->B;   // <p, S p> finished by the step's last CTAs
-      if (it == 0) {
-        a.e = pb[c];
+      if (l.ms_tc) {
+        // on the t-marching step: p = z + beta p_old by a vector pass, then the apply
+        float* pn = it == 0 ? pb[c] : pb[c ^ 1];
+        if (v4)
+          ++p->nlaunch, k_pcg_pd<true><<<gv, MPN_TPB, 0, st>>>(N, ze ? p->ptot : nullptr, slot(p, S_RZ), Prz, rz_old,
+                                                               zv, it == 0 ? nullptr : pb[c], pn);
+        else
+          ++p->nlaunch, k_pcg_pd<false><<<gv, MPN_TPB, 0, st>>>(N, ze ? p->ptot : nullptr, slot(p, S_RZ), Prz, rz_old,
+                                                                zv, it == 0 ? nullptr : pb[c], pn);
+        CKL();
+        if (it > 0) c ^= 1;
+        a.x = pn;
+        stencil(p, 0, a, SM_APPLY, st);
       } else {
-        a.d = pb[c]; a.e = pb[c ^ 1];
-        a.rz = slot(p, S_RZ); a.nrz = Prz; a.rz_old = rz_old;
-        a.rz_tot = ze ? p->ptot : nullptr;
-        c ^= 1;
+        if (it == 0) {
+          a.e = pb[c];
+        } else {
+          a.d = pb[c]; a.e = pb[c ^ 1];
+          a.rz = slot(p, S_RZ); a.nrz = Prz; a.rz_old = rz_old;
+          a.rz_tot = ze ? p->ptot : nullptr;
+          c ^= 1;
+        }
+        stencil(p, 0, a, SM_APPLYP, st);
       }
-      stencil(p, 0, a, SM_APPLYP, st);
       const float* dst = it < iters - 1 ? l.dinv : nullptr;   // a V-cycle follows
       if (v4)
         ++p->nlaunch, k_pcg_xr<true><<<gv, MPN_TPB, 0, st>>>(N, slot(p, S_RZ), slot(p, S_PQ), l.papply, Prz, pb[c], p->q,

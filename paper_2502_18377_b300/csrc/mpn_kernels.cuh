@@ -756,6 +756,37 @@ __global__ void k_pcg_p(int N, const double* __restrict__ part_rz, int P, const 
     vst<V4>(pv + off, i, zz + beta * pp);
   }
 }
+// p = z + beta p_old into another buffer (p_old null: p = z), beta =
+// <r, z> / rz_old with <r, z> the finished sum tot_rz[b] when given, else
+// the sum of P partials (the direction update ahead of an apply on the
+// t-marching step).
+template <bool V4>
+__global__ void k_pcg_pd(int N, const double* __restrict__ tot_rz, const double* __restrict__ part_rz, int P,
+                         const double* __restrict__ rz_old, const float* __restrict__ z,
+                         const float* __restrict__ pold, float* __restrict__ pnew) {
+  const int b = blockIdx.y;
+  const size_t off = (size_t)b * N;
+  const int n = V4 ? N >> 2 : N;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  float4 zz, pp = f4(0.f);
+  if (i0 < n) {
+    zz = vld<V4>(z + off, i0);
+    if (pold) pp = vld<V4>(pold + off, i0);
+  }
+  float beta = 0.f;
+  if (pold) {
+    const double rz = tot_rz ? tot_rz[b] : sum_partials(part_rz, b, P);
+    const double ro = rz_old[b];
+    beta = (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f;
+  }
+  for (int i = i0; i < n; i += stride) {
+    if (i != i0) {
+      zz = vld<V4>(z + off, i);
+      if (pold) pp = vld<V4>(pold + off, i);
+    }
+    vst<V4>(pnew + off, i, zz + beta * pp);
+  }
+}
 // ------------------------------------------------ FGMRES (Section 3.1)
 // Batched right-preconditioned flexible GMRES(m) on S x = r from x = 0, one
 // restart cycle per refinement sweep: Arnoldi basis v_0..v_m (FP32 vectors),

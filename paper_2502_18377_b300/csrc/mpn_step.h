@@ -34,15 +34,17 @@ void step_row_launch(int mode, int tt, bool per1, bool per2, int layout, int B, 
 void step_y_launch(int mode, int tt, int ty, bool per1, bool per2, int layout, int B, size_t smem, cudaStream_t st,
                    const Grid& g, const Coef& cf, const float* rho, const StepArgs& a);
 
-// t-marching fused step (k_march): whether a level qualifies (periodic x and
-// y, n_x % 16 == 0, n_y % 64 == 0, n_t % 8 == 0, the SL_TR or SL_RDI layout);
-// its shared-memory bytes; columns per instance; planes per CTA for B
-// instances on nsm SMs; the attributes (host call, once); one launch (any
-// mode but SM_APPLYP) with tc planes per CTA.
-bool march_has(const Grid& g, bool per1, bool per2, int layout);
-size_t march_smem();
-int march_cols(const Grid& g);
-int march_planes(const Grid& g, int B, int nsm);
+// t-marching fused step (k_march) on columns of mx = 16 or 8 x-rows x 64 y
+// points: whether a level qualifies (periodic x and y, n_x % mx == 0,
+// n_y % 64 == 0, n_t % 8 == 0, the SL_TR or SL_RDI layout); its
+// shared-memory bytes; columns per instance; resident CTAs per SM; planes per
+// CTA for B instances on nsm SMs; the attributes (host call, once); one launch
+// (any mode but SM_APPLYP) with tc planes per CTA.
+bool march_has(const Grid& g, bool per1, bool per2, int layout, int mx);
+size_t march_smem(int mx);
+int march_cols(const Grid& g, int mx);
+int march_ctas_per_sm(int mx);
+int march_planes(const Grid& g, int B, int nsm, int mx);
 int march_attrs();
-void march_launch(int mode, int layout, int B, int tc, cudaStream_t st, const Grid& g, const Coef& cf,
+void march_launch(int mode, int layout, int B, int mx, int tc, cudaStream_t st, const Grid& g, const Coef& cf,
                   const float* rho, const StepArgs& a);

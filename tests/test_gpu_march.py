@@ -1,8 +1,8 @@
 """Parity of the t-marching fused step with the FP64 oracle (fused_step = 4
 puts it on every level it serves; 3, on the levels with enough columns).
 
-The marching kernel serves levels with periodic x and y, n_x % 16 == 0,
-n_y % 64 == 0 and n_t % 8 == 0 in the transport layout (fields on c_x, c_y)
+The marching kernel serves levels with periodic x and y, n_x % 16 == 0
+(columns of 16 x-rows) or n_x % 8 == 0 (8 rows), n_y % 64 == 0 and n_t % 8 == 0 in the transport layout (fields on c_x, c_y)
 and the reaction-diffusion layout with c_xx = c_yy one field.  The cases
 cover one and several columns in x and in y, rows of exactly 64 points (the
 y halo wraps on both sides of one column), chunks of the time extent (the
@@ -55,6 +55,11 @@ CASES = [
     ("transport_2y", lambda: wl.transport_2d(batch=1, n=(8, 16, 128))),
     ("reaction_diffusion_1col", lambda: wl.reaction_diffusion_2d(batch=2, n=(8, 16, 64))),
     ("reaction_diffusion_chunks", lambda: wl.reaction_diffusion_2d(batch=1, n=(16, 16, 128))),
+    # columns of 8 x-rows (n_x not a multiple of 16): one column, three
+    # columns with chunks
+    ("transport_8rows", lambda: wl.transport_2d(batch=2, n=(8, 8, 64))),
+    ("transport_8rows_3x_chunks", lambda: wl.transport_2d(batch=1, n=(16, 24, 64))),
+    ("reaction_diffusion_8rows", lambda: wl.reaction_diffusion_2d(batch=1, n=(16, 8, 128))),
 ]
 
 
