@@ -5,12 +5,12 @@
 // per-instance scalars (the transport layout, and reaction-diffusion with
 // c_xx = c_yy one field).
 //
-// A CTA owns a column of MS_X x-rows x MS_Y y points of one instance over the
+// A CTA owns a column of MX x-rows x MS_Y y points of one instance over the
 // time planes [t0, t1) (the whole time extent, or a chunk of it).  For each
 // plane t in order:
 //   A. y = -rho L x on plane t+1, on the column plus a ring of one x-row and
 //      one y point on each side, into a ring of y planes in shared memory;
-//   B. one CTA barrier;
+//   B. one CTA barrier (then the next planes' copies are issued);
 //   C. q = L^T y - theta 1_B x = -(S x) on plane t of the column, then the
 //      mode's update (as k_step3y), written to global memory.
 // The rows of L that reach plane t lie on planes t-1 .. t+1, and on plane 0
@@ -20,12 +20,15 @@
 //
 // The operand (x-halo 2), the coefficient fields and rho (x-halo 1), each with
 // a y halo of one float4 group, stream plane by plane into ring slots by
-// 16-byte asynchronous copies (cp.async, one commit group per plane step,
-// issued by every thread right after the barrier that frees the slots, two
-// plane steps ahead of their first use; no registers are held while they are
-// in flight).  Warps 0-7 read the right-hand side, the Chebyshev diagonal and
-// the previous iterate of their own point one plane ahead into registers.
-// Shared memory: 111.7 KB, two CTAs per SM; two CTA barriers per plane.
+// 16-byte asynchronous copies (cp.async; each thread copies the same groups of
+// every plane, at offsets computed once), one commit group per plane step,
+// issued right after the step's barrier into the slots it freed and waited
+// for before the next step's barrier; no registers are held while they are
+// in flight.  One CTA barrier per plane publishes both the landed copies and
+// the y plane of pass A.  The threads of pass C read the right-hand side, the
+// Chebyshev diagonal and the previous iterate of their own point one plane
+// ahead into registers.  Shared memory: 111.7 KB (16 rows, two CTAs per SM)
+// or 61.9 KB (8 rows, three).
 #pragma once
 #include "mpn_fused.cuh"
 
@@ -242,6 +245,9 @@ __global__ void __launch_bounds__(ms_tpb(MX), ms_ctas_per_sm(MX))
     passA(c, c == 2 ? xslot(tp - 2) : 0, c != 1 ? xslot(tp - 1) : 0, xslot(tp), c != 2 ? xslot(tp + 1) : 0,
           c == 1 ? xslot(tp + 2) : 0, fslot(tp), rslot(tp), yslot(tp));
   }
+  // the warm-up's planes are free: copies of the planes pass A of t0 + 1 reads
+  __syncthreads();
+  refill(t0 + 4, t0 + 3, t0 + 4);
 
   // slot offsets of the planes around t, rotated by one plane per step:
   // operand t-1 .. t+3, fields t .. t+3, rho t+1 .. t+3, y t-2 .. t+2
@@ -257,23 +263,25 @@ __global__ void __launch_bounds__(ms_tpb(MX), ms_ctas_per_sm(MX))
 
   double accd = 0.0;
   for (int t = t0; t < t1; ++t) {
-    // the copies that plane t's passes read have landed (this thread's),
-    // then one barrier makes every thread's visible and frees the slots of
-    // the planes no later pass reads
-    if (t <= t0 + 1 || t == n0 - 3) cp_async_wait<0>();
-    else cp_async_wait<1>();
+    // A: y(t+1) (plane t+1 is never the first; y(n0-1) is computed with
+    // y(n0-2), after its field and rho planes have landed)
+    if (t + 1 <= n0 - 1 && t != n0 - 2) passA(0, Xs[0], Xs[1], Xs[2], Xs[3], Xs[4], Fs[1], Rs[0], Ys[3]);
+    if (t == n0 - 3) {
+      cp_async_wait<0>();
+      __syncthreads();
+      passA(2, Xs[1], Xs[2], Xs[3], Xs[4], Xs[4], Fs[2], Rs[1], Ys[4]);
+    }
+    // the copies pass A of t + 1 reads have landed (this thread's); one
+    // barrier publishes them and y(t+1), and frees the slots of the operand
+    // and fields of t - 1 and of rho up to t + 1
+    cp_async_wait<0>();
     __syncthreads();
-    refill(t + MS_NX, t + MS_NF, t + 1 + MS_NR);
+    refill(t + MS_NX, t + MS_NF, t + 2 + MS_NR);
     float4 nr4 = f4(0.f), ndi4 = f4(0.f), nd4 = f4(0.f);
     if (cthr) {
       if (t + 1 < t1) load_pt(t + 1, nr4, ndi4, nd4);
       if ((tid & 7) == 0 && t + 2 < t1) prefetch_pt(t + 2);
     }
-    // A: y(t+1) (and y(n0-1) with y(n0-2)); plane t+1 is never the first
-    if (t + 1 <= n0 - 1 && t != n0 - 2)
-      passA(t + 1 == n0 - 1 ? 2 : 0, Xs[0], Xs[1], Xs[2], Xs[3], Xs[4], Fs[1], Rs[0], Ys[3]);
-    if (t == n0 - 3) passA(2, Xs[1], Xs[2], Xs[3], Xs[4], Xs[4], Fs[2], Rs[1], Ys[4]);
-    __syncthreads();
     if (cthr) {
       // C. q = L^T y - theta 1_B x on plane t
       const int fo = Fs[0];
