@@ -476,6 +476,20 @@ __device__ __forceinline__ double block_sum(double v) {
   return r;
 }
 
+// A float that thread 0 of the CTA computes from per-instance FP64 sums and
+// gives to every thread: an FP64 division or square root in every thread
+// costs more than a streaming kernel's memory traffic on this GPU, where FP64
+// runs at a small fraction of the FP32 rate.  All threads must call it; f must
+// not synchronise.
+template <class F>
+__device__ __forceinline__ float cta_scalar(F f) {
+  __shared__ float v;
+  __syncthreads();
+  if (threadIdx.x == 0) v = f();
+  __syncthreads();
+  return v;
+}
+
 // Writes this CTA's partial sum s (valid in thread 0) for instance b; with a
 // counter, the last of the instance's nblk CTAs to finish (a fence, then one
 // atomic increment per CTA) sums all partials in a fixed order into tot[b]

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(FS_TPB) k_step3y(Grid g, Coef cf, const float*
   float beta = 0.f;
   if (MODE == SM_APPLYP && a.d) {
     const double rz = a.rz_tot ? a.rz_tot[b] : sum_partials(a.rz, b, a.nrz), ro = a.rz_old[b];
-    beta = (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f;
+    beta = cta_scalar([&] { return (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f; });
   }
   if (!mbar_wait(&bar, 0, FS_WAIT_LIMIT) && a.err) atomicExch(a.err, 1);
   if (MODE == SM_APPLYP) {

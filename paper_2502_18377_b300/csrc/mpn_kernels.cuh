@@ -653,8 +653,8 @@ __global__ void k_power_w(int N, const float* __restrict__ dinv, const float* __
                           double* __restrict__ part_out) {
   int b = blockIdx.y;
   size_t off = (size_t)b * N;
-  const double nn = sqrt(sum_partials(part_in, b, P));
-  const float inv = nn > 0 ? (float)(1.0 / nn) : 0.f;
+  const double ss = sum_partials(part_in, b, P);
+  const float inv = cta_scalar([&] { const double nn = sqrt(ss); return nn > 0 ? (float)(1.0 / nn) : 0.f; });
   double acc = 0;
   GRID_LOOP(p, N) {
     float v = dinv[off + p] * q[off + p] * inv;
@@ -669,9 +669,12 @@ __global__ void k_power_w(int N, const float* __restrict__ dinv, const float* __
 __global__ void k_scale_dinv(int N, float* __restrict__ dinv, const double* __restrict__ part, int P,
                              float safety, float* __restrict__ lam_out) {
   int b = blockIdx.y;
-  double lam = sqrt(sum_partials(part, b, P));
-  float s = lam > 0 ? (float)(1.0 / (safety * lam)) : 1.f;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && lam_out) lam_out[b] = (float)lam;
+  const double ss = sum_partials(part, b, P);
+  const float s = cta_scalar([&] {
+    const double lam = sqrt(ss);
+    if (blockIdx.x == 0 && lam_out) lam_out[b] = (float)lam;
+    return lam > 0 ? (float)(1.0 / (safety * lam)) : 1.f;
+  });
   size_t off = (size_t)b * N;
   GRID_LOOP(p, N) dinv[off + p] *= s;
 }
@@ -722,7 +725,7 @@ __global__ void k_pcg_xr(int N, const double* __restrict__ part_rz, const double
   // the finished sums where the producing kernels wrote them, else the partials
   const double rz = tot_rz ? tot_rz[b] : sum_partials(part_rz, b, Prz);
   const double pq = tot_pq ? tot_pq[b] : sum_partials(part_pq, b, P);
-  const float alpha = (pq > 0 && rz > 0) ? (float)(rz / pq) : 0.f;
+  const float alpha = cta_scalar([&] { return (pq > 0 && rz > 0) ? (float)(rz / pq) : 0.f; });
   if (blockIdx.x == 0 && threadIdx.x == 0) rz_old[b] = rz;
   for (int i = i0; i < n; i += stride) {
     if (i != i0) {
@@ -750,7 +753,7 @@ __global__ void k_pcg_p(int N, const double* __restrict__ part_rz, int P, const 
   if (i0 < n) { zz = vld<V4>(z + off, i0); pp = vld<V4>(pv + off, i0); }
   const double rz = sum_partials(part_rz, b, P);
   const double ro = rz_old[b];
-  const float beta = (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f;
+  const float beta = cta_scalar([&] { return (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f; });
   for (int i = i0; i < n; i += stride) {
     if (i != i0) { zz = vld<V4>(z + off, i); pp = vld<V4>(pv + off, i); }
     vst<V4>(pv + off, i, zz + beta * pp);
@@ -777,7 +780,7 @@ __global__ void k_pcg_pd(int N, const double* __restrict__ tot_rz, const double*
   if (pold) {
     const double rz = tot_rz ? tot_rz[b] : sum_partials(part_rz, b, P);
     const double ro = rz_old[b];
-    beta = (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f;
+    beta = cta_scalar([&] { return (ro > 0 && rz > 0) ? (float)(rz / ro) : 0.f; });
   }
   for (int i = i0; i < n; i += stride) {
     if (i != i0) {
@@ -887,7 +890,7 @@ __global__ void k_fg_scale(int N, const float* __restrict__ w, const double* __r
                            float* __restrict__ r_in) {
   const int b = blockIdx.y;
   const double h = hnext[b];
-  const float inv = h > 1e-300 ? (float)(1.0 / h) : 0.f;
+  const float inv = cta_scalar([&] { return h > 1e-300 ? (float)(1.0 / h) : 0.f; });
   const size_t off = (size_t)b * N;
   const int n = V4 ? N >> 2 : N;
   GRID_LOOP(q, n) {
