@@ -145,10 +145,17 @@ struct mpn_problem {
 enum { S_RZ = 0, S_PQ, S_RN, S_DU, S_UN, S_PW, S_GN, S_GR0, S_PW0 = S_GR0 + 8, S_PW1 = S_PW0 + MAXL, NSLOT = S_PW1 + MAXL };
 
 static inline double* slot(mpn_problem* p, int k) { return p->part + (size_t)k * p->B * MPN_PMAX; }
+// CTAs per instance of the grid-stride kernels (FP64 refinement, recovery
+// and gradient passes, setup, and the reductions their consumers sum): enough
+// that the FP64 kernels keep warps in flight to hide the FP64 pipe's latency
+// (two waves of 8 CTAs on each of 148 SMs over the batch, 64 at least: every
+// consumer CTA of a reduction sums its partials again, so no more than that)
+static int nblk_cap(int B) { int c = 2 * 148 * 8 / (B > 0 ? B : 1); return c < 64 ? 64 : (c > 512 ? 512 : c); }
+static int nblk(const mpn_problem* p, int N) {
+  const int b = (N + MPN_TPB - 1) / MPN_TPB, c = nblk_cap(p->B);
+  return b < 1 ? 1 : (b > c ? c : b);
+}
 
-// CTAs per instance: vector kernels (and the reductions their consumers sum)
-// use few, stencil kernels many.
-static int nblk(int N) { int b = (N + MPN_TPB - 1) / MPN_TPB; return b < 1 ? 1 : (b > 64 ? 64 : b); }
 static int sblk(int N) { int b = (N + MPN_TPB - 1) / MPN_TPB; return b < 1 ? 1 : (b > 512 ? 512 : b); }
 // PCG vector kernels: one float4 group (or one value) per thread, up to
 // MPN_PMAX blocks per instance (each block writes one partial sum).
@@ -815,10 +822,10 @@ static int setup_body(mpn_problem* p, cudaStream_t st) {
   ++p->nlaunch, k_rep4<<<(V * B + MPN_TPB - 1) / MPN_TPB, MPN_TPB, 0, st>>>(V * B, p->scalars, p->scal4);
   {
     Coef cf = make_coef(p, l0.fields);
-    if (p->D == 3) ++p->nlaunch, k_rho_fine<3><<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, p->rho64);
-    else ++p->nlaunch, k_rho_fine<2><<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, p->rho64);
+    if (p->D == 3) ++p->nlaunch, k_rho_fine<3><<<dim3(nblk(p, l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, p->rho64);
+    else ++p->nlaunch, k_rho_fine<2><<<dim3(nblk(p, l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, p->rho64);
     if (p->mixed)
-      ++p->nlaunch, k_mixed_weights<<<dim3(nblk(l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, l0.r12, l0.r22, p->rho64,
+      ++p->nlaunch, k_mixed_weights<<<dim3(nblk(p, l0.g.N), B), MPN_TPB, 0, st>>>(l0.g, cf, l0.rho, l0.r12, l0.r22, p->rho64,
                                                                           p->r12d, p->r22d);
     CKL();
   }
@@ -826,14 +833,14 @@ static int setup_body(mpn_problem* p, cudaStream_t st) {
     Level& lf = p->lv[k - 1];
     Level& lc = p->lv[k];
     int nd = lf.cz[0] + lf.cz[1] + lf.cz[2];
-    dim3 gf(nblk(lc.g.N), F * B);
+    dim3 gf(nblk(p, lc.g.N), F * B);
     if (F > 0)
       ++p->nlaunch, k_restrict_field<<<gf, MPN_TPB, 0, st>>>(lf.g, lc.g, lf.cz[0], lf.cz[1], lf.cz[2], lf.fields, lc.fields, 1.f);
-    ++p->nlaunch, k_restrict_field<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(lf.g, lc.g, lf.cz[0], lf.cz[1], lf.cz[2], lf.rho,
+    ++p->nlaunch, k_restrict_field<<<dim3(nblk(p, lc.g.N), B), MPN_TPB, 0, st>>>(lf.g, lc.g, lf.cz[0], lf.cz[1], lf.cz[2], lf.rho,
                                                                lc.rho, (float)(1 << nd));
     if (p->mixed) {
       Coef cfc = make_coef(p, lc.fields);
-      ++p->nlaunch, k_mixed_weights<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(lc.g, cfc, lc.rho, lc.r12, lc.r22, nullptr,
+      ++p->nlaunch, k_mixed_weights<<<dim3(nblk(p, lc.g.N), B), MPN_TPB, 0, st>>>(lc.g, cfc, lc.rho, lc.r12, lc.r22, nullptr,
                                                                           nullptr, nullptr);
     }
     CKL();
@@ -848,14 +855,14 @@ static int setup_body(mpn_problem* p, cudaStream_t st) {
   {
     Level& l = p->lv[p->L - 1];
     Coef cf = make_coef(p, l.fields);
-    ++p->nlaunch, k_diag_inv<<<dim3(nblk(l.g.N), B), MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.dinv);
+    ++p->nlaunch, k_diag_inv<<<dim3(nblk(p, l.g.N), B), MPN_TPB, 0, st>>>(l.g, cf, l.rho, l.dinv);
     CKL();
   }
   // coarsest: banded assembly, Cholesky, explicit inverse
   Level& lc = p->lv[p->L - 1];
   Coef cfc = make_coef(p, lc.fields);
   CK(cudaMemsetAsync(p->ferr, 0, sizeof(int) * B, st));
-  ++p->nlaunch, k_coarse_assemble<<<dim3(nblk(p->M), B), MPN_TPB, 0, st>>>(lc.g, cfc, lc.rho, p->bw, p->Kband);
+  ++p->nlaunch, k_coarse_assemble<<<dim3(nblk(p, p->M), B), MPN_TPB, 0, st>>>(lc.g, cfc, lc.rho, p->bw, p->Kband);
   // bands up to FACT1_MAXBW: one barrier per column step (k_coarse_factor1)
   const bool f1 = p->bw <= FACT1_MAXBW;
   if (p->band_smem) {
@@ -886,7 +893,7 @@ static int setup_body(mpn_problem* p, cudaStream_t st) {
   for (int k = 0; k + 1 < p->L; ++k) {
     Level& l = p->lv[k];
     Coef cf = make_coef(p, l.fields);
-    dim3 gr(nblk(l.g.N), B);
+    dim3 gr(nblk(p, l.g.N), B);
     cudaStream_t sk = p->aux[k];
     CK(cudaStreamWaitEvent(sk, p->ev_fork, 0));
     ++p->nlaunch, k_diag_inv<<<gr, MPN_TPB, 0, sk>>>(l.g, cf, l.rho, l.dinv);
@@ -955,7 +962,7 @@ static int setup(mpn_problem* p, const float* fields, const float* scalars, cuda
 static int vcycle(mpn_problem* p, int k, cudaStream_t st, bool started = false, double* zdot = nullptr) {
   Level& l = p->lv[k];
   int B = p->B;
-  dim3 gr(nblk(l.g.N), B);
+  dim3 gr(nblk(p, l.g.N), B);
   if (k == p->tail_k0) {
     launch_tail(p, st);
     CKL();
@@ -1014,7 +1021,7 @@ static int vcycle(mpn_problem* p, int k, cudaStream_t st, bool started = false, 
         l.g, lc.g, l.t, lc.r, start_c ? lc.dinv : nullptr, p->cheb_inv_th, lc.fs_tt ? lc.e2 : lc.e,
         lc.fs_tt ? nullptr : lc.d);
   else
-    ++p->nlaunch, k_restrict_vec<<<dim3(nblk(lc.g.N), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], l.t, lc.r);
+    ++p->nlaunch, k_restrict_vec<<<dim3(nblk(p, lc.g.N), B), MPN_TPB, 0, st>>>(l.g, lc.g, l.cz[0], l.cz[1], l.cz[2], l.t, lc.r);
   CKL();
   TRY(vcycle(p, k + 1, st, start_c));
   if (!l.cz[0] && l.cz[1] && l.cz[2] && l.g.per[1] && l.g.per[2] && l.g.n[2] % 4 == 0)
@@ -1196,7 +1203,7 @@ static int residual64(mpn_problem* p, const double* u, const double* g_adj, doub
                       cudaStream_t st) {
   Level& l = p->lv[0];
   Coef cf = make_coef(p, l.fields);
-  dim3 gr(nblk(l.g.N), p->B);   // partial count per instance = nblk (as every refinement reduction)
+  dim3 gr(nblk(p, l.g.N), p->B);   // partial count per instance = nblk (as every refinement reduction)
   const float* src = g_adj ? nullptr : p->rhs;
   const float* om = g_adj ? nullptr : p->omega;
   if (!u && g_adj) {   // adjoint from zero: the residual is the right-hand side
@@ -1293,7 +1300,7 @@ static int run_sweep(mpn_problem* p, const double* g_adj, int iters, int P, bool
 static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mpn_stats* stats, cudaStream_t st) {
   Level& l = p->lv[0];
   int B = p->B, N = l.g.N;
-  int P = nblk(N);          // partials per instance of every refinement-level reduction
+  int P = nblk(p, N);          // partials per instance of every refinement-level reduction
   std::vector<double> prev_upd(B, 1.0), prev_q(B, 0.0);
   mpn_stats sres;
   memset(&sres, 0, sizeof(sres));
@@ -1376,7 +1383,7 @@ static int forward_impl(mpn_problem* p, const float* fields, const float* scalar
   TRY(setup(p, fields, scalars, st));
   CK(cudaMemcpyAsync(p->rhs, rhs, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(p->omega, omega, sizeof(float) * N0, cudaMemcpyDeviceToDevice, st));
-  dim3 gr(nblk(l.g.N), B);
+  dim3 gr(nblk(p, l.g.N), B);
   ++p->nlaunch, k_set_u<<<gr, MPN_TPB, 0, st>>>(l.g.N, u0, p->u64);
   CKL();
   p->zd_valid = false;
@@ -1425,7 +1432,7 @@ extern "C" int mpn_adjoint(mpn_problem* p, const float* fields, const float* sca
   cudaStream_t st = (cudaStream_t)stream;
   Level& l = p->lv[0];
   int B = p->B, V = p->V;
-  dim3 gr(nblk(l.g.N), B);
+  dim3 gr(nblk(p, l.g.N), B);
   (void)z;
   // the kept forward state serves only the buffers that forward read
   const bool same_inputs = p->fwd_in[0] == (const void*)fields && p->fwd_in[1] == (const void*)scalars &&
@@ -1505,7 +1512,7 @@ extern "C" int mpn_inject_wait_failure(mpn_problem* p) {
 extern "C" int mpn_mse_grad(mpn_problem* p, const float* z, const float* target, float* g_z, void* stream) {
   if (!p || !z || !target || !g_z) return MPN_ERR_INVALID_ARG;
   Level& l = p->lv[0];
-  ++p->nlaunch, k_mse_grad<<<dim3(nblk(l.g.N), p->B), MPN_TPB, 0, (cudaStream_t)stream>>>(l.g.N, p->V, p->B, z, target, g_z);
+  ++p->nlaunch, k_mse_grad<<<dim3(nblk(p, l.g.N), p->B), MPN_TPB, 0, (cudaStream_t)stream>>>(l.g.N, p->V, p->B, z, target, g_z);
   CKL();
   return MPN_OK;
 }
