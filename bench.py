@@ -42,7 +42,7 @@ BATCH, GRID = WORKLOADS[HEADLINE][1], WORKLOADS[HEADLINE][2]
 # DRAM bytes of one finest-level smoothing step of the headline workload from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); None until
 # captured for the current kernel.
-STEP_TRAFFIC_BYTES = 221.4e6
+STEP_TRAFFIC_BYTES = 222.0e6
 
 
 def _peaks():

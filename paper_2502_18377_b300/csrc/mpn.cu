@@ -148,9 +148,10 @@ static inline double* slot(mpn_problem* p, int k) { return p->part + (size_t)k *
 // CTAs per instance of the grid-stride kernels (FP64 refinement, recovery
 // and gradient passes, setup, and the reductions their consumers sum): enough
 // that the FP64 kernels keep warps in flight to hide the FP64 pipe's latency
-// (two waves of 8 CTAs on each of 148 SMs over the batch, 64 at least: every
-// consumer CTA of a reduction sums its partials again, so no more than that)
-static int nblk_cap(int B) { int c = 2 * 148 * 8 / (B > 0 ? B : 1); return c < 64 ? 64 : (c > 512 ? 512 : c); }
+// (one wave of 8 CTAs on each of 148 SMs over the batch, 64 to 512 per
+// instance: every consumer CTA of a reduction sums its partials again, so no
+// more than that)
+static int nblk_cap(int B) { int c = 148 * 8 / (B > 0 ? B : 1); return c < 64 ? 64 : (c > 512 ? 512 : c); }
 static int nblk(const mpn_problem* p, int N) {
   const int b = (N + MPN_TPB - 1) / MPN_TPB, c = nblk_cap(p->B);
   return b < 1 ? 1 : (b > c ? c : b);

@@ -27,7 +27,7 @@
 // in flight.  One CTA barrier per plane publishes both the landed copies and
 // the y plane of pass A.  The threads of pass C read the right-hand side, the
 // Chebyshev diagonal and the previous iterate of their own point one plane
-// ahead into registers.  Shared memory: 111.7 KB (16 rows, two CTAs per SM)
+// ahead into registers, before the step's pass A.  Shared memory: 111.7 KB (16 rows, two CTAs per SM)
 // or 61.9 KB (8 rows, three).
 #pragma once
 #include "mpn_fused.cuh"
@@ -263,6 +263,12 @@ __global__ void __launch_bounds__(ms_tpb(MX), ms_ctas_per_sm(MX))
 
   double accd = 0.0;
   for (int t = t0; t < t1; ++t) {
+    // the point operands of plane t+1 (pass C of the next step), a step ahead
+    float4 nr4 = f4(0.f), ndi4 = f4(0.f), nd4 = f4(0.f);
+    if (cthr) {
+      if (t + 1 < t1) load_pt(t + 1, nr4, ndi4, nd4);
+      if ((tid & 7) == 0 && t + 2 < t1) prefetch_pt(t + 2);
+    }
     // A: y(t+1) (plane t+1 is never the first; y(n0-1) is computed with
     // y(n0-2), after its field and rho planes have landed)
     if (t + 1 <= n0 - 1 && t != n0 - 2) passA(0, Xs[0], Xs[1], Xs[2], Xs[3], Xs[4], Fs[1], Rs[0], Ys[3]);
@@ -277,11 +283,7 @@ __global__ void __launch_bounds__(ms_tpb(MX), ms_ctas_per_sm(MX))
     cp_async_wait<0>();
     __syncthreads();
     refill(t + MS_NX, t + MS_NF, t + 2 + MS_NR);
-    float4 nr4 = f4(0.f), ndi4 = f4(0.f), nd4 = f4(0.f);
-    if (cthr) {
-      if (t + 1 < t1) load_pt(t + 1, nr4, ndi4, nd4);
-      if ((tid & 7) == 0 && t + 2 < t1) prefetch_pt(t + 2);
-    }
+
     if (cthr) {
       // C. q = L^T y - theta 1_B x on plane t
       const int fo = Fs[0];
