@@ -293,10 +293,15 @@ typedef struct mpn_conv_desc {
 #define MPN_CONV_RELU 1   /* y = max(., 0) */
 #define MPN_CONV_F32 2    /* FP32 output (else BF16) */
 #define MPN_CONV_BIAS 4   /* add bias */
+#define MPN_CONV_MMA_SYNC 8   /* run the legacy warp-level tensor-core kernel (mma.sync) instead of tcgen05 */
 #define MPN_WGRAD_CHUNK 65536   /* points per partial sum of the weight gradient */
 #define MPN_MSE_BLOCKS 64
 
-/* y = act(conv(x, W) + b): BF16 tensor-core (mma.sync m16n8k16) implicit GEMM, FP32 accumulation. */
+/* y = act(conv(x, W) + b): BF16 implicit GEMM on the 5th-generation tensor cores, FP32 accumulation
+ * in tensor memory: per tile of 128 points and per 3x3x3 tap, tcgen05.mma of M = 128, N = cout,
+ * K = 16 on the gathered input tile and the tap's weights, both staged in shared memory
+ * (MPN_CONV_MMA_SYNC: the warp-level mma.sync m16n8k16 kernel instead).  Not in the paper: the
+ * the benchmark spec's learned warm start (a 3D-conv network predicting the solution). */
 int mpn_conv3d_forward(const mpn_conv_desc* d, const void* x, const void* w, const float* bias, void* y,
                        int flags, void* stream);
 /* g_in [B][N][cin] FP32 = transposed convolution of g_out [B][N][cout] (BF16) with W;

@@ -19,6 +19,7 @@
 #include <cstdint>
 
 #include "../../include/mpn.h"
+#include "mpn_conv_tc.cuh"
 
 namespace {
 
@@ -421,8 +422,242 @@ void launch_conv(const CGrid& g, int B, int flags, const __nv_bfloat16* x, const
   }
 }
 
-void conv_dispatch(const CGrid& g, int B, int ci, int co, int flags, const __nv_bfloat16* x, const __nv_bfloat16* w,
-                   const float* bias, void* y, cudaStream_t st) {
+// Accumulator read-back: 32 lanes x N FP32 columns of this warp, one lane per
+// thread (tcgen05.ld 32x32b), then the wait for the load.
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[N]);
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// The same convolution as k_conv on the 5th-generation tensor cores (see
+// mpn_conv_tc.cuh): persistent CTAs over tiles of 128 points, warp-specialised;
+// err (nullable) is set when a bounded wait gives up.
+template <int CI, int CO, int FLAGS>
+__global__ void __launch_bounds__(tc::TPB) k_conv_tc(CGrid g, int B, const __nv_bfloat16* __restrict__ x,
+                                                     const __nv_bfloat16* __restrict__ w,
+                                                     const float* __restrict__ bias, void* __restrict__ out,
+                                                     int* __restrict__ err) {
+  constexpr int KS = tc::ks_of(CI), WOP = tc::op_bytes(CO), AOP = tc::op_bytes(tc::TM), ABUF = tc::a_bytes(CI);
+  constexpr int S = tc::slots(CI);
+  extern __shared__ __align__(1024) uint8_t csm[];
+  uint8_t* ws = csm;
+  uint8_t* as = csm + tc::w_bytes(CI, CO);
+  uint64_t* full = reinterpret_cast<uint64_t*>(as + S * ABUF);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;
+  uint64_t* acce = accf + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the weights of every tap as B operands: row co, K chunk of 8 input channels
+  for (int i = tid; i < 27 * CO * (CI / 8); i += tc::TPB) {
+    const int c8 = i % (CI / 8), co = (i / (CI / 8)) % CO, tap = i / ((CI / 8) * CO);
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(w + ((size_t)tap * CO + co) * CI + c8 * 8));
+    *reinterpret_cast<uint4*>(ws + (tap * KS + (c8 >> 1)) * WOP + tc::chunk_off(co, c8 & 1)) = v;
+  }
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) {
+      tc::bar_init(&full[i], tc::TM);
+      tc::bar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::bar_init(&accf[i], 1);
+      tc::bar_init(&acce[i], tc::TM);
+    }
+  }
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::s32(tslot)),
+                 "n"(tc::tmem_cols(CO)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::fence_async_smem();
+  tc::tc_before_sync();
+  __syncthreads();
+  tc::tc_after_sync();
+  const uint32_t tmem = *tslot;
+  const int tpi = (g.N + tc::TM - 1) / tc::TM, ntiles = B * tpi;
+  bool ok = true;
+  auto wait = [&](uint64_t* bar, uint32_t par) {
+    if (!tc::bar_wait(bar, par, ok ? tc::WAIT_LIMIT : 1)) ok = false;
+  };
+
+  if (warp < 4) {
+    // ---- gather: thread tid is row tid of every tile
+    const uint32_t abase = tc::s32(as);
+    int G = 0;   // taps copied by this CTA
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int bb = tile / tpi, pp = (tile - bb * tpi) * tc::TM + tid;
+      const bool valid = pp < g.N;
+      int pos[3] = {0, 0, 0};
+      if (valid) cdecode(g, pp, pos);
+      const __nv_bfloat16* xb = x + (size_t)bb * g.N * CI;
+      for (int t0 = 0; t0 < 27; t0 += tc::TPS, ++G) {
+        const int sl = G % S, use = G / S;
+        if (use > 0) wait(&empty[sl], (use - 1) & 1);   // the MMAs of the slot's last use are done
+#pragma unroll
+        for (int j = 0; j < tc::TPS; ++j) {
+          const int tap = t0 + j;
+          const int nb = valid ? cnbr(g, pos, tap / 9 - 1, (tap / 3) % 3 - 1, tap % 3 - 1) : -1;
+          const __nv_bfloat16* src = nb >= 0 ? xb + (size_t)nb * CI : xb;
+          const uint32_t dst = abase + sl * ABUF + j * KS * AOP;
+#pragma unroll
+          for (int c8 = 0; c8 < CI / 8; ++c8)
+            tc::cp16(dst + (c8 >> 1) * AOP + tc::chunk_off(tid, c8 & 1), src + c8 * 8, nb >= 0 ? 16u : 0u);
+        }
+        tc::cp_arrive(&full[sl]);
+      }
+    }
+    // this thread's last copies have landed before it leaves
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp == 4) {
+    // ---- MMA issue (one thread)
+    if (lane == 0) {
+      const uint32_t id = tc::idesc(tc::TM, CO);
+      const uint32_t wbase = tc::s32(ws), abase = tc::s32(as);
+      int G = 0, i = 0;
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+        const int acc = i & 1;
+        if (i >= 2) wait(&acce[acc], ((i - 2) >> 1) & 1);   // the epilogue has read this accumulator
+        tc::tc_after_sync();
+        for (int t0 = 0; t0 < 27; t0 += tc::TPS, ++G) {
+          const int sl = G % S;
+          wait(&full[sl], (G / S) & 1);
+          tc::fence_async_smem();   // the landed copies before the tensor core's reads
+          tc::tc_after_sync();
+#pragma unroll
+          for (int j = 0; j < tc::TPS; ++j) {
+            const int tap = t0 + j;
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks)
+              tc::mma(tmem + (uint32_t)((acc * tc::NACC + tap % tc::NACC) * CO),
+                      tc::sdesc(abase + sl * ABUF + (j * KS + ks) * AOP), tc::sdesc(wbase + (tap * KS + ks) * WOP), id,
+                      (tap >= tc::NACC || ks > 0) ? 1u : 0u);
+          }
+          tc::commit(&empty[sl]);
+        }
+        tc::commit(&accf[acc]);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31
+    const int q = warp & 3, m = 32 * q + lane;
+    int i = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+      const int acc = i & 1;
+      wait(&accf[acc], (i >> 1) & 1);
+      tc::tc_after_sync();
+      float v[CO];
+      tmem_ld<CO>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * tc::NACC * CO), v);
+#pragma unroll
+      for (int j = 1; j < tc::NACC; ++j) {
+        float u[CO];
+        tmem_ld<CO>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((acc * tc::NACC + j) * CO), u);
+#pragma unroll
+        for (int c = 0; c < CO; ++c) v[c] += u[c];
+      }
+      tc::tc_before_sync();
+      tc::bar_arrive(&acce[acc]);
+      const int b = tile / tpi, p = (tile - b * tpi) * tc::TM + m;
+      if (p < g.N) {
+        const size_t o = ((size_t)b * g.N + p) * CO;
+#pragma unroll
+        for (int c = 0; c < CO; ++c) {
+          if (FLAGS & 4) v[c] += __ldg(bias + c);
+          if (FLAGS & 1) v[c] = fmaxf(v[c], 0.f);
+        }
+        if (FLAGS & 2) {
+          float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + o);
+#pragma unroll
+          for (int c = 0; c < CO / 4; ++c) dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+        } else {
+          uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + o);
+#pragma unroll
+          for (int c = 0; c < CO / 8; ++c) {
+            uint32_t u[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * c + 2 * k], v[8 * c + 2 * k + 1]);
+              u[k] = *reinterpret_cast<const uint32_t*>(&h);
+            }
+            dst[c] = make_uint4(u[0], u[1], u[2], u[3]);
+          }
+        }
+      }
+    }
+  }
+  if (!ok && err) atomicExch(err, 1);
+  // every role is done (the epilogue waited for the last accumulator, so no
+  // MMA is in flight) before the tensor memory is freed
+  tc::tc_before_sync();
+  __syncthreads();
+  if (warp == 4) {
+    tc::tc_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(tc::tmem_cols(CO)) : "memory");
+  }
+}
+
+template <int CI, int CO, int FL>
+void launch_conv_tc1(const CGrid& g, int B, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias,
+                     void* y, cudaStream_t st) {
+  constexpr int smem = tc::smem_bytes(CI, CO);
+  static int nctas = 0;
+  if (!nctas) {
+    cudaFuncSetAttribute(k_conv_tc<CI, CO, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, nsm = 148, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_tc<CI, CO, FL>, tc::TPB, smem);
+    per = per < 1 ? 1 : (per > tc::tmem_ctas(CO) ? tc::tmem_ctas(CO) : per);
+    nctas = nsm * per;
+  }
+  const int ntiles = B * ((g.N + tc::TM - 1) / tc::TM);
+  k_conv_tc<CI, CO, FL><<<ntiles < nctas ? ntiles : nctas, tc::TPB, smem, st>>>(g, B, x, w, bias, y, nullptr);
+}
+
+template <int CI, int CO>
+void launch_conv_tc(const CGrid& g, int B, int flags, const __nv_bfloat16* x, const __nv_bfloat16* w,
+                    const float* bias, void* y, cudaStream_t st) {
+  switch (flags) {
+    case 2: launch_conv_tc1<CI, CO, 2>(g, B, x, w, bias, y, st); break;
+    case 5: launch_conv_tc1<CI, CO, 5>(g, B, x, w, bias, y, st); break;
+    case 6: launch_conv_tc1<CI, CO, 6>(g, B, x, w, bias, y, st); break;
+    default: launch_conv_tc1<CI, CO, 0>(g, B, x, w, bias, y, st); break;
+  }
+}
+
+void conv_dispatch(const CGrid& g, int B, int ci, int co, int flags, bool tcore, const __nv_bfloat16* x,
+                   const __nv_bfloat16* w, const float* bias, void* y, cudaStream_t st) {
+  if (tcore) {
+    if (ci == 16 && co == 32) launch_conv_tc<16, 32>(g, B, flags, x, w, bias, y, st);
+    else if (ci == 32 && co == 32) launch_conv_tc<32, 32>(g, B, flags, x, w, bias, y, st);
+    else if (ci == 32 && co == 16) launch_conv_tc<32, 16>(g, B, flags, x, w, bias, y, st);
+    return;
+  }
   if (ci == 16 && co == 32) launch_conv<16, 32>(g, B, flags, x, w, bias, y, st);
   else if (ci == 32 && co == 32) launch_conv<32, 32>(g, B, flags, x, w, bias, y, st);
   else if (ci == 32 && co == 16) launch_conv<32, 16>(g, B, flags, x, w, bias, y, st);
@@ -436,8 +671,8 @@ extern "C" int mpn_conv3d_forward(const mpn_conv_desc* d, const void* x, const v
   if (s) return s;
   if (!x || !w || !y || ((flags & MPN_CONV_BIAS) && !bias)) return MPN_ERR_INVALID_ARG;
   CGrid g = make_cgrid(d);
-  conv_dispatch(g, d->batch, d->cin, d->cout, flags & 7, (const __nv_bfloat16*)x, (const __nv_bfloat16*)w, bias, y,
-                (cudaStream_t)stream);
+  conv_dispatch(g, d->batch, d->cin, d->cout, flags & 7, !(flags & MPN_CONV_MMA_SYNC), (const __nv_bfloat16*)x,
+                (const __nv_bfloat16*)w, bias, y, (cudaStream_t)stream);
   return cudaGetLastError() == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
 }
 

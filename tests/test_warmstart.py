@@ -60,6 +60,44 @@ def test_conv_forward_matches_oracle(ci, co, flags, periodic):
     assert _rel(got, ref) <= 1e-2, _rel(got, ref)
 
 
+MMA_SYNC = 8   # MPN_CONV_MMA_SYNC: the legacy warp-level kernel
+
+
+@pytest.mark.parametrize("ci,co,flags", [(16, 32, 5), (32, 32, 5), (32, 16, 6), (32, 32, 2), (32, 32, 0)])
+@pytest.mark.parametrize("n,B,periodic", [((6, 10, 16), 2, (False, True, True)),     # 960 points: a ragged tile
+                                          ((5, 7, 9), 3, (False, False, False)),
+                                          ((32, 64, 64), 2, (False, True, True))])  # more tiles than CTAs
+def test_conv_tcgen05_matches_mma_sync_and_oracle(ci, co, flags, n, B, periodic):
+    """The tcgen05 convolution (the default) against the mma.sync kernel on the
+    same BF16 inputs (FP32 accumulation in both, summed in different orders:
+    1e-5 for FP32 output, one BF16 rounding for BF16 output) and, on the small
+    grids, against the oracle."""
+    from paper_2502_18377_b300.binding import _ptr, _stream, load
+    lib = load()
+    N = int(np.prod(n))
+    g = torch.Generator().manual_seed(7 * ci + co + flags + N)
+    xb = _bf(torch.randn(B, N, ci, generator=g, dtype=torch.float64))
+    wb = _bf(torch.randn(27, co, ci, generator=g, dtype=torch.float64) * 0.1)
+    b = torch.randn(co, generator=g, dtype=torch.float64)
+    xd, wd, bd = xb.to(torch.bfloat16).cuda(), wb.to(torch.bfloat16).cuda(), b.float().cuda()
+    dt = torch.float32 if flags & 2 else torch.bfloat16
+    d = _desc(n, periodic, B, ci, co)
+    outs = []
+    for extra in (0, MMA_SYNC, 0):
+        out = torch.full((B, N, co), float("nan"), device="cuda", dtype=dt)
+        assert lib.mpn_conv3d_forward(ctypes.byref(d), _ptr(xd), _ptr(wd), _ptr(bd), _ptr(out), flags | extra,
+                                      _stream()) == 0
+        torch.cuda.synchronize()
+        outs.append(out.double().cpu())
+    tcg, legacy, again = outs
+    assert torch.isfinite(tcg).all()
+    assert torch.equal(tcg, again)                       # deterministic
+    assert _rel(tcg, legacy) <= (1e-5 if flags & 2 else 8e-3), _rel(tcg, legacy)
+    if N <= 1024:
+        ref = oc.conv3d(xb, wb, b if flags & 4 else None, n, periodic, relu=bool(flags & 1))
+        assert _rel(tcg, ref) <= 1e-2, _rel(tcg, ref)
+
+
 @pytest.mark.parametrize("co", [32, 16])
 def test_conv_backward_matches_oracle(co):
     from paper_2502_18377_b300.binding import _ptr, _stream, load
