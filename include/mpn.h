@@ -304,8 +304,9 @@ typedef struct mpn_conv_desc {
  * the benchmark spec's learned warm start (a 3D-conv network predicting the solution). */
 int mpn_conv3d_forward(const mpn_conv_desc* d, const void* x, const void* w, const float* bias, void* y,
                        int flags, void* stream);
-/* g_in [B][N][cin] FP32 = transposed convolution of g_out [B][N][cout] (BF16) with W;
- * wt_scratch: 27*cin*cout BF16 (flipped, transposed W).  Requires cin = 32. */
+/* g_in [B][N][cin] FP32 = transposed convolution of g_out [B][N][cout] (BF16) with W, on the
+ * tcgen05 kernel of mpn_conv3d_forward; wt_scratch: 27*cin*cout BF16 (flipped, transposed W).
+ * Requires cin = 32. */
 int mpn_conv3d_backward_data(const mpn_conv_desc* d, const void* g_out, const void* w, void* wt_scratch,
                              float* g_in, void* stream);
 /* Bytes of FP32 scratch mpn_conv3d_backward_weights needs. */

@@ -628,10 +628,14 @@ void launch_conv_tc1(const CGrid& g, int B, const __nv_bfloat16* x, const __nv_b
   static int nctas = 0;
   if (!nctas) {
     cudaFuncSetAttribute(k_conv_tc<CI, CO, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    int dev = 0, nsm = 148, per = 1;
+    cudaFuncSetAttribute(k_conv_tc<CI, CO, FL>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    int dev = 0, nsm = 148, smem_sm = 233472;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_conv_tc<CI, CO, FL>, tc::TPB, smem);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    // resident CTAs: shared memory (1 KB reserved per CTA) and tensor memory
+    int per = smem_sm / (smem + 1024);
     per = per < 1 ? 1 : (per > tc::tmem_ctas(CO) ? tc::tmem_ctas(CO) : per);
     nctas = nsm * per;
   }
@@ -688,10 +692,10 @@ extern "C" int mpn_conv3d_backward_data(const mpn_conv_desc* d, const void* g_ou
   k_flip_transpose<<<(n + 255) / 256, 256, 0, st>>>(d->cin, d->cout, (const __nv_bfloat16*)w,
                                                     (__nv_bfloat16*)wt_scratch);
   // transposed convolution = convolution of g_out (channels cout) with W'
-  if (d->cout == 32) launch_conv<32, 32>(g, d->batch, MPN_CONV_F32, (const __nv_bfloat16*)g_out,
-                                         (const __nv_bfloat16*)wt_scratch, nullptr, g_in, st);
-  else launch_conv<16, 32>(g, d->batch, MPN_CONV_F32, (const __nv_bfloat16*)g_out, (const __nv_bfloat16*)wt_scratch,
-                           nullptr, g_in, st);
+  if (d->cout == 32) launch_conv_tc<32, 32>(g, d->batch, MPN_CONV_F32, (const __nv_bfloat16*)g_out,
+                                            (const __nv_bfloat16*)wt_scratch, nullptr, g_in, st);
+  else launch_conv_tc<16, 32>(g, d->batch, MPN_CONV_F32, (const __nv_bfloat16*)g_out,
+                              (const __nv_bfloat16*)wt_scratch, nullptr, g_in, st);
   return cudaGetLastError() == cudaSuccess ? MPN_OK : MPN_ERR_CUDA;
 }
 
