@@ -304,6 +304,10 @@ typedef struct mpn_conv_desc {
  * the benchmark spec's learned warm start (a 3D-conv network predicting the solution). */
 int mpn_conv3d_forward(const mpn_conv_desc* d, const void* x, const void* w, const float* bias, void* y,
                        int flags, void* stream);
+/* *flag = 1 if a tcgen05 convolution launched since the last call had a bounded wait for its
+ * pipeline give up (its output is then undefined), else 0; clears the word.  Synchronous (waits
+ * for the device).  Not in the paper: error reporting of the warm-start kernels. */
+int mpn_conv_take_error(int* flag);
 /* g_in [B][N][cin] FP32 = transposed convolution of g_out [B][N][cout] (BF16) with W, on the
  * tcgen05 kernel of mpn_conv3d_forward; wt_scratch: 27*cin*cout BF16 (flipped, transposed W).
  * Requires cin = 32. */

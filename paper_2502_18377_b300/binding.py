@@ -70,6 +70,7 @@ EXPORTS = {
                                    ctypes.POINTER(ctypes.c_longlong)]),
     "mpn_apply_reduced_noalloc": (ctypes.c_int, [ctypes.POINTER(MpnDesc), _P, _P, _P, _P, _P]),
     "mpn_conv3d_forward": (ctypes.c_int, [ctypes.POINTER(MpnConvDesc), _P, _P, _P, _P, ctypes.c_int, _P]),
+    "mpn_conv_take_error": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
     "mpn_conv3d_backward_data": (ctypes.c_int, [ctypes.POINTER(MpnConvDesc), _P, _P, _P, _P, _P]),
     "mpn_conv3d_wgrad_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(MpnConvDesc)]),
     "mpn_conv3d_backward_weights": (ctypes.c_int, [ctypes.POINTER(MpnConvDesc), _P, _P, _P, _P, _P, _P]),

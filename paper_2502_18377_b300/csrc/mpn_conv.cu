@@ -621,6 +621,15 @@ __global__ void __launch_bounds__(tc::TPB) k_conv_tc(CGrid g, int B, const __nv_
   }
 }
 
+// Set by a tcgen05 convolution whose bounded wait gave up (read and cleared
+// by mpn_conv_take_error).
+__device__ int g_conv_err = 0;
+
+int* conv_err_ptr() {
+  int* p = nullptr;
+  return cudaGetSymbolAddress((void**)&p, g_conv_err) == cudaSuccess ? p : nullptr;
+}
+
 template <int CI, int CO, int FL>
 void launch_conv_tc1(const CGrid& g, int B, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias,
                      void* y, cudaStream_t st) {
@@ -640,7 +649,8 @@ void launch_conv_tc1(const CGrid& g, int B, const __nv_bfloat16* x, const __nv_b
     nctas = nsm * per;
   }
   const int ntiles = B * ((g.N + tc::TM - 1) / tc::TM);
-  k_conv_tc<CI, CO, FL><<<ntiles < nctas ? ntiles : nctas, tc::TPB, smem, st>>>(g, B, x, w, bias, y, nullptr);
+  k_conv_tc<CI, CO, FL><<<ntiles < nctas ? ntiles : nctas, tc::TPB, smem, st>>>(g, B, x, w, bias, y,
+                                                                                 conv_err_ptr());
 }
 
 template <int CI, int CO>
@@ -668,6 +678,17 @@ void conv_dispatch(const CGrid& g, int B, int ci, int co, int flags, bool tcore,
 }
 
 }  // namespace
+
+extern "C" int mpn_conv_take_error(int* flag) {
+  if (!flag) return MPN_ERR_INVALID_ARG;
+  int* p = conv_err_ptr();
+  if (!p) return MPN_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MPN_ERR_CUDA;
+  if (v && cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return MPN_ERR_CUDA;
+  *flag = v;
+  return MPN_OK;
+}
 
 extern "C" int mpn_conv3d_forward(const mpn_conv_desc* d, const void* x, const void* w, const float* bias, void* y,
                                   int flags, void* stream) {

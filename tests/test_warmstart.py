@@ -90,6 +90,8 @@ def test_conv_tcgen05_matches_mma_sync_and_oracle(ci, co, flags, n, B, periodic)
         torch.cuda.synchronize()
         outs.append(out.double().cpu())
     tcg, legacy, again = outs
+    flag = ctypes.c_int(-1)
+    assert lib.mpn_conv_take_error(ctypes.byref(flag)) == 0 and flag.value == 0   # no bounded wait gave up
     assert torch.isfinite(tcg).all()
     assert torch.equal(tcg, again)                       # deterministic
     assert _rel(tcg, legacy) <= (1e-5 if flags & 2 else 8e-3), _rel(tcg, legacy)
