@@ -621,6 +621,180 @@ __global__ void __launch_bounds__(tc::TPB) k_conv_tc(CGrid g, int B, const __nv_
   }
 }
 
+// The row-staged tcgen05 convolution (n_y % 128 == 0; see mpn_conv_tc.cuh):
+// tiles of 128 consecutive y points of one (t, x) row, one ring slot per time
+// plane holding the tile's three staged x rows, nine taps per commit.
+template <int CI, int CO, int FLAGS>
+__global__ void __launch_bounds__(tc::TPB) k_conv_tcr(CGrid g, int B, const __nv_bfloat16* __restrict__ x,
+                                                      const __nv_bfloat16* __restrict__ w,
+                                                      const float* __restrict__ bias, void* __restrict__ out,
+                                                      int* __restrict__ err) {
+  constexpr int KS = tc::ks_of(CI), KC = CI / 8, WOP = tc::op_bytes(CO);
+  constexpr int RB = tc::rb_bytes(CI), SLOT = tc::rs_bytes(CI), S = tc::rslots(CI);
+  constexpr uint32_t SBO_A = KC * 128;
+  extern __shared__ __align__(1024) uint8_t csm[];
+  uint8_t* ws = csm;
+  uint8_t* as = csm + tc::w_bytes(CI, CO);
+  uint64_t* full = reinterpret_cast<uint64_t*>(as + S * SLOT);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;
+  uint64_t* acce = accf + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < 27 * CO * (CI / 8); i += tc::TPB) {
+    const int c8 = i % (CI / 8), co = (i / (CI / 8)) % CO, tap = i / ((CI / 8) * CO);
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(w + ((size_t)tap * CO + co) * CI + c8 * 8));
+    *reinterpret_cast<uint4*>(ws + (tap * KS + (c8 >> 1)) * WOP + tc::chunk_off(co, c8 & 1)) = v;
+  }
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) {
+      tc::bar_init(&full[i], tc::TM);
+      tc::bar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::bar_init(&accf[i], 1);
+      tc::bar_init(&acce[i], tc::TM);
+    }
+  }
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::s32(tslot)),
+                 "n"(tc::tmem_cols(CO)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::fence_async_smem();
+  tc::tc_before_sync();
+  __syncthreads();
+  tc::tc_after_sync();
+  const uint32_t tmem = *tslot;
+  const int nyb = g.n[2] / tc::TM, rows = g.n[0] * g.n[1];
+  const int ntiles = B * rows * nyb;
+  bool ok = true;
+  auto wait = [&](uint64_t* bar, uint32_t par) {
+    if (!tc::bar_wait(bar, par, ok ? tc::WAIT_LIMIT : 1)) ok = false;
+  };
+  // tile -> instance, time plane, x row, first y
+  auto tile_of = [&](int tile, int& bb, int& t, int& xr, int& y0) {
+    bb = tile / (rows * nyb);
+    const int q = tile - bb * rows * nyb, row = q / nyb;
+    t = row / g.n[1];
+    xr = row - t * g.n[1];
+    y0 = (q - row * nyb) * tc::TM;
+  };
+
+  if (warp < 4) {
+    // ---- staging: per time plane, the tile's three x rows (entry e = (row dx,
+    //      core row c', chunk kc, row k) holds channels 8 kc.. of point y0 - 1 + c' + 16 k)
+    constexpr int NE = 3 * 18 * KC * 8;
+    const uint32_t abase = tc::s32(as);
+    int G = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      int bb, t, xr, y0;
+      tile_of(tile, bb, t, xr, y0);
+      const __nv_bfloat16* xb = x + (size_t)bb * g.N * CI;
+      for (int dt = 0; dt < 3; ++dt, ++G) {
+        const int sl = G % S, use = G / S;
+        if (use > 0) wait(&empty[sl], (use - 1) & 1);
+        const int tt = t + dt - 1;
+        const uint32_t dst0 = abase + sl * SLOT;
+        for (int e = tid; e < NE; e += tc::TM) {
+          const int k = e & 7, kc = (e >> 3) % KC, cp = (e / (8 * KC)) % 18, dx = e / (8 * KC * 18);
+          int xx = xr + dx - 1, y = y0 - 1 + cp + 16 * k;
+          bool in = tt >= 0 && tt < g.n[0];
+          if (xx < 0 || xx >= g.n[1]) { if (g.per[1]) xx = xx < 0 ? xx + g.n[1] : xx - g.n[1]; else in = false; }
+          if (y < 0 || y >= g.n[2]) { if (g.per[2]) y = y < 0 ? y + g.n[2] : y - g.n[2]; else in = false; }
+          const __nv_bfloat16* src = in ? xb + ((size_t)(tt * g.n[1] + xx) * g.n[2] + y) * CI + kc * 8 : xb;
+          tc::cp16(dst0 + dx * RB + cp * SBO_A + kc * 128 + k * 16, src, in ? 16u : 0u);
+        }
+        tc::cp_arrive(&full[sl]);
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp == 4) {
+    // ---- MMA issue: per slot nine taps (dx, dy), one commit
+    if (lane == 0) {
+      const uint32_t id = tc::idesc(tc::TM, CO);
+      const uint32_t wbase = tc::s32(ws), abase = tc::s32(as);
+      int G = 0, i = 0;
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+        const int acc = i & 1;
+        if (i >= 2) wait(&acce[acc], ((i - 2) >> 1) & 1);
+        tc::tc_after_sync();
+        for (int dt = 0; dt < 3; ++dt, ++G) {
+          const int sl = G % S;
+          wait(&full[sl], (G / S) & 1);
+          tc::fence_async_smem();
+          tc::tc_after_sync();
+#pragma unroll
+          for (int j = 0; j < 9; ++j) {
+            const int dx = j / 3, dy = j % 3, tap = dt * 9 + j;
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks)
+              tc::mma(tmem + (uint32_t)((acc * tc::NACC + tap % tc::NACC) * CO),
+                      tc::sdesc(abase + sl * SLOT + dx * RB + dy * SBO_A + ks * 256, SBO_A),
+                      tc::sdesc(wbase + (tap * KS + ks) * WOP), id, (tap >= tc::NACC || ks > 0) ? 1u : 0u);
+          }
+          tc::commit(&empty[sl]);
+        }
+        tc::commit(&accf[acc]);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: TMEM lane m is the point y0 + (m >> 3) + 16 (m & 7)
+    const int q = warp & 3, m = 32 * q + lane;
+    int i = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+      const int acc = i & 1;
+      wait(&accf[acc], (i >> 1) & 1);
+      tc::tc_after_sync();
+      float v[CO];
+      tmem_ld<CO>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * tc::NACC * CO), v);
+#pragma unroll
+      for (int j = 1; j < tc::NACC; ++j) {
+        float u[CO];
+        tmem_ld<CO>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((acc * tc::NACC + j) * CO), u);
+#pragma unroll
+        for (int c = 0; c < CO; ++c) v[c] += u[c];
+      }
+      tc::tc_before_sync();
+      tc::bar_arrive(&acce[acc]);
+      int bb, t, xr, y0;
+      tile_of(tile, bb, t, xr, y0);
+      const int p = (t * g.n[1] + xr) * g.n[2] + y0 + (m >> 3) + 16 * (m & 7);
+      const size_t o = ((size_t)bb * g.N + p) * CO;
+#pragma unroll
+      for (int c = 0; c < CO; ++c) {
+        if (FLAGS & 4) v[c] += __ldg(bias + c);
+        if (FLAGS & 1) v[c] = fmaxf(v[c], 0.f);
+      }
+      if (FLAGS & 2) {
+        float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + o);
+#pragma unroll
+        for (int c = 0; c < CO / 4; ++c) dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+      } else {
+        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + o);
+#pragma unroll
+        for (int c = 0; c < CO / 8; ++c) {
+          uint32_t u4[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * c + 2 * k], v[8 * c + 2 * k + 1]);
+            u4[k] = *reinterpret_cast<const uint32_t*>(&h);
+          }
+          dst[c] = make_uint4(u4[0], u4[1], u4[2], u4[3]);
+        }
+      }
+    }
+  }
+  if (!ok && err) atomicExch(err, 1);
+  tc::tc_before_sync();
+  __syncthreads();
+  if (warp == 4) {
+    tc::tc_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(tc::tmem_cols(CO)) : "memory");
+  }
+}
+
 // Set by a tcgen05 convolution whose bounded wait gave up (read and cleared
 // by mpn_conv_take_error).
 __device__ int g_conv_err = 0;
@@ -630,27 +804,41 @@ int* conv_err_ptr() {
   return cudaGetSymbolAddress((void**)&p, g_conv_err) == cudaSuccess ? p : nullptr;
 }
 
+// resident CTAs per SM of a tcgen05 convolution kernel with `smem` bytes of
+// dynamic shared memory (the tensor memory bound included), times the SMs
+template <class K>
+int tc_ctas(K kern, int smem, int co_cols_ctas) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  int dev = 0, nsm = 148, smem_sm = 233472;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  // resident CTAs: shared memory (1 KB reserved per CTA) and tensor memory
+  int per = smem_sm / (smem + 1024);
+  per = per < 1 ? 1 : (per > co_cols_ctas ? co_cols_ctas : per);
+  return nsm * per;
+}
+
 template <int CI, int CO, int FL>
 void launch_conv_tc1(const CGrid& g, int B, const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias,
                      void* y, cudaStream_t st) {
+  if (g.n[2] % tc::TM == 0) {
+    // rows of whole 128-point tiles: the row-staged kernel
+    constexpr int smem = tc::rsmem_bytes(CI, CO);
+    static int nctas = 0;
+    if (!nctas) nctas = tc_ctas(k_conv_tcr<CI, CO, FL>, smem, tc::tmem_ctas(CO));
+    const int ntiles = B * g.n[0] * g.n[1] * (g.n[2] / tc::TM);
+    k_conv_tcr<CI, CO, FL><<<ntiles < nctas ? ntiles : nctas, tc::TPB, smem, st>>>(g, B, x, w, bias, y,
+                                                                                  conv_err_ptr());
+    return;
+  }
   constexpr int smem = tc::smem_bytes(CI, CO);
   static int nctas = 0;
-  if (!nctas) {
-    cudaFuncSetAttribute(k_conv_tc<CI, CO, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_conv_tc<CI, CO, FL>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         (int)cudaSharedmemCarveoutMaxShared);
-    int dev = 0, nsm = 148, smem_sm = 233472;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    // resident CTAs: shared memory (1 KB reserved per CTA) and tensor memory
-    int per = smem_sm / (smem + 1024);
-    per = per < 1 ? 1 : (per > tc::tmem_ctas(CO) ? tc::tmem_ctas(CO) : per);
-    nctas = nsm * per;
-  }
+  if (!nctas) nctas = tc_ctas(k_conv_tc<CI, CO, FL>, smem, tc::tmem_ctas(CO));
   const int ntiles = B * ((g.N + tc::TM - 1) / tc::TM);
   k_conv_tc<CI, CO, FL><<<ntiles < nctas ? ntiles : nctas, tc::TPB, smem, st>>>(g, B, x, w, bias, y,
-                                                                                 conv_err_ptr());
+                                                                               conv_err_ptr());
 }
 
 template <int CI, int CO>

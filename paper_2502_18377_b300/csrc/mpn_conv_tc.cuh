@@ -77,9 +77,27 @@ __host__ __device__ constexpr unsigned chunk_off(int r, int kc) {
 
 // shared-memory matrix descriptor: start address, LBO, SBO (all >> 4),
 // descriptor version 1 (bits 46-47), no base offset, no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo = SBO) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
          (1ull << 46);
+}
+
+// Row-staged variant (rows of n_y % 128 == 0): a tile is 128 consecutive y
+// points of one (t, x) row, and M-row r of its MMAs is the point
+// y0 + (r >> 3) + 16 (r & 7).  Each (t + dt, x + dx) input row the tile needs
+// is staged once, as 18 core-matrix rows c' (K-major, CI/8 chunks of 8
+// channels) whose row k holds the point y0 - 1 + c' + 16 k; the operand of the
+// tap with y offset dy then starts dy + 1 core-matrix rows in (SBO =
+// CI/8 x 128 bytes), so the three y taps of a row share one staging.  A ring
+// slot holds the three x rows of one time plane (nine taps, one commit).
+__host__ __device__ constexpr int rb_bytes(int CI) { return 18 * (CI / 8) * 128; }      // one staged row
+__host__ __device__ constexpr int rs_bytes(int CI) { return 3 * rb_bytes(CI); }         // one slot (3 rows)
+__host__ __device__ constexpr int rslots(int CI) { return CI == 16 ? 4 : 2; }
+__host__ __device__ constexpr int rsmem_used(int CI, int CO) {
+  return w_bytes(CI, CO) + rslots(CI) * rs_bytes(CI) + 8 * (2 * rslots(CI) + 4) + 16;
+}
+__host__ __device__ constexpr int rsmem_bytes(int CI, int CO) {
+  return rsmem_used(CI, CO) > 233472 / (tmem_ctas(CO) + 1) ? rsmem_used(CI, CO) : 233472 / (tmem_ctas(CO) + 1);
 }
 // instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0),

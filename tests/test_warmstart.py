@@ -66,10 +66,14 @@ MMA_SYNC = 8   # MPN_CONV_MMA_SYNC: the legacy warp-level kernel
 @pytest.mark.parametrize("ci,co,flags", [(16, 32, 5), (32, 32, 5), (32, 16, 6), (32, 32, 2), (32, 32, 0)])
 @pytest.mark.parametrize("n,B,periodic", [((6, 10, 16), 2, (False, True, True)),     # 960 points: a ragged tile
                                           ((5, 7, 9), 3, (False, False, False)),
-                                          ((32, 64, 64), 2, (False, True, True))])  # more tiles than CTAs
+                                          ((32, 64, 64), 2, (False, True, True)),   # more tiles than CTAs
+                                          # rows of whole 128-point tiles: the row-staged kernel
+                                          ((3, 2, 128), 2, (False, True, True)),
+                                          ((4, 3, 256), 1, (False, False, False)),
+                                          ((16, 32, 128), 2, (False, True, True))])
 def test_conv_tcgen05_matches_mma_sync_and_oracle(ci, co, flags, n, B, periodic):
-    """The tcgen05 convolution (the default) against the mma.sync kernel on the
-    same BF16 inputs (FP32 accumulation in both, summed in different orders:
+    """The tcgen05 convolution (the default; rows of n_y % 128 == 0 take its
+    row-staged kernel) against the mma.sync kernel on the same BF16 inputs (FP32 accumulation in both, summed in different orders:
     1e-5 for FP32 output, one BF16 rounding for BF16 output) and, on the small
     grids, against the oracle."""
     from paper_2502_18377_b300.binding import _ptr, _stream, load
