@@ -13,7 +13,8 @@ steps on one B300 (figures in the design notes):
   (215 ms per step against 316 ms with degree 5 and 5 iterations);
 * reaction-diffusion at 64 x 128 x 128: degree 4, 8 iterations (79 ms
   against 92 ms);
-* reaction-diffusion at 32 x 64 x 64: the library defaults (degree 5,
+* reaction-diffusion at 32 x 64 x 64, linearized Burgers at 128 x 256 and
+  advection-diffusion at 32 x 32: the library defaults (degree 5,
   5 iterations).
 """
 from __future__ import annotations
@@ -26,6 +27,9 @@ BENCH_WORKLOADS = {
     "reaction_diffusion_2d_64x128x128": (wl.reaction_diffusion_2d, 8, (64, 128, 128), 4000,
                                          dict(cheb_degree=4, inner_iters=8)),
     "reaction_diffusion_2d": (wl.reaction_diffusion_2d, 16, (32, 64, 64), 2000, dict()),
+    # the two 1-D+t families (L2-resident: absolute throughput only)
+    "linearized_burgers_1d": (wl.linearized_burgers_1d, 32, (128, 256), 3000, dict()),
+    "advection_diffusion_1d": (wl.advection_diffusion_1d, 4, (32, 32), 1000, dict()),
 }
 
 
