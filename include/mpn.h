@@ -126,6 +126,9 @@ typedef struct mpn_desc {
                              level.  A point on several faces has the row of the first face in the
                              order t = 0, t = t_f, then the spatial axes in order (time faces are
                              Dirichlet).  alpha and beta must be finite and not both zero. */
+  int adj_inner_iters;    /* FP32 PCG iterations per refinement sweep of the adjoint solve (its
+                             right-hand side, the loss gradient, is rougher than the forward data and
+                             may contract per sweep at another rate); 0 (default): inner_iters */
 } mpn_desc;
 
 enum { MPN_KRYLOV_CG = 0, MPN_KRYLOV_FGMRES = 1 };

@@ -30,7 +30,8 @@ class MpnDesc(ctypes.Structure):
                 ("max_coarse", ctypes.c_int), ("fused_coarse", ctypes.c_int),
                 ("fused_step", ctypes.c_int), ("krylov", ctypes.c_int), ("coarsen_time", ctypes.c_int),
                 ("direct", ctypes.c_int), ("variable_steps", ctypes.c_int),
-                ("bc_alpha", ctypes.c_double * 3), ("bc_beta", ctypes.c_double * 3)]
+                ("bc_alpha", ctypes.c_double * 3), ("bc_beta", ctypes.c_double * 3),
+                ("adj_inner_iters", ctypes.c_int)]
 
 KRYLOV = {"cg": 0, "fgmres": 1}
 
@@ -195,7 +196,8 @@ class Solver:
 
     def __init__(self, geom: dict, batch: int, field_of, nfields: int, tol=1e-7, max_refine=12,
                  inner_iters=5, cheb_degree=5, coarse_min=4, max_coarse=2048, fused_coarse=True,
-                 fused_step=3, krylov="cg", coarsen_time=False, direct=False, variable_steps=False):
+                 fused_step=3, krylov="cg", coarsen_time=False, direct=False, variable_steps=False,
+                 adj_inner_iters=0):
         lib = load()
         d = MpnDesc()
         lib.mpn_default_desc(ctypes.byref(d))
@@ -220,6 +222,7 @@ class Solver:
         d.coarsen_time = int(bool(coarsen_time))
         d.direct = int(bool(direct))
         d.variable_steps = int(bool(variable_steps))
+        d.adj_inner_iters = int(adj_inner_iters)
         # boundary rows alpha u + beta du/dx_d = omega per spatial axis
         # (geom["bc"] = {d: (alpha, beta)}; Dirichlet where absent)
         for k, (a, b) in dict(geom.get("bc", {})).items():

@@ -243,6 +243,7 @@ extern "C" int mpn_default_desc(mpn_desc* d) {
   d->coarsen_time = 0;
   d->direct = 0;
   d->variable_steps = 0;
+  d->adj_inner_iters = 0;
   for (int k = 0; k < 3; ++k) { d->bc_alpha[k] = 1.0; d->bc_beta[k] = 0.0; }
   return MPN_OK;
 }
@@ -449,6 +450,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   if (d.stencil == 5) return MPN_ERR_UNSUPPORTED;
   if (d.stencil != 3) return MPN_ERR_INVALID_ARG;
   if (d.inner_iters < 1 || d.max_refine < 1 || d.cheb_degree < 1 || d.cheb_degree > 30) return MPN_ERR_INVALID_ARG;
+  if (d.adj_inner_iters < 0) return MPN_ERR_INVALID_ARG;
   if (d.coarse_min < 3 || !(d.tol > 0)) return MPN_ERR_INVALID_ARG;
   if (d.krylov != MPN_KRYLOV_CG && d.krylov != MPN_KRYLOV_FGMRES) return MPN_ERR_INVALID_ARG;
   if (d.fused_step < 0 || d.fused_step > 4) return MPN_ERR_INVALID_ARG;
@@ -629,7 +631,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
     }
   }
   if (d.krylov == MPN_KRYLOV_FGMRES) {
-    p->mk = std::min(FG_MMAX, 8 * d.inner_iters);
+    p->mk = std::min(FG_MMAX, 8 * std::max(d.inner_iters, d.adj_inner_iters));
     const int mk = p->mk;
     AL(p->fgV, (size_t)(mk + 1) * N0);
     AL(p->fgZ, (size_t)mk * N0);
@@ -1318,7 +1320,8 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
   // first update is already a correction (second sweep)
   const int first = zero_start ? 2 : 1;
   std::vector<double> gnorm(B, 0.0);
-  int iters = p->desc.direct ? 1 : p->desc.inner_iters, total_iters = 0;
+  const int base_iters = (g_adj && p->desc.adj_inner_iters > 0) ? p->desc.adj_inner_iters : p->desc.inner_iters;
+  int iters = p->desc.direct ? 1 : base_iters, total_iters = 0;
   const bool trace = getenv("MPN_TRACE") != nullptr;
   for (int sweep = 0; sweep < p->desc.max_refine; ++sweep) {
     TRY(run_sweep(p, g_adj, iters, P, zero_start && sweep == 0, st));
@@ -1363,7 +1366,7 @@ static int refine_solve(mpn_problem* p, const double* g_adj, bool zero_start, mp
     if ((sweep >= first && maxpred <= p->desc.tol) || (sweep >= 1 && maxupd <= p->desc.tol * 0.1)) { status = MPN_OK; break; }
     const int done_iters = iters;
     // a sweep that gained less than a digit: lengthen the inner solve
-    if (!p->desc.direct && sweep >= 1 && maxrate > 0.1 && iters < 8 * p->desc.inner_iters) iters *= 2;
+    if (!p->desc.direct && sweep >= 1 && maxrate > 0.1 && iters < 8 * base_iters) iters *= 2;
     if (trace)
       fprintf(stderr, "[mpn] %s sweep %d: %d inner iterations, update %.3e, residual %.3e, predicted error %.3e, "
                       "gain %.3e -> next %d\n", g_adj ? "adjoint" : "forward", sweep, done_iters, maxupd, maxres,

@@ -4,7 +4,7 @@ else on the GPU.
 
 python -m paper_2502_18377_b300.profile_step [--workload transport_2d]
     [--batch B] [--grid T X Y] [--steps K] [--warmup W] [--fused-step 0|1|2|3|4]
-    [--inner-iters N] [--cheb-degree M]
+    [--inner-iters N] [--adj-inner-iters N] [--cheb-degree M]
 
 The environment variable MPN_TRACE makes the library print every refinement
 sweep (inner iterations, update, residual, predicted error) to stderr.
@@ -29,12 +29,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--fused-step", type=int, default=3)
     ap.add_argument("--inner-iters", type=int, help="default: the workload's benchmark setting")
+    ap.add_argument("--adj-inner-iters", type=int, help="default: the workload's benchmark setting")
     ap.add_argument("--cheb-degree", type=int, help="default: the workload's benchmark setting")
     a = ap.parse_args()
     w = settings.make(a.workload, batch=a.batch, grid=a.grid)
     kw = settings.solver_kwargs(a.workload)
     if a.inner_iters:
         kw["inner_iters"] = a.inner_iters
+    if a.adj_inner_iters:
+        kw["adj_inner_iters"] = a.adj_inner_iters
     if a.cheb_degree:
         kw["cheb_degree"] = a.cheb_degree
     dev = lambda x: torch.tensor(np.asarray(x, dtype=np.float32), device="cuda").contiguous()
