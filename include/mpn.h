@@ -146,7 +146,7 @@ typedef struct mpn_problem mpn_problem;
 
 /* Fills *desc with defaults (tol 1e-7, max_refine 12, inner_iters 5,
  * cheb_degree 5, coarse_min 4, max_coarse 2048, stencil 3, fused_coarse 1, fused_step 3, krylov CG, coarsen_time 0, direct 0,
- * variable_steps 0, Dirichlet boundary rows: bc_alpha 1, bc_beta 0). */
+ * variable_steps 0, Dirichlet boundary rows: bc_alpha 1, bc_beta 0; adj_inner_iters 0). */
 int mpn_default_desc(mpn_desc* desc);
 
 /* Validates the descriptor, builds the grid hierarchy (spatial halving, time
