@@ -48,6 +48,10 @@ def test_error_strings_without_gpu():
     d.periodic[0] = 0
     d.krylov = 7
     assert lib.mpn_create(ctypes.byref(d), ctypes.byref(h)) == 1      # unknown inner solver: invalid
+    d.krylov = 0
+    assert d.adj_inner_iters == 0                                     # the last field: the adjoint's own count unset
+    d.adj_inner_iters = -1
+    assert lib.mpn_create(ctypes.byref(d), ctypes.byref(h)) == 1      # negative iteration count: invalid
 
 
 def test_binding_rejects_missized_tensors_without_launching():

@@ -291,20 +291,24 @@ def test_one_problem_solves_new_coefficients_each_call():
             assert _rel(dz[b].ravel(), dzr) <= FWD_TOL, (b, _rel(dz[b].ravel(), dzr))
 
 
-@pytest.mark.parametrize("cheb_degree,inner_iters", [(1, 5), (2, 5), (5, 1), (3, 2)])
-def test_smoother_degree_and_inner_iterations_meet_the_oracle(cheb_degree, inner_iters):
+@pytest.mark.parametrize("cheb_degree,inner_iters,adj_inner_iters",
+                         [(1, 5, 0), (2, 5, 0), (5, 1, 0), (3, 2, 0), (5, 5, 9), (3, 7, 2)])
+def test_smoother_degree_and_inner_iterations_meet_the_oracle(cheb_degree, inner_iters, adj_inner_iters):
     """The finest level's folded steps depend on the schedule: with degree 1
     the V-cycle has no Chebyshev post-smoothing step to sum <z, r> (z is
     copied out), one PCG iteration per sweep never updates the direction, and
-    short smoothers change which buffer each step reads.  Every combination
-    meets the oracle in both directions."""
+    short smoothers change which buffer each step reads; the adjoint may run
+    its own count per sweep.  Every combination meets the oracle in both
+    directions."""
     w = _round(wl.reaction_diffusion_2d(batch=2, n=(8, 16, 16)))
-    s = _solver(w, cheb_degree=cheb_degree, inner_iters=inner_iters)
+    s = _solver(w, cheb_degree=cheb_degree, inner_iters=inner_iters, adj_inner_iters=adj_inner_iters)
     V, N = asm.n_vars(w.ndim), w.npoints
     g = np.random.default_rng(11).normal(size=(w.batch, V, N)).astype(np.float32)
     args = (_dev(w.fields), _dev(w.scalars), _dev(w.rhs), _dev(w.omega))
     z = s.forward(*args)
     _, _, _, _, dz = s.adjoint(*args, z, _dev(g), reuse_setup=True, want_dz=True)
+    if adj_inner_iters:
+        assert s.last_stats["pcg_iters"] % adj_inner_iters == 0, s.last_stats   # sweeps of the adjoint's count
     z, dz = z.cpu().numpy(), dz.cpu().numpy()
     for b in range(w.batch):
         A, d, kind, owner, zr, lam, el = _oracle_instance(w, b)
