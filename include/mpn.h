@@ -264,8 +264,9 @@ int mpn_profile(mpn_problem* p, int enable, double* ms_total, long long* launche
  *   desc     host; grid, batch, coefficient layout (solver fields unused)
  *   fields   device [F][B][N], scalars device [V][B], u device [B][N]
  *   q        device [B][N] output, q = S u
- * B * N above MPN_NOALLOC_MAX_POINTS, or B above 65535, returns
- * MPN_ERR_UNSUPPORTED.  Every call looks up the array's device address on
+ * B * N above MPN_NOALLOC_MAX_POINTS, B above 65535, per-interval steps
+ * (variable_steps) or a Neumann / mixed boundary row (bc_alpha, bc_beta other
+ * than 1, 0 on an open axis) returns MPN_ERR_UNSUPPORTED.  Every call looks up the array's device address on
  * the current device (a host-side query that allocates nothing); the first
  * call on a device also loads the library's device code there, so make it
  * before any stream capture.  All calls share the array: calls that overlap

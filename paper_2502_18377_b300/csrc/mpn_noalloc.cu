@@ -72,6 +72,16 @@ extern "C" int mpn_apply_reduced_noalloc(const mpn_desc* desc, const float* fiel
   if (d.ndim != 2 && d.ndim != 3) return MPN_ERR_INVALID_ARG;
   if (d.periodic[0] || d.batch < 1 || d.nfields < 0 || d.nfields > 7) return MPN_ERR_INVALID_ARG;
   if (d.stencil != 3) return d.stencil == 5 ? MPN_ERR_UNSUPPORTED : MPN_ERR_INVALID_ARG;
+  // uniform steps and Dirichlet faces only: the kernels below apply that
+  // operator, so per-interval steps or Neumann / mixed rows are refused
+  // rather than silently treated as Dirichlet
+  if (d.variable_steps) return MPN_ERR_UNSUPPORTED;
+  for (int k = 1; k < d.ndim; ++k) {
+    if (d.periodic[k]) continue;
+    const double a = d.bc_alpha[k], bt = d.bc_beta[k];
+    if (!(a == a) || !(bt == bt) || (a == 0.0 && bt == 0.0)) return MPN_ERR_INVALID_ARG;
+    if (a != 1.0 || bt != 0.0) return MPN_ERR_UNSUPPORTED;
+  }
   const int V = 1 + 2 * d.ndim;
   long long N = 1;
   for (int k = 0; k < d.ndim; ++k) {

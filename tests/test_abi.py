@@ -72,3 +72,23 @@ def test_binding_rejects_missized_tensors_without_launching():
         args[name] = bad
         with pytest.raises(ValueError, match=name):
             binding.apply_reduced_noalloc(desc, args["fields"], args["scalars"], args["u"], args["q"])
+
+
+def test_noalloc_refuses_operators_it_does_not_apply():
+    """The allocation-free apply implements uniform steps and Dirichlet faces
+    only: per-interval steps and Neumann / mixed rows are refused with
+    UNSUPPORTED, and a face with alpha = beta = 0 with INVALID_ARG, by the
+    host-side checks before any launch (the pointers are never used)."""
+    from paper_2502_18377_b300 import binding
+    lib = binding.load()
+    geom = dict(n=(8, 16, 16), step=(1 / 7, 1 / 15, 1 / 16), periodic=(False, False, True))
+    fake = ctypes.c_void_p(256)
+    call = lambda d: lib.mpn_apply_reduced_noalloc(ctypes.byref(d), fake, fake, fake, fake, None)
+    d = binding.make_desc(geom, 2, [1, -1, -1, -1, 0, -1, 0], 2)
+    d.variable_steps = 1
+    assert call(d) == 2
+    d = binding.make_desc(geom, 2, [1, -1, -1, -1, 0, -1, 0], 2)
+    d.bc_alpha[1], d.bc_beta[1] = 1.0, 0.5
+    assert call(d) == 2
+    d.bc_alpha[1], d.bc_beta[1] = 0.0, 0.0
+    assert call(d) == 1
