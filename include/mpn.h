@@ -236,7 +236,9 @@ int mpn_mse_grad(mpn_problem* p, const float* z, const float* target, float* g_z
 
 /* Diagnostic: q = S u for the reduced normal operator S on the finest grid
  * (the Schur complement of A^T A onto the u unknowns, FP32), with the
- * multigrid setup of the given coefficients.  u, q: [B][N]. */
+ * multigrid setup of the given coefficients.  u, q: [B][N], 16-byte aligned
+ * (the operator kernels move float4 groups; an unaligned one returns
+ * MPN_ERR_INVALID_ARG). */
 int mpn_apply_reduced(mpn_problem* p, const float* fields, const float* scalars,
                       const float* u, float* q, void* stream);
 
@@ -286,6 +288,9 @@ int mpn_apply_reduced_noalloc(const mpn_desc* desc, const float* fields, const f
  * with tap = (dt+1)*9 + (dx+1)*3 + (dy+1); biases FP32 [Cout]; all device
  * memory owned by the caller.  Supported (Cin, Cout): (16, 32), (32, 32),
  * (32, 16).  Time is zero-padded; x, y wrap when periodic, else zero-padded.
+ * Array arguments of the convolutions (activations, weights, outputs,
+ * scratch) must be 16-byte aligned (they move in 16-byte pieces); an
+ * unaligned one returns MPN_ERR_INVALID_ARG before any launch.
  * ------------------------------------------------------------------------ */
 typedef struct mpn_conv_desc {
   int n[3];          /* n_t, n_x, n_y */
@@ -305,7 +310,7 @@ typedef struct mpn_conv_desc {
  * in tensor memory: per tile of 128 points and per 3x3x3 tap, tcgen05.mma of M = 128, N = cout,
  * K = 16 on the gathered input tile and the tap's weights, both staged in shared memory
  * (MPN_CONV_MMA_SYNC: the warp-level mma.sync m16n8k16 kernel instead).  Not in the paper: the
- * the benchmark spec's learned warm start (a 3D-conv network predicting the solution). */
+ * learned warm start (a 3D-conv network predicting the solution). */
 int mpn_conv3d_forward(const mpn_conv_desc* d, const void* x, const void* w, const float* bias, void* y,
                        int flags, void* stream);
 /* *flag = 1 if a tcgen05 convolution launched since the last call had a bounded wait for its

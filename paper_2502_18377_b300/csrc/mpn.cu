@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 #include <algorithm>
@@ -47,6 +48,7 @@ static thread_local char g_cuda_err[256] = "";
 struct Level {
   Grid g;
   int vec4 = 0;        // float4 stencil kernels apply (D = 3, n_y % 4 == 0)
+  int vec2 = 0;        // float4 stencil kernels of 1-D + t grids apply (D = 2, n_x % 4 == 0)
   int papply = 0;      // partial sums per instance written by an operator apply
   int cz[3];           // dims halved from this level to the next
   int fs_tt = 0;       // > 0: operator steps as one fused kernel with TT-plane tiles
@@ -514,7 +516,8 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
     Level& l = p->lv[k];
     // per-interval steps, Neumann / mixed rows: the general (scalar) kernels only
     l.vec4 = (p->D == 3 && l.g.n[2] % 4 == 0 && l.g.n[2] >= 8 && !d.variable_steps && !mixed) ? 1 : 0;
-    l.papply = l.vec4 ? sblk(l.g.N / 4) : sblk(l.g.N);
+    l.vec2 = (p->D == 2 && l.g.n[1] % 4 == 0 && l.g.n[1] >= 8 && !d.variable_steps && !mixed) ? 1 : 0;
+    l.papply = (l.vec4 || l.vec2) ? sblk(l.g.N / 4) : sblk(l.g.N);
     // fused operator step: tiles that divide the t and x extents, with whole
     // y rows of at most FS_MAX_NY points, or 64-point y segments of wider rows
     // (or of rows >= 128 with fused_step = 2)
@@ -720,6 +723,17 @@ static void stencil(mpn_problem* p, int k, StepArgs a, int mode, cudaStream_t st
       case SM_CHEB: ++p->nlaunch, k_LTy4<SM_CHEB><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
       case SM_RES: ++p->nlaunch, k_LTy4<SM_RES><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
       default: ++p->nlaunch, k_LTy4<SM_APPLY><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
+    }
+    return;
+  }
+  if (l.vec2) {
+    dim3 g4(sblk(l.g.N / 4), p->B);
+    ++p->nlaunch, k_Ly4_2<<<g4, MPN_TPB, 0, st>>>(l.g, cf, l.rho, a.x, l.y);
+    switch (mode) {
+      case SM_POST0: ++p->nlaunch, k_LTy4_2<SM_POST0><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
+      case SM_CHEB: ++p->nlaunch, k_LTy4_2<SM_CHEB><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
+      case SM_RES: ++p->nlaunch, k_LTy4_2<SM_RES><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
+      default: ++p->nlaunch, k_LTy4_2<SM_APPLY><<<g4, MPN_TPB, 0, st>>>(l.g, cf, a); break;
     }
     return;
   }
@@ -1524,6 +1538,9 @@ extern "C" int mpn_mse_grad(mpn_problem* p, const float* z, const float* target,
 extern "C" int mpn_apply_reduced(mpn_problem* p, const float* fields, const float* scalars, const float* u, float* q,
                                  void* stream) {
   if (!p || !scalars || !u || !q) return MPN_ERR_INVALID_ARG;
+  // u and q go to the operator kernels as they are, and those read and write
+  // float4 groups: 16-byte alignment is checked here, before p is touched
+  if (((uintptr_t)u | (uintptr_t)q) & 15) return MPN_ERR_INVALID_ARG;
   if (p->F > 0 && !fields) return MPN_ERR_INVALID_ARG;
   if (p->desc.variable_steps && !p->steps_set) return MPN_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;

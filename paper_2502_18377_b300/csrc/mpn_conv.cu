@@ -867,6 +867,13 @@ void conv_dispatch(const CGrid& g, int B, int ci, int co, int flags, bool tcore,
 
 }  // namespace
 
+// The kernels move activations and weights in 16-byte pieces (cp.async,
+// uint4 loads, vector stores): every array argument must be 16-byte aligned.
+static bool unaligned16(const void* a, const void* b = nullptr, const void* c = nullptr,
+                        const void* d = nullptr) {
+  return (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d) & 15) != 0;
+}
+
 extern "C" int mpn_conv_take_error(int* flag) {
   if (!flag) return MPN_ERR_INVALID_ARG;
   int* p = conv_err_ptr();
@@ -883,6 +890,7 @@ extern "C" int mpn_conv3d_forward(const mpn_conv_desc* d, const void* x, const v
   int s = check(d);
   if (s) return s;
   if (!x || !w || !y || ((flags & MPN_CONV_BIAS) && !bias)) return MPN_ERR_INVALID_ARG;
+  if (unaligned16(x, w, y)) return MPN_ERR_INVALID_ARG;
   CGrid g = make_cgrid(d);
   conv_dispatch(g, d->batch, d->cin, d->cout, flags & 7, !(flags & MPN_CONV_MMA_SYNC), (const __nv_bfloat16*)x,
                 (const __nv_bfloat16*)w, bias, y, (cudaStream_t)stream);
@@ -894,6 +902,7 @@ extern "C" int mpn_conv3d_backward_data(const mpn_conv_desc* d, const void* g_ou
   int s = check(d);
   if (s) return s;
   if (!g_out || !w || !wt_scratch || !g_in) return MPN_ERR_INVALID_ARG;
+  if (unaligned16(g_out, w, wt_scratch, g_in)) return MPN_ERR_INVALID_ARG;
   if (d->cin != 32) return MPN_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   CGrid g = make_cgrid(d);
@@ -920,6 +929,7 @@ extern "C" int mpn_conv3d_backward_weights(const mpn_conv_desc* d, const void* g
   int s = check(d);
   if (s) return s;
   if (!g_out || !x || !scratch || !dw || !db) return MPN_ERR_INVALID_ARG;
+  if (unaligned16(g_out, x, scratch)) return MPN_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   CGrid g = make_cgrid(d);
   long long total = (long long)d->batch * g.N;

@@ -291,7 +291,160 @@ __global__ void __launch_bounds__(256, 5) k_LTy4(Grid g, Coef cf, StepArgs a) {
     } else {
       float4 res = ld4(a.r + j) + qv;
       float4 dn = a.c2 * (ld4(a.dinv + j) * res);
-      if (MODE == SM_CHEB) dn = dn + a.c1 * ld4(a.d + j);
+      // the previous direction: overwritten below by this thread, so a
+      // coherent load (not the read-only path)
+      if (MODE == SM_CHEB) dn = dn + a.c1 * __ldcg(reinterpret_cast<const float4*>(a.d + j));
+      *reinterpret_cast<float4*>(a.d + j) = dn;
+      *reinterpret_cast<float4*>(a.e + j) = xj + dn;
+    }
+  }
+  if (MODE == SM_APPLY && a.part) {
+    double s = block_sum((double)acc);
+    if (threadIdx.x == 0) a.part[b * MPN_PMAX + blockIdx.x] = s;
+  }
+}
+
+// D = 2 and n_x % 4 == 0: the same float4 scheme with x (the contiguous axis)
+// in the role of y above.  The four points of a group share their position
+// class along t, so t neighbours come as float4 rows n_x apart; along x the
+// neighbours come from the group plus one value on each side.  A group that
+// touches a non-periodic x edge falls back to the scalar formulas point by
+// point.  Uniform steps and Dirichlet rows only (as for D = 3).
+__device__ __forceinline__ void group_pos2(const Grid& g, int q, float inv_ng, int pos[3]) {
+  int r;
+  pos[0] = fdivmod(q, g.n[1] >> 2, inv_ng, r);
+  pos[1] = r << 2;
+  pos[2] = 0;
+}
+
+__device__ __forceinline__ bool xedge2(const Grid& g, const int pos[3]) {
+  return !g.per[1] && (pos[1] < 3 || pos[1] + 3 > g.n[1] - 4);
+}
+
+__global__ void __launch_bounds__(256, 4) k_Ly4_2(Grid g, Coef cf, const float* __restrict__ rho,
+                                               const float* __restrict__ x, float* __restrict__ y) {
+  const int b = blockIdx.y;
+  const size_t off = (size_t)b * g.N;
+  const float* xb = x + off;
+  const CoefB4 C(cf, b);
+  const int NG = g.N >> 2, n1 = g.n[1];
+  const float inv_ng = 1.f / (float)(n1 >> 2);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < NG; q += gridDim.x * blockDim.x) {
+    int pos[3]; group_pos2(g, q, inv_ng, pos);
+    const int p0 = q << 2;
+    if (xedge2(g, pos)) {
+      for (int k = 0; k < 4; ++k) {
+        int pk[3] = {pos[0], pos[1] + k, 0};
+        y[off + p0 + k] = -rho[off + p0 + k] * Lrow<float, 2>(g, cf, b, p0 + k, pk, xb, nullptr);
+      }
+      continue;
+    }
+    const float4 xc = ld4(xb + p0);
+    float4 Lx = C.at4(0, p0) * xc;
+    // t: central forms inside, the one-sided forms on the first and last plane
+    if (pos[0] > 0 && pos[0] < g.n[0] - 1) {
+      const float4 xm = ld4(xb + p0 - n1), xp = ld4(xb + p0 + n1);
+      Lx = Lx + ((0.5f * g.is1[0]) * C.at4(1, p0)) * (xp - xm) + (g.is2[0] * C.at4(2, p0)) * (xp - 2.f * xc + xm);
+    } else {
+      float4 a1 = f4(0.f), a2 = f4(0.f);
+#pragma unroll
+      for (int o = -2; o <= 2; ++o) {
+        const float w1 = dweight(1, pos[0], g.n[0], 0, o), w2 = dweight(2, pos[0], g.n[0], 0, o);
+        if (w1 == 0.f && w2 == 0.f) continue;
+        const float4 xv = o == 0 ? xc : ld4(xb + nbr(g, p0, pos, 0, o));
+        a1 = a1 + w1 * xv; a2 = a2 + w2 * xv;
+      }
+      Lx = Lx + (g.is1[0] * C.at4(1, p0)) * a1 + (g.is2[0] * C.at4(2, p0)) * a2;
+    }
+    // x: central forms (periodic, or a group away from both faces)
+    {
+      const int row0 = p0 - pos[1];
+      const float xl = xb[row0 + (pos[1] == 0 ? n1 - 1 : pos[1] - 1)];
+      const float xr = xb[row0 + (pos[1] + 4 == n1 ? 0 : pos[1] + 4)];
+      const float4 xm = make_float4(xl, xc.x, xc.y, xc.z), xp = make_float4(xc.y, xc.z, xc.w, xr);
+      Lx = Lx + (0.5f * g.is1[1]) * (C.at4(3, p0) * (xp - xm)) + g.is2[1] * (C.at4(4, p0) * (xp - 2.f * xc + xm));
+    }
+    const float4 r4 = ld4(rho + off + p0);
+    *reinterpret_cast<float4*>(y + off + p0) = make_float4(-r4.x * Lx.x, -r4.y * Lx.y, -r4.z * Lx.z, -r4.w * Lx.w);
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 5) k_LTy4_2(Grid g, Coef cf, StepArgs a) {
+  const int b = blockIdx.y;
+  const size_t off = (size_t)b * g.N;
+  const float* yb = a.y + off;
+  const CoefB4 C(cf, b);
+  const int NG = g.N >> 2, n1 = g.n[1];
+  const float inv_ng = 1.f / (float)(n1 >> 2);
+  float acc = 0.f;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < NG; q += gridDim.x * blockDim.x) {
+    int pos[3]; group_pos2(g, q, inv_ng, pos);
+    const int p0 = q << 2;
+    float4 qv;
+    if (xedge2(g, pos)) {
+      float t[4];
+      for (int k = 0; k < 4; ++k) {
+        int pk[3] = {pos[0], pos[1] + k, 0};
+        t[k] = LTgather<float, 2>(g, cf, b, p0 + k, pk, yb);
+      }
+      qv = make_float4(t[0], t[1], t[2], t[3]);
+    } else {
+      const float4 yc = ld4(yb + p0);
+      qv = C.at4(0, p0) * yc;
+      // t: rows i = j - o e_t share their position class across the group
+      if (pos[0] > 2 && pos[0] < g.n[0] - 3) {
+        const int pm = p0 - n1, pp = p0 + n1;
+        const float4 ym = ld4(yb + pm), yp = ld4(yb + pp);
+        qv = qv + (0.5f * g.is1[0]) * (C.at4(1, pm) * ym - C.at4(1, pp) * yp) +
+             g.is2[0] * (C.at4(2, pm) * ym - 2.f * (C.at4(2, p0) * yc) + C.at4(2, pp) * yp);
+      } else {
+#pragma unroll
+        for (int o = -2; o <= 2; ++o) {
+          const int ip = pos[0] - o;
+          if (ip < 0 || ip >= g.n[0]) continue;
+          const float w1 = dweight(1, ip, g.n[0], 0, o), w2 = dweight(2, ip, g.n[0], 0, o);
+          if (w1 == 0.f && w2 == 0.f) continue;
+          const int pi = p0 + (ip - pos[0]) * n1;
+          const float4 yv = o == 0 ? yc : ld4(yb + pi);
+          qv = qv + yv * ((w1 * g.is1[0]) * C.at4(1, pi) + (w2 * g.is2[0]) * C.at4(2, pi));
+        }
+      }
+      // x: central rows j-1, j, j+1
+      const int row0 = p0 - pos[1];
+      const int pl = row0 + (pos[1] == 0 ? n1 - 1 : pos[1] - 1), pr = row0 + (pos[1] + 4 == n1 ? 0 : pos[1] + 4);
+      const float4 c1 = C.at4(3, p0), c2 = C.at4(4, p0);
+      const float yl = yb[pl], yr = yb[pr], c1l = C.at(3, pl), c1r = C.at(3, pr), c2l = C.at(4, pl), c2r = C.at(4, pr);
+      const float4 ym = make_float4(yl, yc.x, yc.y, yc.z), yp = make_float4(yc.y, yc.z, yc.w, yr);
+      const float4 c1m = make_float4(c1l, c1.x, c1.y, c1.z), c1p = make_float4(c1.y, c1.z, c1.w, c1r);
+      const float4 c2m = make_float4(c2l, c2.x, c2.y, c2.z), c2p = make_float4(c2.y, c2.z, c2.w, c2r);
+      qv = qv + (0.5f * g.is1[1]) * (c1m * ym - c1p * yp) + g.is2[1] * (c2m * ym - 2.f * (c2 * yc) + c2p * yp);
+    }
+    const float4 xj = ld4(a.x + off + p0);
+    // Dirichlet rows: the t faces are shared by the group, the x faces per point
+    if (pos[0] == 0 || (g.final_rows && pos[0] == g.n[0] - 1)) {
+      qv = qv - g.theta * xj;
+    } else if (!g.per[1]) {
+      float t4[4] = {qv.x, qv.y, qv.z, qv.w};
+      for (int k = 0; k < 4; ++k) {
+        const int ix = pos[1] + k;
+        if (ix == 0 || ix == n1 - 1) t4[k] -= g.theta * get(xj, k);
+      }
+      qv = make_float4(t4[0], t4[1], t4[2], t4[3]);
+    }
+    // qv = -(S x) on the group
+    const size_t j = off + p0;
+    if (MODE == SM_APPLY) {
+      *reinterpret_cast<float4*>(a.out + j) = make_float4(-qv.x, -qv.y, -qv.z, -qv.w);
+      acc -= qv.x * xj.x + qv.y * xj.y + qv.z * xj.z + qv.w * xj.w;
+    } else if (MODE == SM_RES) {
+      *reinterpret_cast<float4*>(a.out + j) = ld4(a.r + j) + qv;
+    } else {
+      const float4 res = ld4(a.r + j) + qv;
+      float4 dn = a.c2 * (ld4(a.dinv + j) * res);
+      // the previous direction: overwritten below by this thread, so a
+      // coherent load (not the read-only path)
+      if (MODE == SM_CHEB) dn = dn + a.c1 * __ldcg(reinterpret_cast<const float4*>(a.d + j));
       *reinterpret_cast<float4*>(a.d + j) = dn;
       *reinterpret_cast<float4*>(a.e + j) = xj + dn;
     }

@@ -92,3 +92,23 @@ def test_noalloc_refuses_operators_it_does_not_apply():
     assert call(d) == 2
     d.bc_alpha[1], d.bc_beta[1] = 0.0, 0.0
     assert call(d) == 1
+
+
+def test_unaligned_arrays_are_refused_before_any_launch():
+    """The operator and convolution kernels move 16-byte pieces: an array
+    argument that is not 16-byte aligned is refused with INVALID_ARG by the
+    host-side checks, before the problem object or any pointer is used."""
+    from paper_2502_18377_b300 import binding
+    lib = binding.load()
+    ok, odd = ctypes.c_void_p(4096), ctypes.c_void_p(4096 + 4)
+    fake_problem = ctypes.c_void_p(64)   # never dereferenced: the check comes first
+    assert lib.mpn_apply_reduced(fake_problem, ok, ok, odd, ok, None) == 1
+    assert lib.mpn_apply_reduced(fake_problem, ok, ok, ok, odd, None) == 1
+    d = binding.MpnConvDesc()
+    for k in range(3):
+        d.n[k], d.periodic[k] = 8, int(k > 0)
+    d.batch, d.cin, d.cout = 1, 32, 32
+    assert lib.mpn_conv3d_forward(ctypes.byref(d), odd, ok, None, ok, 0, None) == 1
+    assert lib.mpn_conv3d_forward(ctypes.byref(d), ok, ok, None, odd, 0, None) == 1
+    assert lib.mpn_conv3d_backward_data(ctypes.byref(d), ok, ok, odd, ok, None) == 1
+    assert lib.mpn_conv3d_backward_weights(ctypes.byref(d), ok, odd, ok, ok, ok, None) == 1

@@ -98,6 +98,9 @@ CASES = [
     ("rand_dirichlet_3d", lambda: _no_utt(wl.random_problem(26, (8, 16, 12), (False, False, False), batch=2))),
     ("rand_final_3d", lambda: _no_utt(wl.random_problem(27, (12, 8, 16), (False, False, True), batch=2,
                                                         final_time_rows=True))),
+    # 1-D + t float4 groups: Dirichlet x faces inside the groups, final-time rows
+    ("rand_final_2d", lambda: _no_utt(wl.random_problem(28, (9, 16), (False, False), batch=2,
+                                                        final_time_rows=True))),
     # Laplace's equation (elliptic in both axes, Dirichlet on all four faces)
     ("laplace_32", lambda: wl.laplace_2d(batch=2, n=32)),
 ]
@@ -242,6 +245,8 @@ def test_adjoint_and_gradients_match_oracle(name, make):
 def test_reduced_operator_matches_oracle_schur():
     """S u (FP32 kernels) against the oracle's Schur complement of A^T A."""
     for w in (wl.random_problem(31, (9, 20), (False, True), batch=2),
+              # 1-D + t float4 groups with Dirichlet x faces and final-time rows
+              wl.random_problem(34, (10, 24), (False, False), batch=2, final_time_rows=True),
               wl.random_problem(32, (6, 10, 12), (False, False, True), batch=2, final_time_rows=True),
               _round(wl.reaction_diffusion_2d(batch=2, n=(8, 16, 16))),
               wl.random_problem(33, (8, 12, 16), (False, False, False), batch=2, final_time_rows=True)):
