@@ -160,10 +160,10 @@ def make_desc(geom: dict, batch: int, field_of, nfields: int) -> MpnDesc:
     return d
 
 
-def _check_numel(name, t, n):
-    """float32 with exactly n elements (the C ABI reads and writes n floats)."""
-    if t.dtype != torch.float32:
-        raise ValueError(f"{name} must be float32, got {t.dtype}")
+def _check_numel(name, t, n, dtype=torch.float32):
+    """`dtype` with exactly n elements (the C ABI reads and writes n of them)."""
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
     if t.numel() != n:
         raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
 
@@ -287,6 +287,13 @@ class Solver:
     def forward(self, fields, scalars, rhs, omega, u0=None, z=None, z64=None, allow_not_converged=False):
         """Returns z [B][V][N] (float32); z64 (float64) is filled if given."""
         self._inputs(fields, scalars, rhs, omega)
+        BN, BVN = self.B * self.N, self.B * self.V * self.N
+        if u0 is not None:
+            _check_numel("u0", u0, BN)
+        if z is not None:
+            _check_numel("z", z, BVN)
+        if z64 is not None:
+            _check_numel("z64", z64, BVN, torch.float64)
         if z is None:
             z = torch.empty((self.B, self.V, self.N), device=rhs.device, dtype=torch.float32)
         st = MpnStats()
@@ -302,6 +309,8 @@ class Solver:
         [B][V][N]), if given, receives d_z as the FP64 refinement holds it."""
         self._inputs(fields, scalars, rhs, omega)
         _check_f32("g_z", g_z, (self.B, self.V, self.N))
+        if z is not None:
+            _check_numel("z", z, self.B * self.V * self.N)
         dev = rhs.device
         dfields = torch.empty((max(self.F, 1), self.B, self.N), device=dev, dtype=torch.float32)
         dscal = torch.empty((self.V, self.B), device=dev, dtype=torch.float32)
@@ -353,8 +362,12 @@ class Solver:
         return parts
 
     def mse_grad(self, z, target, g_z=None):
+        """dl/dz of the mean squared error of u against target [B][N]."""
+        _check_numel("z", z, self.B * self.V * self.N)
+        _check_numel("target", target, self.B * self.N)
         if g_z is None:
             g_z = torch.empty_like(z)
+        _check_numel("g_z", g_z, self.B * self.V * self.N)
         s = self.lib.mpn_mse_grad(self._h, _ptr(z), _ptr(target), _ptr(g_z), _stream())
         if s != 0:
             raise MpnError(s, "mpn_mse_grad")

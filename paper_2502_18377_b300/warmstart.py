@@ -20,7 +20,7 @@ import ctypes
 import numpy as np
 import torch
 
-from .binding import MpnConvDesc, MpnError, _ptr, _stream, load
+from .binding import MpnConvDesc, MpnError, _check_numel, _ptr, _stream, load
 
 LAYERS = [(16, 32), (32, 32), (32, 32), (32, 16)]
 RELU, F32, BIAS = 1, 2, 4
@@ -129,6 +129,10 @@ class WarmStartNet:
         return self._ws
 
     def _forward(self, fields, rhs):
+        # the kernels read F*B*N field values and B*N right-hand-side values
+        if self.F:
+            _check_numel("fields", fields, self.F * self.B * self.N)
+        _check_numel("rhs", rhs, self.B * self.N)
         ws = self._workspace()
         L, st = self.lib, _stream()
         _chk(L.mpn_pack_inputs(ctypes.byref(self.desc[0]), self.F, _ptr(fields) if self.F else None, _ptr(rhs),
@@ -157,6 +161,7 @@ class WarmStartNet:
         ws = self._workspace()
         L, st = self.lib, _stream()
         y = self._forward(fields, rhs)
+        _check_numel("u_target", u_target, self.B * self.N)
         tgt = (u_target / self.out_scale).contiguous()
         _chk(L.mpn_mse_u(ctypes.byref(self.desc[3]), _ptr(y), _ptr(tgt), _ptr(ws["gy"]), _ptr(ws["loss"]), st), "mse")
         acts = [ws["x0"]] + ws["a"]

@@ -112,3 +112,28 @@ def test_unaligned_arrays_are_refused_before_any_launch():
     assert lib.mpn_conv3d_forward(ctypes.byref(d), ok, ok, None, odd, 0, None) == 1
     assert lib.mpn_conv3d_backward_data(ctypes.byref(d), ok, ok, odd, ok, None) == 1
     assert lib.mpn_conv3d_backward_weights(ctypes.byref(d), ok, odd, ok, ok, ok, None) == 1
+
+
+def test_solver_rejects_missized_tensors_without_launching():
+    """The solve, the adjoint and the loss gradient read and write B*V*N (or
+    B*N) values through raw pointers: a tensor of another size or dtype is
+    refused on the host before the library is called (CPU tensors and a
+    Solver without a problem object: nothing here can reach a GPU)."""
+    import pytest
+    import torch
+    from paper_2502_18377_b300.binding import Solver
+    s = object.__new__(Solver)
+    s.B, s.V, s.N, s.F = 2, 7, 64, 2
+    args = (torch.zeros(2, 2, 64), torch.zeros(7, 2), torch.zeros(2, 64), torch.zeros(2, 64))
+    with pytest.raises(ValueError, match="u0"):
+        s.forward(*args, u0=torch.zeros(2, 63))
+    with pytest.raises(ValueError, match="z"):
+        s.forward(*args, z=torch.zeros(2, 7, 63))
+    with pytest.raises(ValueError, match="z64"):
+        s.forward(*args, z64=torch.zeros(2, 7, 64))            # float32, not float64
+    with pytest.raises(ValueError, match="z"):
+        s.adjoint(*args, torch.zeros(2, 6, 64), torch.zeros(2, 7, 64))
+    with pytest.raises(ValueError, match="target"):
+        s.mse_grad(torch.zeros(2, 7, 64), torch.zeros(2, 65))
+    with pytest.raises(ValueError, match="g_z"):
+        s.mse_grad(torch.zeros(2, 7, 64), torch.zeros(2, 64), g_z=torch.zeros(2, 7, 64, dtype=torch.float64))
