@@ -151,7 +151,9 @@ int mpn_default_desc(mpn_desc* desc);
 
 /* Validates the descriptor, builds the grid hierarchy (spatial halving, time
  * kept) and allocates the workspace on the current device.  *out receives the
- * problem.  Errors: INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA. */
+ * problem.  Errors: INVALID_ARG, UNSUPPORTED (five-point rows, a batch above
+ * 65535 instances, a hierarchy whose coarsest system is too large), NO_MEMORY,
+ * CUDA. */
 int mpn_create(const mpn_desc* desc, mpn_problem** out);
 
 /* Bytes of device workspace owned by the problem. */

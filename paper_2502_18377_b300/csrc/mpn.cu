@@ -448,6 +448,7 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   const mpn_desc& d = *desc;
   if (d.ndim != 2 && d.ndim != 3) return MPN_ERR_INVALID_ARG;
   if (d.batch < 1 || d.nfields < 0 || d.nfields > 7) return MPN_ERR_INVALID_ARG;
+  if (d.batch > 65535) return MPN_ERR_UNSUPPORTED;   // instances are the grid's y (or z) extent
   if (d.periodic[0]) return MPN_ERR_INVALID_ARG;
   if (d.stencil == 5) return MPN_ERR_UNSUPPORTED;
   if (d.stencil != 3) return MPN_ERR_INVALID_ARG;

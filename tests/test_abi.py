@@ -49,6 +49,9 @@ def test_error_strings_without_gpu():
     d.krylov = 7
     assert lib.mpn_create(ctypes.byref(d), ctypes.byref(h)) == 1      # unknown inner solver: invalid
     d.krylov = 0
+    d.batch = 65536
+    assert lib.mpn_create(ctypes.byref(d), ctypes.byref(h)) == 2      # more instances than a grid extent: unsupported
+    d.batch = 1
     assert d.adj_inner_iters == 0                                     # the last field: the adjoint's own count unset
     d.adj_inner_iters = -1
     assert lib.mpn_create(ctypes.byref(d), ctypes.byref(h)) == 1      # negative iteration count: invalid
