@@ -231,6 +231,19 @@ long long mpn_generation(const mpn_problem* p);
  * starts with the word cleared). */
 int mpn_inject_wait_failure(mpn_problem* p);
 
+/* Bounds-checked build (the library compiled with -DMPN_DEBUG, built as
+ * libmpn_debug.so): the index helpers of the stencil, transfer, FP64 and
+ * two-pass operator kernels check every neighbour and point index they form;
+ * an index out of range is replaced by an in-range one (no fault, no trap)
+ * and the first one's code is recorded in a device word of the problem:
+ * 1 neighbour (general forms), 2 neighbour (+-1 forms), 3 point, 4 float4
+ * group, 5 float4 time neighbour of a 1-D + t level.  Synchronises the
+ * device, writes the recorded code (0: none) to *code and clears it.  The
+ * fused tile and marching kernels form their indices themselves and are not
+ * covered.  Release builds: *code = 0 and MPN_ERR_UNSUPPORTED.  Not in the
+ * paper (a replacement for a sanitizer run). */
+int mpn_debug_take(mpn_problem* p, int* code);
+
 /* dl/dz of l = mean over (b, i) of (u - target)^2, written into g_z [B][V][N]
  * (zero on the derivative unknowns): the loss used by the benchmarks. */
 int mpn_mse_grad(mpn_problem* p, const float* z, const float* target, float* g_z,

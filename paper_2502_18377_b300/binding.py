@@ -14,6 +14,7 @@ import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmpn.so")
+DEBUG_LIB_PATH = os.path.join(_HERE, "libmpn_debug.so")   # bounds-checked build (MPN_DEBUG)
 
 MPN_REUSE_SETUP = 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "not converged",
@@ -65,6 +66,7 @@ EXPORTS = {
     "mpn_step_grads": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "mpn_inject_wait_failure": (ctypes.c_int, [_P]),
     "mpn_mse_grad": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "mpn_debug_take": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "mpn_apply_reduced": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "mpn_profile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
@@ -255,6 +257,18 @@ class Solver:
     @property
     def workspace_bytes(self):
         return int(self.lib.mpn_workspace_bytes(self._h))
+
+    def debug_take(self):
+        """Bounds-checked build: the code of the first out-of-range index a
+        kernel formed since the last call (0: none), cleared; None with the
+        release library."""
+        code = ctypes.c_int()
+        s = self.lib.mpn_debug_take(self._h, ctypes.byref(code))
+        if s == 2:
+            return None
+        if s != 0:
+            raise MpnError(s, "mpn_debug_take")
+        return code.value
 
     def generation(self):
         """Forward solves completed on this problem so far."""

@@ -73,6 +73,7 @@ struct mpn_problem {
   float *Kband = nullptr, *Kinv = nullptr;
   int* ferr = nullptr;
   int* kerr = nullptr;     // device word a kernel sets when a bounded wait gives up (cleared per solve)
+  int* dbg = nullptr;      // bounds-checked build: first out-of-range index code (see dbg_index)
   int inject_wait = 0;     // host-side fault injection: the next solve sets kerr itself
   float *scalars = nullptr, *rhs = nullptr, *omega = nullptr;
   float* scal4 = nullptr;  // scalars replicated 4 times, [V][B][4]
@@ -589,6 +590,11 @@ extern "C" int mpn_create(const mpn_desc* desc, mpn_problem** out) {
   AL(p->Kinv, (size_t)B * p->M * p->M);
   AL(p->ferr, B);
   AL(p->kerr, 1);
+#ifdef MPN_DEBUG
+  AL(p->dbg, 1);
+  if (cudaMemset(p->dbg, 0, sizeof(int)) != cudaSuccess) { mpn_destroy(p); return MPN_ERR_CUDA; }
+  for (int k = 0; k < p->L; ++k) p->lv[k].g.dbg = p->dbg;
+#endif
   AL(p->scalars, (size_t)V * B);
   AL(p->scal4, (size_t)V * B * 4);
   AL(p->rhs, N0); AL(p->omega, N0);
@@ -1518,6 +1524,21 @@ extern "C" int mpn_step_grads(mpn_problem* p, const double* z64, const double* d
   ++p->nlaunch, k_step_grads<<<dim3(p->stn, p->D, p->B), MPN_TPB, 0, st>>>(p->lv[0].g, p->hlev, z64, dz64, dsteps, p->B);
   CKL();
   return MPN_OK;
+}
+
+extern "C" int mpn_debug_take(mpn_problem* p, int* code) {
+  if (!p || !code) return MPN_ERR_INVALID_ARG;
+#ifdef MPN_DEBUG
+  CK(cudaDeviceSynchronize());
+  int v = 0;
+  CK(cudaMemcpy(&v, p->dbg, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v) CK(cudaMemset(p->dbg, 0, sizeof(int)));
+  *code = v;
+  return MPN_OK;
+#else
+  *code = 0;
+  return MPN_ERR_UNSUPPORTED;
+#endif
 }
 
 extern "C" long long mpn_generation(const mpn_problem* p) { return p ? p->gen : -1; }

@@ -71,7 +71,24 @@ struct Grid {
   const double* r12d;
   const double* r22d;
   double* y2d;
+  // Bounds-checked build (MPN_DEBUG): device word receiving the code of the
+  // first out-of-range index a kernel computed (null: nothing recorded).
+  int* dbg;
 };
+
+// Index check of the bounds-checked build: an index outside [0, n) records
+// `code` in g.dbg (first one wins) and is replaced by 0, so the access stays
+// in bounds and the kernel runs on; release builds return i unchanged.
+__device__ __forceinline__ int dbg_index(const Grid& g, int i, int n, int code) {
+#ifdef MPN_DEBUG
+  if ((unsigned)i >= (unsigned)n) {
+    if (g.dbg) atomicCAS(g.dbg, 0, code);
+    return 0;
+  }
+#endif
+  (void)g; (void)n; (void)code;
+  return i;
+}
 
 // Step record of one grid position along one dimension (per-interval steps).
 // In the scaled unknowns w = (sbar u', sbar^2 u'') of the position, with
@@ -148,6 +165,7 @@ __device__ __forceinline__ int fdivmod(int q, int n, float inv_n, int& r) {
 // Point index -> (t, x, y) without an integer division; any_edge: the point is within 2 of a
 // time edge or of a non-periodic spatial edge (one-sided forms nearby).
 __device__ __forceinline__ void decode_fast(const Grid& g, int p, int pos[3]) {
+  p = dbg_index(g, p, g.N, 3);
   int rem, i2;
   pos[0] = fdivmod(p, g.n[1] * g.n[2], g.inv_pl, rem);
   pos[1] = fdivmod(rem, g.n[2], g.inv_n2, i2);
@@ -172,7 +190,7 @@ __device__ __forceinline__ int wrap1(int c, int n) { return c < 0 ? c + n : (c >
 __device__ __forceinline__ int nbr(const Grid& g, int p, const int pos[3], int d, int o) {
   int c = pos[d] + o;
   if (g.per[d]) c = wrap1(c, g.n[d]);
-  return p + (c - pos[d]) * g.stride[d];
+  return dbg_index(g, p + (c - pos[d]) * g.stride[d], g.N, 1);
 }
 
 // Weight of u_{pos+o} in the difference form of order `order` at coordinate

@@ -28,9 +28,9 @@ __device__ __forceinline__ void decode_f(const Grid& g, int p, float inv12, floa
 __device__ __forceinline__ int nb1(const Grid& g, int p, const int pos[3], int d, int o) {
   int c = pos[d] + o;
   int s = g.stride[d];
-  if (c < 0) return p + (g.n[d] - 1) * s;
-  if (c >= g.n[d]) return p - (g.n[d] - 1) * s;
-  return p + o * s;
+  if (c < 0) return dbg_index(g, p + (g.n[d] - 1) * s, g.N, 2);
+  if (c >= g.n[d]) return dbg_index(g, p - (g.n[d] - 1) * s, g.N, 2);
+  return dbg_index(g, p + o * s, g.N, 2);
 }
 
 template <int D>
@@ -144,6 +144,7 @@ struct CoefB4 {
 // group (it, ix, iy0) of p0 = first point; returns false if the group needs
 // the scalar fallback (touches a non-periodic y edge region)
 __device__ __forceinline__ void group_pos(const Grid& g, int q, float inv_ng, float inv_n1, int pos[3]) {
+  q = dbg_index(g, q, g.N >> 2, 4);
   int ng = g.n[2] >> 2, r;
   int row = fdivmod(q, ng, inv_ng, r);
   pos[2] = r << 2;
@@ -311,6 +312,7 @@ __global__ void __launch_bounds__(256, 5) k_LTy4(Grid g, Coef cf, StepArgs a) {
 // touches a non-periodic x edge falls back to the scalar formulas point by
 // point.  Uniform steps and Dirichlet rows only (as for D = 3).
 __device__ __forceinline__ void group_pos2(const Grid& g, int q, float inv_ng, int pos[3]) {
+  q = dbg_index(g, q, g.N >> 2, 4);
   int r;
   pos[0] = fdivmod(q, g.n[1] >> 2, inv_ng, r);
   pos[1] = r << 2;
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(256, 4) k_Ly4_2(Grid g, Coef cf, const float* 
     float4 Lx = C.at4(0, p0) * xc;
     // t: central forms inside, the one-sided forms on the first and last plane
     if (pos[0] > 0 && pos[0] < g.n[0] - 1) {
-      const float4 xm = ld4(xb + p0 - n1), xp = ld4(xb + p0 + n1);
+      const float4 xm = ld4(xb + dbg_index(g, p0 - n1, g.N - 3, 5)), xp = ld4(xb + dbg_index(g, p0 + n1, g.N - 3, 5));
       Lx = Lx + ((0.5f * g.is1[0]) * C.at4(1, p0)) * (xp - xm) + (g.is2[0] * C.at4(2, p0)) * (xp - 2.f * xc + xm);
     } else {
       float4 a1 = f4(0.f), a2 = f4(0.f);
@@ -394,7 +396,7 @@ __global__ void __launch_bounds__(256, 5) k_LTy4_2(Grid g, Coef cf, StepArgs a) 
       qv = C.at4(0, p0) * yc;
       // t: rows i = j - o e_t share their position class across the group
       if (pos[0] > 2 && pos[0] < g.n[0] - 3) {
-        const int pm = p0 - n1, pp = p0 + n1;
+        const int pm = dbg_index(g, p0 - n1, g.N - 3, 5), pp = dbg_index(g, p0 + n1, g.N - 3, 5);
         const float4 ym = ld4(yb + pm), yp = ld4(yb + pp);
         qv = qv + (0.5f * g.is1[0]) * (C.at4(1, pm) * ym - C.at4(1, pp) * yp) +
              g.is2[0] * (C.at4(2, pm) * ym - 2.f * (C.at4(2, p0) * yc) + C.at4(2, pp) * yp);
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(256, 5) k_LTy4_2(Grid g, Coef cf, StepArgs a) 
           if (ip < 0 || ip >= g.n[0]) continue;
           const float w1 = dweight(1, ip, g.n[0], 0, o), w2 = dweight(2, ip, g.n[0], 0, o);
           if (w1 == 0.f && w2 == 0.f) continue;
-          const int pi = p0 + (ip - pos[0]) * n1;
+          const int pi = dbg_index(g, p0 + (ip - pos[0]) * n1, g.N - 3, 5);
           const float4 yv = o == 0 ? yc : ld4(yb + pi);
           qv = qv + yv * ((w1 * g.is1[0]) * C.at4(1, pi) + (w2 * g.is2[0]) * C.at4(2, pi));
         }
