@@ -17,4 +17,7 @@ Modules
                 size (consistent equation and boundary data for any u; adjoint
                 sources on u with their exact solution), for full-size checks
   conv          the warm-start network's 3x3x3 convolution, written plainly
+  nonuniform    per-interval steps (three-point forms through unequal
+                intervals), Neumann / mixed boundary rows, dl/dsteps through
+                the entries of A
 """
