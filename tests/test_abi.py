@@ -140,3 +140,20 @@ def test_solver_rejects_missized_tensors_without_launching():
         s.mse_grad(torch.zeros(2, 7, 64), torch.zeros(2, 65))
     with pytest.raises(ValueError, match="g_z"):
         s.mse_grad(torch.zeros(2, 7, 64), torch.zeros(2, 64), g_z=torch.zeros(2, 7, 64, dtype=torch.float64))
+
+
+def test_benchmark_settings_are_solver_options():
+    """Every benchmark workload's solver settings name options the solver
+    takes, with values the descriptor accepts (iteration counts >= 1, the
+    adjoint's >= 0, degrees 1..30), so the benchmark, the profiling driver
+    and the full-size tests cannot fail on a misspelt or invalid setting."""
+    import inspect
+    from paper_2502_18377_b300 import settings
+    from paper_2502_18377_b300.binding import Solver
+    params = inspect.signature(Solver.__init__).parameters
+    for name, (gen, batch, grid, seed, kw) in settings.BENCH_WORKLOADS.items():
+        assert callable(gen) and batch >= 1 and all(n >= 8 for n in grid), name
+        for k, v in kw.items():
+            assert k in params, (name, k)
+        assert kw.get("inner_iters", 5) >= 1 and kw.get("adj_inner_iters", 0) >= 0, name
+        assert 1 <= kw.get("cheb_degree", 5) <= 30, name
