@@ -9,8 +9,10 @@ u_t + v1 u_x + v2 u_y - 1e-3 (u_xx + u_yy) = sin(4 y), batch 4 per GPU, grid
 field with a k^-3 spectrum; forward solve, MSE loss gradient against a
 seeded target, adjoint solve, parameter gradients.  The 2D+time
 reaction-diffusion family at B = 8, 64 x 128 x 128 and at B = 16,
-32 x 64 x 64 is measured the same way and reported under "other_workloads".
-Inputs are resident in HBM when the timed region starts.
+32 x 64 x 64, the 1D+time linearized Burgers family at B = 32, 128 x 256 and
+the 1D+time advection-diffusion family at B = 4, 32 x 32 are measured the
+same way and reported under "other_workloads".  Inputs are resident in HBM
+when the timed region starts.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
